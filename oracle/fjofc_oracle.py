@@ -1,0 +1,275 @@
+"""FP64 CPU oracle for fJOFC (Lyzinski et al., "Fast Embedding for JOFC Using the
+Raw Stress Criterion", arXiv 1502.03391).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.  The CUDA library never
+calls it and shares no code with it.
+
+What it computes is the plain definition of the JOFC method, written with dense
+matrices and numpy float64 so that every step can be checked against the paper by
+eye:
+
+* the omnibus dissimilarity (Eq. jofcdelta) and weight matrix (Eq. W / Eq. W2),
+* the combinatorial Laplacian ``L = D - W`` (Sec. 1.2.2, item 2),
+* ``B(X)`` of Eq. (B) and the raw stress of Eq. (stress) as the double sum
+  ``sum_{i<j} W_ij (Delta_ij - d_ij(X))^2``,
+* Algorithm 1's loop ``X_t = L^+ B(X_{t-1}) X_{t-1}`` with ``L^+`` the
+  Moore-Penrose pseudoinverse from ``numpy.linalg.pinv`` (SVD),
+* the out-of-sample Guttman transform of Eq. (joosupdate) with the dense blocks
+  ``L_12, L_22, B_12, B_22`` of Sec. 3 and ``numpy.linalg.inv(L_22)``.
+
+Readings of the paper taken here (each is listed in the design doc):
+
+* stopping rule: Algorithm 1 prints ``sigma(X_t) - sigma(X_{t-1}) > eps``, which a
+  descent method never satisfies; the loop continues while the *decrease*
+  ``sigma(X_{t-1}) - sigma(X_t)`` exceeds the tolerance.  The tolerance is either
+  the paper's normalised one (Remark eps: decrease of sigma/C(mn,2)) or relative
+  (decrease / sigma(X_{t-1})).  A negative tolerance runs exactly ``max_iter``
+  transforms.  The returned configuration is the last computed iterate.
+* Eq. (B)'s diagonal sums over all off-diagonal entries of row i (the printed index
+  range is a typo).
+* General weights (Eq. W2) carry over to the out-of-sample problem: a new point in
+  modality j has weight ``w_jj`` to the in-sample points of modality j and weight
+  ``w_ij`` to the new point of modality i.  For Eq. (W) this is the paper's W^(o).
+* Several new objects are independent problems (Sec. 3, last paragraph).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+__all__ = [
+    "modified_weight_matrix",
+    "omnibus_weights",
+    "omnibus_dissimilarity",
+    "laplacian",
+    "pairwise_distances",
+    "guttman_B",
+    "raw_stress",
+    "EmbedResult",
+    "jofc_embed",
+    "guttman_step",
+    "oos_blocks",
+    "oos_stress",
+    "OOSResult",
+    "oos_embed",
+    "continue_iterating",
+]
+
+
+# ---------------------------------------------------------------------------
+# Weights and dissimilarities (Sec. 1.2.2 and Sec. 2.1)
+# ---------------------------------------------------------------------------
+
+def modified_weight_matrix(Wm: np.ndarray, n: int) -> np.ndarray:
+    """The m x m matrix of Eq. (modW): diagonal ``n w_ii + sum_{j != i} w_ij``,
+    off-diagonal ``-w_ij``."""
+    Wm = np.asarray(Wm, dtype=np.float64)
+    m = Wm.shape[0]
+    M = -Wm.copy()
+    for i in range(m):
+        M[i, i] = n * Wm[i, i] + sum(Wm[i, j] for j in range(m) if j != i)
+    return M
+
+
+def omnibus_weights(Wm: np.ndarray, n: int) -> np.ndarray:
+    """Dense mn x mn weight matrix of Eq. (W2): block (i,i) is ``w_ii (J_n - I_n)``,
+    block (i,j) is ``w_ij I_n``.  With ``w_ii = 1`` and ``w_ij = w`` this is Eq. (W)."""
+    Wm = np.asarray(Wm, dtype=np.float64)
+    m = Wm.shape[0]
+    W = np.zeros((m * n, m * n))
+    J = np.ones((n, n))
+    I = np.eye(n)
+    for i in range(m):
+        for j in range(m):
+            blk = Wm[i, i] * (J - I) if i == j else Wm[i, j] * I
+            W[i * n:(i + 1) * n, j * n:(j + 1) * n] = blk
+    return W
+
+
+def omnibus_dissimilarity(deltas: Sequence[np.ndarray]) -> np.ndarray:
+    """Dense mn x mn omnibus dissimilarity of Eq. (jofcdelta): ``Delta_i`` on the
+    diagonal blocks, the eta blocks elsewhere (0 on the matched diagonal; the NA
+    entries carry weight 0, so any finite value works and 0 is stored)."""
+    m = len(deltas)
+    n = np.asarray(deltas[0]).shape[0]
+    D = np.zeros((m * n, m * n))
+    for i in range(m):
+        D[i * n:(i + 1) * n, i * n:(i + 1) * n] = np.asarray(deltas[i], dtype=np.float64)
+    return D
+
+
+def laplacian(W: np.ndarray) -> np.ndarray:
+    """Combinatorial Laplacian ``L = D - W`` with ``D_ii = sum_j W_ij``."""
+    return np.diag(W.sum(axis=1)) - W
+
+
+# ---------------------------------------------------------------------------
+# Distances, B(X) and stress (Eq. B, Eq. stress)
+# ---------------------------------------------------------------------------
+
+def pairwise_distances(X: np.ndarray) -> np.ndarray:
+    """``d_ij(X) = ||x_i - x_j||_2`` for all rows, by explicit differences."""
+    X = np.asarray(X, dtype=np.float64)
+    diff = X[:, None, :] - X[None, :, :]
+    return np.sqrt(np.einsum("ijk,ijk->ij", diff, diff))
+
+
+def guttman_B(X: np.ndarray, W: np.ndarray, Delta: np.ndarray) -> np.ndarray:
+    """Eq. (B): off-diagonal ``-W_ij Delta_ij / d_ij(X)`` where ``d_ij != 0`` and 0
+    where ``d_ij = 0``; diagonal = minus the sum of the row's off-diagonal entries."""
+    D = pairwise_distances(X)
+    N = D.shape[0]
+    B = np.zeros((N, N))
+    off = ~np.eye(N, dtype=bool)
+    nz = off & (D != 0.0)
+    B[nz] = -W[nz] * Delta[nz] / D[nz]
+    B[np.diag_indices(N)] = -B.sum(axis=1)
+    return B
+
+
+def raw_stress(X: np.ndarray, W: np.ndarray, Delta: np.ndarray) -> float:
+    """Raw stress ``sum_{i<j} W_ij (Delta_ij - d_ij(X))^2`` (Eq. stress written over
+    the omnibus matrix, Sec. 1.2.2)."""
+    D = pairwise_distances(X)
+    iu = np.triu_indices(D.shape[0], k=1)
+    return float(np.sum(W[iu] * (Delta[iu] - D[iu]) ** 2))
+
+
+def continue_iterating(prev: float, cur: float, tol: float, tol_mode: str, n_pairs: int) -> bool:
+    """Algorithm 1's loop test with the sign reading: keep going while the decrease
+    exceeds the tolerance.  ``tol < 0`` never stops early."""
+    if tol < 0:
+        return True
+    dec = prev - cur
+    if tol_mode == "abs_normalized":          # Remark eps: sigma_N = sigma / C(nm, 2)
+        return dec / n_pairs > tol
+    if tol_mode == "relative":
+        return dec > tol * prev
+    raise ValueError(tol_mode)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 (JOFC with a dense pseudoinverse)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class EmbedResult:
+    X: np.ndarray                 # final configuration, (m*n) x d
+    iters: int                    # number of Guttman transforms applied
+    stress: List[float]           # sigma(X_0), ..., sigma(X_iters)
+    iterates: Optional[List[np.ndarray]] = None
+
+
+def guttman_step(X: np.ndarray, Lp: np.ndarray, W: np.ndarray, Delta: np.ndarray) -> np.ndarray:
+    """One Guttman transform ``L^+ B(X) X`` (Algorithm 1, loop body)."""
+    return Lp @ (guttman_B(X, W, Delta) @ X)
+
+
+def jofc_embed(deltas: Sequence[np.ndarray], Wm: np.ndarray, X0: np.ndarray, max_iter: int,
+               tol: float = -1.0, tol_mode: str = "relative", keep_iterates: bool = False,
+               Lp: Optional[np.ndarray] = None) -> EmbedResult:
+    """Algorithm 1 from a given ``X_0`` (its cMDS initialisation is not part of the
+    loop): compute sigma(X_0); then repeat ``X_t = L^+ B(X_{t-1}) X_{t-1}`` and
+    sigma(X_t) until the stopping test fails or ``max_iter`` transforms are done."""
+    m = len(deltas)
+    n = np.asarray(deltas[0]).shape[0]
+    W = omnibus_weights(Wm, n)
+    Delta = omnibus_dissimilarity(deltas)
+    if Lp is None:
+        Lp = np.linalg.pinv(laplacian(W))
+    X = np.array(X0, dtype=np.float64)
+    n_pairs = (m * n) * (m * n - 1) // 2
+    hist = [raw_stress(X, W, Delta)]
+    its = [X.copy()] if keep_iterates else None
+    t = 0
+    while t < max_iter:
+        X = guttman_step(X, Lp, W, Delta)
+        t += 1
+        hist.append(raw_stress(X, W, Delta))
+        if keep_iterates:
+            its.append(X.copy())
+        if not continue_iterating(hist[-2], hist[-1], tol, tol_mode, n_pairs):
+            break
+    return EmbedResult(X=X, iters=t, stress=hist, iterates=its)
+
+
+# ---------------------------------------------------------------------------
+# Out-of-sample embedding (Sec. 3)
+# ---------------------------------------------------------------------------
+
+def oos_blocks(X: np.ndarray, delta_new: np.ndarray, y: np.ndarray, Wm: np.ndarray):
+    """Dense out-of-sample quantities for one new object.
+
+    ``X`` is the (m*n) x d in-sample configuration, ``delta_new`` the m x n
+    dissimilarities delta_j(k) of the new object to in-sample object k in modality j,
+    ``y`` the m x d configuration of the new object.  Returns ``(Wo, Do, Xo)``: the
+    (mn+m) x (mn+m) weight matrix W^(o) (in-sample points first, then y_1..y_m), the
+    omnibus dissimilarity Delta^(o) in the same order and the stacked configuration.
+    """
+    Wm = np.asarray(Wm, dtype=np.float64)
+    m = Wm.shape[0]
+    n = X.shape[0] // m
+    N = m * n + m
+    Wo = np.zeros((N, N))
+    Do = np.zeros((N, N))
+    for j in range(m):
+        rows = slice(j * n, (j + 1) * n)
+        col = m * n + j
+        Wo[rows, col] = Wm[j, j]
+        Wo[col, rows] = Wm[j, j]
+        Do[rows, col] = delta_new[j]
+        Do[col, rows] = delta_new[j]
+        for i in range(m):
+            if i != j:
+                Wo[m * n + i, col] = Wm[i, j]      # matched new points: Delta = 0
+    Xo = np.vstack([X, y])
+    return Wo, Do, Xo
+
+
+def oos_stress(X: np.ndarray, delta_new: np.ndarray, y: np.ndarray, Wm: np.ndarray) -> float:
+    """Eq. (joos) as the omnibus double sum ``sum_{i<j} W^(o)_ij (Delta^(o)_ij - d_ij)^2``."""
+    Wo, Do, Xo = oos_blocks(X, delta_new, y, Wm)
+    return raw_stress(Xo, Wo, Do)
+
+
+@dataclasses.dataclass
+class OOSResult:
+    y: np.ndarray                 # m x d
+    iters: int
+    stress: List[float]
+
+
+def oos_step(X: np.ndarray, delta_new: np.ndarray, y: np.ndarray, Wm: np.ndarray) -> np.ndarray:
+    """Eq. (joosupdate): ``y_t = L22^+ (B12^T - L12^T) X + L22^+ B22 y_{t-1}`` with the
+    blocks of the Laplacian of W^(o) and of B(X^(o)) (Eq. B), L22 inverted by
+    ``numpy.linalg.inv`` (it is non-singular when every ``w_jj > 0``)."""
+    m = np.asarray(Wm).shape[0]
+    mn = X.shape[0]
+    Wo, Do, Xo = oos_blocks(X, delta_new, y, Wm)
+    Lo = laplacian(Wo)
+    Bo = guttman_B(Xo, Wo, Do)
+    L12, L22 = Lo[:mn, mn:], Lo[mn:, mn:]
+    B12, B22 = Bo[:mn, mn:], Bo[mn:, mn:]
+    L22inv = np.linalg.inv(L22)
+    return L22inv @ ((B12.T - L12.T) @ X) + L22inv @ (B22 @ y)
+
+
+def oos_embed(X: np.ndarray, delta_new: np.ndarray, y0: np.ndarray, Wm: np.ndarray,
+              max_iter: int, tol: float = -1.0, tol_mode: str = "relative") -> OOSResult:
+    """Out-of-sample procedure of Sec. 3 for one new object from ``y0``."""
+    y = np.array(y0, dtype=np.float64)
+    m = y.shape[0]
+    hist = [oos_stress(X, delta_new, y, Wm)]
+    # weighted terms of Eq. (joos): m*n fidelity distances + C(m,2) commensurability ones
+    n_pairs = X.shape[0] + m * (m - 1) // 2
+    t = 0
+    while t < max_iter:
+        y = oos_step(X, delta_new, y, Wm)
+        t += 1
+        hist.append(oos_stress(X, delta_new, y, Wm))
+        if not continue_iterating(hist[-2], hist[-1], tol, tol_mode, n_pairs):
+            break
+    return OOSResult(y=y, iters=t, stress=hist)

@@ -1,0 +1,405 @@
+"""Pins of the float64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the paper's
+printed closed forms (hand-evaluated golden values and the general formulas of
+Sec. 2.1 / Appendix A), the paper's fast update (Eq. update) and out-of-sample
+simplification (Sec. 3), textbook SMACOF for m = 1, exact identities (Eq. stress,
+Eq. comm, Remark faststress), the majorization guarantee, exact-configuration fixed
+points and invariances.  All run on the CPU in a few seconds.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import fjofc_oracle as O
+import synthetic
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.txt")
+
+
+def _golden():
+    rows = []
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        rows.append(line.split())
+    return rows
+
+
+def _eqW(m, w):
+    return synthetic.weights_matrix(m, 1.0, w)
+
+
+def _lp(Wm, n):
+    return np.linalg.pinv(O.laplacian(O.omnibus_weights(Wm, n)))
+
+
+def _rand_sym_weights(rng, m, lo=0.2, hi=2.0):
+    A = rng.uniform(lo, hi, size=(m, m))
+    return np.triu(A) + np.triu(A, 1).T
+
+
+# ---------------------------------------------------------------- closed forms
+
+def test_golden_closed_forms_pin_pinv_and_L22():
+    """The oracle's pinv(L) (built from Eq. W) splits as Winv (x) I_n + Z (x) J_n with the
+    hand-evaluated Eq. (W1inv) and J-coefficient values; inv(L22) of the oracle's
+    out-of-sample blocks equals the printed L22^+ (Sec. 3)."""
+    for row in _golden():
+        name = row[0]
+        if name in ("Winv_eqW", "Z_eqW"):
+            m, n, w = int(row[1]), int(row[2]), float(row[3])
+            diag, off = float(Fraction(row[4])), float(Fraction(row[5]))
+            Lp = _lp(_eqW(m, w), n)
+            # Winv (x) I_n + Z (x) J_n: block (a,b) entry (0,0) = Winv_ab + Z_ab, entry (0,1) = Z_ab
+            Zo = Lp[0:n * m:n, 1:n * m:n]                  # (a,b) -> entry (a*n, b*n+1)
+            Wo = Lp[0:n * m:n, 0:n * m:n] - Zo
+            got = Wo if name == "Winv_eqW" else Zo
+            exp = np.full((m, m), off)
+            np.fill_diagonal(exp, diag)
+            np.testing.assert_allclose(got, exp, rtol=1e-10, atol=1e-13)
+        elif name == "L22inv":
+            m, n, w = int(row[1]), int(row[2]), float(row[3])
+            diag, off = float(Fraction(row[4])), float(Fraction(row[5]))
+            rng = np.random.default_rng(1)
+            X = rng.standard_normal((m * n, 2))
+            Wo, Do, Xo = O.oos_blocks(X, rng.uniform(1, 2, (m, n)), rng.standard_normal((m, 2)), _eqW(m, w))
+            L22 = O.laplacian(Wo)[m * n:, m * n:]
+            exp = np.full((m, m), off)
+            np.fill_diagonal(exp, diag)
+            np.testing.assert_allclose(np.linalg.inv(L22), exp, rtol=1e-12)
+        elif name == "W3inv":
+            n, w11, w22 = int(row[1]), float(row[2]), float(row[3])
+            Wm = np.array([[w11, w11 * w22], [w11 * w22, w22]])
+            exp = np.array([[Fraction(row[4]), Fraction(row[5])], [Fraction(row[5]), Fraction(row[6])]], dtype=float)
+            np.testing.assert_allclose(np.linalg.inv(O.modified_weight_matrix(Wm, n)), exp, rtol=1e-13)
+            # and W3 Laplacian: pinv(L) restricted to the I_n part carries the same Winv
+            Lp = _lp(Wm, n)
+            Zo = Lp[0:2 * n:n, 1:2 * n:n]
+            np.testing.assert_allclose(Lp[0:2 * n:n, 0:2 * n:n] - Zo, exp, rtol=1e-10, atol=1e-13)
+        else:
+            raise AssertionError(name)
+
+
+@pytest.mark.parametrize("m,n", [(2, 3), (3, 4), (4, 5), (2, 9)])
+def test_corollary1_general_weights(m, n):
+    """Cor. 1 / Thm 1 (Appendix A) for random Eq. (W2) weights: pinv(L) equals
+    Winv (x) I_n + [Z - J_m/(mn)] (x) J_n; Prop. 1: pinv(L) = inv(L + J/mn) - J/mn;
+    and L = Wmod (x) I_n - diag(w_ii) (x) J_n."""
+    rng = np.random.default_rng(100 + m * 10 + n)
+    Wm = _rand_sym_weights(rng, m)
+    L = O.laplacian(O.omnibus_weights(Wm, n))
+    Lp = np.linalg.pinv(L)
+    Wmod = O.modified_weight_matrix(Wm, n)
+    Jm = np.ones((m, m))
+    dw = np.diag(np.diag(Wm))
+    np.testing.assert_allclose(L, np.kron(Wmod, np.eye(n)) - np.kron(dw, np.ones((n, n))), atol=1e-13)
+    Winv = np.linalg.inv(Wmod)
+    Zm = -np.linalg.inv(Wmod + n * (Jm / (m * n) - dw)) @ (Jm / (m * n) - dw) @ Winv - Jm / (m * n)
+    np.testing.assert_allclose(Lp, np.kron(Winv, np.eye(n)) + np.kron(Zm, np.ones((n, n))), atol=1e-12)
+    N = m * n
+    np.testing.assert_allclose(Lp, np.linalg.inv(L + np.ones((N, N)) / N) - np.ones((N, N)) / N, atol=1e-12)
+
+
+def test_woodbury_kronecker_identity():
+    """Remark after Eq. (W1inv): (A (x) I_n + B (x) J_n)^-1 = A^-1 (x) I_n - (A + nB)^-1 B A^-1 (x) J_n,
+    checked on the oracle's L + J/mn for random weights."""
+    rng = np.random.default_rng(5)
+    m, n = 3, 6
+    Wm = _rand_sym_weights(rng, m)
+    L = O.laplacian(O.omnibus_weights(Wm, n))
+    A = O.modified_weight_matrix(Wm, n)
+    Bm = np.ones((m, m)) / (m * n) - np.diag(np.diag(Wm))
+    lhs = np.linalg.inv(L + np.ones((m * n, m * n)) / (m * n))
+    Ai = np.linalg.inv(A)
+    rhs = np.kron(Ai, np.eye(n)) - np.kron(np.linalg.inv(A + n * Bm) @ Bm @ Ai, np.ones((n, n)))
+    np.testing.assert_allclose(lhs, rhs, atol=1e-12)
+
+
+# ---------------------------------------------------------------- the Guttman step
+
+def _small_problem(m=2, n=12, d=2, seed=3, w=0.5):
+    prob = synthetic.make_insample(0, n=n, m=m, d=d, seed=seed, w_comm=w)
+    return prob.deltas, prob.W, prob.X0
+
+
+@pytest.mark.parametrize("m,n,d,w", [(2, 12, 2, 0.5), (3, 9, 3, 2.0), (4, 7, 1, 0.1)])
+def test_fast_update_equals_dense_step(m, n, d, w):
+    """Eq. (update) with the c4 reading of Algorithm 2's coefficients: the oracle's
+    pinv(L) B(X) X equals (1/(n+mw)) B_j X^(j) + (w/(n(n+mw))) sum_l B_l X^(l), with the
+    B_l the diagonal blocks of B(X) built from a plain per-modality loop."""
+    deltas, Wm, X = _small_problem(m, n, d, seed=10 + m, w=w)
+    W = O.omnibus_weights(Wm, n)
+    D = O.omnibus_dissimilarity(deltas)
+    Xn = O.guttman_step(X, _lp(Wm, n), W, D)
+    # per-modality B_l X^(l) by loops over pairs (fidelity weight 1)
+    BX = []
+    for l in range(m):
+        Xl = X[l * n:(l + 1) * n]
+        out = np.zeros_like(Xl)
+        for i in range(n):
+            for j in range(n):
+                if i == j:
+                    continue
+                dij = np.linalg.norm(Xl[i] - Xl[j])
+                if dij > 0:
+                    out[i] += deltas[l][i, j] / dij * (Xl[i] - Xl[j])
+        BX.append(out)
+    S = sum(BX)
+    for j in range(m):
+        exp = BX[j] / (n + m * w) + w / (n * (n + m * w)) * S
+        np.testing.assert_allclose(Xn[j * n:(j + 1) * n], exp, rtol=1e-11, atol=1e-12)
+
+
+def test_B_structure():
+    """B(X) is block diagonal with zero row and column sums (Sec. 2.2)."""
+    deltas, Wm, X = _small_problem(3, 8, 2)
+    n, m = 8, 3
+    B = O.guttman_B(X, O.omnibus_weights(Wm, n), O.omnibus_dissimilarity(deltas))
+    np.testing.assert_allclose(B.sum(0), 0, atol=1e-12)
+    np.testing.assert_allclose(B.sum(1), 0, atol=1e-12)
+    for a in range(m):
+        for b in range(m):
+            if a != b:
+                assert np.all(B[a * n:(a + 1) * n, b * n:(b + 1) * n] == 0)
+
+
+def test_zero_distance_rule():
+    """Eq. (B) sets b_ij = 0 when d_ij = 0: two coincident points do not pull each other."""
+    deltas, Wm, X = _small_problem(2, 6, 2)
+    X = X.copy()
+    X[1] = X[0]
+    W = O.omnibus_weights(Wm, 6)
+    B = O.guttman_B(X, W, O.omnibus_dissimilarity(deltas))
+    assert B[0, 1] == 0 and B[1, 0] == 0
+    assert np.all(np.isfinite(B))
+
+
+def test_m1_is_textbook_smacof():
+    """m = 1: the Guttman transform is the unit-weight SMACOF update X <- n^-1 B(X) X
+    (Borg & Groenen, Ch. 8), written here as an explicit loop."""
+    deltas, Wm, X = _small_problem(1, 10, 2, seed=4)
+    n = 10
+    Wm = np.array([[1.0]])
+    Xn = O.guttman_step(X, _lp(Wm, n), O.omnibus_weights(Wm, n), O.omnibus_dissimilarity(deltas))
+    exp = np.zeros_like(X)
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                dij = np.sqrt(np.sum((X[i] - X[j]) ** 2))
+                exp[i] += deltas[0][i, j] / dij * (X[i] - X[j])
+    np.testing.assert_allclose(Xn, exp / n, rtol=1e-12, atol=1e-13)
+
+
+# ---------------------------------------------------------------- stress identities
+
+def test_stress_identity_and_majorizer():
+    """sigma(X) = sum W Delta^2 + tr X'LX - 2 tr X'B(X)X (Sec. 1.2.2) and the majorizer of
+    Eq. (major) bounds sigma(Y) from above for a Y other than X."""
+    deltas, Wm, X = _small_problem(2, 10, 2, seed=8)
+    n = 10
+    W = O.omnibus_weights(Wm, n)
+    D = O.omnibus_dissimilarity(deltas)
+    L = O.laplacian(W)
+    iu = np.triu_indices(2 * n, 1)
+    c = np.sum(W[iu] * D[iu] ** 2)
+    s = O.raw_stress(X, W, D)
+    np.testing.assert_allclose(s, c + np.trace(X.T @ L @ X) - 2 * np.trace(X.T @ O.guttman_B(X, W, D) @ X), rtol=1e-12)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        Y = X + 0.3 * rng.standard_normal(X.shape)
+        major = c + np.trace(Y.T @ L @ Y) - 2 * np.trace(Y.T @ O.guttman_B(X, W, D) @ X)
+        assert O.raw_stress(Y, W, D) <= major + 1e-10
+
+
+@pytest.mark.parametrize("m,w", [(2, 0.5), (3, 1.5)])
+def test_faststress_and_commensurability_identities(m, w):
+    """Remark faststress: the omnibus stress equals half the Frobenius fidelity plus
+    w times commensurability; Eq. (comm): commensurability = m sum_i ||X^(i) - Xbar||^2."""
+    n = 9
+    deltas, Wm, X = _small_problem(m, n, 3, seed=20 + m, w=w)
+    W = O.omnibus_weights(Wm, n)
+    D = O.omnibus_dissimilarity(deltas)
+    fid = 0.0
+    for i in range(m):
+        Xi = X[i * n:(i + 1) * n]
+        Di = np.sqrt(((Xi[:, None, :] - Xi[None, :, :]) ** 2).sum(-1))
+        fid += 0.5 * np.sum((deltas[i] - Di) ** 2)
+    comm = sum(np.sum((X[i * n:(i + 1) * n] - X[j * n:(j + 1) * n]) ** 2)
+               for i in range(m) for j in range(i + 1, m))
+    np.testing.assert_allclose(O.raw_stress(X, W, D), fid + w * comm, rtol=1e-12)
+    Xbar = sum(X[i * n:(i + 1) * n] for i in range(m)) / m
+    np.testing.assert_allclose(comm, m * sum(np.sum((X[i * n:(i + 1) * n] - Xbar) ** 2) for i in range(m)), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- the loop
+
+def test_monotone_descent_and_centering():
+    """Majorization guarantees non-increasing stress (Sec. 1.2.2, Sec. 5); every
+    Guttman output is centred (Sec. 1.2.2)."""
+    deltas, Wm, X0 = _small_problem(2, 20, 2, seed=30)
+    res = O.jofc_embed(deltas, Wm, X0, max_iter=60, keep_iterates=True)
+    s = np.array(res.stress)
+    assert np.all(np.diff(s) <= 1e-12 * s[:-1])
+    assert s[-1] < s[0]
+    for Xt in res.iterates[1:]:
+        np.testing.assert_allclose(Xt.mean(0), 0, atol=1e-12)
+
+
+def test_exact_configuration_fixed_point_and_recovery():
+    """When every Delta_i holds the distances of one configuration Y, X = [Y; Y] has
+    zero stress and is a fixed point; from a perturbed start stress falls to ~0."""
+    rng = np.random.default_rng(11)
+    n, m, d = 15, 2, 2
+    Y = rng.standard_normal((n, d))
+    Y -= Y.mean(0)
+    Dy = np.sqrt(((Y[:, None] - Y[None]) ** 2).sum(-1))
+    deltas = [Dy, Dy]
+    Wm = _eqW(m, 0.5)
+    X = np.vstack([Y, Y])
+    W = O.omnibus_weights(Wm, n)
+    D = O.omnibus_dissimilarity(deltas)
+    assert O.raw_stress(X, W, D) < 1e-25
+    np.testing.assert_allclose(O.guttman_step(X, _lp(Wm, n), W, D), X, atol=1e-12)
+    X0 = X + 0.01 * rng.standard_normal(X.shape)
+    res = O.jofc_embed(deltas, Wm, X0, max_iter=200)
+    assert res.stress[-1] < 1e-8 * res.stress[0]
+
+
+def test_invariances():
+    """Translation of X0 leaves X_1 unchanged; rotation rotates it; a consistent
+    permutation of objects permutes it; scaling all weights by c leaves X_1 unchanged
+    and scales the stress by c."""
+    n, m = 10, 2
+    deltas, Wm, X0 = _small_problem(m, n, 2, seed=40)
+    W = O.omnibus_weights(Wm, n)
+    D = O.omnibus_dissimilarity(deltas)
+    Lp = _lp(Wm, n)
+    X1 = O.guttman_step(X0, Lp, W, D)
+    np.testing.assert_allclose(O.guttman_step(X0 + np.array([3.0, -2.0]), Lp, W, D), X1, atol=1e-11)
+    th = 0.7
+    R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    np.testing.assert_allclose(O.guttman_step(X0 @ R, Lp, W, D), X1 @ R, atol=1e-11)
+    perm = np.random.default_rng(1).permutation(n)
+    dp = [dl[np.ix_(perm, perm)] for dl in deltas]
+    idx = np.concatenate([perm + l * n for l in range(m)])
+    Xp = O.guttman_step(X0[idx], Lp, W, O.omnibus_dissimilarity(dp))
+    np.testing.assert_allclose(Xp, X1[idx], atol=1e-11)
+    c = 3.5
+    Wc = O.omnibus_weights(c * Wm, n)
+    np.testing.assert_allclose(O.guttman_step(X0, _lp(c * Wm, n), Wc, D), X1, atol=1e-11)
+    np.testing.assert_allclose(O.raw_stress(X0, Wc, D), c * O.raw_stress(X0, W, D), rtol=1e-12)
+
+
+def test_stopping_rule_semantics():
+    """The loop stops at the first transform whose stress decrease is within the
+    tolerance and returns that iterate; a negative tolerance runs max_iter transforms."""
+    deltas, Wm, X0 = _small_problem(2, 15, 2, seed=50)
+    fixed = O.jofc_embed(deltas, Wm, X0, max_iter=25, tol=-1)
+    assert fixed.iters == 25 and len(fixed.stress) == 26
+    tol = 1e-4
+    res = O.jofc_embed(deltas, Wm, X0, max_iter=500, tol=tol, tol_mode="relative")
+    s = res.stress
+    assert res.iters < 500
+    for t in range(1, res.iters):
+        assert s[t - 1] - s[t] > tol * s[t - 1]
+    assert s[-2] - s[-1] <= tol * s[-2]
+    n_pairs = 30 * 29 // 2
+    res2 = O.jofc_embed(deltas, Wm, X0, max_iter=500, tol=1e-6, tol_mode="abs_normalized")
+    assert (res2.stress[-2] - res2.stress[-1]) / n_pairs <= 1e-6
+
+
+# ---------------------------------------------------------------- out of sample
+
+def _oos_setup(m=2, n=10, d=2, w=0.5, seed=60):
+    rng = np.random.default_rng(seed)
+    deltas, Wm, X0 = _small_problem(m, n, d, seed=seed, w=w)
+    X = O.jofc_embed(deltas, Wm, X0, max_iter=30).X
+    delta_new = rng.uniform(0.5, 3.0, size=(m, n))
+    y0 = rng.standard_normal((m, d))
+    return X, delta_new, y0, Wm
+
+
+@pytest.mark.parametrize("m,w", [(2, 0.5), (3, 2.0)])
+def test_oos_closed_form_update(m, w):
+    """Sec. 3: the dense update of Eq. (joosupdate) equals the O(nmd) form
+    y_j = xi_j/(n+mw) + w/(n(n+mw)) sum_k xi_k + psi_j y_j/(n+mw) + w/(n(n+mw)) sum_k psi_k y_k
+    with xi_j = sum_k (1 - delta_j(k)/d_jk) X^(j)_k and psi_j = sum_k delta_j(k)/d_jk."""
+    n, d = 10, 2
+    X, dn, y, Wm = _oos_setup(m, n, d, w)
+    got = O.oos_step(X, dn, y, Wm)
+    xi = np.zeros((m, d))
+    psi = np.zeros(m)
+    for j in range(m):
+        for k in range(n):
+            dist = np.linalg.norm(X[j * n + k] - y[j])
+            xi[j] += (1 - dn[j, k] / dist) * X[j * n + k]
+            psi[j] += dn[j, k] / dist
+    c1, c2 = 1 / (n + m * w), w / (n * (n + m * w))
+    exp = np.array([xi[j] * c1 + c2 * xi.sum(0) + psi[j] * y[j] * c1 + c2 * (psi[:, None] * y).sum(0)
+                    for j in range(m)])
+    np.testing.assert_allclose(got, exp, rtol=1e-12, atol=1e-13)
+
+
+def test_oos_stress_equals_eq_joos_and_descends():
+    """The omnibus out-of-sample stress equals Eq. (joos) written directly, and the
+    out-of-sample Guttman iterations do not increase it."""
+    m, n, d, w = 2, 10, 2, 0.5
+    X, dn, y0, Wm = _oos_setup(m, n, d, w)
+    direct = sum((dn[j, k] - np.linalg.norm(X[j * n + k] - y0[j])) ** 2 for j in range(m) for k in range(n))
+    direct += w * sum(np.sum((y0[i] - y0[j]) ** 2) for i in range(m) for j in range(i + 1, m))
+    np.testing.assert_allclose(O.oos_stress(X, dn, y0, Wm), direct, rtol=1e-12)
+    res = O.oos_embed(X, dn, y0, Wm, max_iter=40)
+    s = np.array(res.stress)
+    assert np.all(np.diff(s) <= 1e-12 * s[:-1])
+
+
+def test_oos_fixed_point_exact_configuration():
+    """If the new object repeats in-sample object k of a zero-stress embedding with
+    equal X^(i), then y_j = X^(j)_k is a fixed point with zero out-of-sample stress."""
+    rng = np.random.default_rng(70)
+    n, m, d = 12, 2, 2
+    Y = rng.standard_normal((n, d))
+    Y -= Y.mean(0)
+    Dy = np.sqrt(((Y[:, None] - Y[None]) ** 2).sum(-1))
+    X = np.vstack([Y, Y])
+    Wm = _eqW(m, 0.5)
+    k = 4
+    dn = np.stack([Dy[k], Dy[k]])
+    y = np.stack([Y[k], Y[k]])
+    assert O.oos_stress(X, dn, y, Wm) < 1e-25
+    np.testing.assert_allclose(O.oos_step(X, dn, y, Wm), y, atol=1e-12)
+
+
+def test_oos_general_weights_and_uncentred_X():
+    """General weights (reading of Sec. 3 for Eq. W2): the out-of-sample L22 equals the
+    in-sample modified weight matrix of Eq. (modW), and the update is
+    y = Wmod^-1 (xi + psi * y) with xi_j = w_jj sum_k (1 - delta_j(k)/d_jk) X^(j)_k and
+    psi_j = w_jj sum_k delta_j(k)/d_jk.  An uncentred in-sample X keeps the -L12' X term
+    visible.  The stress matches Eq. (joos) with w_jj on fidelity and w_ij on
+    commensurability."""
+    rng = np.random.default_rng(80)
+    m, n, d = 3, 8, 2
+    Wm = _rand_sym_weights(rng, m)
+    X = rng.standard_normal((m * n, d)) + np.array([1.5, -0.7])
+    dn = rng.uniform(0.5, 3.0, size=(m, n))
+    y = rng.standard_normal((m, d))
+    Wo, Do, Xo = O.oos_blocks(X, dn, y, Wm)
+    L22 = O.laplacian(Wo)[m * n:, m * n:]
+    np.testing.assert_allclose(L22, O.modified_weight_matrix(Wm, n), atol=1e-13)
+    xi = np.zeros((m, d))
+    psi = np.zeros(m)
+    for j in range(m):
+        for k in range(n):
+            dist = np.linalg.norm(X[j * n + k] - y[j])
+            xi[j] += Wm[j, j] * (1 - dn[j, k] / dist) * X[j * n + k]
+            psi[j] += Wm[j, j] * dn[j, k] / dist
+    exp = np.linalg.inv(O.modified_weight_matrix(Wm, n)) @ (xi + psi[:, None] * y)
+    np.testing.assert_allclose(O.oos_step(X, dn, y, Wm), exp, rtol=1e-11, atol=1e-12)
+    direct = sum(Wm[j, j] * (dn[j, k] - np.linalg.norm(X[j * n + k] - y[j])) ** 2
+                 for j in range(m) for k in range(n))
+    direct += sum(Wm[i, j] * np.sum((y[i] - y[j]) ** 2) for i in range(m) for j in range(i + 1, m))
+    np.testing.assert_allclose(O.oos_stress(X, dn, y, Wm), direct, rtol=1e-12)
