@@ -14,7 +14,7 @@ eye:
 * ``B(X)`` of Eq. (B) and the raw stress of Eq. (stress) as the double sum
   ``sum_{i<j} W_ij (Delta_ij - d_ij(X))^2``,
 * Algorithm 1's loop ``X_t = L^+ B(X_{t-1}) X_{t-1}`` with ``L^+`` the
-  Moore-Penrose pseudoinverse from ``numpy.linalg.pinv`` (SVD),
+  Moore-Penrose pseudoinverse from ``numpy.linalg.pinv`` (SVD, rank-revealing cutoff),
 * the out-of-sample Guttman transform of Eq. (joosupdate) with the dense blocks
   ``L_12, L_22, B_12, B_22`` of Sec. 3 and ``numpy.linalg.inv(L_22)``.
 
@@ -45,6 +45,7 @@ __all__ = [
     "omnibus_weights",
     "omnibus_dissimilarity",
     "laplacian",
+    "pseudoinverse",
     "pairwise_distances",
     "guttman_B",
     "raw_stress",
@@ -56,6 +57,12 @@ __all__ = [
     "OOSResult",
     "oos_embed",
     "continue_iterating",
+    "modality_BX",
+    "guttman_step_closed_form",
+    "stress_blocks",
+    "oos_step_closed_form",
+    "oos_stress_direct",
+    "oos_embed_closed_form",
 ]
 
 
@@ -104,6 +111,20 @@ def omnibus_dissimilarity(deltas: Sequence[np.ndarray]) -> np.ndarray:
 def laplacian(W: np.ndarray) -> np.ndarray:
     """Combinatorial Laplacian ``L = D - W`` with ``D_ii = sum_j W_ij``."""
     return np.diag(W.sum(axis=1)) - W
+
+
+def pseudoinverse(L: np.ndarray) -> np.ndarray:
+    """Moore-Penrose pseudoinverse of the symmetric Laplacian by SVD (``numpy.linalg.pinv``),
+    with the rank-revealing cutoff N * eps * sigma_max.  The Laplacian of a connected
+    JOFC weight graph has exactly one zero singular value (its null space is the constant
+    vector, Prop. 1); numpy's default cutoff (1e-15 * sigma_max) can keep that singular
+    value's rounding residue and return a wrong pseudoinverse."""
+    N = L.shape[0]
+    cut = N * np.finfo(np.float64).eps
+    try:
+        return np.linalg.pinv(L, rtol=cut, hermitian=True)
+    except TypeError:                      # numpy < 2.0 names the cutoff rcond
+        return np.linalg.pinv(L, rcond=cut, hermitian=True)
 
 
 # ---------------------------------------------------------------------------
@@ -179,7 +200,7 @@ def jofc_embed(deltas: Sequence[np.ndarray], Wm: np.ndarray, X0: np.ndarray, max
     W = omnibus_weights(Wm, n)
     Delta = omnibus_dissimilarity(deltas)
     if Lp is None:
-        Lp = np.linalg.pinv(laplacian(W))
+        Lp = pseudoinverse(laplacian(W))
     X = np.array(X0, dtype=np.float64)
     n_pairs = (m * n) * (m * n - 1) // 2
     hist = [raw_stress(X, W, Delta)]
@@ -270,6 +291,136 @@ def oos_embed(X: np.ndarray, delta_new: np.ndarray, y0: np.ndarray, Wm: np.ndarr
         y = oos_step(X, delta_new, y, Wm)
         t += 1
         hist.append(oos_stress(X, delta_new, y, Wm))
+        if not continue_iterating(hist[-2], hist[-1], tol, tol_mode, n_pairs):
+            break
+    return OOSResult(y=y, iters=t, stress=hist)
+
+
+# ---------------------------------------------------------------------------
+# Large-n forms used to check full-size runs.  Both are pinned against the dense
+# definitions above at small sizes (tests/test_oracle_pins.py).
+# ---------------------------------------------------------------------------
+
+def modality_BX(delta: np.ndarray, Xl: np.ndarray, w_ll: float = 1.0, row_block: int = 1024) -> np.ndarray:
+    """The diagonal block B_l X^(l) of B(X) X (Eq. B restricted to modality l, whose only
+    non-zero weights are w_ll on the off-diagonal pairs), in float64 by row blocks:
+    (B_l X)_i = sum_{j != i, d_ij != 0} w_ll Delta_ij / d_ij (x_i - x_j)."""
+    Xl = np.asarray(Xl, dtype=np.float64)
+    n = Xl.shape[0]
+    out = np.zeros_like(Xl)
+    for a in range(0, n, row_block):
+        blk = slice(a, min(n, a + row_block))
+        diff = Xl[blk, None, :] - Xl[None, :, :]
+        dist = np.sqrt(np.einsum("ijk,ijk->ij", diff, diff))
+        coef = np.zeros_like(dist)
+        nz = dist != 0.0
+        idx = np.arange(blk.start, blk.stop)
+        nz[np.arange(len(idx)), idx] = False
+        coef[nz] = w_ll * np.asarray(delta, dtype=np.float64)[blk][nz] / dist[nz]
+        out[blk] = np.einsum("ij,ijk->ik", coef, diff)
+    return out
+
+
+def guttman_step_closed_form(deltas: Sequence[np.ndarray], Wm: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """One Guttman transform L^+ B(X) X with L^+ written as in Cor. 1 (Appendix A):
+    L^+ = Wmod^-1 (x) I_n + [Z - J_m/(mn)] (x) J_n,
+    Z = -(Wmod + n(J_m/(mn) - diag w_ii))^-1 (J_m/(mn) - diag w_ii) Wmod^-1,
+    applied to the block-diagonal B(X) X (the J_n term is kept, not assumed zero)."""
+    Wm = np.asarray(Wm, dtype=np.float64)
+    m = Wm.shape[0]
+    n = X.shape[0] // m
+    BX = [modality_BX(deltas[l], X[l * n:(l + 1) * n], Wm[l, l]) for l in range(m)]
+    Wmod = modified_weight_matrix(Wm, n)
+    Winv = np.linalg.inv(Wmod)
+    Jm = np.ones((m, m))
+    dw = np.diag(np.diag(Wm))
+    Z = -np.linalg.inv(Wmod + n * (Jm / (m * n) - dw)) @ (Jm / (m * n) - dw) @ Winv - Jm / (m * n)
+    colsum = [b.sum(axis=0) for b in BX]
+    out = np.zeros_like(np.asarray(X, dtype=np.float64))
+    for j in range(m):
+        blk = sum(Winv[j, l] * BX[l] for l in range(m))
+        blk = blk + sum(Z[j, l] * colsum[l] for l in range(m))[None, :]
+        out[j * n:(j + 1) * n] = blk
+    return out
+
+
+def stress_blocks(deltas: Sequence[np.ndarray], Wm: np.ndarray, X: np.ndarray, row_block: int = 1024) -> float:
+    """Eq. (stress) summed block by block: sum_l w_ll sum_{i<j} (Delta_l,ij - d_ij(X^(l)))^2
+    + sum_{i<j} w_ij ||X^(i) - X^(j)||_F^2 (the omnibus double sum restricted to its
+    non-zero weights), in float64 for large n."""
+    Wm = np.asarray(Wm, dtype=np.float64)
+    m = Wm.shape[0]
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0] // m
+    tot = 0.0
+    for l in range(m):
+        Xl = X[l * n:(l + 1) * n]
+        Dl = np.asarray(deltas[l], dtype=np.float64)
+        for a in range(0, n, row_block):
+            b = min(n, a + row_block)
+            diff = Xl[a:b, None, :] - Xl[None, :, :]
+            dist = np.sqrt(np.einsum("ijk,ijk->ij", diff, diff))
+            mask = np.arange(n)[None, :] > np.arange(a, b)[:, None]
+            tot += Wm[l, l] * float(np.sum(((Dl[a:b] - dist) ** 2)[mask]))
+    for i in range(m):
+        for j in range(i + 1, m):
+            tot += Wm[i, j] * float(np.sum((X[i * n:(i + 1) * n] - X[j * n:(j + 1) * n]) ** 2))
+    return tot
+
+
+def oos_step_closed_form(X: np.ndarray, delta_new: np.ndarray, y: np.ndarray, Wm: np.ndarray) -> np.ndarray:
+    """The O(nmd) out-of-sample update of Sec. 3 with general weights:
+    xi_j = w_jj sum_k (1 - delta_j(k)/d_jk) X^(j)_k, psi_j = w_jj sum_k delta_j(k)/d_jk (terms
+    with d_jk = 0 contribute X^(j)_k to xi_j and nothing to psi_j, Eq. B), and
+    y_t = L22^-1 (xi + psi o y_{t-1}) with L22 the modified weight matrix of Eq. (modW)."""
+    Wm = np.asarray(Wm, dtype=np.float64)
+    m = Wm.shape[0]
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0] // m
+    y = np.asarray(y, dtype=np.float64)
+    xi = np.zeros_like(y)
+    psi = np.zeros(m)
+    for j in range(m):
+        Xj = X[j * n:(j + 1) * n]
+        dist = np.sqrt(np.sum((Xj - y[j]) ** 2, axis=1))
+        ratio = np.zeros(n)
+        nz = dist != 0.0
+        ratio[nz] = np.asarray(delta_new[j], dtype=np.float64)[nz] / dist[nz]
+        xi[j] = Wm[j, j] * ((1.0 - ratio)[:, None] * Xj).sum(axis=0)
+        psi[j] = Wm[j, j] * ratio.sum()
+    return np.linalg.inv(modified_weight_matrix(Wm, n)) @ (xi + psi[:, None] * y)
+
+
+def oos_stress_direct(X: np.ndarray, delta_new: np.ndarray, y: np.ndarray, Wm: np.ndarray) -> float:
+    """Eq. (joos) with general weights, summed directly."""
+    Wm = np.asarray(Wm, dtype=np.float64)
+    m = Wm.shape[0]
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0] // m
+    y = np.asarray(y, dtype=np.float64)
+    s = 0.0
+    for j in range(m):
+        dist = np.sqrt(np.sum((X[j * n:(j + 1) * n] - y[j]) ** 2, axis=1))
+        s += Wm[j, j] * float(np.sum((np.asarray(delta_new[j], dtype=np.float64) - dist) ** 2))
+    for i in range(m):
+        for j in range(i + 1, m):
+            s += Wm[i, j] * float(np.sum((y[i] - y[j]) ** 2))
+    return s
+
+
+def oos_embed_closed_form(X, delta_new, y0, Wm, max_iter: int, tol: float = -1.0,
+                          tol_mode: str = "relative") -> OOSResult:
+    """The out-of-sample loop with the O(nmd) update and direct stress (for large n)."""
+    y = np.array(y0, dtype=np.float64)
+    m = y.shape[0]
+    n = np.asarray(X).shape[0] // m
+    hist = [oos_stress_direct(X, delta_new, y, Wm)]
+    n_pairs = m * n + m * (m - 1) // 2
+    t = 0
+    while t < max_iter:
+        y = oos_step_closed_form(X, delta_new, y, Wm)
+        t += 1
+        hist.append(oos_stress_direct(X, delta_new, y, Wm))
         if not continue_iterating(hist[-2], hist[-1], tol, tol_mode, n_pairs):
             break
     return OOSResult(y=y, iters=t, stress=hist)

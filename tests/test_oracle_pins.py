@@ -34,7 +34,7 @@ def _eqW(m, w):
 
 
 def _lp(Wm, n):
-    return np.linalg.pinv(O.laplacian(O.omnibus_weights(Wm, n)))
+    return O.pseudoinverse(O.laplacian(O.omnibus_weights(Wm, n)))
 
 
 def _rand_sym_weights(rng, m, lo=0.2, hi=2.0):
@@ -92,7 +92,7 @@ def test_corollary1_general_weights(m, n):
     rng = np.random.default_rng(100 + m * 10 + n)
     Wm = _rand_sym_weights(rng, m)
     L = O.laplacian(O.omnibus_weights(Wm, n))
-    Lp = np.linalg.pinv(L)
+    Lp = O.pseudoinverse(L)
     Wmod = O.modified_weight_matrix(Wm, n)
     Jm = np.ones((m, m))
     dw = np.diag(np.diag(Wm))
@@ -403,3 +403,60 @@ def test_oos_general_weights_and_uncentred_X():
                  for j in range(m) for k in range(n))
     direct += sum(Wm[i, j] * np.sum((y[i] - y[j]) ** 2) for i in range(m) for j in range(i + 1, m))
     np.testing.assert_allclose(O.oos_stress(X, dn, y, Wm), direct, rtol=1e-12)
+
+
+@pytest.mark.parametrize("m,n,d", [(2, 11, 2), (3, 7, 3), (1, 9, 2)])
+def test_large_n_forms_match_dense_definition(m, n, d):
+    """The block forms used for full-size checks (Cor. 1's L^+ applied to B(X) X, and the
+    block-wise stress) agree with the dense pinv step and the omnibus double sum, for
+    general Eq. (W2) weights and with a duplicated point (d_ij = 0)."""
+    rng = np.random.default_rng(90 + m)
+    deltas, _, X = _small_problem(m, n, d, seed=91 + m)
+    Wm = _rand_sym_weights(rng, m)
+    X = X.copy()
+    X[1] = X[0]
+    W = O.omnibus_weights(Wm, n)
+    D = O.omnibus_dissimilarity(deltas)
+    dense = O.guttman_step(X, _lp(Wm, n), W, D)
+    np.testing.assert_allclose(O.guttman_step_closed_form(deltas, Wm, X), dense, rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(O.stress_blocks(deltas, Wm, X, row_block=4), O.raw_stress(X, W, D), rtol=1e-12)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_oos_large_n_forms_match_dense(m):
+    """The O(nmd) out-of-sample forms used at large n agree with the dense Eq. (joosupdate)
+    step and the omnibus stress, for general weights, an uncentred X and a new point that
+    coincides with an in-sample point (d_jk = 0)."""
+    rng = np.random.default_rng(95 + m)
+    n, d = 9, 3
+    Wm = _rand_sym_weights(rng, m)
+    X = rng.standard_normal((m * n, d)) + 0.4
+    dn = rng.uniform(0.5, 3.0, size=(m, n))
+    y = rng.standard_normal((m, d))
+    y[0] = X[2]
+    np.testing.assert_allclose(O.oos_step_closed_form(X, dn, y, Wm), O.oos_step(X, dn, y, Wm), rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(O.oos_stress_direct(X, dn, y, Wm), O.oos_stress(X, dn, y, Wm), rtol=1e-12)
+    a = O.oos_embed_closed_form(X, dn, y, Wm, max_iter=8)
+    b = O.oos_embed(X, dn, y, Wm, max_iter=8)
+    np.testing.assert_allclose(a.y, b.y, rtol=1e-10, atol=1e-11)
+    np.testing.assert_allclose(a.stress, b.stress, rtol=1e-11)
+
+
+@pytest.mark.parametrize("seed,m,n", [(11, 3, 150), (12, 2, 200), (13, 4, 60)])
+def test_pseudoinverse_moore_penrose_conditions(seed, m, n):
+    """The oracle's L^+ satisfies the four Moore-Penrose conditions and Prop. 1 for random
+    Eq. (W2) weights at sizes where the cutoff between L's zero singular value and the rest
+    matters (n up to 200)."""
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(0.2, 2.0, (m, m))
+    Wm = np.triu(A) + np.triu(A, 1).T
+    L = O.laplacian(O.omnibus_weights(Wm, n))
+    P = O.pseudoinverse(L)
+    N = m * n
+    scale = np.abs(L).max()
+    assert np.abs(L @ P @ L - L).max() <= 1e-10 * scale
+    assert np.abs(P @ L @ P - P).max() <= 1e-10 * np.abs(P).max()
+    assert np.abs(L @ P - (L @ P).T).max() <= 1e-10
+    assert np.abs(P @ L - (P @ L).T).max() <= 1e-10
+    J = np.ones((N, N)) / N
+    np.testing.assert_allclose(P, np.linalg.inv(L + J) - J, atol=1e-10 * np.abs(P).max())
