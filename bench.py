@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the fJOFC in-sample hot path on GB300.
+
+One step = one ``fjofc_embed`` call on the m=2, n=5000, d=3 workload (float32 Delta,
+200 Guttman transforms or relative stress change < 1e-7), i.e. every row of the hot path:
+the closed-form W^-1 set-up, the fused all-pairs passes (K1), the W^-1/centring/stress
+passes (K2) and the device-side stopping test.  Inputs are resident in HBM when the timed
+region starts; Delta (200 MB) is larger than L2, so no L2 flush is needed.
+
+Output: one JSON line (rank 0).  ``value`` = Guttman pair-updates/s summed over all
+ranks, with pair-updates per transform = m*C(n,2) + C(m,2)*n (the distances of
+Remark faststress).  Extra keys: roofline of the all-pairs kernel (algorithmic bytes of
+the upper triangles of Delta / measured device time of the kernel, against the measured
+HBM copy bandwidth), the CPU oracle timed on a bounded sample, an end-to-end figure
+through the public API with host buffers, clocks sampled during the timed region.
+
+``--impl reference`` times the float64 CPU oracle (the dense Algorithm 1) instead, on a
+bounded sample of the same workload; with several ranks only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(k=1, m=2, n=5000, d=3, max_iter=200, tol=1e-7, tol_mode="relative")
+CPU_SAMPLE = dict(n=1000, iters=30)
+
+
+def pairs_per_transform(m, n):
+    return m * n * (n - 1) // 2 + (m * (m - 1) // 2) * n
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for rel in ("paper_1502_03391_gb300/csrc/k_guttman_pass.cuh", "paper_1502_03391_gb300/csrc/fjofc_device.cuh",
+                "paper_1502_03391_gb300/csrc/k1_d01_04.cu"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the all-pairs kernel from the committed ncu summary, if it
+    was captured on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_guttman_pass_workload1.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    msha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    mtr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not msha or not mtr or msha.group(1) != kernel_source_sha():
+        return None
+    return float(mtr.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- oracle arm
+
+def oracle_rate(n, iters, seed_rep=0):
+    """Pair-updates/s of the float64 dense oracle (Algorithm 1 with pinv) on a workload-1
+    shaped sample of n objects."""
+    import numpy as np
+    import synthetic
+    from oracle import fjofc_oracle as O
+    prob = synthetic.make_insample(WORKLOAD["k"], n=n, rep=seed_rep)
+    t0 = time.perf_counter()
+    res = O.jofc_embed(prob.deltas, prob.W, prob.X0, max_iter=iters)
+    dt = time.perf_counter() - t0
+    return pairs_per_transform(WORKLOAD["m"], n) * res.iters / dt, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n, iters = CPU_SAMPLE["n"], CPU_SAMPLE["iters"]
+    for _ in range(args.warmup):
+        oracle_rate(200, 3)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt = oracle_rate(n, iters)
+        vals.append(v)
+        times.append(dt)
+    value = sum(iters * pairs_per_transform(WORKLOAD["m"], n) for _ in vals) / sum(times)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": "Guttman pair-updates/s", "value": value, "unit": "pair-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "insample-m2-n5000-d3", "sample": f"n={n} objects of the same generator, {iters} transforms",
+                   "m": WORKLOAD["m"], "d": WORKLOAD["d"], "parallelism": "cpu"},
+        "cpu_baseline": {"value": value, "unit": "pair-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"dense float64 Algorithm 1 (pinv + dense B(X)) on n={n} (mn={2 * n}), {iters} transforms"},
+        "e2e": {"value": value, "unit": "pair-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+def make_device_problem(torch, fj, seed_rep, device):
+    import numpy as np
+    import synthetic
+    prob = synthetic.make_insample(WORKLOAD["k"], rep=seed_rep, with_deltas=False)
+    deltas = []
+    for Fi in prob.F:
+        buf = fj.empty_delta(prob.spec.n, torch.float32, device)
+        buf.copy_(synthetic.torch_distances(Fi, device, torch.float32))
+        deltas.append(buf)
+    X0 = torch.as_tensor(np.asarray(prob.X0, np.float32), device=device).contiguous()
+    return prob, deltas, X0
+
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1502_03391_gb300 as fj
+
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    m, n, d = WORKLOAD["m"], WORKLOAD["n"], WORKLOAD["d"]
+    prob, deltas, X0 = make_device_problem(torch, fj, rank, device)
+    X = torch.empty_like(X0)
+    stream = torch.cuda.current_stream(device)
+
+    def step(profile=True):
+        X.copy_(X0)
+        return fj.embed(deltas, prob.W, X, max_iter=WORKLOAD["max_iter"], tol=WORKLOAD["tol"],
+                        tol_mode=WORKLOAD["tol_mode"], history=False, profile=profile)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    iters, ms_pass, passes, launches = 0, 0.0, 0, 0
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = step()
+            iters += r.iters
+            ms_pass += r.ms_pass
+            passes += r.passes
+            launches += r.launches
+        ev1.record(stream)
+        barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        it = torch.tensor([iters], device=device, dtype=torch.float64)
+        dist.all_reduce(it)
+        total_iters = float(it.item())
+    else:
+        total_iters = float(iters)
+    ppt = pairs_per_transform(m, n)
+    value = ppt * total_iters / (elapsed_ms / 1e3)
+
+    # roofline of the all-pairs kernel: algorithmic bytes = strict upper triangles of Delta
+    alg_bytes = m * n * (n - 1) // 2 * 4
+    k1_avg_ms = ms_pass / max(passes, 1)
+    achieved = alg_bytes / (k1_avg_ms / 1e3) / 1e9
+    peaks, src = measured_peaks()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(),
+            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
+            "kernel": "k_guttman_pass<3,float>", "algorithmic_bytes_per_launch": alg_bytes,
+            "avg_launch_ms": k1_avg_ms, "launches_timed": passes}
+
+    # end to end through the public API with host buffers (pinned): Delta and X0 in, X and
+    # the stress out, every step
+    e2e = None
+    if not args.no_e2e:
+        hostD = [dd.cpu().pin_memory() for dd in deltas]
+        hostX0 = X0.cpu().pin_memory()
+        hostX = torch.empty_like(hostX0).pin_memory()
+        devD = [torch.empty_like(dd) for dd in deltas]
+        for _ in range(2):
+            for a, b in zip(devD, hostD):
+                a.copy_(b, non_blocking=True)
+            X.copy_(hostX0, non_blocking=True)
+            fj.embed(devD, prob.W, X, max_iter=WORKLOAD["max_iter"], tol=WORKLOAD["tol"], tol_mode=WORKLOAD["tol_mode"],
+                     history=False)
+            hostX.copy_(X, non_blocking=True)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it2 = 0
+        for _ in range(args.steps):
+            for a, b in zip(devD, hostD):
+                a.copy_(b, non_blocking=True)
+            X.copy_(hostX0, non_blocking=True)
+            r = fj.embed(devD, prob.W, X, max_iter=WORKLOAD["max_iter"], tol=WORKLOAD["tol"],
+                         tol_mode=WORKLOAD["tol_mode"], history=False)
+            hostX.copy_(X, non_blocking=True)
+            it2 += r.iters
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ems], device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+            itt = torch.tensor([it2], device=device, dtype=torch.float64)
+            dist.all_reduce(itt)
+            it2 = float(itt.item())
+        h2d = sum(dd.numel() * dd.element_size() for dd in hostD) + hostX0.numel() * 4
+        e2e = {"value": ppt * it2 / (ems / 1e3), "unit": "pair-updates/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(hostX.numel() * 4 + 8 + 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt = oracle_rate(CPU_SAMPLE["n"], CPU_SAMPLE["iters"])
+        cpu = {"value": v, "unit": "pair-updates/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"dense float64 Algorithm 1 (pinv + dense B(X)) on n={CPU_SAMPLE['n']} objects of the same "
+                         f"generator (mn={2 * CPU_SAMPLE['n']}), {CPU_SAMPLE['iters']} transforms, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": "Guttman pair-updates/s", "value": value, "unit": "pair-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "insample-m2-n5000-d3: fjofc_embed, float32 Delta, 200 transforms or relative "
+                                   "stress change < 1e-7", "m": m, "n": n, "d": d,
+                       "transforms_per_step": total_iters / args.steps / world,
+                       "l2": "inputs larger than L2 (Delta 200 MB per replica), no flush",
+                       "parallelism": f"{world} independent replica(s)"},
+            "hbm_gbs_step": alg_bytes * total_iters / (elapsed_ms / 1e3) / 1e9,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * fjofc.h -- C ABI of the GB300 (sm_103a) fJOFC library.
+ *
+ * fJOFC (Lyzinski, Park, Priebe, Trosset: "Fast Embedding for JOFC Using the Raw
+ * Stress Criterion") embeds m matched dissimilarity matrices Delta_1..Delta_m on the
+ * same n objects into R^d by minimising the JOFC raw stress (Eq. stress) with
+ * successive Guttman transforms X_t = L^+ B(X_{t-1}) X_{t-1} (Algorithm 1), where the
+ * pseudoinverse is applied in the closed form of Sec. 2.1 / Cor. 1 so that each
+ * iteration is X_t^(j) = sum_l [Wmod^-1]_{jl} B_l X_{t-1}^(l) (Eq. update), with B_l the
+ * l-th diagonal block of B(X) (Eq. B).  New objects are embedded by the
+ * out-of-sample Guttman transform of Sec. 3 (Eq. joosupdate).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named "device" are CUDA device pointers owned by the caller; the
+ *    library never frees them and never keeps them after the call returns.
+ *  - Pointers named "host" are ordinary host memory read (or written) during the call.
+ *  - Calls are ordered on the CUDA stream passed as `cuda_stream` (a cudaStream_t;
+ *    NULL = legacy default stream).  A call enqueues its kernels and then waits for
+ *    that stream once, to copy the small result block back; it allocates temporary
+ *    device memory with the stream-ordered allocator and releases it on the stream.
+ *  - Return value: FJOFC_OK (0) or a negative FJOFC_ERR_* status; fjofc_strerror()
+ *    gives a message.  Argument errors are detected before anything is enqueued.
+ *  - Floating point: Delta is read as float32 (or float16/bfloat16 scaled by a
+ *    per-modality factor), all distance/B(X) arithmetic is float32, stress sums and
+ *    the m x m weight algebra are float64.
+ *  - At most FJOFC_MAX_M modalities and 1 <= d <= FJOFC_MAX_D.
+ *  - Delta row strides (`ld`, in elements) must make each row start on a 16-byte
+ *    boundary (ld * element size % 16 == 0) and each Delta base pointer must be
+ *    16-byte aligned: the kernels stage Delta tiles with the Tensor Memory
+ *    Accelerator, which requires it.
+ */
+#ifndef FJOFC_H
+#define FJOFC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FJOFC_MAX_M 8
+#define FJOFC_MAX_D 16
+
+/* status codes */
+#define FJOFC_OK             0
+#define FJOFC_ERR_ARG       -1   /* invalid argument (sizes, weights, pointers, alignment) */
+#define FJOFC_ERR_CUDA      -2   /* a CUDA runtime call failed */
+#define FJOFC_ERR_NONFINITE -3   /* the stress became NaN/Inf; the last finite iterate is returned */
+#define FJOFC_ERR_TIMEOUT   -4   /* a bounded device-side wait gave up (no GPU hang) */
+#define FJOFC_ERR_NOMEM     -5   /* temporary device memory could not be allocated */
+#define FJOFC_ERR_UNSUPPORTED -6 /* valid but not supported here (e.g. d or m beyond the built range) */
+
+/* element type of Delta */
+#define FJOFC_F32  0
+#define FJOFC_F16  1
+#define FJOFC_BF16 2
+
+/* stopping rule (Algorithm 1, Remark eps).  Iteration continues while the stress
+ * DECREASE sigma(X_{t-1}) - sigma(X_t) exceeds the tolerance (the paper prints the
+ * difference with the opposite sign, which a descent method never satisfies):
+ *   FJOFC_TOL_ABS_NORMALIZED: decrease / C(mn, 2) > tol   (the paper's setting, Remark eps)
+ *   FJOFC_TOL_RELATIVE:       decrease / sigma(X_{t-1}) > tol
+ * A negative tol disables the test: exactly max_iter transforms are applied. */
+#define FJOFC_TOL_ABS_NORMALIZED 0
+#define FJOFC_TOL_RELATIVE       1
+
+typedef struct fjofc_opts {
+    int32_t max_iter;     /* maximum number of Guttman transforms (>= 0) */
+    double  tol;          /* tolerance of the stopping rule; < 0 = run max_iter transforms */
+    int32_t tol_mode;     /* FJOFC_TOL_* */
+    int32_t profile;      /* 1: time every all-pairs pass and every W^-1 pass with CUDA events
+                             recorded on cuda_stream (result fields ms_pass, ms_apply) */
+    int32_t reserved[4];  /* must be zero */
+} fjofc_opts;
+
+typedef struct fjofc_result {
+    int32_t status;             /* copy of the return value */
+    int32_t iters;              /* number of transforms T applied to produce the returned X */
+    double  stress;             /* raw stress sigma(X_T) (Eq. stress), float64 */
+    double  stress_normalized;  /* sigma(X_T) / C(mn, 2) (Remark eps) */
+    double* stress_history;     /* host, caller-owned, length >= max_iter + 1, or NULL:
+                                   receives sigma(X_0) .. sigma(X_T) */
+    float   ms_total;           /* device time of the call, milliseconds (CUDA events) */
+    /* filled when opts->profile == 1 (else 0): */
+    int32_t passes;             /* all-pairs passes that did work (= iters + 1) */
+    float   ms_pass;            /* summed device time of those all-pairs passes (K1) */
+    float   ms_apply;           /* summed device time of the matching W^-1/stress passes (K2) */
+    int32_t launches;           /* kernels this call launched */
+} fjofc_result;
+
+/*
+ * fjofc_embed -- in-sample fJOFC (Algorithm 2's loop from a given X_0).
+ *
+ *  m, n, d      : modalities (1..FJOFC_MAX_M), objects (>= 2), embedding dimension
+ *                 (1..FJOFC_MAX_D).
+ *  delta        : host array of m DEVICE pointers; delta[i] is Delta_{i+1}, an n x n
+ *                 row-major matrix with row stride `ld` elements (ld >= n) of element
+ *                 type `delta_dtype`.  Delta must be symmetric with finite non-negative
+ *                 entries (the dissimilarities of Sec. 1.2); the kernels read only the
+ *                 strictly upper triangle (the diagonal is ignored, Eq. W has w=0 there).
+ *  delta_scale  : host array of m float scales, or NULL (= all 1).  The dissimilarity
+ *                 used is delta_scale[i] * Delta_i[a][b]; meant for float16/bfloat16
+ *                 storage of data whose range needs rescaling.
+ *  weights      : host m x m row-major float64 matrix of Eq. (W2): w_ii > 0 is the
+ *                 fidelity weight of modality i, w_ij = w_ji >= 0 (i != j) the
+ *                 commensurability weight of matched pairs across modalities i and j.
+ *                 Eq. (W) is w_ii = 1, w_ij = w.
+ *  X            : DEVICE float32 (m*n) x d row-major, rows modality-major (the n rows of
+ *                 X^(1), then X^(2), ...).  In: X_0.  Out: the final iterate X_T, with
+ *                 each modality block's column means removed in float64 (Guttman
+ *                 outputs are centred in exact arithmetic, Sec. 1.2.2).  X_0 itself is
+ *                 used as given (its stress is that of the uncentred input).
+ *  opts, res    : host; see above.  res may be NULL.
+ *  cuda_stream  : cudaStream_t.
+ *
+ * Errors: FJOFC_ERR_ARG (sizes, NULL pointers, w_ii <= 0, w_ij < 0, asymmetric
+ * weights, misaligned Delta), FJOFC_ERR_UNSUPPORTED (d or m beyond the built range),
+ * FJOFC_ERR_NONFINITE (X holds the last iterate whose stress was finite),
+ * FJOFC_ERR_TIMEOUT, FJOFC_ERR_NOMEM, FJOFC_ERR_CUDA.  Reaching max_iter is not an
+ * error.
+ */
+int fjofc_embed(int32_t m, int64_t n, int32_t d,
+                const void* const* delta, int64_t ld, int32_t delta_dtype,
+                const float* delta_scale, const double* weights,
+                float* X, const fjofc_opts* opts, fjofc_result* res, void* cuda_stream);
+
+/*
+ * fjofc_stress -- the raw stress sigma(X) of Eq. (stress) for a configuration X, by the
+ * same all-pairs pass (fidelity over the upper triangle of each Delta_i, Remark
+ * faststress) plus the commensurability term.  Arguments as in fjofc_embed; X is
+ * read only.  *stress_out (host) receives sigma(X).
+ */
+int fjofc_stress(int32_t m, int64_t n, int32_t d,
+                 const void* const* delta, int64_t ld, int32_t delta_dtype,
+                 const float* delta_scale, const double* weights,
+                 const float* X, double* stress_out, void* cuda_stream);
+
+/*
+ * fjofc_oos -- out-of-sample embedding of k new objects (Sec. 3, Eq. joosupdate),
+ * each an independent problem against the fixed in-sample configuration X.
+ *
+ *  X          : DEVICE float32 (m*n) x d in-sample configuration (read only).
+ *  delta_new  : DEVICE k x m x n dissimilarities, element type `delta_dtype`, row
+ *               stride `ld` elements (ld >= n, 16-byte aligned rows): delta_new[o][j][:]
+ *               holds delta_j of new object o to the n in-sample objects of modality j.
+ *  weights    : host m x m float64 as in fjofc_embed (fidelity w_jj towards the
+ *               in-sample points of modality j, commensurability w_ij between the new
+ *               object's m points).
+ *  Y          : DEVICE float32 k x m x d.  In: y_0 per object.  Out: final y per object.
+ *  iters_out  : DEVICE int32[k] or NULL: transforms applied per object.
+ *  stress_out : DEVICE float64[k] or NULL: final out-of-sample stress (Eq. joos).
+ *  opts       : max_iter and the stopping rule, applied per object; the normalised
+ *               mode divides by the number of weighted terms m*n + C(m,2).
+ *  res        : res->iters receives the largest per-object count, res->stress the sum
+ *               of the final stresses.  May be NULL.
+ */
+int fjofc_oos(int32_t m, int64_t n, int32_t d, int64_t k,
+              const float* X, const void* delta_new, int64_t ld, int32_t delta_dtype,
+              const float* delta_scale, const double* weights,
+              float* Y, int32_t* iters_out, double* stress_out,
+              const fjofc_opts* opts, fjofc_result* res, void* cuda_stream);
+
+/* Message for a status code (static string). */
+const char* fjofc_strerror(int status);
+
+/* Library version string and the list of compiled embedding dimensions. */
+const char* fjofc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FJOFC_H */

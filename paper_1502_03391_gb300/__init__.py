@@ -1,0 +1,286 @@
+"""GB300-native fJOFC: Python binding of the C ABI in ``include/fjofc.h``.
+
+The functions here only marshal arguments (torch CUDA tensors -> device pointers,
+strides, the current CUDA stream) and call ``_lib/libfjofc.so``; every step of the
+method runs in that library's CUDA kernels.  There is no CPU fallback: if the library
+is missing or cannot be loaded, importing this package raises.
+
+    import paper_1502_03391_gb300 as fj
+    res = fj.embed(deltas, W, X, max_iter=200, tol=1e-7, tol_mode="relative")
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfjofc.so")
+
+FJOFC_OK = 0
+FJOFC_ERR_ARG = -1
+FJOFC_ERR_CUDA = -2
+FJOFC_ERR_NONFINITE = -3
+FJOFC_ERR_TIMEOUT = -4
+FJOFC_ERR_NOMEM = -5
+FJOFC_ERR_UNSUPPORTED = -6
+
+F32, F16, BF16 = 0, 1, 2
+TOL_ABS_NORMALIZED, TOL_RELATIVE = 0, 1
+MAX_M, MAX_D = 8, 16
+
+# Every symbol declared in include/fjofc.h.
+EXPORTS = ("fjofc_embed", "fjofc_stress", "fjofc_oos", "fjofc_strerror", "fjofc_version")
+
+
+class FjofcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"fjofc status {status}: {message}")
+        self.status = status
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("tol_mode", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("stress", ctypes.c_double),
+                ("stress_normalized", ctypes.c_double), ("stress_history", ctypes.POINTER(ctypes.c_double)),
+                ("ms_total", ctypes.c_float), ("passes", ctypes.c_int32), ("ms_pass", ctypes.c_float),
+                ("ms_apply", ctypes.c_float), ("launches", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"fJOFC CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    lib.fjofc_embed.argtypes = [i32, i64, i32, ctypes.POINTER(vp), i64, i32, ctypes.POINTER(ctypes.c_float), dp,
+                                vp, ctypes.POINTER(_Opts), ctypes.POINTER(_Result), vp]
+    lib.fjofc_embed.restype = ctypes.c_int
+    lib.fjofc_stress.argtypes = [i32, i64, i32, ctypes.POINTER(vp), i64, i32, ctypes.POINTER(ctypes.c_float), dp,
+                                 vp, dp, vp]
+    lib.fjofc_stress.restype = ctypes.c_int
+    lib.fjofc_oos.argtypes = [i32, i64, i32, i64, vp, vp, i64, i32, ctypes.POINTER(ctypes.c_float), dp, vp, vp, vp,
+                              ctypes.POINTER(_Opts), ctypes.POINTER(_Result), vp]
+    lib.fjofc_oos.restype = ctypes.c_int
+    lib.fjofc_strerror.argtypes = [ctypes.c_int]
+    lib.fjofc_strerror.restype = ctypes.c_char_p
+    lib.fjofc_version.argtypes = []
+    lib.fjofc_version.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def version() -> str:
+    return _lib.fjofc_version().decode()
+
+
+def strerror(status: int) -> str:
+    return _lib.fjofc_strerror(int(status)).decode()
+
+
+def _check(status: int):
+    if status != FJOFC_OK:
+        raise FjofcError(status, strerror(status))
+
+
+# ------------------------------------------------------------------ marshalling helpers
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float16:
+        return F16
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError(f"unsupported Delta dtype {t.dtype}")
+
+
+def _stream_handle(stream, device):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _weights(W, m) -> np.ndarray:
+    Wn = np.ascontiguousarray(np.asarray(W, dtype=np.float64))
+    if Wn.shape != (m, m):
+        raise ValueError(f"weights must be {m}x{m}")
+    return Wn
+
+
+def _scales(delta_scale, m):
+    if delta_scale is None:
+        return None
+    arr = (ctypes.c_float * m)(*[float(v) for v in delta_scale])
+    return arr
+
+
+def _delta_layout(deltas: Sequence, n: int):
+    """Row stride (elements) shared by all Delta matrices; each must be n x n with unit
+    column stride."""
+    ld = None
+    code = None
+    for D in deltas:
+        if D.dim() != 2 or D.shape[0] != n or D.shape[1] != n or D.stride(1) != 1:
+            raise ValueError("each Delta must be an n x n view with unit column stride")
+        if not D.is_cuda:
+            raise ValueError("Delta must be a CUDA tensor")
+        c = _dtype_code(D)
+        if code is None:
+            code, ld = c, D.stride(0)
+        elif c != code or D.stride(0) != ld:
+            raise ValueError("all Delta matrices must share dtype and row stride")
+    return ld, code
+
+
+def padded_ld(n: int, dtype) -> int:
+    """Smallest row stride >= n whose rows start on 16-byte boundaries."""
+    torch = _torch()
+    per = 16 // torch.tensor([], dtype=dtype).element_size()
+    return (n + per - 1) // per * per
+
+
+def empty_delta(n: int, dtype=None, device="cuda"):
+    """An n x n CUDA matrix view whose row stride satisfies the library's alignment."""
+    torch = _torch()
+    dtype = dtype or torch.float32
+    ld = padded_ld(n, dtype)
+    buf = torch.zeros((n, ld), dtype=dtype, device=device)
+    return buf[:, :n]
+
+
+def to_device_delta(D: np.ndarray, dtype=None, device="cuda", scale: float = 1.0):
+    """Copy a host dissimilarity matrix into an aligned CUDA view (optionally divided by
+    ``scale`` before rounding to a 16-bit type)."""
+    torch = _torch()
+    out = empty_delta(D.shape[0], dtype, device)
+    src = torch.as_tensor(np.asarray(D, dtype=np.float64) / scale)
+    out.copy_(src.to(device=device, dtype=out.dtype))
+    return out
+
+
+# ------------------------------------------------------------------ public API
+
+@dataclasses.dataclass
+class EmbedResult:
+    status: int
+    iters: int
+    stress: float
+    stress_normalized: float
+    history: Optional[np.ndarray]
+    ms: float
+    passes: int = 0          # profiled all-pairs passes that did work
+    ms_pass: float = 0.0     # their summed device time (profile=True)
+    ms_apply: float = 0.0    # summed device time of the matching W^-1 passes
+    launches: int = 0        # kernels launched by the call
+
+
+def embed(deltas: Sequence, weights, X, max_iter: int, tol: float = -1.0, tol_mode: str = "relative",
+          delta_scale=None, stream=None, history: bool = True, check: bool = True,
+          profile: bool = False) -> EmbedResult:
+    """In-sample fJOFC from ``X`` (in place).  ``deltas``: m CUDA n x n views (float32,
+    float16 or bfloat16; row stride a multiple of 16 bytes); ``weights``: m x m;
+    ``X``: contiguous float32 CUDA tensor of shape (m*n, d).  See ``fjofc_embed``."""
+    m = len(deltas)
+    n = int(deltas[0].shape[0])
+    if X.dtype != _torch().float32 or not X.is_contiguous() or X.dim() != 2 or X.shape[0] != m * n:
+        raise ValueError("X must be a contiguous float32 (m*n, d) CUDA tensor")
+    d = int(X.shape[1])
+    ld, code = _delta_layout(deltas, n)
+    ptrs = (ctypes.c_void_p * m)(*[D.data_ptr() for D in deltas])
+    Wn = _weights(weights, m)
+    opts = _Opts(int(max_iter), float(tol), TOL_RELATIVE if tol_mode == "relative" else TOL_ABS_NORMALIZED,
+                 1 if profile else 0)
+    hist = np.zeros(int(max_iter) + 1, dtype=np.float64) if history else None
+    res = _Result()
+    if hist is not None:
+        res.stress_history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = _lib.fjofc_embed(m, n, d, ptrs, ld, code, _scales(delta_scale, m),
+                          Wn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(X.data_ptr()),
+                          ctypes.byref(opts), ctypes.byref(res), _stream_handle(stream, X.device))
+    if check and st not in (FJOFC_OK,):
+        _check(st)
+    if hist is not None:
+        upto = res.iters + 1 if st in (FJOFC_OK, FJOFC_ERR_NONFINITE) else 0
+        hist = hist[:upto]
+    return EmbedResult(st, res.iters, res.stress, res.stress_normalized, hist, res.ms_total, res.passes,
+                       res.ms_pass, res.ms_apply, res.launches)
+
+
+def stress(deltas: Sequence, weights, X, delta_scale=None, stream=None) -> float:
+    """Raw stress sigma(X) (Eq. stress) through the library's all-pairs pass."""
+    m = len(deltas)
+    n = int(deltas[0].shape[0])
+    d = int(X.shape[1])
+    ld, code = _delta_layout(deltas, n)
+    ptrs = (ctypes.c_void_p * m)(*[D.data_ptr() for D in deltas])
+    Wn = _weights(weights, m)
+    out = ctypes.c_double(0.0)
+    st = _lib.fjofc_stress(m, n, d, ptrs, ld, code, _scales(delta_scale, m),
+                           Wn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(X.data_ptr()),
+                           ctypes.byref(out), _stream_handle(stream, X.device))
+    _check(st)
+    return out.value
+
+
+@dataclasses.dataclass
+class OOSResult:
+    status: int
+    max_iters: int
+    stress_sum: float
+    ms: float
+
+
+def oos(X, delta_new, weights, Y, max_iter: int, tol: float = -1.0, tol_mode: str = "relative",
+        iters_out=None, stress_out=None, delta_scale=None, stream=None, check: bool = True) -> OOSResult:
+    """Out-of-sample embedding of k new objects (in place in ``Y``).  ``X``: float32 CUDA
+    (m*n, d) in-sample configuration; ``delta_new``: CUDA (k, m, n) view with unit stride in
+    the last dimension, row stride ``ld`` = stride(1), stride(0) = m*ld; ``Y``: contiguous
+    float32 CUDA (k, m, d).  ``iters_out`` (int32 [k]) and ``stress_out`` (float64 [k]) are
+    optional CUDA outputs."""
+    torch = _torch()
+    k, m, n = (int(s) for s in delta_new.shape)
+    d = int(X.shape[1])
+    if delta_new.stride(2) != 1 or delta_new.stride(0) != m * delta_new.stride(1):
+        raise ValueError("delta_new must be a (k, m, n) view over a (k, m, ld) buffer")
+    if not (Y.is_contiguous() and Y.dtype == torch.float32 and tuple(Y.shape) == (k, m, d)):
+        raise ValueError("Y must be a contiguous float32 (k, m, d) tensor")
+    if not (X.is_contiguous() and X.dtype == torch.float32 and tuple(X.shape) == (m * n, d)):
+        raise ValueError("X must be a contiguous float32 (m*n, d) tensor")
+    ld = delta_new.stride(1)
+    code = _dtype_code(delta_new)
+    Wn = _weights(weights, m)
+    opts = _Opts(int(max_iter), float(tol), TOL_RELATIVE if tol_mode == "relative" else TOL_ABS_NORMALIZED)
+    res = _Result()
+    ip = ctypes.c_void_p(iters_out.data_ptr()) if iters_out is not None else None
+    sp = ctypes.c_void_p(stress_out.data_ptr()) if stress_out is not None else None
+    st = _lib.fjofc_oos(m, n, d, k, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(delta_new.data_ptr()), ld, code,
+                        _scales(delta_scale, m), Wn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        ctypes.c_void_p(Y.data_ptr()), ip, sp, ctypes.byref(opts), ctypes.byref(res),
+                        _stream_handle(stream, X.device))
+    if check:
+        _check(st)
+    return OOSResult(st, res.iters, res.stress, res.ms_total)
+
+
+def empty_oos_delta(k: int, m: int, n: int, dtype=None, device="cuda"):
+    """A (k, m, n) CUDA view whose rows satisfy the library's 16-byte alignment."""
+    torch = _torch()
+    dtype = dtype or torch.float32
+    ld = padded_ld(n, dtype)
+    buf = torch.zeros((k, m, ld), dtype=dtype, device=device)
+    return buf[:, :, :n]

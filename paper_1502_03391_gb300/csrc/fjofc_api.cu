@@ -1,0 +1,643 @@
+// Host side of the fJOFC C ABI: argument validation, the m x m weight algebra of
+// Sec. 2.1 in float64, TMA descriptors, workspace layout and the launch sequence of
+// the in-sample loop and of the out-of-sample solver.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "fjofc_device.cuh"
+#include "k1_decl.h"
+#include "k3_decl.h"
+
+using namespace fjofc;
+
+namespace {
+
+// ------------------------------------------------------------------ errors
+#define FJ_CUDA(call)                                         \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) {                              \
+            set_last_error(cudaGetErrorString(e_), #call);    \
+            return FJOFC_ERR_CUDA;                            \
+        }                                                     \
+    } while (0)
+
+thread_local char g_last_msg[512] = "";
+
+void set_last_error(const char* what, const char* where) {
+    snprintf(g_last_msg, sizeof(g_last_msg), "%s (%s)", what, where);
+}
+
+int arg_error(const char* msg) {
+    snprintf(g_last_msg, sizeof(g_last_msg), "%s", msg);
+    return FJOFC_ERR_ARG;
+}
+
+// ------------------------------------------------------------------ weights (Sec. 2.1)
+// Validates the m x m weights of Eq. (W2) and returns Wmod^-1 (Eq. modW inverted by
+// Gauss-Jordan elimination with partial pivoting, float64).  Wmod is strictly
+// diagonally dominant when every w_ii > 0 (proof of Thm 1), hence invertible.
+int weights_inverse(int m, int64_t n, const double* w, double* winv) {
+    if (!w) return arg_error("weights is NULL");
+    for (int i = 0; i < m; ++i) {
+        if (!(w[i * m + i] > 0.0) || !std::isfinite(w[i * m + i]))
+            return arg_error("fidelity weights w_ii must be finite and > 0");
+        for (int j = 0; j < m; ++j) {
+            if (i == j) continue;
+            const double a = w[i * m + j], b = w[j * m + i];
+            if (!(a >= 0.0) || !std::isfinite(a)) return arg_error("commensurability weights must be finite and >= 0");
+            if (a != b) return arg_error("weights must be symmetric (w_ij == w_ji)");
+        }
+    }
+    std::vector<double> A(size_t(m) * 2 * m, 0.0);
+    for (int i = 0; i < m; ++i) {
+        double diag = double(n) * w[i * m + i];
+        for (int j = 0; j < m; ++j)
+            if (j != i) {
+                diag += w[i * m + j];
+                A[size_t(i) * 2 * m + j] = -w[i * m + j];
+            }
+        A[size_t(i) * 2 * m + i] = diag;
+        A[size_t(i) * 2 * m + m + i] = 1.0;
+    }
+    for (int c = 0; c < m; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < m; ++r)
+            if (std::fabs(A[size_t(r) * 2 * m + c]) > std::fabs(A[size_t(piv) * 2 * m + c])) piv = r;
+        if (A[size_t(piv) * 2 * m + c] == 0.0) return arg_error("modified weight matrix is singular");
+        if (piv != c)
+            for (int j = 0; j < 2 * m; ++j) std::swap(A[size_t(c) * 2 * m + j], A[size_t(piv) * 2 * m + j]);
+        const double inv = 1.0 / A[size_t(c) * 2 * m + c];
+        for (int j = 0; j < 2 * m; ++j) A[size_t(c) * 2 * m + j] *= inv;
+        for (int r = 0; r < m; ++r) {
+            if (r == c) continue;
+            const double f = A[size_t(r) * 2 * m + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < 2 * m; ++j) A[size_t(r) * 2 * m + j] -= f * A[size_t(c) * 2 * m + j];
+        }
+    }
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) winv[i * m + j] = A[size_t(i) * 2 * m + m + j];
+    return FJOFC_OK;
+}
+
+size_t dtype_size(int dt) { return dt == FJOFC_F32 ? 4 : 2; }
+
+int check_delta_layout(const void* const* ptrs, int count, int64_t n, int64_t ld, int dtype) {
+    if (dtype != FJOFC_F32 && dtype != FJOFC_F16 && dtype != FJOFC_BF16) return arg_error("unknown delta_dtype");
+    if (ld < n) return arg_error("ld must be >= n");
+    if ((ld * int64_t(dtype_size(dtype))) % 16 != 0)
+        return arg_error("Delta row stride must be a multiple of 16 bytes (ld*elem_size % 16 == 0)");
+    for (int i = 0; i < count; ++i) {
+        if (!ptrs[i]) return arg_error("Delta pointer is NULL");
+        if (reinterpret_cast<uintptr_t>(ptrs[i]) % 16 != 0) return arg_error("Delta base pointer must be 16-byte aligned");
+    }
+    return FJOFC_OK;
+}
+
+// ------------------------------------------------------------------ TMA descriptors
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+int get_encoder() {
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_encode) {
+        set_last_error("cuTensorMapEncodeTiled unavailable", "cudaGetDriverEntryPointByVersion");
+        return FJOFC_ERR_CUDA;
+    }
+    return FJOFC_OK;
+}
+
+CUtensorMapDataType tma_dtype(int dt) {
+    return dt == FJOFC_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+         : dt == FJOFC_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+}
+
+// rank-r tiled map; dims/strides innermost first, strides in bytes (rank-1 entries)
+int encode_map(CUtensorMap* map, int dtype, int rank, const void* base, const cuuint64_t* dims,
+               const cuuint64_t* strides, const cuuint32_t* box) {
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = g_encode(map, tma_dtype(dtype), cuuint32_t(rank), const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(g_last_msg, sizeof(g_last_msg), "cuTensorMapEncodeTiled failed (CUresult %d)", int(r));
+        return FJOFC_ERR_CUDA;
+    }
+    return FJOFC_OK;
+}
+
+// ------------------------------------------------------------------ K1 dispatch
+template <typename TD>
+cudaError_t k1_launch_dt(int d, int grid, const TMaps& tm, const K1Params& p, cudaStream_t s) {
+    switch (d) {
+#define C_(D) case D: return k1_launch_impl<D, TD>(grid, tm, p, s);
+        C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13) C_(14) C_(15) C_(16)
+#undef C_
+    }
+    return cudaErrorInvalidValue;
+}
+template <typename TD>
+int k1_bps_dt(int d) {
+    switch (d) {
+#define C_(D) case D: return k1_bps_impl<D, TD>();
+        C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13) C_(14) C_(15) C_(16)
+#undef C_
+    }
+    return 0;
+}
+template <typename TD>
+K1Geom k1_geom_dt(int d) {
+    switch (d) {
+#define C_(D) case D: return k1_geom_impl<D, TD>();
+        C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13) C_(14) C_(15) C_(16)
+#undef C_
+    }
+    return K1Geom{};
+}
+
+// ------------------------------------------------------------------ K3 dispatch
+template <typename TD>
+cudaError_t k3_launch_dt(int d, int grid, const CUtensorMap& tm, const K3Params& p, cudaStream_t s) {
+    switch (d) {
+#define C_(D) case D: return k3_launch_impl<D, TD>(grid, tm, p, s);
+        C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13) C_(14) C_(15) C_(16)
+#undef C_
+    }
+    return cudaErrorInvalidValue;
+}
+template <typename TD>
+int k3_bps_dt(int d) {
+    switch (d) {
+#define C_(D) case D: return k3_bps_impl<D, TD>();
+        C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13) C_(14) C_(15) C_(16)
+#undef C_
+    }
+    return 0;
+}
+template <typename TD>
+K3Geom k3_geom_dt(int d) {
+    switch (d) {
+#define C_(D) case D: return k3_geom_impl<D, TD>();
+        C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13) C_(14) C_(15) C_(16)
+#undef C_
+    }
+    return K3Geom{};
+}
+
+// ------------------------------------------------------------------ device scratch
+// One stream-ordered allocation per call, carved into 256-byte aligned pieces.
+struct Carver {
+    size_t off = 0;
+    template <typename T> size_t take(size_t count) {
+        const size_t o = (off + 255) & ~size_t(255);
+        off = o + count * sizeof(T);
+        return o;
+    }
+};
+
+struct ScopedDeviceMem {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    ~ScopedDeviceMem() { if (p) cudaFreeAsync(p, s); }
+};
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+struct EmbedPlan {
+    K1Geom g;
+    int nRB = 0, G = 0, nbx = 0;
+    int64_t Tm = 0, T = 0;
+};
+
+EmbedPlan make_plan(int m, int64_t n, int d, int dtype) {
+    EmbedPlan P;
+    P.g = fjofc::k1_geometry(d, dtype);
+    P.nRB = int((n + P.g.RB - 1) / P.g.RB);
+    int64_t Tm = 0;
+    for (int I = 0; I < P.nRB; ++I) Tm += (n - int64_t(I) * P.g.RB + P.g.CW - 1) / P.g.CW;
+    P.Tm = Tm;
+    P.T = Tm * m;
+    const int bps = std::max(1, fjofc::k1_blocks_per_sm(d, dtype));
+    int64_t G = int64_t(bps) * sm_count();
+    if (G > P.T) G = P.T;
+    P.G = int(G);
+    P.nbx = int((n + 255) / 256);
+    return P;
+}
+
+// Common validation of the in-sample arguments.
+int validate_insample(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t dtype,
+                      const float* delta_scale, const void* X) {
+    if (m < 1) return arg_error("m must be >= 1");
+    if (m > FJOFC_MAX_M) { snprintf(g_last_msg, sizeof(g_last_msg), "m > %d is not built", FJOFC_MAX_M); return FJOFC_ERR_UNSUPPORTED; }
+    if (n < 2) return arg_error("n must be >= 2");
+    if (n > (int64_t(1) << 30)) return arg_error("n too large");
+    if (d < 1) return arg_error("d must be >= 1");
+    if (d > FJOFC_MAX_D) { snprintf(g_last_msg, sizeof(g_last_msg), "d > %d is not built", FJOFC_MAX_D); return FJOFC_ERR_UNSUPPORTED; }
+    if (!delta) return arg_error("delta is NULL");
+    if (!X) return arg_error("X is NULL");
+    if (delta_scale)
+        for (int i = 0; i < m; ++i)
+            if (!(delta_scale[i] > 0.f) || !std::isfinite(delta_scale[i])) return arg_error("delta_scale must be finite and > 0");
+    return check_delta_layout(delta, m, n, ld, dtype);
+}
+
+// The in-sample loop.  mode 0: embed; mode 1: stress of X only.
+int run_insample(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t dtype,
+                 const float* delta_scale, const double* weights, float* X, const fjofc_opts* opts,
+                 fjofc_result* res, cudaStream_t stream, bool stress_only, double* stress_out) {
+    int rc = validate_insample(m, n, d, delta, ld, dtype, delta_scale, X);
+    if (rc) return rc;
+    fjofc_opts o{};
+    if (!stress_only) {
+        if (!opts) return arg_error("opts is NULL");
+        o = *opts;
+        if (o.max_iter < 0) return arg_error("max_iter must be >= 0");
+        if (o.tol_mode != FJOFC_TOL_ABS_NORMALIZED && o.tol_mode != FJOFC_TOL_RELATIVE) return arg_error("unknown tol_mode");
+        if (std::isnan(o.tol)) return arg_error("tol is NaN");
+        if (o.profile != 0 && o.profile != 1) return arg_error("profile must be 0 or 1");
+        for (int r = 0; r < 4; ++r)
+            if (o.reserved[r] != 0) return arg_error("opts.reserved must be zero");
+    } else {
+        o.max_iter = 0;
+        o.tol = -1.0;
+        o.tol_mode = FJOFC_TOL_RELATIVE;
+    }
+    double winv[FJOFC_MAX_M * FJOFC_MAX_M];
+    rc = weights_inverse(m, n, weights, winv);
+    if (rc) return rc;
+    if ((rc = get_encoder())) return rc;
+
+    const EmbedPlan P = make_plan(m, n, d, dtype);
+    if (P.g.RB == 0) { snprintf(g_last_msg, sizeof(g_last_msg), "no kernel for d=%d", d); return FJOFC_ERR_UNSUPPORTED; }
+    const int RB = P.g.RB, CW = P.g.CW;
+    const int64_t mnd = int64_t(m) * n * d;
+
+    // ---- scratch layout
+    Carver cv;
+    const size_t o_buf1 = cv.take<float>(mnd);
+    const size_t o_buf2 = cv.take<float>(mnd);
+    const size_t o_col = cv.take<float>(size_t(P.T) * d * CW);
+    const size_t o_head = cv.take<float>(size_t(m) * P.nRB * d * RB);
+    const size_t o_cont = cv.take<float>(size_t(P.G) * d * RB);
+    const size_t o_fid = cv.take<double>(P.G);
+    const size_t o_woff = cv.take<int64_t>(P.nRB + 1);
+    const size_t o_mu = cv.take<double>(2 * FJOFC_MAX_M * FJOFC_MAX_D);
+    const size_t o_bpart = cv.take<double>(size_t(d) * P.nbx * (m + 1));
+    const size_t o_ticket = cv.take<unsigned>(1);
+    const size_t o_st = cv.take<DevStatus>(1);
+    const size_t o_hist = cv.take<double>(size_t(o.max_iter) + 2);
+    const size_t total = cv.off;
+
+    ScopedDeviceMem mem;
+    mem.s = stream;
+    if (cudaMallocAsync(&mem.p, total, stream) != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(g_last_msg, sizeof(g_last_msg), "cudaMallocAsync(%zu bytes) failed", total);
+        return FJOFC_ERR_NOMEM;
+    }
+    char* base = static_cast<char*>(mem.p);
+    float* buf1 = reinterpret_cast<float*>(base + o_buf1);
+    float* buf2 = reinterpret_cast<float*>(base + o_buf2);
+    DevStatus* st = reinterpret_cast<DevStatus*>(base + o_st);
+    double* hist = reinterpret_cast<double*>(base + o_hist);
+
+    // ---- TMA descriptors: Delta_l as a 2-D tensor {n cols, n rows}, box {CW, RB}
+    TMaps tm;
+    std::memset(&tm, 0, sizeof(tm));
+    for (int l = 0; l < m; ++l) {
+        const cuuint64_t dims[2] = {cuuint64_t(n), cuuint64_t(n)};
+        const cuuint64_t strides[1] = {cuuint64_t(ld) * dtype_size(dtype)};
+        const cuuint32_t box[2] = {cuuint32_t(CW), cuuint32_t(RB)};
+        if ((rc = encode_map(&tm.map[l], dtype, 2, delta[l], dims, strides, box))) return rc;
+    }
+
+    K1Params k1{};
+    k1.colpart = reinterpret_cast<float*>(base + o_col);
+    k1.rowhead = reinterpret_cast<float*>(base + o_head);
+    k1.rowcont = reinterpret_cast<float*>(base + o_cont);
+    k1.fid = reinterpret_cast<double*>(base + o_fid);
+    k1.walk_off = reinterpret_cast<int64_t*>(base + o_woff);
+    k1.st = st;
+    k1.m = m; k1.n = int(n); k1.d = d; k1.nRB = P.nRB; k1.G = P.G;
+    k1.Tm = P.Tm; k1.T = P.T;
+    for (int l = 0; l < FJOFC_MAX_M; ++l) {
+        k1.wfid[l] = l < m ? float(weights[l * m + l]) : 0.f;
+        k1.dscale[l] = (l < m && delta_scale) ? delta_scale[l] : 1.f;
+    }
+
+    K2Params k2{};
+    k2.colpart = k1.colpart; k2.rowhead = k1.rowhead; k2.rowcont = k1.rowcont; k2.fid = k1.fid;
+    k2.walk_off = k1.walk_off;
+    k2.mu = reinterpret_cast<double*>(base + o_mu);
+    k2.bpart = reinterpret_cast<double*>(base + o_bpart);
+    k2.ticket = reinterpret_cast<unsigned*>(base + o_ticket);
+    k2.st = st;
+    k2.hist = hist;
+    k2.m = m; k2.n = int(n); k2.d = d; k2.RB = RB; k2.CW = CW; k2.nRB = P.nRB; k2.G = P.G; k2.nbx = P.nbx;
+    k2.Tm = P.Tm; k2.T = P.T;
+    k2.tol_mode = o.tol_mode; k2.tol = o.tol;
+    k2.npairs = double(m * n) * double(m * n - 1) / 2.0;
+    for (int j = 0; j < m; ++j)
+        for (int l = 0; l < m; ++l) {
+            k2.coef[j][l] = winv[j * m + l] * weights[l * m + l] * double(k1.dscale[l]);
+            k2.wcomm[j][l] = (j < l) ? weights[j * m + l] : 0.0;
+        }
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    FJ_CUDA(cudaEventCreate(&ev0));
+    FJ_CUDA(cudaEventCreate(&ev1));
+    FJ_CUDA(cudaEventRecord(ev0, stream));
+
+    InitParams ip{st, k2.ticket, k2.mu, const_cast<int64_t*>(k1.walk_off), int(n), RB, CW, P.nRB};
+    FJ_CUDA(launch_init(ip, stream));
+
+    float* bufs[3] = {X, buf1, buf2};
+    const bool prof = o.profile == 1;
+    std::vector<cudaEvent_t> pev;
+    if (prof) {
+        pev.resize(size_t(3) * (o.max_iter + 1));
+        for (auto& e : pev) FJ_CUDA(cudaEventCreate(&e));
+    }
+    int launches = 2;   // init + finalize
+    auto k1_launch = [&](cudaError_t& e) {
+        e = (dtype == FJOFC_F32) ? k1_launch_dt<float>(d, P.G, tm, k1, stream)
+          : (dtype == FJOFC_F16) ? k1_launch_dt<__half>(d, P.G, tm, k1, stream)
+                                 : k1_launch_dt<__nv_bfloat16>(d, P.G, tm, k1, stream);
+    };
+    for (int t = 1; t <= o.max_iter + 1; ++t) {
+        const bool final_pass = (t == o.max_iter + 1);
+        k1.X = bufs[(t - 1) % 3];
+        cudaError_t e;
+        if (prof) FJ_CUDA(cudaEventRecord(pev[3 * (t - 1)], stream));
+        k1_launch(e);
+        FJ_CUDA(e);
+        if (prof) FJ_CUDA(cudaEventRecord(pev[3 * (t - 1) + 1], stream));
+        k2.Xprev = bufs[(t - 1) % 3];
+        k2.Xnext = bufs[t % 3];
+        k2.t = t;
+        k2.final_pass = final_pass ? 1 : 0;
+        FJ_CUDA(launch_k2(k2, stream));
+        if (prof) FJ_CUDA(cudaEventRecord(pev[3 * (t - 1) + 2], stream));
+        launches += 2;
+    }
+    FJ_CUDA(launch_finalize(X, buf1, buf2, mnd, st, stream));
+    FJ_CUDA(cudaEventRecord(ev1, stream));
+
+    DevStatus hst;
+    std::vector<double> hh(size_t(o.max_iter) + 1);
+    FJ_CUDA(cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, stream));
+    FJ_CUDA(cudaMemcpyAsync(hh.data(), hist, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    FJ_CUDA(cudaStreamSynchronize(stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    // passes that did work: the one that computed sigma(X_final) and all before it
+    const int worked = std::min(o.max_iter + 1, hst.final_iter + 1 + (hst.error == FJOFC_ERR_NONFINITE ? 1 : 0));
+    float ms_pass = 0.f, ms_apply = 0.f;
+    if (prof) {
+        for (int t = 0; t < worked; ++t) {
+            float a = 0.f, b2 = 0.f;
+            cudaEventElapsedTime(&a, pev[3 * t], pev[3 * t + 1]);
+            cudaEventElapsedTime(&b2, pev[3 * t + 1], pev[3 * t + 2]);
+            ms_pass += a;
+            ms_apply += b2;
+        }
+        for (auto& e : pev) cudaEventDestroy(e);
+    }
+
+    rc = hst.error;
+    if (rc == FJOFC_ERR_TIMEOUT) snprintf(g_last_msg, sizeof(g_last_msg), "device wait timed out (site %d)", hst.timeout_site);
+    if (rc == FJOFC_ERR_NONFINITE) snprintf(g_last_msg, sizeof(g_last_msg), "stress became non-finite");
+    if (stress_out) *stress_out = (hst.error == FJOFC_ERR_NONFINITE) ? hh[0] : hst.stress;
+    if (res) {
+        res->status = rc;
+        res->iters = hst.final_iter;
+        res->stress = hst.stress;
+        res->stress_normalized = hst.stress / k2.npairs;
+        res->ms_total = ms;
+        res->passes = prof ? worked : 0;
+        res->ms_pass = ms_pass;
+        res->ms_apply = ms_apply;
+        res->launches = launches;
+        if (res->stress_history) {
+            const int upto = (hst.error == FJOFC_ERR_NONFINITE) ? hst.final_iter + 1 : hst.final_iter;
+            for (int t = 0; t <= upto && t <= o.max_iter; ++t) res->stress_history[t] = hh[t];
+        }
+    }
+    return rc;
+}
+
+// Out-of-sample solve (Sec. 3): k independent objects, each iterated to its own stop.
+int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const void* delta_new, int64_t ld,
+            int32_t dtype, const float* delta_scale, const double* weights, float* Y, int32_t* iters_out,
+            double* stress_out, const fjofc_opts* opts, fjofc_result* res, cudaStream_t stream) {
+    if (m < 1) return arg_error("m must be >= 1");
+    if (m > FJOFC_MAX_M) { snprintf(g_last_msg, sizeof(g_last_msg), "m > %d is not built", FJOFC_MAX_M); return FJOFC_ERR_UNSUPPORTED; }
+    if (n < 1) return arg_error("n must be >= 1");
+    if (n > (int64_t(1) << 30)) return arg_error("n too large");
+    if (d < 1) return arg_error("d must be >= 1");
+    if (d > FJOFC_MAX_D) { snprintf(g_last_msg, sizeof(g_last_msg), "d > %d is not built", FJOFC_MAX_D); return FJOFC_ERR_UNSUPPORTED; }
+    if (k < 0) return arg_error("k must be >= 0");
+    if (k > (int64_t(1) << 31)) return arg_error("k too large");
+    if (!X || !Y) return arg_error("X or Y is NULL");
+    if (!opts) return arg_error("opts is NULL");
+    const fjofc_opts o = *opts;
+    if (o.max_iter < 0) return arg_error("max_iter must be >= 0");
+    if (o.tol_mode != FJOFC_TOL_ABS_NORMALIZED && o.tol_mode != FJOFC_TOL_RELATIVE) return arg_error("unknown tol_mode");
+    if (std::isnan(o.tol)) return arg_error("tol is NaN");
+    if (delta_scale)
+        for (int i = 0; i < m; ++i)
+            if (!(delta_scale[i] > 0.f) || !std::isfinite(delta_scale[i])) return arg_error("delta_scale must be finite and > 0");
+    int rc;
+    if (k > 0) {
+        const void* ptrs[1] = {delta_new};
+        if ((rc = check_delta_layout(ptrs, 1, n, ld, dtype))) return rc;
+    }
+    double winv[FJOFC_MAX_M * FJOFC_MAX_M];
+    if ((rc = weights_inverse(m, n, weights, winv))) return rc;
+    if (k == 0) {
+        if (res) { res->status = 0; res->iters = 0; res->stress = 0.0; res->stress_normalized = 0.0; res->ms_total = 0.f; }
+        return FJOFC_OK;
+    }
+    if ((rc = get_encoder())) return rc;
+    const K3Geom g = (dtype == FJOFC_F32) ? k3_geom_dt<float>(d) : (dtype == FJOFC_F16) ? k3_geom_dt<__half>(d)
+                                                                                      : k3_geom_dt<__nv_bfloat16>(d);
+    const int nx = int((n + 3) / 4 * 4);
+
+    Carver cv;
+    const size_t o_xt = cv.take<float>(size_t(m) * d * nx);
+    const size_t o_sx = cv.take<double>(size_t(m) * d);
+    const size_t o_ctr = cv.take<unsigned long long>(1);
+    const size_t o_st = cv.take<DevStatus>(1);
+    const size_t o_it = cv.take<int32_t>(size_t(k));
+    const size_t o_sig = cv.take<double>(size_t(k));
+    const size_t o_sum = cv.take<double>(2);
+    const size_t total = cv.off;
+    ScopedDeviceMem mem;
+    mem.s = stream;
+    if (cudaMallocAsync(&mem.p, total, stream) != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(g_last_msg, sizeof(g_last_msg), "cudaMallocAsync(%zu bytes) failed", total);
+        return FJOFC_ERR_NOMEM;
+    }
+    char* base = static_cast<char*>(mem.p);
+    DevStatus* st = reinterpret_cast<DevStatus*>(base + o_st);
+
+    // delta_new as a 3-D tensor {n points, m modalities, k objects}, box {CW, 1, R}
+    CUtensorMap tmap;
+    {
+        const cuuint64_t dims[3] = {cuuint64_t(n), cuuint64_t(m), cuuint64_t(k)};
+        const cuuint64_t strides[2] = {cuuint64_t(ld) * dtype_size(dtype), cuuint64_t(ld) * m * dtype_size(dtype)};
+        const cuuint32_t box[3] = {cuuint32_t(g.CW), 1u, cuuint32_t(g.R)};
+        if ((rc = encode_map(&tmap, dtype, 3, delta_new, dims, strides, box))) return rc;
+    }
+
+    K3Params p{};
+    p.X = X;
+    p.XT = reinterpret_cast<float*>(base + o_xt);
+    p.SX = reinterpret_cast<double*>(base + o_sx);
+    p.Y = Y;
+    p.iters_out = iters_out ? iters_out : reinterpret_cast<int32_t*>(base + o_it);
+    p.stress_out = stress_out ? stress_out : reinterpret_cast<double*>(base + o_sig);
+    p.next_block = reinterpret_cast<unsigned long long*>(base + o_ctr);
+    p.st = st;
+    p.m = m; p.n = int(n); p.nx = nx; p.d = d; p.max_iter = o.max_iter; p.tol_mode = o.tol_mode; p.k = k;
+    p.tol = o.tol;
+    p.npairs = double(m) * double(n) + double(m) * (m - 1) / 2.0;
+    for (int j = 0; j < FJOFC_MAX_M; ++j) {
+        p.wfid[j] = j < m ? float(weights[j * m + j]) : 0.f;
+        p.dscale[j] = (j < m && delta_scale) ? delta_scale[j] : 1.f;
+    }
+    for (int j = 0; j < m; ++j)
+        for (int l = 0; l < m; ++l) {
+            p.winv[j][l] = winv[j * m + l];
+            p.wcomm[j][l] = (j != l) ? weights[j * m + l] : 0.0;
+        }
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    FJ_CUDA(cudaEventCreate(&ev0));
+    FJ_CUDA(cudaEventCreate(&ev1));
+    FJ_CUDA(cudaEventRecord(ev0, stream));
+    OOSPrepParams pp{X, const_cast<float*>(p.XT), const_cast<double*>(p.SX), m, int(n), nx, d, p.next_block, st};
+    FJ_CUDA(launch_oos_prep(pp, stream));
+    const int bps = std::max(1, (dtype == FJOFC_F32) ? k3_bps_dt<float>(d) : (dtype == FJOFC_F16) ? k3_bps_dt<__half>(d)
+                                                                                              : k3_bps_dt<__nv_bfloat16>(d));
+    const int64_t groups = (k + g.R - 1) / g.R;
+    int64_t grid = int64_t(bps) * sm_count();
+    const int64_t need = (groups + g.WARPS - 1) / g.WARPS;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    cudaError_t e = (dtype == FJOFC_F32) ? k3_launch_dt<float>(d, int(grid), tmap, p, stream)
+                  : (dtype == FJOFC_F16) ? k3_launch_dt<__half>(d, int(grid), tmap, p, stream)
+                                         : k3_launch_dt<__nv_bfloat16>(d, int(grid), tmap, p, stream);
+    FJ_CUDA(e);
+    double* sums = reinterpret_cast<double*>(base + o_sum);
+    FJ_CUDA(launch_oos_summary(p.iters_out, p.stress_out, k, reinterpret_cast<int32_t*>(sums + 1), sums, stream));
+    FJ_CUDA(cudaEventRecord(ev1, stream));
+    DevStatus hst;
+    double hsum[2];
+    FJ_CUDA(cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, stream));
+    FJ_CUDA(cudaMemcpyAsync(hsum, sums, sizeof(hsum), cudaMemcpyDeviceToHost, stream));
+    FJ_CUDA(cudaStreamSynchronize(stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    rc = hst.error;
+    if (rc == FJOFC_ERR_TIMEOUT) snprintf(g_last_msg, sizeof(g_last_msg), "device wait timed out (site %d)", hst.timeout_site);
+    if (res) {
+        res->status = rc;
+        int32_t it;
+        std::memcpy(&it, &hsum[1], sizeof(it));
+        res->iters = it;
+        res->stress = hsum[0];
+        res->stress_normalized = hsum[0] / p.npairs;
+        res->ms_total = ms;
+        res->passes = 0;
+        res->ms_pass = 0.f;
+        res->ms_apply = 0.f;
+        res->launches = 3;
+    }
+    return rc;
+}
+
+}  // namespace
+
+namespace fjofc {
+K1Geom k1_geometry(int d, int dtype) {
+    if (d < 1 || d > FJOFC_MAX_D) return K1Geom{};
+    return dtype == FJOFC_F32 ? k1_geom_dt<float>(d) : dtype == FJOFC_F16 ? k1_geom_dt<__half>(d) : k1_geom_dt<__nv_bfloat16>(d);
+}
+int k1_blocks_per_sm(int d, int dtype) {
+    return dtype == FJOFC_F32 ? k1_bps_dt<float>(d) : dtype == FJOFC_F16 ? k1_bps_dt<__half>(d) : k1_bps_dt<__nv_bfloat16>(d);
+}
+}  // namespace fjofc
+
+// ====================================================================== C ABI
+extern "C" {
+
+int fjofc_embed(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t delta_dtype,
+                const float* delta_scale, const double* weights, float* X, const fjofc_opts* opts,
+                fjofc_result* res, void* cuda_stream) {
+    const int rc = run_insample(m, n, d, delta, ld, delta_dtype, delta_scale, weights, X, opts, res,
+                                static_cast<cudaStream_t>(cuda_stream), false, nullptr);
+    if (res) res->status = rc;
+    return rc;
+}
+
+int fjofc_stress(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t delta_dtype,
+                 const float* delta_scale, const double* weights, const float* X, double* stress_out,
+                 void* cuda_stream) {
+    if (!stress_out) return arg_error("stress_out is NULL");
+    // max_iter = 0: one pass over X; the kernels centre X in place only when a Guttman
+    // output is returned, and X_0 is returned as given (mu_0 = 0), so X is not modified.
+    return run_insample(m, n, d, delta, ld, delta_dtype, delta_scale, weights, const_cast<float*>(X), nullptr,
+                        nullptr, static_cast<cudaStream_t>(cuda_stream), true, stress_out);
+}
+
+int fjofc_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const void* delta_new, int64_t ld,
+              int32_t delta_dtype, const float* delta_scale, const double* weights, float* Y, int32_t* iters_out,
+              double* stress_out, const fjofc_opts* opts, fjofc_result* res, void* cuda_stream) {
+    const int rc = run_oos(m, n, d, k, X, delta_new, ld, delta_dtype, delta_scale, weights, Y, iters_out, stress_out,
+                           opts, res, static_cast<cudaStream_t>(cuda_stream));
+    if (res) res->status = rc;
+    return rc;
+}
+
+const char* fjofc_strerror(int status) {
+    switch (status) {
+        case FJOFC_OK: return "ok";
+        case FJOFC_ERR_ARG: return g_last_msg[0] ? g_last_msg : "invalid argument";
+        case FJOFC_ERR_CUDA: return g_last_msg[0] ? g_last_msg : "CUDA error";
+        case FJOFC_ERR_NONFINITE: return "stress became non-finite (NaN/Inf)";
+        case FJOFC_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+        case FJOFC_ERR_NOMEM: return g_last_msg[0] ? g_last_msg : "out of device memory";
+        case FJOFC_ERR_UNSUPPORTED: return g_last_msg[0] ? g_last_msg : "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+const char* fjofc_version(void) { return "fjofc-gb300 0.1 (sm_103a; d=1..16; m<=8; f32/f16/bf16 Delta)"; }
+
+}  // extern "C"

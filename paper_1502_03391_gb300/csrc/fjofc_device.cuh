@@ -1,0 +1,174 @@
+// Device-side building blocks shared by the fJOFC kernels: inline-PTX wrappers for
+// mbarriers and TMA (cp.async.bulk.tensor), bounded waits, packed float math and the
+// device status block.  sm_100+ only (built for sm_103a).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "fjofc_internal.h"
+
+namespace fjofc {
+
+// ----------------------------------------------------------------- status block
+// Written by the kernels, read by later kernels of the same call and copied to the
+// host once at the end of a call.
+struct DevStatus {
+    int done;          // 1 once the loop has stopped (converged, max_iter, error)
+    int error;         // 0 or an FJOFC_ERR_* code raised on the device
+    int final_iter;    // index T of the returned iterate X_T
+    int timeout_site;  // where a bounded wait gave up (diagnostics)
+    double stress;     // sigma(X_T)
+};
+
+__device__ __forceinline__ int ld_volatile(const int* p) {
+    return *reinterpret_cast<const volatile int*>(p);
+}
+
+__device__ __forceinline__ void raise_error(DevStatus* st, int code, int site) {
+    atomicCAS(&st->error, 0, code);
+    atomicExch(&st->timeout_site, site);
+    atomicExch(&st->done, 1);
+}
+
+// ----------------------------------------------------------------- timers / waits
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Upper bound of any device-side wait.  A healthy wait completes in microseconds; on
+// expiry the kernel records FJOFC_ERR_TIMEOUT and returns instead of spinning.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on phase `parity` of an mbarrier.  Returns false after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0u && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+// 2-D tiled TMA load of box {x (inner), y} into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+
+// 3-D tiled TMA load of box {x, y, z}.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ----------------------------------------------------------------- math helpers
+// Hardware reciprocal square root (MUFU); inputs are clamped to >= FLT_MIN by callers.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <typename T> struct DeltaLoad;
+template <> struct DeltaLoad<float> {
+    static __device__ __forceinline__ float to_f32(float v) { return v; }
+};
+template <> struct DeltaLoad<__half> {
+    static __device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+};
+template <> struct DeltaLoad<__nv_bfloat16> {
+    static __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+};
+
+// Load C consecutive Delta values from shared memory (vectorised) as float.
+template <typename TD, int C>
+__device__ __forceinline__ void load_delta_row(const TD* p, float (&out)[C]) {
+    if constexpr (sizeof(TD) == 4) {
+        if constexpr (C % 4 == 0) {
+#pragma unroll
+            for (int c = 0; c < C; c += 4) {
+                float4 v = *reinterpret_cast<const float4*>(p + c);
+                out[c] = v.x; out[c + 1] = v.y; out[c + 2] = v.z; out[c + 3] = v.w;
+            }
+        } else if constexpr (C % 2 == 0) {
+#pragma unroll
+            for (int c = 0; c < C; c += 2) {
+                float2 v = *reinterpret_cast<const float2*>(p + c);
+                out[c] = v.x; out[c + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) out[c] = reinterpret_cast<const float*>(p)[c];
+        }
+    } else {
+        if constexpr (C % 2 == 0) {
+#pragma unroll
+            for (int c = 0; c < C; c += 2) {
+                if constexpr (std::is_same<TD, __half>::value) {
+                    float2 v = __half22float2(*reinterpret_cast<const __half2*>(p + c));
+                    out[c] = v.x; out[c + 1] = v.y;
+                } else {
+                    float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + c));
+                    out[c] = v.x; out[c + 1] = v.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) out[c] = DeltaLoad<TD>::to_f32(p[c]);
+        }
+    }
+}
+
+// Full-warp float64 sum (xor butterfly, every lane gets the total).
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace fjofc

@@ -1,0 +1,133 @@
+// Internal declarations of the fJOFC library: kernel parameter blocks, tile
+// configurations and the host-side launch entry points of each translation unit.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fjofc.h"
+
+namespace fjofc {
+
+struct DevStatus;
+
+// Tensor maps of the m dissimilarity matrices (one 2-D map per modality), passed to
+// the kernels as a __grid_constant__ parameter.
+struct TMaps {
+    CUtensorMap map[FJOFC_MAX_M];
+};
+
+// ---------------------------------------------------------------------------
+// Tile geometry of the all-pairs pass (K1)
+//
+// The upper triangle of each Delta_l is covered by "walks": row block I (RB rows
+// starting at I*RB) visits the column sub-tiles [I*RB + s*CW, I*RB + (s+1)*CW) for
+// s = 0 .. L(I)-1, L(I) = ceil((n - I*RB)/CW).  Sub-tiles are numbered linearly
+// t = l*Tm + walk_off[I] + s; CTA b processes t in [b*T/G, (b+1)*T/G).
+// ---------------------------------------------------------------------------
+struct K1Geom {
+    int R, C, WARPS, STAGES;    // rows per thread, columns per lane, warps, pipeline depth
+    int RB, CW;                 // row-block height (WARPS*R), sub-tile width (32*C)
+    int threads;
+    size_t smem_bytes;
+};
+
+// Geometry of the K1 instantiation used for embedding dimension d.
+K1Geom k1_geometry(int d, int dtype);
+
+struct K1Params {
+    const float* X;            // X_{t-1}: (m*n) x d row-major
+    float* colpart;            // [T][d][CW]   column partials of B'X per sub-tile
+    float* rowhead;            // [m][nRB][d][RB] row partials of the segment that starts a walk
+    float* rowcont;            // [G][d][RB]   row partial of a CTA whose range starts mid-walk
+    double* fid;               // [G]          weighted fidelity partial per CTA
+    const int64_t* walk_off;   // [nRB+1]      prefix sums of the walk lengths
+    DevStatus* st;
+    int m, n, d, nRB, G;
+    int64_t Tm, T;             // sub-tiles per modality, total
+    float wfid[FJOFC_MAX_M];   // w_ll: fidelity weight of modality l
+    float dscale[FJOFC_MAX_M]; // s_l: Delta scale of modality l
+};
+
+// CTAs of the K1 instantiation that fit on one SM.
+int k1_blocks_per_sm(int d, int dtype);
+
+// ---------------------------------------------------------------------------
+// K2: apply Wmod^-1, centre, commensurability, stress, stopping test
+// ---------------------------------------------------------------------------
+struct K2Params {
+    float* Xprev;              // X_{t-1}; its modality blocks are centred in place
+    float* Xnext;              // X_t (written unless final_pass)
+    const float* colpart;
+    const float* rowhead;
+    const float* rowcont;
+    const double* fid;
+    const int64_t* walk_off;
+    double* mu;                // [2][FJOFC_MAX_M][FJOFC_MAX_D] modality column means, by t parity
+    double* bpart;             // [d][nbx][m+1] per-block partial sums
+    unsigned* ticket;
+    DevStatus* st;
+    double* hist;              // sigma(X_0..X_max_iter)
+    int m, n, d, RB, CW, nRB, G, nbx;
+    int64_t Tm, T;
+    int t;                     // pass index: reads X_{t-1}, writes X_t
+    int final_pass;            // 1: only sigma(X_{t-1}) and the centring
+    int tol_mode;
+    double tol, npairs;        // tolerance, C(mn,2)
+    double coef[FJOFC_MAX_M][FJOFC_MAX_M];   // [Wmod^-1]_{jl} * w_ll * s_l
+    double wcomm[FJOFC_MAX_M][FJOFC_MAX_M];  // w_jl for j < l, else 0
+};
+
+cudaError_t launch_k2(const K2Params& p, cudaStream_t s);
+
+struct InitParams {
+    DevStatus* st;
+    unsigned* ticket;
+    double* mu;
+    int64_t* walk_off;
+    int n, RB, CW, nRB;
+};
+cudaError_t launch_init(const InitParams& p, cudaStream_t s);
+cudaError_t launch_finalize(float* Xout, const float* buf1, const float* buf2, int64_t count,
+                            const DevStatus* st, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// K3: out-of-sample Guttman iterations (one CTA per block of new objects)
+// ---------------------------------------------------------------------------
+struct K3Geom {
+    int R, C, WARPS, STAGES, OB, CW, threads;
+    size_t smem_bytes;
+};
+
+struct K3Params {
+    const float* X;            // in-sample (m*n) x d
+    const float* XT;           // in-sample transposed: [m][d][nx] (nx = n rounded up to 4)
+    const double* SX;          // [m][d] column sums of each X^(j)
+    float* Y;                  // k x m x d
+    int32_t* iters_out;        // may be NULL
+    double* stress_out;        // never NULL (internal buffer when the caller passes NULL)
+    unsigned long long* next_block;   // work counter (object groups)
+    DevStatus* st;
+    int m, n, nx, d, max_iter, tol_mode;
+    int64_t k;
+    double tol, npairs;
+    float wfid[FJOFC_MAX_M];
+    float dscale[FJOFC_MAX_M];
+    double winv[FJOFC_MAX_M][FJOFC_MAX_M];   // Wmod^-1
+    double wcomm[FJOFC_MAX_M][FJOFC_MAX_M];  // w_jl, j != l
+};
+
+struct OOSPrepParams {
+    const float* X;
+    float* XT;
+    double* SX;
+    int m, n, nx, d;
+    unsigned long long* next_block;
+    DevStatus* st;
+};
+cudaError_t launch_oos_prep(const OOSPrepParams& p, cudaStream_t s);
+cudaError_t launch_oos_summary(const int32_t* iters, const double* stress, int64_t k, int32_t* it_out,
+                               double* st_out, cudaStream_t s);
+
+}  // namespace fjofc

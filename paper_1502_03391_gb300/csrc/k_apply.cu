@@ -1,0 +1,292 @@
+// K2 and the small per-call kernels of the in-sample loop.
+//
+// K2 (one launch per Guttman transform) finishes iteration t:
+//   * (B'_l X_l)_i = sum of the K1 partials of object i in modality l, in a fixed order
+//     (its row-walk head, the continuation segments, then the column partials of the
+//     walks of row blocks 0..I(i));
+//   * X_t^(j)_i = sum_l [Wmod^-1]_{jl} w_ll s_l (B'_l X_l)_i      (Eq. update / Cor. 1:
+//     L^+ = Wmod^-1 (x) I_n + Z (x) J_n, and the J_n part vanishes on B(X) X because the
+//     rows and columns of every B_l sum to zero, Sec. 2.1);
+//   * sigma(X_{t-1}) = (fidelity from K1) + sum_{j<l} w_jl ||X^(j) - X^(l)||^2 (Eq. stress,
+//     Remark faststress), with X_{t-1} first centred per modality in float64 (Guttman
+//     outputs are centred in exact arithmetic; this removes float32 drift);
+//   * the column means of X_t (for the next centring) and, in the last CTA to finish,
+//     the stress history entry and the stopping test of Algorithm 1 (read as "continue
+//     while the decrease exceeds the tolerance").
+#include "fjofc_device.cuh"
+
+namespace fjofc {
+
+constexpr int K2_THREADS = 256;
+
+__device__ __forceinline__ double block_sum_f64(double v, double* sh) {
+    // sh: >= K2_THREADS/32 doubles; returns the total in thread 0
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum_f64(v);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    }
+    return t;
+}
+
+__global__ void __launch_bounds__(K2_THREADS)
+k_apply(const K2Params p) {
+    __shared__ double s_part[FJOFC_MAX_M + 1][K2_THREADS / 32];
+    __shared__ double s_tmp[K2_THREADS / 32];
+    __shared__ bool s_last;
+
+    if (ld_volatile(&p.st->done)) return;
+
+    const int k = blockIdx.y;
+    const int i = blockIdx.x * K2_THREADS + threadIdx.x;
+    const int m = p.m, n = p.n, d = p.d;
+    const double* mu_prev = p.mu + ((p.t - 1) & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
+    double* mu_next = p.mu + (p.t & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
+
+    double colsum[FJOFC_MAX_M];
+    double comm = 0.0;
+#pragma unroll
+    for (int j = 0; j < FJOFC_MAX_M; ++j) colsum[j] = 0.0;
+
+    if (i < n) {
+        // centre X_{t-1} (in place) and its commensurability term
+        double xc[FJOFC_MAX_M];
+        for (int j = 0; j < m; ++j) {
+            const int64_t off = (int64_t(j) * n + i) * d + k;
+            xc[j] = double(p.Xprev[off]) - mu_prev[j * FJOFC_MAX_D + k];
+            if (p.t > 1) p.Xprev[off] = float(xc[j]);   // X_0 (mu_0 = 0) is left untouched
+        }
+        for (int j = 0; j < m; ++j)
+            for (int l = j + 1; l < m; ++l) {
+                const double df = xc[j] - xc[l];
+                comm += p.wcomm[j][l] * df * df;
+            }
+
+        if (!p.final_pass) {
+            const int RB = p.RB, CW = p.CW;
+            const int I = i / RB, ri = i - I * RB;
+            double bx[FJOFC_MAX_M];
+            for (int l = 0; l < m; ++l) {
+                float acc = p.rowhead[((int64_t(l) * p.nRB + I) * d + k) * RB + ri];
+                // continuation segments: CTAs whose range starts strictly inside this walk
+                const int64_t ws = int64_t(l) * p.Tm + p.walk_off[I];
+                const int64_t we = int64_t(l) * p.Tm + p.walk_off[I + 1];
+                int64_t bcta = ((ws + 1) * p.G + p.T - 1) / p.T;   // first b with b*T/G > ws
+                for (; bcta < p.G; ++bcta) {
+                    const int64_t pb = bcta * p.T / p.G;
+                    if (pb >= we) break;
+                    if (pb > ws) acc += p.rowcont[(bcta * d + k) * RB + ri];
+                }
+                // column partials from the walks of row blocks 0..I
+                const int64_t tl = int64_t(l) * p.Tm;
+                float cacc = 0.f;
+                for (int J = 0; J <= I; ++J) {
+                    const int rel = i - J * RB;
+                    const int s = rel / CW, c = rel - s * CW;
+                    const int64_t t = tl + p.walk_off[J] + s;
+                    cacc += p.colpart[(t * d + k) * CW + c];
+                }
+                bx[l] = double(acc) + double(cacc);
+            }
+            for (int j = 0; j < m; ++j) {
+                double v = 0.0;
+                for (int l = 0; l < m; ++l) v += p.coef[j][l] * bx[l];
+                const float vf = float(v);
+                p.Xnext[(int64_t(j) * n + i) * d + k] = vf;
+                colsum[j] = double(vf);
+            }
+        }
+    }
+
+    // per-block partial sums: column sums of X_t per modality, and commensurability
+    for (int j = 0; j <= m; ++j) {
+        const double v = (j < m) ? colsum[j] : comm;
+        const double tot = block_sum_f64(v, s_tmp);
+        if (threadIdx.x == 0) s_part[j][0] = tot;
+    }
+    const int blk = k * p.nbx + blockIdx.x;
+    if (threadIdx.x == 0) {
+        for (int j = 0; j <= m; ++j) p.bpart[int64_t(blk) * (m + 1) + j] = s_part[j][0];
+        __threadfence();
+        const unsigned prev = atomicAdd(p.ticket, 1u);
+        s_last = (prev == gridDim.x * gridDim.y - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+
+    // ---- last CTA: totals in a fixed order
+    const volatile double* bp = p.bpart;
+    const int nblk = gridDim.x * gridDim.y;
+    // column means of X_t: one thread per (modality, coordinate)
+    for (int e = threadIdx.x; e < m * d; e += blockDim.x) {
+        const int j = e / d, kk = e - j * d;
+        double s = 0.0;
+        for (int bx = 0; bx < p.nbx; ++bx) s += bp[int64_t(kk * p.nbx + bx) * (m + 1) + j];
+        mu_next[j * FJOFC_MAX_D + kk] = p.final_pass ? 0.0 : s / double(n);
+    }
+    double c = 0.0;
+    for (int e = threadIdx.x; e < nblk; e += blockDim.x) c += bp[int64_t(e) * (m + 1) + m];
+    const double comm_tot = block_sum_f64(c, s_tmp);
+    double f = 0.0;
+    const volatile double* fidp = p.fid;
+    for (int e = threadIdx.x; e < p.G; e += blockDim.x) f += fidp[e];
+    const double fid_tot = block_sum_f64(f, s_tmp);
+
+    if (threadIdx.x == 0) {
+        const double sigma = fid_tot + comm_tot;
+        const int tp = p.t - 1;                 // index of the iterate whose stress this is
+        p.hist[tp] = sigma;
+        DevStatus* st = p.st;
+        if (!isfinite(sigma)) {
+            st->error = FJOFC_ERR_NONFINITE;    // final_iter keeps the last finite iterate
+            st->done = 1;
+        } else {
+            st->final_iter = tp;
+            st->stress = sigma;
+            bool stop = p.final_pass != 0;
+            if (!stop && tp >= 1 && p.tol >= 0.0) {
+                const double prev = p.hist[tp - 1];
+                const double dec = prev - sigma;
+                const bool cont = (p.tol_mode == FJOFC_TOL_RELATIVE) ? (dec > p.tol * prev)
+                                                                     : (dec / p.npairs > p.tol);
+                stop = !cont;
+            }
+            if (stop) st->done = 1;
+        }
+        __threadfence();
+        *p.ticket = 0u;                          // ready for the next launch
+    }
+}
+
+cudaError_t launch_k2(const K2Params& p, cudaStream_t s) {
+    dim3 grid(p.nbx, p.d);
+    k_apply<<<grid, K2_THREADS, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// Per-call initialisation: status block, ticket, mu_0 = 0, walk offsets.
+__global__ void k_init(const InitParams p) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        p.st->done = 0;
+        p.st->error = 0;
+        p.st->final_iter = 0;
+        p.st->timeout_site = 0;
+        p.st->stress = 0.0;
+        *p.ticket = 0u;
+    }
+    for (int e = tid; e < 2 * FJOFC_MAX_M * FJOFC_MAX_D; e += gridDim.x * blockDim.x) p.mu[e] = 0.0;
+    for (int I = tid; I <= p.nRB; I += gridDim.x * blockDim.x) {
+        int64_t s = 0;
+        for (int J = 0; J < I; ++J) {
+            const int64_t cols = int64_t(p.n) - int64_t(J) * p.RB;
+            s += (cols + p.CW - 1) / p.CW;
+        }
+        p.walk_off[I] = s;
+    }
+}
+
+cudaError_t launch_init(const InitParams& p, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = (p.nRB + 1 + threads - 1) / threads;
+    k_init<<<blocks, threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// Copy the returned iterate to the caller's buffer when it lives in a workspace buffer
+// (iterate t is stored in buffer t % 3; buffer 0 is the caller's X).
+__global__ void k_finalize(float* Xout, const float* buf1, const float* buf2, int64_t count,
+                           const DevStatus* st) {
+    const int f = st->final_iter;
+    const int slot = f % 3;
+    if (slot == 0) return;
+    const float* src = (slot == 1) ? buf1 : buf2;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < count; e += int64_t(gridDim.x) * blockDim.x)
+        Xout[e] = src[e];
+}
+
+cudaError_t launch_finalize(float* Xout, const float* buf1, const float* buf2, int64_t count,
+                            const DevStatus* st, cudaStream_t s) {
+    const int threads = 256;
+    int64_t blocks = (count + threads - 1) / threads;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) blocks = 1;
+    k_finalize<<<int(blocks), threads, 0, s>>>(Xout, buf1, buf2, count, st);
+    return cudaGetLastError();
+}
+
+}  // namespace fjofc
+
+namespace fjofc {
+
+// Out-of-sample set-up: X transposed to [m][d][nx] (row stride nx, a multiple of 4 so
+// that vector loads stay aligned), the column sums of every X^(j) in float64 (fixed
+// order per block), the group counter and the status block.
+__global__ void k_oos_prep(const OOSPrepParams p) {
+    const int j = blockIdx.x / p.d, kk = blockIdx.x - j * p.d;
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < p.nx; i += blockDim.x) {
+        const float v = (i < p.n) ? p.X[(int64_t(j) * p.n + i) * p.d + kk] : 0.f;
+        p.XT[(int64_t(j) * p.d + kk) * p.nx + i] = v;
+        s += double(v);
+    }
+    s = warp_sum_f64(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
+        p.SX[j * p.d + kk] = t;
+        if (blockIdx.x == 0) {
+            *p.next_block = 0ull;
+            p.st->done = 0;
+            p.st->error = 0;
+            p.st->final_iter = 0;
+            p.st->timeout_site = 0;
+            p.st->stress = 0.0;
+        }
+    }
+}
+
+cudaError_t launch_oos_prep(const OOSPrepParams& p, cudaStream_t s) {
+    k_oos_prep<<<p.m * p.d, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// Fixed-order reduction of the per-object results: max iterations, total stress.
+__global__ void k_oos_summary(const int32_t* iters, const double* stress, int64_t k, int32_t* it_out,
+                              double* st_out) {
+    __shared__ double sh[32];
+    __shared__ int shi[32];
+    double s = 0.0;
+    int mx = 0;
+    for (int64_t o = threadIdx.x; o < k; o += blockDim.x) {
+        s += stress[o];
+        mx = max(mx, iters[o]);
+    }
+    s = warp_sum_f64(s);
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) { sh[threadIdx.x >> 5] = s; shi[threadIdx.x >> 5] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        int m2 = 0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) { t += sh[w]; m2 = max(m2, shi[w]); }
+        *st_out = t;
+        *it_out = m2;
+    }
+}
+
+cudaError_t launch_oos_summary(const int32_t* iters, const double* stress, int64_t k, int32_t* it_out,
+                               double* st_out, cudaStream_t s) {
+    k_oos_summary<<<1, 1024, 0, s>>>(iters, stress, k, it_out, st_out);
+    return cudaGetLastError();
+}
+
+}  // namespace fjofc

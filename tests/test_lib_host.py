@@ -1,0 +1,123 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The shared library must load on a machine without a GPU, export every function that
+``include/fjofc.h`` declares, and reject invalid arguments before it touches CUDA
+(argument validation precedes any runtime call, so dummy device pointers are safe).
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fjofc.h")
+
+
+def _lib():
+    from conftest import ensure_library
+    return ensure_library()
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fjofc_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_expected_api():
+    assert _declared_functions() == sorted(["fjofc_embed", "fjofc_stress", "fjofc_oos", "fjofc_strerror",
+                                            "fjofc_version"])
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    fj = _lib()
+    raw = ctypes.CDLL(fj.LIB_PATH)
+    for name in _declared_functions():
+        assert hasattr(raw, name), name
+    assert set(fj.EXPORTS) == set(_declared_functions())
+    assert "sm_103a" in fj.version()
+    assert fj.strerror(0) == "ok"
+
+
+# ------------------------------------------------------------------ argument validation
+
+class _Call:
+    """Calls fjofc_embed with dummy (never dereferenced) device pointers."""
+
+    def __init__(self, fj):
+        self.fj = fj
+        self.lib = ctypes.CDLL(fj.LIB_PATH)
+        self.lib.fjofc_embed.restype = ctypes.c_int
+
+    def embed(self, m=2, n=8, d=2, ld=8, dtype=0, W=None, ptr=4096, X=8192, max_iter=5, tol_mode=1,
+              scales=None):
+        fj = self.fj
+        W = np.array([[1.0, 0.5], [0.5, 1.0]]) if W is None else np.asarray(W, dtype=np.float64)
+        ptrs = (ctypes.c_void_p * max(m, 1))(*([ptr] * max(m, 1)))
+        opts = fj._Opts(max_iter, -1.0, tol_mode)
+        sc = None if scales is None else (ctypes.c_float * m)(*scales)
+        return self.lib.fjofc_embed(ctypes.c_int32(m), ctypes.c_int64(n), ctypes.c_int32(d), ptrs,
+                                    ctypes.c_int64(ld), ctypes.c_int32(dtype), sc,
+                                    W.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(X),
+                                    ctypes.byref(opts), None, None)
+
+
+@pytest.fixture(scope="module")
+def call():
+    return _Call(_lib())
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(m=0), -1),
+    (dict(m=9, W=np.eye(9)), -6),
+    (dict(n=1, ld=4), -1),
+    (dict(d=0), -1),
+    (dict(d=17), -6),
+    (dict(n=5, ld=6), -1),                  # 24-byte rows are not 16-byte aligned
+    (dict(ld=4), -1),                       # ld < n
+    (dict(ptr=4100), -1),                   # misaligned Delta base
+    (dict(X=0), -1),
+    (dict(max_iter=-1), -1),
+    (dict(tol_mode=7), -1),
+    (dict(dtype=5), -1),
+    (dict(W=[[1.0, 0.5], [0.4, 1.0]]), -1),  # asymmetric
+    (dict(W=[[0.0, 0.5], [0.5, 1.0]]), -1),  # w_ii must be > 0
+    (dict(W=[[1.0, -0.5], [-0.5, 1.0]]), -1),  # w_ij must be >= 0
+    (dict(W=[[np.nan, 0.5], [0.5, 1.0]]), -1),
+    (dict(scales=[1.0, 0.0]), -1),
+    (dict(dtype=1, n=8, ld=12), -1),        # f16 rows of 24 bytes
+])
+def test_invalid_arguments_rejected_before_cuda(call, kw, code):
+    assert call.embed(**kw) == code
+    assert call.fj.strerror(code)
+
+
+def test_error_messages_name_the_problem(call):
+    assert call.embed(n=5, ld=6) == -1
+    assert "16 bytes" in call.fj.strerror(-1)
+    assert call.embed(W=[[1.0, 0.5], [0.4, 1.0]]) == -1
+    assert "symmetric" in call.fj.strerror(-1)
+
+
+def test_oos_argument_validation(call):
+    fj = call.fj
+    lib = call.lib
+    lib.fjofc_oos.restype = ctypes.c_int
+    W = np.array([[1.0, 0.5], [0.5, 1.0]])
+    opts = fj._Opts(3, -1.0, 1)
+
+    def oos(m=2, n=8, d=2, k=4, ld=8, dptr=4096, X=8192, Y=12288, W=W):
+        return lib.fjofc_oos(ctypes.c_int32(m), ctypes.c_int64(n), ctypes.c_int32(d), ctypes.c_int64(k),
+                             ctypes.c_void_p(X), ctypes.c_void_p(dptr), ctypes.c_int64(ld), ctypes.c_int32(0), None,
+                             np.asarray(W, dtype=np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             ctypes.c_void_p(Y), None, None, ctypes.byref(opts), None, None)
+
+    assert oos(k=-1) == -1
+    assert oos(n=5, ld=6) == -1
+    assert oos(dptr=4104) == -1
+    assert oos(Y=0) == -1
+    assert oos(d=17) == -6
+    assert oos(W=[[1.0, 0.5], [0.3, 1.0]]) == -1
+    assert oos(k=0) == 0          # nothing to embed: success without touching the GPU
