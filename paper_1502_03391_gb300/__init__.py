@@ -18,7 +18,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libfjofc.so")
+# FJOFC_LIBRARY selects another build of the same library (e.g. a tuning variant).
+LIB_PATH = os.environ.get("FJOFC_LIBRARY") or os.path.join(_HERE, "_lib", "libfjofc.so")
 
 FJOFC_OK = 0
 FJOFC_ERR_ARG = -1

@@ -240,7 +240,7 @@ EmbedPlan make_plan(int m, int64_t n, int d, int dtype) {
     int64_t G = int64_t(bps) * sm_count();
     if (G > P.T) G = P.T;
     P.G = int(G);
-    P.nbx = int((n + 255) / 256);
+    P.nbx = fjofc::k2_blocks(int(n));
     return P;
 }
 
@@ -302,7 +302,7 @@ int run_insample(int32_t m, int64_t n, int32_t d, const void* const* delta, int6
     const size_t o_fid = cv.take<double>(P.G);
     const size_t o_woff = cv.take<int64_t>(P.nRB + 1);
     const size_t o_mu = cv.take<double>(2 * FJOFC_MAX_M * FJOFC_MAX_D);
-    const size_t o_bpart = cv.take<double>(size_t(d) * P.nbx * (m + 1));
+    const size_t o_bpart = cv.take<double>(size_t(P.nbx) * (size_t(m) * d + 1));
     const size_t o_ticket = cv.take<unsigned>(1);
     const size_t o_st = cv.take<DevStatus>(1);
     const size_t o_hist = cv.take<double>(size_t(o.max_iter) + 2);

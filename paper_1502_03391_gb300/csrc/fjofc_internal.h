@@ -65,11 +65,11 @@ struct K2Params {
     const double* fid;
     const int64_t* walk_off;
     double* mu;                // [2][FJOFC_MAX_M][FJOFC_MAX_D] modality column means, by t parity
-    double* bpart;             // [d][nbx][m+1] per-block partial sums
+    double* bpart;             // [nbx][m*d+1] per-block partial sums (column sums, commensurability)
     unsigned* ticket;
     DevStatus* st;
     double* hist;              // sigma(X_0..X_max_iter)
-    int m, n, d, RB, CW, nRB, G, nbx;
+    int m, n, d, RB, CW, nRB, G, nbx;   // nbx = number of K2 CTAs (k2_blocks(n))
     int64_t Tm, T;
     int t;                     // pass index: reads X_{t-1}, writes X_t
     int final_pass;            // 1: only sigma(X_{t-1}) and the centring
@@ -80,6 +80,7 @@ struct K2Params {
 };
 
 cudaError_t launch_k2(const K2Params& p, cudaStream_t s);
+int k2_blocks(int n);
 
 struct InitParams {
     DevStatus* st;

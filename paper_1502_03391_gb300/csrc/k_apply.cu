@@ -18,6 +18,8 @@
 namespace fjofc {
 
 constexpr int K2_THREADS = 256;
+constexpr int K2_OBJ = 32;                 // objects per CTA (one per lane)
+constexpr int K2_WOFF_SMEM_MAX = 4096;     // walk offsets staged in shared memory up to this many
 
 __device__ __forceinline__ double block_sum_f64(double v, double* sh) {
     // sh: >= K2_THREADS/32 doubles; returns the total in thread 0
@@ -33,87 +35,111 @@ __device__ __forceinline__ double block_sum_f64(double v, double* sh) {
     return t;
 }
 
+// One CTA per 32 consecutive objects.  Phase 1: warp w sums the partials of (modality l,
+// coordinate k) pairs w, w+8, ... for its 32 objects (lane = object), with independent
+// loads.  Phase 2: warp w handles coordinate k = w, w+8, ...: centre X_{t-1}, its
+// commensurability, the Wmod^-1 mix into X_t and the per-block column sums.
 __global__ void __launch_bounds__(K2_THREADS)
 k_apply(const K2Params p) {
-    __shared__ double s_part[FJOFC_MAX_M + 1][K2_THREADS / 32];
+    extern __shared__ int64_t s_woff[];
+    __shared__ float s_bx[FJOFC_MAX_M * FJOFC_MAX_D][K2_OBJ];
     __shared__ double s_tmp[K2_THREADS / 32];
+    __shared__ double s_part[FJOFC_MAX_M * FJOFC_MAX_D + 1];
     __shared__ bool s_last;
 
     if (ld_volatile(&p.st->done)) return;
 
-    const int k = blockIdx.y;
-    const int i = blockIdx.x * K2_THREADS + threadIdx.x;
     const int m = p.m, n = p.n, d = p.d;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i = blockIdx.x * K2_OBJ + lane;
+    const bool woff_smem = (p.nRB + 1) <= K2_WOFF_SMEM_MAX;
+    const int64_t* woff = woff_smem ? s_woff : p.walk_off;
+    if (woff_smem)
+        for (int e = tid; e <= p.nRB; e += K2_THREADS) s_woff[e] = p.walk_off[e];
+    __syncthreads();
+
     const double* mu_prev = p.mu + ((p.t - 1) & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
     double* mu_next = p.mu + (p.t & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
 
-    double colsum[FJOFC_MAX_M];
-    double comm = 0.0;
-#pragma unroll
-    for (int j = 0; j < FJOFC_MAX_M; ++j) colsum[j] = 0.0;
-
-    if (i < n) {
-        // centre X_{t-1} (in place) and its commensurability term
-        double xc[FJOFC_MAX_M];
-        for (int j = 0; j < m; ++j) {
-            const int64_t off = (int64_t(j) * n + i) * d + k;
-            xc[j] = double(p.Xprev[off]) - mu_prev[j * FJOFC_MAX_D + k];
-            if (p.t > 1) p.Xprev[off] = float(xc[j]);   // X_0 (mu_0 = 0) is left untouched
-        }
-        for (int j = 0; j < m; ++j)
-            for (int l = j + 1; l < m; ++l) {
-                const double df = xc[j] - xc[l];
-                comm += p.wcomm[j][l] * df * df;
-            }
-
-        if (!p.final_pass) {
-            const int RB = p.RB, CW = p.CW;
-            const int I = i / RB, ri = i - I * RB;
-            double bx[FJOFC_MAX_M];
-            for (int l = 0; l < m; ++l) {
-                float acc = p.rowhead[((int64_t(l) * p.nRB + I) * d + k) * RB + ri];
+    if (!p.final_pass) {
+        const int RB = p.RB, CW = p.CW;
+        for (int lk = warp; lk < m * d; lk += K2_THREADS / 32) {
+            const int l = lk / d, k = lk - l * d;
+            float acc = 0.f;
+            if (i < n) {
+                const int I = i / RB, ri = i - I * RB;
+                acc = p.rowhead[((int64_t(l) * p.nRB + I) * d + k) * RB + ri];
                 // continuation segments: CTAs whose range starts strictly inside this walk
-                const int64_t ws = int64_t(l) * p.Tm + p.walk_off[I];
-                const int64_t we = int64_t(l) * p.Tm + p.walk_off[I + 1];
-                int64_t bcta = ((ws + 1) * p.G + p.T - 1) / p.T;   // first b with b*T/G > ws
-                for (; bcta < p.G; ++bcta) {
-                    const int64_t pb = bcta * p.T / p.G;
+                const int64_t ws = int64_t(l) * p.Tm + woff[I];
+                const int64_t we = int64_t(l) * p.Tm + woff[I + 1];
+                for (int64_t b = ((ws + 1) * p.G + p.T - 1) / p.T; b < p.G; ++b) {
+                    const int64_t pb = b * p.T / p.G;
                     if (pb >= we) break;
-                    if (pb > ws) acc += p.rowcont[(bcta * d + k) * RB + ri];
+                    if (pb > ws) acc += p.rowcont[(b * d + k) * RB + ri];
                 }
-                // column partials from the walks of row blocks 0..I
-                const int64_t tl = int64_t(l) * p.Tm;
-                float cacc = 0.f;
-                for (int J = 0; J <= I; ++J) {
+                // column partials of the walks of row blocks 0..I (independent loads)
+                const float* cp = p.colpart + int64_t(l) * p.Tm * d * CW;
+                float c4[4] = {0.f, 0.f, 0.f, 0.f};
+                int J = 0;
+                for (; J + 4 <= I + 1; J += 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int rel = i - (J + u) * RB;
+                        const int s = rel / CW, c = rel - s * CW;
+                        c4[u] += cp[((woff[J + u] + s) * d + k) * CW + c];
+                    }
+                }
+                for (; J <= I; ++J) {
                     const int rel = i - J * RB;
                     const int s = rel / CW, c = rel - s * CW;
-                    const int64_t t = tl + p.walk_off[J] + s;
-                    cacc += p.colpart[(t * d + k) * CW + c];
+                    c4[0] += cp[((woff[J] + s) * d + k) * CW + c];
                 }
-                bx[l] = double(acc) + double(cacc);
+                acc += (c4[0] + c4[1]) + (c4[2] + c4[3]);
             }
+            s_bx[lk][lane] = acc;
+        }
+    }
+    __syncthreads();
+
+    double comm = 0.0;
+    for (int k = warp; k < d; k += K2_THREADS / 32) {
+        double xc[FJOFC_MAX_M];
+        if (i < n) {
+            // centre X_{t-1} (in place) and its commensurability term
             for (int j = 0; j < m; ++j) {
-                double v = 0.0;
-                for (int l = 0; l < m; ++l) v += p.coef[j][l] * bx[l];
-                const float vf = float(v);
-                p.Xnext[(int64_t(j) * n + i) * d + k] = vf;
-                colsum[j] = double(vf);
+                const int64_t off = (int64_t(j) * n + i) * d + k;
+                xc[j] = double(p.Xprev[off]) - mu_prev[j * FJOFC_MAX_D + k];
+                if (p.t > 1) p.Xprev[off] = float(xc[j]);   // X_0 (mu_0 = 0) is left untouched
+            }
+            for (int j = 0; j < m; ++j)
+                for (int l = j + 1; l < m; ++l) {
+                    const double df = xc[j] - xc[l];
+                    comm += p.wcomm[j][l] * df * df;
+                }
+        }
+        if (!p.final_pass) {
+            for (int j = 0; j < m; ++j) {
+                double cs = 0.0;
+                if (i < n) {
+                    double v = 0.0;
+                    for (int l = 0; l < m; ++l) v += p.coef[j][l] * double(s_bx[l * d + k][lane]);
+                    const float vf = float(v);
+                    p.Xnext[(int64_t(j) * n + i) * d + k] = vf;
+                    cs = double(vf);
+                }
+                cs = warp_sum_f64(cs);
+                if (lane == 0) s_part[j * d + k] = cs;
             }
         }
     }
-
-    // per-block partial sums: column sums of X_t per modality, and commensurability
-    for (int j = 0; j <= m; ++j) {
-        const double v = (j < m) ? colsum[j] : comm;
-        const double tot = block_sum_f64(v, s_tmp);
-        if (threadIdx.x == 0) s_part[j][0] = tot;
-    }
-    const int blk = k * p.nbx + blockIdx.x;
-    if (threadIdx.x == 0) {
-        for (int j = 0; j <= m; ++j) p.bpart[int64_t(blk) * (m + 1) + j] = s_part[j][0];
+    const double ctot = block_sum_f64(comm, s_tmp);
+    const int npart = m * d + 1;
+    if (tid == 0) {
+        for (int e = 0; e < m * d; ++e) p.bpart[int64_t(blockIdx.x) * npart + e] = p.final_pass ? 0.0 : s_part[e];
+        p.bpart[int64_t(blockIdx.x) * npart + m * d] = ctot;
         __threadfence();
         const unsigned prev = atomicAdd(p.ticket, 1u);
-        s_last = (prev == gridDim.x * gridDim.y - 1);
+        s_last = (prev == gridDim.x - 1);
     }
     __syncthreads();
     if (!s_last) return;
@@ -121,23 +147,22 @@ k_apply(const K2Params p) {
 
     // ---- last CTA: totals in a fixed order
     const volatile double* bp = p.bpart;
-    const int nblk = gridDim.x * gridDim.y;
-    // column means of X_t: one thread per (modality, coordinate)
-    for (int e = threadIdx.x; e < m * d; e += blockDim.x) {
+    const int nblk = gridDim.x;
+    for (int e = tid; e < m * d; e += K2_THREADS) {
         const int j = e / d, kk = e - j * d;
         double s = 0.0;
-        for (int bx = 0; bx < p.nbx; ++bx) s += bp[int64_t(kk * p.nbx + bx) * (m + 1) + j];
-        mu_next[j * FJOFC_MAX_D + kk] = p.final_pass ? 0.0 : s / double(n);
+        for (int b = 0; b < nblk; ++b) s += bp[int64_t(b) * npart + e];
+        mu_next[j * FJOFC_MAX_D + kk] = s / double(n);
     }
     double c = 0.0;
-    for (int e = threadIdx.x; e < nblk; e += blockDim.x) c += bp[int64_t(e) * (m + 1) + m];
+    for (int e = tid; e < nblk; e += K2_THREADS) c += bp[int64_t(e) * npart + m * d];
     const double comm_tot = block_sum_f64(c, s_tmp);
     double f = 0.0;
     const volatile double* fidp = p.fid;
-    for (int e = threadIdx.x; e < p.G; e += blockDim.x) f += fidp[e];
+    for (int e = tid; e < p.G; e += K2_THREADS) f += fidp[e];
     const double fid_tot = block_sum_f64(f, s_tmp);
 
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         const double sigma = fid_tot + comm_tot;
         const int tp = p.t - 1;                 // index of the iterate whose stress this is
         p.hist[tp] = sigma;
@@ -163,9 +188,11 @@ k_apply(const K2Params p) {
     }
 }
 
+int k2_blocks(int n) { return (n + K2_OBJ - 1) / K2_OBJ; }
+
 cudaError_t launch_k2(const K2Params& p, cudaStream_t s) {
-    dim3 grid(p.nbx, p.d);
-    k_apply<<<grid, K2_THREADS, 0, s>>>(p);
+    const size_t smem = (p.nRB + 1) <= K2_WOFF_SMEM_MAX ? size_t(p.nRB + 1) * sizeof(int64_t) : 0;
+    k_apply<<<p.nbx, K2_THREADS, smem, s>>>(p);
     return cudaGetLastError();
 }
 

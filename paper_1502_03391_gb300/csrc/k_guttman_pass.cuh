@@ -5,21 +5,24 @@
 //     d_ij = ||x_i - x_j||,  b_ij = Delta_ij / d_ij  (0 when d_ij = 0, Eq. B),
 // and adds   b_ij (x_i - x_j)  to row i and  b_ij (x_j - x_i)  to row j of B'_l X_l
 // (B'_l = B_l / w_ll; since B_l's diagonal is minus its off-diagonal row sum,
-// (B_l X_l)_i = sum_j b_ij (x_i - x_j) w_ll), plus w_ll (s_l Delta_ij - d_ij)^2 to the
+// (B_l X_l)_i = w_ll sum_j b_ij (x_i - x_j)), plus w_ll (s_l Delta_ij - d_ij)^2 to the
 // fidelity.  Reading the symmetric Delta once per unordered pair is the half of
 // Remark faststress's 1/2 ||Delta_i - d(X^(i))||_F^2.
 //
 // Work layout (GB300): a persistent grid of G CTAs, CTA b owning the contiguous range
-// [b*T/G, (b+1)*T/G) of RB x CW sub-tiles in walk order.  Each sub-tile is staged
-// HBM -> shared memory by one TMA (cp.async.bulk.tensor) into a STAGES-deep ring
-// completed on mbarriers; thread 0 refills a stage right after the CTA-wide barrier
-// that ends its use.  Warp w owns R consecutive rows of the row block (x_i and the
-// row accumulators live in registers for the whole walk segment); lane owns C
-// consecutive columns of every sub-tile.  Column accumulators are reduced across
-// warps through shared memory once per sub-tile and written as one partial per
-// (sub-tile, column); row accumulators are reduced across the warp once per walk
-// segment.  K2 sums all partials in a fixed order, so results are bitwise
-// reproducible run to run.
+// [b*T/G, (b+1)*T/G) of RB x CW sub-tiles in walk order (row block I visits column
+// sub-tiles from its diagonal to n).  Each sub-tile is staged HBM -> shared memory by
+// one 2-D TMA (cp.async.bulk.tensor) into a STAGES-deep ring completed on mbarriers;
+// the last warp to finish reading a stage (shared-memory counter) issues its refill.
+// Warp w owns R consecutive rows of the row block (x_i and the row accumulators stay in
+// registers for the whole walk segment); lane owns C consecutive columns of every
+// sub-tile.  Column accumulators go through a small ring of shared-memory slots; each
+// warp reduces its share of the previous sub-tile's columns in a fixed order and writes
+// one partial per (sub-tile, column).  Row accumulators are reduced across the warp at
+// walk-segment ends.  Warps never meet at a CTA-wide barrier inside the loop; they
+// synchronise only through mbarriers and the stage counters, with one sub-tile of
+// slack.  K2 sums every partial in a fixed order, so results are bitwise reproducible
+// run to run.  Every wait is bounded.
 #pragma once
 
 #include <float.h>
@@ -29,38 +32,57 @@
 namespace fjofc {
 
 template <int D> struct K1Cfg;
-// rows/thread, cols/lane, warps, pipeline stages (stage bytes at float32 in comments)
-#define FJOFC_K1CFG(DMIN, DMAX, R_, C_, W_, S_)                                  \
-    template <> struct K1Cfg<DMIN> { static constexpr int R = R_, C = C_, WARPS = W_, STAGES = S_; };
-FJOFC_K1CFG(1, 1, 16, 2, 8, 5)    // 128 x 64, 32 KB
-FJOFC_K1CFG(2, 2, 16, 2, 8, 5)
-FJOFC_K1CFG(3, 3, 16, 2, 8, 5)
-FJOFC_K1CFG(4, 4, 16, 2, 8, 5)
-FJOFC_K1CFG(5, 5, 8, 2, 8, 6)     // 64 x 64, 16 KB
-FJOFC_K1CFG(6, 6, 8, 2, 8, 6)
-FJOFC_K1CFG(7, 7, 8, 2, 8, 6)
-FJOFC_K1CFG(8, 8, 8, 2, 8, 6)
-FJOFC_K1CFG(9, 9, 4, 2, 8, 8)     // 32 x 64, 8 KB
-FJOFC_K1CFG(10, 10, 4, 2, 8, 8)
-FJOFC_K1CFG(11, 11, 4, 2, 8, 8)
-FJOFC_K1CFG(12, 12, 4, 2, 8, 8)
-FJOFC_K1CFG(13, 13, 4, 2, 8, 8)
-FJOFC_K1CFG(14, 14, 4, 2, 8, 8)
-FJOFC_K1CFG(15, 15, 4, 2, 8, 8)
-FJOFC_K1CFG(16, 16, 4, 2, 8, 8)
+// rows/thread, cols/lane, compute warps, pipeline stages (float32)
+#define FJOFC_K1CFG(D_, R_, C_, W_, S_)                                                     \
+    template <> struct K1Cfg<D_> { static constexpr int R = R_, C = C_, CWARPS = W_, STAGES = S_; };
+// The d <= 4 tile can be overridden at build time (tuning sweeps).
+#ifndef FJOFC_K1_SMALLD_R
+#define FJOFC_K1_SMALLD_R 16
+#endif
+#ifndef FJOFC_K1_SMALLD_C
+#define FJOFC_K1_SMALLD_C 4
+#endif
+#ifndef FJOFC_K1_SMALLD_WARPS
+#define FJOFC_K1_SMALLD_WARPS 8
+#endif
+#ifndef FJOFC_K1_SMALLD_STAGES
+#define FJOFC_K1_SMALLD_STAGES 3
+#endif
+#define FJOFC_SMALLD FJOFC_K1_SMALLD_R, FJOFC_K1_SMALLD_C, FJOFC_K1_SMALLD_WARPS, FJOFC_K1_SMALLD_STAGES
+#define FJOFC_K1CFG_X(...) FJOFC_K1CFG(__VA_ARGS__)
+FJOFC_K1CFG_X(1, FJOFC_SMALLD)    // default: 128 x 128 sub-tile, 64 KB at float32
+FJOFC_K1CFG_X(2, FJOFC_SMALLD)
+FJOFC_K1CFG_X(3, FJOFC_SMALLD)
+FJOFC_K1CFG_X(4, FJOFC_SMALLD)
+FJOFC_K1CFG(5, 8, 4, 8, 3)        // 64 x 128, 32 KB
+FJOFC_K1CFG(6, 8, 4, 8, 3)
+FJOFC_K1CFG(7, 8, 2, 8, 5)        // 64 x 64, 16 KB
+FJOFC_K1CFG(8, 8, 2, 8, 5)
+FJOFC_K1CFG(9, 4, 2, 8, 6)        // 32 x 64, 8 KB
+FJOFC_K1CFG(10, 4, 2, 8, 6)
+FJOFC_K1CFG(11, 4, 2, 8, 6)
+FJOFC_K1CFG(12, 4, 2, 8, 6)
+FJOFC_K1CFG(13, 4, 2, 8, 6)
+FJOFC_K1CFG(14, 2, 2, 8, 8)       // 16 x 64, 4 KB
+FJOFC_K1CFG(15, 2, 2, 8, 8)
+FJOFC_K1CFG(16, 2, 2, 8, 8)
+#undef FJOFC_K1CFG_X
 #undef FJOFC_K1CFG
 
 template <int D, typename TD>
 struct K1Shape {
-    static constexpr int R = K1Cfg<D>::R, C = K1Cfg<D>::C, WARPS = K1Cfg<D>::WARPS,
-                         STAGES = K1Cfg<D>::STAGES;
-    static constexpr int NT = WARPS * 32;
-    static constexpr int RB = WARPS * R;
+    static constexpr int R = K1Cfg<D>::R, C = K1Cfg<D>::C, CWARPS = K1Cfg<D>::CWARPS;
+    // 16-bit Delta halves the stage: keep about the same bytes in flight
+    static constexpr int STAGES = sizeof(TD) == 4 ? K1Cfg<D>::STAGES : 2 * K1Cfg<D>::STAGES;
+    static constexpr int SLOTS = 2;                    // column-partial ring
+    static constexpr int NT = CWARPS * 32;
+    static constexpr int RB = CWARPS * R;
     static constexpr int CW = 32 * C;
     static constexpr int STAGE_ELEMS = RB * CW;
     static constexpr uint32_t STAGE_BYTES = STAGE_ELEMS * sizeof(TD);
-    static constexpr size_t RED_BYTES = size_t(2) * WARPS * D * CW * sizeof(float);
-    static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + RED_BYTES + STAGES * 8 + 128;
+    static constexpr size_t RED_FLOATS = size_t(SLOTS) * CWARPS * D * CW;
+    static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + RED_FLOATS * sizeof(float) +
+                                   size_t(STAGES + 2 * SLOTS) * 8 + size_t(STAGES) * 4 + 128;
 };
 
 // Position of a sub-tile: modality l, row block I, walk position s (walk length L).
@@ -92,21 +114,36 @@ __device__ __forceinline__ void cursor_next(Cursor& c, const K1Params& p) {
     }
 }
 
+// Kahan-compensated float32 accumulator (fidelity of one modality within a CTA).
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
 template <int D, typename TD>
 __global__ void __launch_bounds__(K1Shape<D, TD>::NT, 1)
 k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
     using S = K1Shape<D, TD>;
-    constexpr int R = S::R, C = S::C, WARPS = S::WARPS, STAGES = S::STAGES, NT = S::NT;
+    constexpr int R = S::R, C = S::C, CWARPS = S::CWARPS, STAGES = S::STAGES, SLOTS = S::SLOTS;
     constexpr int RB = S::RB, CW = S::CW;
 
     extern __shared__ unsigned char smem_raw[];
-    // 128-byte aligned base for the TMA destinations
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     TD* stages = reinterpret_cast<TD*>(smem);
-    float* red = reinterpret_cast<float*>(smem + size_t(STAGES) * S::STAGE_BYTES);
-    uint64_t* full = reinterpret_cast<uint64_t*>(red + 2 * WARPS * D * CW);
-    __shared__ double s_red64[WARPS];
+    float* red = reinterpret_cast<float*>(smem + size_t(STAGES) * S::STAGE_BYTES);   // [SLOTS][CWARPS][D][CW]
+    uint64_t* full = reinterpret_cast<uint64_t*>(red + S::RED_FLOATS);
+    uint64_t* rfull = full + STAGES;
+    uint64_t* rempty = rfull + SLOTS;
+    int* released = reinterpret_cast<int*>(rempty + SLOTS);       // [STAGES] releases so far (monotone)
+    __shared__ double s_red64[CWARPS];
+    __shared__ int s_abort;
+    __shared__ int s_issued;                                       // sub-tiles issued so far
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b = blockIdx.x;
@@ -115,195 +152,263 @@ k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
 
     const int64_t t_begin = int64_t(b) * p.T / p.G;
     const int64_t t_end = int64_t(b + 1) * p.T / p.G;
-    const int64_t nq = t_end - t_begin;      // >= 1 because G <= T
+    const int nq = static_cast<int>(t_end - t_begin);   // >= 1 because G <= T
 
-    Cursor pc;   // producer cursor (thread 0 only)
+    auto issue = [&](int q, const Cursor& c) {
+        const int stage = q % STAGES;
+        atomicMax(&s_issued, q + 1);
+        const uint32_t bar = smem_u32(&full[stage]);
+        mbar_arrive_expect_tx(bar, S::STAGE_BYTES);
+        tma_load_2d(smem_u32(stages + size_t(stage) * S::STAGE_ELEMS), &tm.map[c.l], c.I * RB + c.s * CW,
+                    c.I * RB, bar);
+    };
+
+    Cursor pc;   // cursor of the sub-tile STAGES ahead (every warp keeps its own copy)
+    cursor_init(pc, t_begin, p);
     if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(smem_u32(&full[s]), 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            released[s] = 0;
+        }
+        for (int s = 0; s < SLOTS; ++s) {
+            mbar_init(smem_u32(&rfull[s]), CWARPS);
+            mbar_init(smem_u32(&rempty[s]), CWARPS);
+        }
+        s_abort = 0;
+        s_issued = 0;
         fence_barrier_init();
         for (int l = 0; l < p.m; ++l) tma_prefetch_desc(&tm.map[l]);
+        Cursor c0 = pc;
+        for (int q = 0; q < STAGES && q < nq; ++q) {
+            issue(q, c0);
+            cursor_next(c0, p);
+        }
     }
+    for (int q = 0; q < STAGES && q < nq; ++q) cursor_next(pc, p);
     __syncthreads();
-    if (tid == 0) {
-        cursor_init(pc, t_begin, p);
-        for (int64_t q = 0; q < STAGES && q < nq; ++q) {
-            const uint32_t bar = smem_u32(&full[q]);
-            mbar_arrive_expect_tx(bar, S::STAGE_BYTES);
-            tma_load_2d(smem_u32(stages + q * S::STAGE_ELEMS), &tm.map[pc.l],
-                        pc.I * RB + pc.s * CW, pc.I * RB, bar);
-            cursor_next(pc, p);
-        }
-    }
+    const volatile int* abort_flag = &s_abort;
+    double fid_total = 0.0;
 
-    Cursor cc;
-    cursor_init(cc, t_begin, p);
-    bool seg_head = (cc.s == 0);
-
-    const int n = p.n;
-    float xi[R][D], racc[R][D];
-    auto load_rows = [&](const Cursor& c) {
-        const float* Xl = p.X + int64_t(c.l) * n * D;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int i = c.I * RB + warp * R + r;
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                xi[r][k] = (i < n) ? __ldg(Xl + int64_t(i) * D + k) : 0.f;
-                racc[r][k] = 0.f;
-            }
-        }
-    };
-    load_rows(cc);
-
-    double sfid = 0.0;
-    bool failed = false;
-
-    for (int64_t q = 0; q < nq; ++q) {
-        const int stage = static_cast<int>(q % STAGES);
-        const uint32_t parity = static_cast<uint32_t>((q / STAGES) & 1);
-        const int r0 = cc.I * RB;
-        const int c0 = r0 + cc.s * CW;
-        const float* Xl = p.X + int64_t(cc.l) * n * D;
-
-        float xj[C][D], cacc[C][D];
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const int j = c0 + lane * C + c;
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                xj[c][k] = (j < n) ? __ldg(Xl + int64_t(j) * D + k) : 0.f;
-                cacc[c][k] = 0.f;
-            }
-        }
-        const float sc = p.dscale[cc.l];
-
-        failed |= !mbar_wait_bounded(smem_u32(&full[stage]), parity);
-
-        const TD* tile = stages + size_t(stage) * S::STAGE_ELEMS;
-        const bool masked = (cc.s * CW < RB) || (c0 + CW > n);
-        float sf = 0.f;
-        if (!masked) {
+    {
+        // ------------------------------------------------------------ compute
+        const int n = p.n;
+        Cursor cc, cn;
+        cursor_init(cc, t_begin, p);
+        cn = cc;
+        bool seg_head = (cc.s == 0);
+        float xi[R][D], racc[R][D];
+        auto load_rows = [&](const Cursor& c) {
+            const float* Xl = p.X + int64_t(c.l) * n * D;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                float dl[C];
-                load_delta_row<TD, C>(tile + (warp * R + r) * CW + lane * C, dl);
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    float diff[D];
-                    float d2 = 0.f;
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        diff[k] = xi[r][k] - xj[c][k];
-                        d2 = fmaf(diff[k], diff[k], d2);
-                    }
-                    const float rinv = rsqrt_approx(fmaxf(d2, FLT_MIN));
-                    const float bb = dl[c] * rinv;
-                    const float e = fmaf(sc, dl[c], -(d2 * rinv));
-                    sf = fmaf(e, e, sf);
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        racc[r][k] = fmaf(bb, diff[k], racc[r][k]);
-                        cacc[c][k] = fmaf(-bb, diff[k], cacc[c][k]);
-                    }
-                }
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int i = r0 + warp * R + r;
-                float dl[C];
-                load_delta_row<TD, C>(tile + (warp * R + r) * CW + lane * C, dl);
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    const int j = c0 + lane * C + c;
-                    const bool valid = (j > i) && (j < n);
-                    float diff[D];
-                    float d2 = 0.f;
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        diff[k] = xi[r][k] - xj[c][k];
-                        d2 = fmaf(diff[k], diff[k], d2);
-                    }
-                    const float rinv = rsqrt_approx(fmaxf(d2, FLT_MIN));
-                    const float bb = valid ? dl[c] * rinv : 0.f;
-                    const float e = valid ? fmaf(sc, dl[c], -(d2 * rinv)) : 0.f;
-                    sf = fmaf(e, e, sf);
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        racc[r][k] = fmaf(bb, diff[k], racc[r][k]);
-                        cacc[c][k] = fmaf(-bb, diff[k], cacc[c][k]);
-                    }
-                }
-            }
-        }
-        sfid += double(p.wfid[cc.l]) * double(sf);
-
-        float* rbuf = red + (q & 1) * (WARPS * D * CW);
-#pragma unroll
-        for (int k = 0; k < D; ++k)
-#pragma unroll
-            for (int c = 0; c < C; ++c) rbuf[(warp * D + k) * CW + lane * C + c] = cacc[c][k];
-
-        if (__syncthreads_or(failed)) {
-            // A stage never arrived within the wait limit: record it, wait (bounded)
-            // for the copies this CTA still has in flight, and leave.
-            if (tid == 0) {
-                raise_error(p.st, FJOFC_ERR_TIMEOUT, 1);
-                for (int64_t qq = q; qq < q + STAGES && qq < nq; ++qq)
-                    (void)mbar_wait_bounded(smem_u32(&full[qq % STAGES]), uint32_t((qq / STAGES) & 1));
-            }
-            return;
-        }
-
-        // refill the stage everyone has just finished reading
-        if (tid == 0 && q + STAGES < nq) {
-            const uint32_t bar = smem_u32(&full[stage]);
-            mbar_arrive_expect_tx(bar, S::STAGE_BYTES);
-            tma_load_2d(smem_u32(stages + size_t(stage) * S::STAGE_ELEMS), &tm.map[pc.l],
-                        pc.I * RB + pc.s * CW, pc.I * RB, bar);
-            cursor_next(pc, p);
-        }
-
-        // column partials of this sub-tile: fixed-order sum over the warps
-        float* cp = p.colpart + cc.t * int64_t(D * CW);
-        for (int e = tid; e < D * CW; e += NT) {
-            const int k = e / CW, c = e - k * CW;
-            float v = 0.f;
-#pragma unroll
-            for (int w = 0; w < WARPS; ++w) v += rbuf[(w * D + k) * CW + c];
-            cp[e] = v;
-        }
-
-        const bool walk_ends = (cc.s + 1 == cc.L);
-        const bool last = (q + 1 == nq);
-        if (walk_ends || last) {
-            // row partials of this walk segment: full-warp sum of each accumulator
-            float* dst = seg_head
-                ? p.rowhead + (int64_t(cc.l) * p.nRB + cc.I) * (D * RB)
-                : p.rowcont + int64_t(b) * (D * RB);
-#pragma unroll
-            for (int r = 0; r < R; ++r)
+                const int i = c.I * RB + warp * R + r;
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
-                    const float v = warp_sum_f32(racc[r][k]);
-                    if (lane == ((r * D + k) & 31)) dst[k * RB + warp * R + r] = v;
+                    xi[r][k] = (i < n) ? __ldg(Xl + int64_t(i) * D + k) : 0.f;
+                    racc[r][k] = 0.f;
                 }
+            }
+        };
+        float xjn[C][D];
+        auto load_cols = [&](const Cursor& c) {
+            const float* Xl = p.X + int64_t(c.l) * n * D;
+            const int c0 = c.I * RB + c.s * CW + lane * C;
+#pragma unroll
+            for (int cidx = 0; cidx < C; ++cidx)
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+                    xjn[cidx][k] = (c0 + cidx < n) ? __ldg(Xl + int64_t(c0 + cidx) * D + k) : 0.f;
+        };
+        load_rows(cc);
+        load_cols(cn);
+        Kahan fid;
+        int cur_l = cc.l;
+
+        // reduce this warp's share of the columns of sub-tile qq (deferred by one)
+        auto reduce_share = [&](int qq) -> bool {
+            const int slot = qq % SLOTS;
+            if (!mbar_wait_or_abort(smem_u32(&rfull[slot]), uint32_t((qq / SLOTS) & 1), abort_flag)) return false;
+            const float* rb = red + size_t(slot) * CWARPS * D * CW;
+            float* cp = p.colpart + (t_begin + qq) * int64_t(D * CW);
+            constexpr int SHARE = (D * CW + CWARPS - 1) / CWARPS;
+            for (int e = warp * SHARE + lane; e < (warp + 1) * SHARE && e < D * CW; e += 32) {
+                float v = 0.f;
+#pragma unroll
+                for (int w = 0; w < CWARPS; ++w) v += rb[w * D * CW + e];
+                cp[e] = v;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&rempty[slot]));
+            return true;
+        };
+
+        bool ok = true;
+        for (int q = 0; q < nq && ok; ++q) {
+            const int stage = q % STAGES;
+            const int slot = q % SLOTS;
+            const int r0 = cc.I * RB;
+            const int c0 = r0 + cc.s * CW;
+            float xj[C][D];
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int k = 0; k < D; ++k) xj[c][k] = xjn[c][k];
+            if (q + 1 < nq) {           // prefetch the next sub-tile's columns
+                cursor_next(cn, p);
+                load_cols(cn);
+            }
+            if (cc.l != cur_l) {        // modality changed inside this CTA's range
+                fid_total += double(p.wfid[cur_l]) * double(fid.s);
+                fid = Kahan();
+                cur_l = cc.l;
+            }
+            const float sc = p.dscale[cc.l];
+
+            if (!mbar_wait_or_abort(smem_u32(&full[stage]), uint32_t((q / STAGES) & 1), abort_flag)) {
+                ok = false;
+                break;
+            }
+            const TD* tile = stages + size_t(stage) * S::STAGE_ELEMS;
+            const bool masked = (cc.s * CW < RB) || (c0 + CW > n);
+            float cacc0[C][D], cacc1[C][D];
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int k = 0; k < D; ++k) { cacc0[c][k] = 0.f; cacc1[c][k] = 0.f; }
+            float sf0 = 0.f, sf1 = 0.f;
+            if (!masked) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float dl[C];
+                    load_delta_row<TD, C>(tile + (warp * R + r) * CW + lane * C, dl);
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        float diff[D];
+                        float d2 = 0.f;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            diff[k] = xi[r][k] - xj[c][k];
+                            d2 = fmaf(diff[k], diff[k], d2);
+                        }
+                        const float rinv = rsqrt_approx(fmaxf(d2, FLT_MIN));
+                        const float bb = dl[c] * rinv;
+                        const float e = fmaf(sc, dl[c], -(d2 * rinv));
+                        if (r & 1) sf1 = fmaf(e, e, sf1); else sf0 = fmaf(e, e, sf0);
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            racc[r][k] = fmaf(bb, diff[k], racc[r][k]);
+                            if (r & 1) cacc1[c][k] = fmaf(-bb, diff[k], cacc1[c][k]);
+                            else cacc0[c][k] = fmaf(-bb, diff[k], cacc0[c][k]);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = r0 + warp * R + r;
+                    float dl[C];
+                    load_delta_row<TD, C>(tile + (warp * R + r) * CW + lane * C, dl);
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        const int j = c0 + lane * C + c;
+                        const bool valid = (j > i) && (j < n);
+                        float diff[D];
+                        float d2 = 0.f;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            diff[k] = xi[r][k] - xj[c][k];
+                            d2 = fmaf(diff[k], diff[k], d2);
+                        }
+                        const float rinv = rsqrt_approx(fmaxf(d2, FLT_MIN));
+                        const float bb = valid ? dl[c] * rinv : 0.f;
+                        const float e = valid ? fmaf(sc, dl[c], -(d2 * rinv)) : 0.f;
+                        if (r & 1) sf1 = fmaf(e, e, sf1); else sf0 = fmaf(e, e, sf0);
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            racc[r][k] = fmaf(bb, diff[k], racc[r][k]);
+                            if (r & 1) cacc1[c][k] = fmaf(-bb, diff[k], cacc1[c][k]);
+                            else cacc0[c][k] = fmaf(-bb, diff[k], cacc0[c][k]);
+                        }
+                    }
+                }
+            }
+            // release the stage; the last warp to do so refills it with sub-tile q + STAGES
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                // use k = q / STAGES of this stage is fully released at count (k+1)*CWARPS
+                if (atomicAdd(&released[stage], 1) == (q / STAGES + 1) * CWARPS - 1) {
+                    __threadfence_block();
+                    if (q + STAGES < nq) issue(q + STAGES, pc);
+                }
+            }
+            if (q + STAGES < nq) cursor_next(pc, p);
+            fid.add(sf0 + sf1);
+
+            // column partials of this sub-tile into its ring slot
+            if (q >= SLOTS &&
+                !mbar_wait_or_abort(smem_u32(&rempty[slot]), uint32_t(((q / SLOTS) - 1) & 1), abort_flag)) {
+                ok = false;
+                break;
+            }
+            float* rb = red + (size_t(slot) * CWARPS + warp) * D * CW;
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+#pragma unroll
+                for (int c = 0; c < C; ++c) rb[k * CW + lane * C + c] = cacc0[c][k] + cacc1[c][k];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&rfull[slot]));
+
+            if (q >= 1 && !reduce_share(q - 1)) {
+                ok = false;
+                break;
+            }
+
+            const bool walk_ends = (cc.s + 1 == cc.L);
+            const bool last = (q + 1 == nq);
+            if (walk_ends || last) {
+                // row partials of this walk segment: full-warp sum of each accumulator
+                float* dst = seg_head
+                    ? p.rowhead + (int64_t(cc.l) * p.nRB + cc.I) * (D * RB)
+                    : p.rowcont + int64_t(b) * (D * RB);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const float v = warp_sum_f32(racc[r][k]);
+                        if (lane == ((r * D + k) & 31)) dst[k * RB + warp * R + r] = v;
+                    }
+            }
+            cursor_next(cc, p);
+            if (walk_ends && !last) {
+                seg_head = true;
+                load_rows(cc);
+            }
         }
-        cursor_next(cc, p);
-        if (walk_ends && !last) {
-            seg_head = true;
-            load_rows(cc);
+        if (ok) ok = reduce_share(nq - 1);
+        if (!ok) {
+            atomicExch(&s_abort, 1);
+            if (lane == 0) raise_error(p.st, FJOFC_ERR_TIMEOUT, 2);
         }
+        fid_total += double(p.wfid[cur_l]) * double(fid.s);
+    }
+    __syncthreads();
+    if (*abort_flag && tid == 0) {
+        // wait (bounded) for the copies this CTA may still have in flight: the most
+        // recent use of every stage
+        const int hi = s_issued;
+        for (int qq = (hi > STAGES ? hi - STAGES : 0); qq < hi; ++qq)
+            (void)mbar_wait_bounded(smem_u32(&full[qq % STAGES]), uint32_t((qq / STAGES) & 1));
     }
 
     // fidelity partial of this CTA (fixed-order float64 reduction)
-    const double ws = warp_sum_f64(sfid);
+    const double ws = warp_sum_f64(fid_total);
     if (lane == 0) s_red64[warp] = ws;
     __syncthreads();
     if (tid == 0) {
         double tot = 0.0;
 #pragma unroll
-        for (int w = 0; w < WARPS; ++w) tot += s_red64[w];
+        for (int w = 0; w < CWARPS; ++w) tot += s_red64[w];
         p.fid[b] = tot;
     }
 }
@@ -311,12 +416,14 @@ k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
 template <int D, typename TD>
 cudaError_t k1_launch_impl(int grid, const TMaps& tm, const K1Params& p, cudaStream_t s) {
     using S = K1Shape<D, TD>;
-    static bool configured = false;   // attribute set once per process and device family
-    if (!configured) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static bool configured[64] = {};
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
         cudaError_t e = cudaFuncSetAttribute(k_guttman_pass<D, TD>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::SMEM));
         if (e != cudaSuccess) return e;
-        configured = true;
+        if (dev >= 0 && dev < 64) configured[dev] = true;
     }
     k_guttman_pass<D, TD><<<grid, S::NT, S::SMEM, s>>>(tm, p);
     return cudaGetLastError();
@@ -335,7 +442,7 @@ int k1_bps_impl() {
 template <int D, typename TD>
 K1Geom k1_geom_impl() {
     using S = K1Shape<D, TD>;
-    return K1Geom{S::R, S::C, S::WARPS, S::STAGES, S::RB, S::CW, S::NT, S::SMEM};
+    return K1Geom{S::R, S::C, S::CWARPS, S::STAGES, S::RB, S::CW, S::NT, S::SMEM};
 }
 
 #define FJOFC_INSTANTIATE_K1(D)                                                                   \
