@@ -161,6 +161,41 @@ int fjofc_oos(int32_t m, int64_t n, int32_t d, int64_t k,
               float* Y, int32_t* iters_out, double* stress_out,
               const fjofc_opts* opts, fjofc_result* res, void* cuda_stream);
 
+/*
+ * fjofc_embed_noalloc -- fjofc_embed without any allocation at call time.
+ *
+ * Some callers cannot allocate device memory while they run: code that runs inside a
+ * host callback or a driver-managed context where cudaMalloc/cudaMallocAsync is not
+ * allowed, real-time loops that must not enter an allocator (CUDA's or a framework's
+ * caching allocator) after start-up, and processes whose device memory was carved up
+ * once at launch by another component.  This entry point takes exactly the arguments of
+ * fjofc_embed and works in the caller's buffers plus one fixed device array of
+ * FJOFC_NOALLOC_SCRATCH_BYTES inside the library (the paper has no counterpart: this is
+ * a deployment variant of the same computation).  It calls no cudaMalloc, cudaFree,
+ * stream-ordered allocator, event creation or host heap allocation.
+ *
+ *  - The array is part of the library's device code: every GPU on which that code is
+ *    loaded holds it until the process exits.
+ *  - The first call on a device looks up the array's device address on that device
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ *    capture on the device.
+ *  - Calls share the array: two calls that overlap on the GPU (different streams, or
+ *    different host threads on the same device) race and corrupt each other's results.
+ *    Serialise them.  Each call clears what must start at zero.
+ *  - A problem whose scratch does not fit (roughly 12 m n^2 d / RB bytes of partials
+ *    plus 8 m n d bytes of iterates; n up to about 11000 at m = 2, d = 3) is rejected
+ *    with FJOFC_ERR_UNSUPPORTED and a message naming the bytes it would need.
+ *  - opts->profile must be 0; res->ms_total and the profiling fields are returned as 0;
+ *    res->stress_history, when given, receives max_iter + 1 entries (those past iters
+ *    are 0).
+ * Otherwise the results are those of fjofc_embed on the same inputs.
+ */
+#define FJOFC_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int fjofc_embed_noalloc(int32_t m, int64_t n, int32_t d,
+                        const void* const* delta, int64_t ld, int32_t delta_dtype,
+                        const float* delta_scale, const double* weights,
+                        float* X, const fjofc_opts* opts, fjofc_result* res, void* cuda_stream);
+
 /* Message for a status code (static string). */
 const char* fjofc_strerror(int status);
 

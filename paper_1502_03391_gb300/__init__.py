@@ -34,7 +34,7 @@ TOL_ABS_NORMALIZED, TOL_RELATIVE = 0, 1
 MAX_M, MAX_D = 8, 16
 
 # Every symbol declared in include/fjofc.h.
-EXPORTS = ("fjofc_embed", "fjofc_stress", "fjofc_oos", "fjofc_strerror", "fjofc_version")
+EXPORTS = ("fjofc_embed", "fjofc_embed_noalloc", "fjofc_stress", "fjofc_oos", "fjofc_strerror", "fjofc_version")
 
 
 class FjofcError(RuntimeError):

@@ -261,10 +261,15 @@ int validate_insample(int32_t m, int64_t n, int32_t d, const void* const* delta,
     return check_delta_layout(delta, m, n, ld, dtype);
 }
 
-// The in-sample loop.  mode 0: embed; mode 1: stress of X only.
-int run_insample(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t dtype,
-                 const float* delta_scale, const double* weights, float* X, const fjofc_opts* opts,
-                 fjofc_result* res, cudaStream_t stream, bool stress_only, double* stress_out) {
+}  // namespace
+
+namespace {
+// The in-sample loop.  stress_only: sigma(X) of X only.  ext: run in a caller-supplied
+// scratch region with no allocation of any kind (no events, no host buffers).
+int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t dtype,
+                      const float* delta_scale, const double* weights, float* X, const fjofc_opts* opts,
+                      fjofc_result* res, cudaStream_t stream, bool stress_only, double* stress_out,
+                      const fjofc::ExtScratch* ext) {
     int rc = validate_insample(m, n, d, delta, ld, dtype, delta_scale, X);
     if (rc) return rc;
     fjofc_opts o{};
@@ -282,6 +287,7 @@ int run_insample(int32_t m, int64_t n, int32_t d, const void* const* delta, int6
         o.tol = -1.0;
         o.tol_mode = FJOFC_TOL_RELATIVE;
     }
+    if (ext && o.profile) return arg_error("profile timing is not available without allocation");
     double winv[FJOFC_MAX_M * FJOFC_MAX_M];
     rc = weights_inverse(m, n, weights, winv);
     if (rc) return rc;
@@ -310,12 +316,23 @@ int run_insample(int32_t m, int64_t n, int32_t d, const void* const* delta, int6
 
     ScopedDeviceMem mem;
     mem.s = stream;
-    if (cudaMallocAsync(&mem.p, total, stream) != cudaSuccess) {
-        cudaGetLastError();
-        snprintf(g_last_msg, sizeof(g_last_msg), "cudaMallocAsync(%zu bytes) failed", total);
-        return FJOFC_ERR_NOMEM;
+    char* base = nullptr;
+    if (ext) {
+        if (total > ext->capacity) {
+            snprintf(g_last_msg, sizeof(g_last_msg),
+                     "problem needs %zu bytes of scratch; the fixed scratch array holds %zu bytes", total,
+                     ext->capacity);
+            return FJOFC_ERR_UNSUPPORTED;
+        }
+        base = static_cast<char*>(ext->base);
+    } else {
+        if (cudaMallocAsync(&mem.p, total, stream) != cudaSuccess) {
+            cudaGetLastError();
+            snprintf(g_last_msg, sizeof(g_last_msg), "cudaMallocAsync(%zu bytes) failed", total);
+            return FJOFC_ERR_NOMEM;
+        }
+        base = static_cast<char*>(mem.p);
     }
-    char* base = static_cast<char*>(mem.p);
     float* buf1 = reinterpret_cast<float*>(base + o_buf1);
     float* buf2 = reinterpret_cast<float*>(base + o_buf2);
     DevStatus* st = reinterpret_cast<DevStatus*>(base + o_st);
@@ -364,9 +381,11 @@ int run_insample(int32_t m, int64_t n, int32_t d, const void* const* delta, int6
         }
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    FJ_CUDA(cudaEventCreate(&ev0));
-    FJ_CUDA(cudaEventCreate(&ev1));
-    FJ_CUDA(cudaEventRecord(ev0, stream));
+    if (!ext) {
+        FJ_CUDA(cudaEventCreate(&ev0));
+        FJ_CUDA(cudaEventCreate(&ev1));
+        FJ_CUDA(cudaEventRecord(ev0, stream));
+    }
 
     InitParams ip{st, k2.ticket, k2.mu, const_cast<int64_t*>(k1.walk_off), int(n), RB, CW, P.nRB};
     FJ_CUDA(launch_init(ip, stream));
@@ -401,9 +420,36 @@ int run_insample(int32_t m, int64_t n, int32_t d, const void* const* delta, int6
         launches += 2;
     }
     FJ_CUDA(launch_finalize(X, buf1, buf2, mnd, st, stream));
-    FJ_CUDA(cudaEventRecord(ev1, stream));
+    if (!ext) FJ_CUDA(cudaEventRecord(ev1, stream));
 
     DevStatus hst;
+    if (ext) {
+        // no host buffers: the history goes straight into the caller's array
+        FJ_CUDA(cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, stream));
+        if (res && res->stress_history)
+            FJ_CUDA(cudaMemcpyAsync(res->stress_history, hist, (size_t(o.max_iter) + 1) * sizeof(double),
+                                    cudaMemcpyDeviceToHost, stream));
+        FJ_CUDA(cudaStreamSynchronize(stream));
+        rc = hst.error;
+        if (rc == FJOFC_ERR_TIMEOUT) snprintf(g_last_msg, sizeof(g_last_msg), "device wait timed out (site %d)", hst.timeout_site);
+        if (rc == FJOFC_ERR_NONFINITE) snprintf(g_last_msg, sizeof(g_last_msg), "stress became non-finite");
+        if (res) {
+            res->status = rc;
+            res->iters = hst.final_iter;
+            res->stress = hst.stress;
+            res->stress_normalized = hst.stress / k2.npairs;
+            res->ms_total = 0.f;
+            res->passes = 0;
+            res->ms_pass = 0.f;
+            res->ms_apply = 0.f;
+            res->launches = launches;
+            if (res->stress_history) {
+                const int upto = (hst.error == FJOFC_ERR_NONFINITE) ? hst.final_iter + 1 : hst.final_iter;
+                for (int t = upto + 1; t <= o.max_iter; ++t) res->stress_history[t] = 0.0;
+            }
+        }
+        return rc;
+    }
     std::vector<double> hh(size_t(o.max_iter) + 1);
     FJ_CUDA(cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, stream));
     FJ_CUDA(cudaMemcpyAsync(hh.data(), hist, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -585,6 +631,17 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
 }  // namespace
 
 namespace fjofc {
+int run_insample(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t dtype,
+                 const float* delta_scale, const double* weights, float* X, const fjofc_opts* opts,
+                 fjofc_result* res, cudaStream_t stream, bool stress_only, double* stress_out,
+                 const ExtScratch* ext) {
+    return run_insample_impl(m, n, d, delta, ld, dtype, delta_scale, weights, X, opts, res, stream, stress_only,
+                             stress_out, ext);
+}
+const char* set_message(const char* msg) {
+    snprintf(g_last_msg, sizeof(g_last_msg), "%s", msg);
+    return g_last_msg;
+}
 K1Geom k1_geometry(int d, int dtype) {
     if (d < 1 || d > FJOFC_MAX_D) return K1Geom{};
     return dtype == FJOFC_F32 ? k1_geom_dt<float>(d) : dtype == FJOFC_F16 ? k1_geom_dt<__half>(d) : k1_geom_dt<__nv_bfloat16>(d);
@@ -600,8 +657,8 @@ extern "C" {
 int fjofc_embed(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t delta_dtype,
                 const float* delta_scale, const double* weights, float* X, const fjofc_opts* opts,
                 fjofc_result* res, void* cuda_stream) {
-    const int rc = run_insample(m, n, d, delta, ld, delta_dtype, delta_scale, weights, X, opts, res,
-                                static_cast<cudaStream_t>(cuda_stream), false, nullptr);
+    const int rc = run_insample_impl(m, n, d, delta, ld, delta_dtype, delta_scale, weights, X, opts, res,
+                                     static_cast<cudaStream_t>(cuda_stream), false, nullptr, nullptr);
     if (res) res->status = rc;
     return rc;
 }
@@ -612,8 +669,8 @@ int fjofc_stress(int32_t m, int64_t n, int32_t d, const void* const* delta, int6
     if (!stress_out) return arg_error("stress_out is NULL");
     // max_iter = 0: one pass over X; the kernels centre X in place only when a Guttman
     // output is returned, and X_0 is returned as given (mu_0 = 0), so X is not modified.
-    return run_insample(m, n, d, delta, ld, delta_dtype, delta_scale, weights, const_cast<float*>(X), nullptr,
-                        nullptr, static_cast<cudaStream_t>(cuda_stream), true, stress_out);
+    return run_insample_impl(m, n, d, delta, ld, delta_dtype, delta_scale, weights, const_cast<float*>(X), nullptr,
+                             nullptr, static_cast<cudaStream_t>(cuda_stream), true, stress_out, nullptr);
 }
 
 int fjofc_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const void* delta_new, int64_t ld,

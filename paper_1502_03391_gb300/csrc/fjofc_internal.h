@@ -119,6 +119,21 @@ struct K3Params {
     double wcomm[FJOFC_MAX_M][FJOFC_MAX_M];  // w_jl, j != l
 };
 
+// ---------------------------------------------------------------------------
+// In-sample driver (fjofc_api.cu).  ext != NULL runs it in a caller-supplied scratch
+// region without any allocation, event or host buffer (fjofc_embed_noalloc).
+// ---------------------------------------------------------------------------
+struct ExtScratch {
+    void* base;
+    size_t capacity;
+};
+int run_insample(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t dtype,
+                 const float* delta_scale, const double* weights, float* X, const fjofc_opts* opts,
+                 fjofc_result* res, cudaStream_t stream, bool stress_only, double* stress_out,
+                 const ExtScratch* ext);
+// Stores msg as the text fjofc_strerror returns for the next error; returns it.
+const char* set_message(const char* msg);
+
 struct OOSPrepParams {
     const float* X;
     float* XT;

@@ -27,8 +27,8 @@ def _declared_functions():
 
 
 def test_header_declares_expected_api():
-    assert _declared_functions() == sorted(["fjofc_embed", "fjofc_stress", "fjofc_oos", "fjofc_strerror",
-                                            "fjofc_version"])
+    assert _declared_functions() == sorted(["fjofc_embed", "fjofc_embed_noalloc", "fjofc_stress", "fjofc_oos",
+                                            "fjofc_strerror", "fjofc_version"])
 
 
 def test_library_loads_and_exports_every_declared_symbol():
