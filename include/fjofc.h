@@ -69,8 +69,10 @@ typedef struct fjofc_opts {
     int32_t max_iter;     /* maximum number of Guttman transforms (>= 0) */
     double  tol;          /* tolerance of the stopping rule; < 0 = run max_iter transforms */
     int32_t tol_mode;     /* FJOFC_TOL_* */
-    int32_t profile;      /* 1: time every all-pairs pass and every W^-1 pass with CUDA events
-                             recorded on cuda_stream (result fields ms_pass, ms_apply) */
+    int32_t profile;      /* 0: no timing.  The loop runs as one persistent cooperative kernel.
+                             1: one launch per all-pairs pass (K1) and per W^-1 pass (K2),
+                                each timed with CUDA events on cuda_stream (ms_pass, ms_apply).
+                             2: the persistent kernel, its launch timed (ms_pass). */
     int32_t reserved[4];  /* must be zero */
 } fjofc_opts;
 
@@ -82,10 +84,11 @@ typedef struct fjofc_result {
     double* stress_history;     /* host, caller-owned, length >= max_iter + 1, or NULL:
                                    receives sigma(X_0) .. sigma(X_T) */
     float   ms_total;           /* device time of the call, milliseconds (CUDA events) */
-    /* filled when opts->profile == 1 (else 0): */
+    /* filled when opts->profile != 0 (else 0): */
     int32_t passes;             /* all-pairs passes that did work (= iters + 1) */
-    float   ms_pass;            /* summed device time of those all-pairs passes (K1) */
-    float   ms_apply;           /* summed device time of the matching W^-1/stress passes (K2) */
+    float   ms_pass;            /* profile 1: summed device time of those all-pairs passes (K1);
+                                   profile 2: device time of the persistent loop kernel */
+    float   ms_apply;           /* profile 1: summed device time of the matching W^-1 passes */
     int32_t launches;           /* kernels this call launched */
 } fjofc_result;
 

@@ -192,10 +192,12 @@ class EmbedResult:
 
 def embed(deltas: Sequence, weights, X, max_iter: int, tol: float = -1.0, tol_mode: str = "relative",
           delta_scale=None, stream=None, history: bool = True, check: bool = True,
-          profile: bool = False) -> EmbedResult:
+          profile: int = 0) -> EmbedResult:
     """In-sample fJOFC from ``X`` (in place).  ``deltas``: m CUDA n x n views (float32,
     float16 or bfloat16; row stride a multiple of 16 bytes); ``weights``: m x m;
-    ``X``: contiguous float32 CUDA tensor of shape (m*n, d).  See ``fjofc_embed``."""
+    ``X``: contiguous float32 CUDA tensor of shape (m*n, d).  ``profile``: 0 none, 1 one
+    launch per pass with per-kernel timing, 2 the persistent loop kernel timed.  See
+    ``fjofc_embed``."""
     m = len(deltas)
     n = int(deltas[0].shape[0])
     if X.dtype != _torch().float32 or not X.is_contiguous() or X.dim() != 2 or X.shape[0] != m * n:
@@ -205,7 +207,7 @@ def embed(deltas: Sequence, weights, X, max_iter: int, tol: float = -1.0, tol_mo
     ptrs = (ctypes.c_void_p * m)(*[D.data_ptr() for D in deltas])
     Wn = _weights(weights, m)
     opts = _Opts(int(max_iter), float(tol), TOL_RELATIVE if tol_mode == "relative" else TOL_ABS_NORMALIZED,
-                 1 if profile else 0)
+                 int(profile))
     hist = np.zeros(int(max_iter) + 1, dtype=np.float64) if history else None
     res = _Result()
     if hist is not None:

@@ -169,6 +169,25 @@ K1Geom k1_geom_dt(int d) {
     return K1Geom{};
 }
 
+template <typename TD>
+cudaError_t persist_launch_dt(int d, int grid, const TMaps& tm, const PersistParams& P, cudaStream_t s) {
+    switch (d) {
+#define C_(D) case D: return persist_launch_impl<D, TD>(grid, tm, P, s);
+        C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13) C_(14) C_(15) C_(16)
+#undef C_
+    }
+    return cudaErrorInvalidValue;
+}
+template <typename TD>
+int persist_bps_dt(int d) {
+    switch (d) {
+#define C_(D) case D: return persist_bps_impl<D, TD>();
+        C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13) C_(14) C_(15) C_(16)
+#undef C_
+    }
+    return 0;
+}
+
 // ------------------------------------------------------------------ K3 dispatch
 template <typename TD>
 cudaError_t k3_launch_dt(int d, int grid, const CUtensorMap& tm, const K3Params& p, cudaStream_t s) {
@@ -228,7 +247,19 @@ struct EmbedPlan {
     int64_t Tm = 0, T = 0;
 };
 
-EmbedPlan make_plan(int m, int64_t n, int d, int dtype) {
+bool cooperative_ok() {
+    int dev = 0, coop = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) return false;
+    return coop != 0;
+}
+
+int persist_blocks_per_sm(int d, int dtype) {
+    return dtype == FJOFC_F32 ? persist_bps_dt<float>(d) : dtype == FJOFC_F16 ? persist_bps_dt<__half>(d)
+                                                                               : persist_bps_dt<__nv_bfloat16>(d);
+}
+
+EmbedPlan make_plan(int m, int64_t n, int d, int dtype, bool persistent) {
     EmbedPlan P;
     P.g = fjofc::k1_geometry(d, dtype);
     P.nRB = int((n + P.g.RB - 1) / P.g.RB);
@@ -236,7 +267,7 @@ EmbedPlan make_plan(int m, int64_t n, int d, int dtype) {
     for (int I = 0; I < P.nRB; ++I) Tm += (n - int64_t(I) * P.g.RB + P.g.CW - 1) / P.g.CW;
     P.Tm = Tm;
     P.T = Tm * m;
-    const int bps = std::max(1, fjofc::k1_blocks_per_sm(d, dtype));
+    const int bps = std::max(1, persistent ? persist_blocks_per_sm(d, dtype) : fjofc::k1_blocks_per_sm(d, dtype));
     int64_t G = int64_t(bps) * sm_count();
     if (G > P.T) G = P.T;
     P.G = int(G);
@@ -279,7 +310,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         if (o.max_iter < 0) return arg_error("max_iter must be >= 0");
         if (o.tol_mode != FJOFC_TOL_ABS_NORMALIZED && o.tol_mode != FJOFC_TOL_RELATIVE) return arg_error("unknown tol_mode");
         if (std::isnan(o.tol)) return arg_error("tol is NaN");
-        if (o.profile != 0 && o.profile != 1) return arg_error("profile must be 0 or 1");
+        if (o.profile < 0 || o.profile > 2) return arg_error("profile must be 0, 1 or 2");
         for (int r = 0; r < 4; ++r)
             if (o.reserved[r] != 0) return arg_error("opts.reserved must be zero");
     } else {
@@ -293,7 +324,10 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     if (rc) return rc;
     if ((rc = get_encoder())) return rc;
 
-    const EmbedPlan P = make_plan(m, n, d, dtype);
+    // One persistent cooperative launch runs the whole loop; profile == 1 (per-kernel
+    // timing) uses one launch per all-pairs pass and per W^-1 pass instead.
+    const bool persist = (o.profile != 1) && cooperative_ok() && persist_blocks_per_sm(d, dtype) >= 1;
+    const EmbedPlan P = make_plan(m, n, d, dtype, persist);
     if (P.g.RB == 0) { snprintf(g_last_msg, sizeof(g_last_msg), "no kernel for d=%d", d); return FJOFC_ERR_UNSUPPORTED; }
     const int RB = P.g.RB, CW = P.g.CW;
     const int64_t mnd = int64_t(m) * n * d;
@@ -305,13 +339,16 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     const size_t o_col = cv.take<float>(size_t(P.T) * d * CW);
     const size_t o_head = cv.take<float>(size_t(m) * P.nRB * d * RB);
     const size_t o_cont = cv.take<float>(size_t(P.G) * d * RB);
-    const size_t o_fid = cv.take<double>(P.G);
+    const size_t o_fid = cv.take<float2>(P.G);
     const size_t o_woff = cv.take<int64_t>(P.nRB + 1);
-    const size_t o_mu = cv.take<double>(2 * FJOFC_MAX_M * FJOFC_MAX_D);
-    const size_t o_bpart = cv.take<double>(size_t(P.nbx) * (size_t(m) * d + 1));
+    const size_t o_cta = cv.take<int64_t>(size_t(P.G) + 1);
+    const size_t o_mu = cv.take<float>(2 * FJOFC_MAX_M * FJOFC_MAX_D);
+    const size_t o_bpart = cv.take<float2>(size_t(P.nbx) * (size_t(m) * d + 1));
     const size_t o_ticket = cv.take<unsigned>(1);
     const size_t o_st = cv.take<DevStatus>(1);
     const size_t o_hist = cv.take<double>(size_t(o.max_iter) + 2);
+    const size_t o_fid2 = cv.take<float2>(2 * size_t(P.G));
+    const size_t o_bar = cv.take<unsigned>(1);
     const size_t total = cv.off;
 
     ScopedDeviceMem mem;
@@ -352,7 +389,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     k1.colpart = reinterpret_cast<float*>(base + o_col);
     k1.rowhead = reinterpret_cast<float*>(base + o_head);
     k1.rowcont = reinterpret_cast<float*>(base + o_cont);
-    k1.fid = reinterpret_cast<double*>(base + o_fid);
+    k1.fid = reinterpret_cast<float2*>(base + o_fid);
     k1.walk_off = reinterpret_cast<int64_t*>(base + o_woff);
     k1.st = st;
     k1.m = m; k1.n = int(n); k1.d = d; k1.nRB = P.nRB; k1.G = P.G;
@@ -365,19 +402,28 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     K2Params k2{};
     k2.colpart = k1.colpart; k2.rowhead = k1.rowhead; k2.rowcont = k1.rowcont; k2.fid = k1.fid;
     k2.walk_off = k1.walk_off;
-    k2.mu = reinterpret_cast<double*>(base + o_mu);
-    k2.bpart = reinterpret_cast<double*>(base + o_bpart);
+    k2.cta_start = reinterpret_cast<int64_t*>(base + o_cta);
+    k2.mu = reinterpret_cast<float*>(base + o_mu);
+    k2.bpart = reinterpret_cast<float2*>(base + o_bpart);
     k2.ticket = reinterpret_cast<unsigned*>(base + o_ticket);
     k2.st = st;
     k2.hist = hist;
     k2.m = m; k2.n = int(n); k2.d = d; k2.RB = RB; k2.CW = CW; k2.nRB = P.nRB; k2.G = P.G; k2.nbx = P.nbx;
+    k2.rb_shift = 0;
+    while ((1 << k2.rb_shift) < RB) ++k2.rb_shift;
+    k2.cw_shift = 0;
+    while ((1 << k2.cw_shift) < CW) ++k2.cw_shift;
+    if ((1 << k2.rb_shift) != RB || (1 << k2.cw_shift) != CW) {
+        snprintf(g_last_msg, sizeof(g_last_msg), "internal: tile sizes must be powers of two");
+        return FJOFC_ERR_UNSUPPORTED;
+    }
     k2.Tm = P.Tm; k2.T = P.T;
     k2.tol_mode = o.tol_mode; k2.tol = o.tol;
     k2.npairs = double(m * n) * double(m * n - 1) / 2.0;
     for (int j = 0; j < m; ++j)
         for (int l = 0; l < m; ++l) {
-            k2.coef[j][l] = winv[j * m + l] * weights[l * m + l] * double(k1.dscale[l]);
-            k2.wcomm[j][l] = (j < l) ? weights[j * m + l] : 0.0;
+            k2.coef[j][l] = float(winv[j * m + l] * weights[l * m + l] * double(k1.dscale[l]));
+            k2.wcomm[j][l] = (j < l) ? float(weights[j * m + l]) : 0.f;
         }
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -387,7 +433,9 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         FJ_CUDA(cudaEventRecord(ev0, stream));
     }
 
-    InitParams ip{st, k2.ticket, k2.mu, const_cast<int64_t*>(k1.walk_off), int(n), RB, CW, P.nRB};
+    unsigned* bar = reinterpret_cast<unsigned*>(base + o_bar);
+    InitParams ip{st, k2.ticket, k2.mu, const_cast<int64_t*>(k1.walk_off), const_cast<int64_t*>(k2.cta_start),
+                  bar, int(n), RB, CW, P.nRB, P.G, P.T};
     FJ_CUDA(launch_init(ip, stream));
 
     float* bufs[3] = {X, buf1, buf2};
@@ -397,13 +445,39 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         pev.resize(size_t(3) * (o.max_iter + 1));
         for (auto& e : pev) FJ_CUDA(cudaEventCreate(&e));
     }
-    int launches = 2;   // init + finalize
+    int launches = 2;   // init + finalize (or init + the persistent kernel)
+    cudaEvent_t pe0 = nullptr, pe1 = nullptr;
+    if (persist) {
+        PersistParams pp{};
+        pp.k1 = k1;
+        pp.buf[0] = X; pp.buf[1] = buf1; pp.buf[2] = buf2;
+        pp.cta_start = k2.cta_start;
+        pp.fid2 = reinterpret_cast<float2*>(base + o_fid2);
+        pp.bpart = k2.bpart;
+        pp.bar = bar;
+        pp.hist = hist;
+        pp.ngroups = P.nbx;
+        pp.rb_shift = k2.rb_shift; pp.cw_shift = k2.cw_shift;
+        pp.max_iter = o.max_iter; pp.tol_mode = o.tol_mode; pp.tol = o.tol; pp.npairs = k2.npairs;
+        for (int j = 0; j < FJOFC_MAX_M; ++j)
+            for (int l = 0; l < FJOFC_MAX_M; ++l) { pp.coef[j][l] = k2.coef[j][l]; pp.wcomm[j][l] = k2.wcomm[j][l]; }
+        if (o.profile == 2) {
+            FJ_CUDA(cudaEventCreate(&pe0));
+            FJ_CUDA(cudaEventCreate(&pe1));
+            FJ_CUDA(cudaEventRecord(pe0, stream));
+        }
+        const cudaError_t e = (dtype == FJOFC_F32) ? persist_launch_dt<float>(d, P.G, tm, pp, stream)
+                            : (dtype == FJOFC_F16) ? persist_launch_dt<__half>(d, P.G, tm, pp, stream)
+                                                   : persist_launch_dt<__nv_bfloat16>(d, P.G, tm, pp, stream);
+        FJ_CUDA(e);
+        if (o.profile == 2) FJ_CUDA(cudaEventRecord(pe1, stream));
+    }
     auto k1_launch = [&](cudaError_t& e) {
         e = (dtype == FJOFC_F32) ? k1_launch_dt<float>(d, P.G, tm, k1, stream)
           : (dtype == FJOFC_F16) ? k1_launch_dt<__half>(d, P.G, tm, k1, stream)
                                  : k1_launch_dt<__nv_bfloat16>(d, P.G, tm, k1, stream);
     };
-    for (int t = 1; t <= o.max_iter + 1; ++t) {
+    for (int t = 1; !persist && t <= o.max_iter + 1; ++t) {
         const bool final_pass = (t == o.max_iter + 1);
         k1.X = bufs[(t - 1) % 3];
         cudaError_t e;
@@ -419,7 +493,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         if (prof) FJ_CUDA(cudaEventRecord(pev[3 * (t - 1) + 2], stream));
         launches += 2;
     }
-    FJ_CUDA(launch_finalize(X, buf1, buf2, mnd, st, stream));
+    if (!persist) FJ_CUDA(launch_finalize(X, buf1, buf2, mnd, st, stream));
     if (!ext) FJ_CUDA(cudaEventRecord(ev1, stream));
 
     DevStatus hst;
@@ -461,6 +535,11 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     // passes that did work: the one that computed sigma(X_final) and all before it
     const int worked = std::min(o.max_iter + 1, hst.final_iter + 1 + (hst.error == FJOFC_ERR_NONFINITE ? 1 : 0));
     float ms_pass = 0.f, ms_apply = 0.f;
+    if (pe0) {
+        cudaEventElapsedTime(&ms_pass, pe0, pe1);
+        cudaEventDestroy(pe0);
+        cudaEventDestroy(pe1);
+    }
     if (prof) {
         for (int t = 0; t < worked; ++t) {
             float a = 0.f, b2 = 0.f;
@@ -482,7 +561,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         res->stress = hst.stress;
         res->stress_normalized = hst.stress / k2.npairs;
         res->ms_total = ms;
-        res->passes = prof ? worked : 0;
+        res->passes = (prof || o.profile == 2) ? worked : 0;
         res->ms_pass = ms_pass;
         res->ms_apply = ms_apply;
         res->launches = launches;
@@ -533,7 +612,7 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
 
     Carver cv;
     const size_t o_xt = cv.take<float>(size_t(m) * d * nx);
-    const size_t o_sx = cv.take<double>(size_t(m) * d);
+    const size_t o_sx = cv.take<float>(size_t(m) * d);
     const size_t o_ctr = cv.take<unsigned long long>(1);
     const size_t o_st = cv.take<DevStatus>(1);
     const size_t o_it = cv.take<int32_t>(size_t(k));
@@ -562,7 +641,7 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
     K3Params p{};
     p.X = X;
     p.XT = reinterpret_cast<float*>(base + o_xt);
-    p.SX = reinterpret_cast<double*>(base + o_sx);
+    p.SX = reinterpret_cast<float*>(base + o_sx);
     p.Y = Y;
     p.iters_out = iters_out ? iters_out : reinterpret_cast<int32_t*>(base + o_it);
     p.stress_out = stress_out ? stress_out : reinterpret_cast<double*>(base + o_sig);
@@ -577,7 +656,7 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
     }
     for (int j = 0; j < m; ++j)
         for (int l = 0; l < m; ++l) {
-            p.winv[j][l] = winv[j * m + l];
+            p.winv[j][l] = float(winv[j * m + l]);
             p.wcomm[j][l] = (j != l) ? weights[j * m + l] : 0.0;
         }
 
@@ -585,7 +664,7 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
     FJ_CUDA(cudaEventCreate(&ev0));
     FJ_CUDA(cudaEventCreate(&ev1));
     FJ_CUDA(cudaEventRecord(ev0, stream));
-    OOSPrepParams pp{X, const_cast<float*>(p.XT), const_cast<double*>(p.SX), m, int(n), nx, d, p.next_block, st};
+    OOSPrepParams pp{X, const_cast<float*>(p.XT), const_cast<float*>(p.SX), m, int(n), nx, d, p.next_block, st};
     FJ_CUDA(launch_oos_prep(pp, stream));
     const int bps = std::max(1, (dtype == FJOFC_F32) ? k3_bps_dt<float>(d) : (dtype == FJOFC_F16) ? k3_bps_dt<__half>(d)
                                                                                               : k3_bps_dt<__nv_bfloat16>(d));

@@ -34,6 +34,18 @@ __device__ __forceinline__ void raise_error(DevStatus* st, int code, int site) {
     atomicExch(&st->done, 1);
 }
 
+// ----------------------------------------------------------------- walk order
+// The all-pairs pass visits the row-block walks of a modality in alternating long/short
+// order (row blocks 0, nRB-1, 1, nRB-2, ...), so that any contiguous range of sub-tiles
+// holds the same mix of full and diagonal/ragged (masked) sub-tiles and walk changes.
+// walk_off[] is indexed by walk position.
+__host__ __device__ __forceinline__ int walk_row(int pos, int nRB) {
+    return (pos & 1) ? nRB - 1 - (pos >> 1) : (pos >> 1);
+}
+__host__ __device__ __forceinline__ int walk_pos(int I, int nRB) {
+    return (2 * I < nRB) ? 2 * I : 2 * (nRB - 1 - I) + 1;
+}
+
 // ----------------------------------------------------------------- timers / waits
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
@@ -176,6 +188,46 @@ __device__ __forceinline__ void load_delta_row(const TD* p, float (&out)[C]) {
             for (int c = 0; c < C; ++c) out[c] = DeltaLoad<TD>::to_f32(p[c]);
         }
     }
+}
+
+// ----------------------------------------------------------------- float-float sums
+// GB300 executes float64 at a small fraction of the float32 rate, so reductions that
+// need more than float32 accuracy carry an unevaluated float pair (hi + lo) combined with
+// error-free transformations (Knuth's TwoSum); float64 appears only in a few scalars.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bp = s - a;
+    const float e = (a - (s - bp)) + (b - bp);
+    return FF{s, e};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    FF s = ff_two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return ff_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ FF ff_add(FF a, float b) {
+    FF s = ff_two_sum(a.hi, b);
+    s.lo += a.lo;
+    return ff_two_sum(s.hi, s.lo);
+}
+// (a.hi + a.lo) * w as a float-float (TwoProd by fma).
+__device__ __forceinline__ FF ff_mul(FF a, float w) {
+    const float ph = a.hi * w;
+    const float pe = fmaf(a.hi, w, -ph) + a.lo * w;
+    return ff_two_sum(ph, pe);
+}
+// Full-warp float-float sum (xor butterfly: every lane gets the same total).
+__device__ __forceinline__ FF warp_sum_ff(FF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        FF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        // combine in a lane-independent order so every lane computes the same value
+        v = ((threadIdx.x & o) == 0) ? ff_add(v, w) : ff_add(w, v);
+    }
+    return v;
 }
 
 // Full-warp float64 sum (xor butterfly, every lane gets the total).

@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/fjofc.h"
+#include "fjofc.h"
 
 namespace fjofc {
 
@@ -41,8 +41,8 @@ struct K1Params {
     float* colpart;            // [T][d][CW]   column partials of B'X per sub-tile
     float* rowhead;            // [m][nRB][d][RB] row partials of the segment that starts a walk
     float* rowcont;            // [G][d][RB]   row partial of a CTA whose range starts mid-walk
-    double* fid;               // [G]          weighted fidelity partial per CTA
-    const int64_t* walk_off;   // [nRB+1]      prefix sums of the walk lengths
+    float2* fid;               // [G]          weighted fidelity partial per CTA (float-float)
+    const int64_t* walk_off;   // [nRB+1]      prefix sums of the walk lengths, by walk position
     DevStatus* st;
     int m, n, d, nRB, G;
     int64_t Tm, T;             // sub-tiles per modality, total
@@ -62,32 +62,53 @@ struct K2Params {
     const float* colpart;
     const float* rowhead;
     const float* rowcont;
-    const double* fid;
+    const float2* fid;         // float-float fidelity partials of the K1 CTAs
     const int64_t* walk_off;
-    double* mu;                // [2][FJOFC_MAX_M][FJOFC_MAX_D] modality column means, by t parity
-    double* bpart;             // [nbx][m*d+1] per-block partial sums (column sums, commensurability)
+    const int64_t* cta_start;  // [G+1] first sub-tile of every K1 CTA (b*T/G)
+    float* mu;                 // [2][FJOFC_MAX_M][FJOFC_MAX_D] modality column means, by t parity
+    float2* bpart;             // [nbx][m*d+1] per-block float-float sums (column sums, commensurability)
     unsigned* ticket;
     DevStatus* st;
     double* hist;              // sigma(X_0..X_max_iter)
-    int m, n, d, RB, CW, nRB, G, nbx;   // nbx = number of K2 CTAs (k2_blocks(n))
+    int m, n, d, RB, CW, rb_shift, cw_shift, nRB, G, nbx;   // nbx = number of K2 CTAs (k2_blocks(n))
     int64_t Tm, T;
     int t;                     // pass index: reads X_{t-1}, writes X_t
     int final_pass;            // 1: only sigma(X_{t-1}) and the centring
     int tol_mode;
     double tol, npairs;        // tolerance, C(mn,2)
-    double coef[FJOFC_MAX_M][FJOFC_MAX_M];   // [Wmod^-1]_{jl} * w_ll * s_l
-    double wcomm[FJOFC_MAX_M][FJOFC_MAX_M];  // w_jl for j < l, else 0
+    float coef[FJOFC_MAX_M][FJOFC_MAX_M];    // [Wmod^-1]_{jl} * w_ll * s_l
+    float wcomm[FJOFC_MAX_M][FJOFC_MAX_M];   // w_jl for j < l, else 0
 };
 
 cudaError_t launch_k2(const K2Params& p, cudaStream_t s);
 int k2_blocks(int n);
 
+// Parameters of the persistent in-sample loop kernel (k_embed_persistent.cuh).
+struct PersistParams {
+    K1Params k1;                // geometry, partial buffers, weights (k1.X unused)
+    float* buf[3];              // iterate t lives in buf[t % 3]; buf[0] is the caller's X
+    const int64_t* cta_start;   // [G+1]
+    float2* fid2;               // [2][G] fidelity partials by pass parity
+    float2* bpart;              // [ngroups][m*d+1]
+    unsigned* bar;              // grid barrier counter (zeroed before launch)
+    double* hist;               // sigma(X_0..X_max_iter)
+    int ngroups;                // ceil(n / 32)
+    int rb_shift, cw_shift;
+    int max_iter, tol_mode;
+    double tol, npairs;
+    float coef[FJOFC_MAX_M][FJOFC_MAX_M];
+    float wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
+};
+
 struct InitParams {
     DevStatus* st;
     unsigned* ticket;
-    double* mu;
+    float* mu;
     int64_t* walk_off;
-    int n, RB, CW, nRB;
+    int64_t* cta_start;
+    unsigned* bar;             // grid barrier counter of the persistent kernel (may be NULL)
+    int n, RB, CW, nRB, G;
+    int64_t T;
 };
 cudaError_t launch_init(const InitParams& p, cudaStream_t s);
 cudaError_t launch_finalize(float* Xout, const float* buf1, const float* buf2, int64_t count,
@@ -104,7 +125,7 @@ struct K3Geom {
 struct K3Params {
     const float* X;            // in-sample (m*n) x d
     const float* XT;           // in-sample transposed: [m][d][nx] (nx = n rounded up to 4)
-    const double* SX;          // [m][d] column sums of each X^(j)
+    const float* SX;           // [m][d] column sums of each X^(j)
     float* Y;                  // k x m x d
     int32_t* iters_out;        // may be NULL
     double* stress_out;        // never NULL (internal buffer when the caller passes NULL)
@@ -115,8 +136,8 @@ struct K3Params {
     double tol, npairs;
     float wfid[FJOFC_MAX_M];
     float dscale[FJOFC_MAX_M];
-    double winv[FJOFC_MAX_M][FJOFC_MAX_M];   // Wmod^-1
-    double wcomm[FJOFC_MAX_M][FJOFC_MAX_M];  // w_jl, j != l
+    float winv[FJOFC_MAX_M][FJOFC_MAX_M];    // Wmod^-1
+    double wcomm[FJOFC_MAX_M][FJOFC_MAX_M];  // w_jl, j != l (per-object stress, once per pass)
 };
 
 // ---------------------------------------------------------------------------
@@ -137,7 +158,7 @@ const char* set_message(const char* msg);
 struct OOSPrepParams {
     const float* X;
     float* XT;
-    double* SX;
+    float* SX;
     int m, n, nx, d;
     unsigned long long* next_block;
     DevStatus* st;

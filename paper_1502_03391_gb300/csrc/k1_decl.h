@@ -9,3 +9,8 @@ template <int D, typename TD> cudaError_t k1_launch_impl(int grid, const TMaps& 
 template <int D, typename TD> int k1_bps_impl();
 template <int D, typename TD> K1Geom k1_geom_impl();
 }  // namespace fjofc
+
+namespace fjofc {
+template <int D, typename TD> cudaError_t persist_launch_impl(int grid, const TMaps& tm, const PersistParams& P, cudaStream_t s);
+template <int D, typename TD> int persist_bps_impl();
+}  // namespace fjofc

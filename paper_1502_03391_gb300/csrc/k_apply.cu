@@ -19,32 +19,31 @@ namespace fjofc {
 
 constexpr int K2_THREADS = 256;
 constexpr int K2_OBJ = 32;                 // objects per CTA (one per lane)
-constexpr int K2_WOFF_SMEM_MAX = 4096;     // walk offsets staged in shared memory up to this many
+constexpr int K2_TAB_SMEM_MAX = 4096;      // walk/CTA tables staged in shared memory up to this many
 
-__device__ __forceinline__ double block_sum_f64(double v, double* sh) {
-    // sh: >= K2_THREADS/32 doubles; returns the total in thread 0
+// Fixed-order float-float sum over the CTA; every thread receives the total.
+__device__ __forceinline__ FF block_sum_ff(FF v, FF* sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum_f64(v);
+    v = warp_sum_ff(v);
     __syncthreads();
     if (lane == 0) sh[warp] = v;
     __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0) {
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    }
+    FF t{0.f, 0.f};
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t = ff_add(t, sh[w]);
     return t;
 }
 
 // One CTA per 32 consecutive objects.  Phase 1: warp w sums the partials of (modality l,
-// coordinate k) pairs w, w+8, ... for its 32 objects (lane = object), with independent
-// loads.  Phase 2: warp w handles coordinate k = w, w+8, ...: centre X_{t-1}, its
-// commensurability, the Wmod^-1 mix into X_t and the per-block column sums.
+// coordinate k) pairs w, w+8, ... for its 32 objects (lane = object), 16 independent loads
+// in flight.  Phase 2: warp w handles coordinate k = w, w+8, ...: centre X_{t-1}, its
+// commensurability, the Wmod^-1 mix into X_t and the per-block column sums.  Arithmetic
+// is float32; cross-object sums are float-float (GB300's float64 rate is low).
 __global__ void __launch_bounds__(K2_THREADS)
 k_apply(const K2Params p) {
-    extern __shared__ int64_t s_woff[];
+    extern __shared__ int64_t s_tab[];          // walk_off [nRB+1] then cta_start [G+1]
     __shared__ float s_bx[FJOFC_MAX_M * FJOFC_MAX_D][K2_OBJ];
-    __shared__ double s_tmp[K2_THREADS / 32];
-    __shared__ double s_part[FJOFC_MAX_M * FJOFC_MAX_D + 1];
+    __shared__ FF s_ff[K2_THREADS / 32];
+    __shared__ FF s_part[FJOFC_MAX_M * FJOFC_MAX_D];
     __shared__ bool s_last;
 
     if (ld_volatile(&p.st->done)) return;
@@ -52,91 +51,100 @@ k_apply(const K2Params p) {
     const int m = p.m, n = p.n, d = p.d;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int i = blockIdx.x * K2_OBJ + lane;
-    const bool woff_smem = (p.nRB + 1) <= K2_WOFF_SMEM_MAX;
-    const int64_t* woff = woff_smem ? s_woff : p.walk_off;
-    if (woff_smem)
-        for (int e = tid; e <= p.nRB; e += K2_THREADS) s_woff[e] = p.walk_off[e];
+    const bool tab_smem = (p.nRB + 1 + p.G + 1) <= K2_TAB_SMEM_MAX;
+    const int64_t* woff = tab_smem ? s_tab : p.walk_off;
+    const int64_t* cstart = tab_smem ? s_tab + (p.nRB + 1) : p.cta_start;
+    if (tab_smem) {
+        for (int e = tid; e <= p.nRB; e += K2_THREADS) s_tab[e] = p.walk_off[e];
+        for (int e = tid; e <= p.G; e += K2_THREADS) s_tab[p.nRB + 1 + e] = p.cta_start[e];
+    }
     __syncthreads();
 
-    const double* mu_prev = p.mu + ((p.t - 1) & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
-    double* mu_next = p.mu + (p.t & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
+    const float* mu_prev = p.mu + ((p.t - 1) & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
+    float* mu_next = p.mu + (p.t & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
 
     if (!p.final_pass) {
-        const int RB = p.RB, CW = p.CW;
+        const int RB = p.RB, CW = p.CW, rbs = p.rb_shift, cws = p.cw_shift, nRB = p.nRB;
         for (int lk = warp; lk < m * d; lk += K2_THREADS / 32) {
             const int l = lk / d, k = lk - l * d;
             float acc = 0.f;
             if (i < n) {
-                const int I = i / RB, ri = i - I * RB;
-                acc = p.rowhead[((int64_t(l) * p.nRB + I) * d + k) * RB + ri];
+                const int I = i >> rbs, ri = i & (RB - 1);
+                acc = p.rowhead[((int64_t(l) * nRB + I) * d + k) * RB + ri];
                 // continuation segments: CTAs whose range starts strictly inside this walk
-                const int64_t ws = int64_t(l) * p.Tm + woff[I];
-                const int64_t we = int64_t(l) * p.Tm + woff[I + 1];
-                for (int64_t b = ((ws + 1) * p.G + p.T - 1) / p.T; b < p.G; ++b) {
-                    const int64_t pb = b * p.T / p.G;
-                    if (pb >= we) break;
-                    if (pb > ws) acc += p.rowcont[(b * d + k) * RB + ri];
+                const int P = walk_pos(I, nRB);
+                const int64_t ws = int64_t(l) * p.Tm + woff[P];
+                const int64_t we = int64_t(l) * p.Tm + woff[P + 1];
+                int lo = 0, hi = p.G;                 // first CTA b with cta_start[b] > ws
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cstart[mid] > ws) hi = mid; else lo = mid + 1;
                 }
-                // column partials of the walks of row blocks 0..I (independent loads)
+                for (int b = lo; b < p.G && cstart[b] < we; ++b)
+                    acc += p.rowcont[(int64_t(b) * d + k) * RB + ri];
+                // column partials of the walks of row blocks 0..I: 16 independent loads in
+                // flight, summed in a fixed order
                 const float* cp = p.colpart + int64_t(l) * p.Tm * d * CW;
-                float c4[4] = {0.f, 0.f, 0.f, 0.f};
-                int J = 0;
-                for (; J + 4 <= I + 1; J += 4) {
+                float csum = 0.f;
+                for (int J0 = 0; J0 <= I; J0 += 16) {
+                    float v[16];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int rel = i - (J + u) * RB;
-                        const int s = rel / CW, c = rel - s * CW;
-                        c4[u] += cp[((woff[J + u] + s) * d + k) * CW + c];
+                    for (int u = 0; u < 16; ++u) {
+                        const int J = J0 + u;
+                        v[u] = 0.f;
+                        if (J <= I) {
+                            const int rel = i - (J << rbs);
+                            const int sidx = rel >> cws, c = rel & (CW - 1);
+                            v[u] = cp[((woff[walk_pos(J, nRB)] + sidx) * d + k) * CW + c];
+                        }
                     }
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) csum += v[u];
                 }
-                for (; J <= I; ++J) {
-                    const int rel = i - J * RB;
-                    const int s = rel / CW, c = rel - s * CW;
-                    c4[0] += cp[((woff[J] + s) * d + k) * CW + c];
-                }
-                acc += (c4[0] + c4[1]) + (c4[2] + c4[3]);
+                acc += csum;
             }
             s_bx[lk][lane] = acc;
         }
     }
     __syncthreads();
 
-    double comm = 0.0;
+    FF comm{0.f, 0.f};
     for (int k = warp; k < d; k += K2_THREADS / 32) {
-        double xc[FJOFC_MAX_M];
+        float xc[FJOFC_MAX_M];
+        float cm = 0.f;
         if (i < n) {
             // centre X_{t-1} (in place) and its commensurability term
             for (int j = 0; j < m; ++j) {
                 const int64_t off = (int64_t(j) * n + i) * d + k;
-                xc[j] = double(p.Xprev[off]) - mu_prev[j * FJOFC_MAX_D + k];
-                if (p.t > 1) p.Xprev[off] = float(xc[j]);   // X_0 (mu_0 = 0) is left untouched
+                xc[j] = p.Xprev[off] - mu_prev[j * FJOFC_MAX_D + k];
+                if (p.t > 1) p.Xprev[off] = xc[j];   // X_0 (mu_0 = 0) is left untouched
             }
             for (int j = 0; j < m; ++j)
                 for (int l = j + 1; l < m; ++l) {
-                    const double df = xc[j] - xc[l];
-                    comm += p.wcomm[j][l] * df * df;
+                    const float df = xc[j] - xc[l];
+                    cm = fmaf(p.wcomm[j][l] * df, df, cm);
                 }
         }
+        comm = ff_add(comm, cm);
         if (!p.final_pass) {
             for (int j = 0; j < m; ++j) {
-                double cs = 0.0;
+                float v = 0.f;
                 if (i < n) {
-                    double v = 0.0;
-                    for (int l = 0; l < m; ++l) v += p.coef[j][l] * double(s_bx[l * d + k][lane]);
-                    const float vf = float(v);
-                    p.Xnext[(int64_t(j) * n + i) * d + k] = vf;
-                    cs = double(vf);
+                    for (int l = 0; l < m; ++l) v = fmaf(p.coef[j][l], s_bx[l * d + k][lane], v);
+                    p.Xnext[(int64_t(j) * n + i) * d + k] = v;
                 }
-                cs = warp_sum_f64(cs);
+                const FF cs = warp_sum_ff(FF{v, 0.f});
                 if (lane == 0) s_part[j * d + k] = cs;
             }
         }
     }
-    const double ctot = block_sum_f64(comm, s_tmp);
+    const FF ctot = block_sum_ff(comm, s_ff);
     const int npart = m * d + 1;
     if (tid == 0) {
-        for (int e = 0; e < m * d; ++e) p.bpart[int64_t(blockIdx.x) * npart + e] = p.final_pass ? 0.0 : s_part[e];
-        p.bpart[int64_t(blockIdx.x) * npart + m * d] = ctot;
+        for (int e = 0; e < m * d; ++e)
+            p.bpart[int64_t(blockIdx.x) * npart + e] = p.final_pass ? make_float2(0.f, 0.f)
+                                                                     : make_float2(s_part[e].hi, s_part[e].lo);
+        p.bpart[int64_t(blockIdx.x) * npart + m * d] = make_float2(ctot.hi, ctot.lo);
         __threadfence();
         const unsigned prev = atomicAdd(p.ticket, 1u);
         s_last = (prev == gridDim.x - 1);
@@ -145,25 +153,32 @@ k_apply(const K2Params p) {
     if (!s_last) return;
     __threadfence();
 
-    // ---- last CTA: totals in a fixed order
-    const volatile double* bp = p.bpart;
+    // ---- last CTA: totals in a fixed order (per-thread strided sums, then a tree)
     const int nblk = gridDim.x;
-    for (int e = tid; e < m * d; e += K2_THREADS) {
-        const int j = e / d, kk = e - j * d;
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += bp[int64_t(b) * npart + e];
-        mu_next[j * FJOFC_MAX_D + kk] = s / double(n);
+    for (int e = 0; e < m * d; ++e) {
+        FF acc{0.f, 0.f};
+        for (int b = tid; b < nblk; b += K2_THREADS) {
+            const float2 v = __ldcg(p.bpart + int64_t(b) * npart + e);
+            acc = ff_add(acc, FF{v.x, v.y});
+        }
+        const FF tot = block_sum_ff(acc, s_ff);
+        if (tid == 0) mu_next[(e / d) * FJOFC_MAX_D + (e % d)] = (tot.hi + tot.lo) / float(n);
     }
-    double c = 0.0;
-    for (int e = tid; e < nblk; e += K2_THREADS) c += bp[int64_t(e) * npart + m * d];
-    const double comm_tot = block_sum_f64(c, s_tmp);
-    double f = 0.0;
-    const volatile double* fidp = p.fid;
-    for (int e = tid; e < p.G; e += K2_THREADS) f += fidp[e];
-    const double fid_tot = block_sum_f64(f, s_tmp);
+    FF c{0.f, 0.f};
+    for (int b = tid; b < nblk; b += K2_THREADS) {
+        const float2 v = __ldcg(p.bpart + int64_t(b) * npart + m * d);
+        c = ff_add(c, FF{v.x, v.y});
+    }
+    const FF comm_tot = block_sum_ff(c, s_ff);
+    FF f{0.f, 0.f};
+    for (int e = tid; e < p.G; e += K2_THREADS) {
+        const float2 v = __ldcg(p.fid + e);
+        f = ff_add(f, FF{v.x, v.y});
+    }
+    const FF fid_tot = block_sum_ff(f, s_ff);
 
     if (tid == 0) {
-        const double sigma = fid_tot + comm_tot;
+        const double sigma = (double(fid_tot.hi) + double(fid_tot.lo)) + (double(comm_tot.hi) + double(comm_tot.lo));
         const int tp = p.t - 1;                 // index of the iterate whose stress this is
         p.hist[tp] = sigma;
         DevStatus* st = p.st;
@@ -191,7 +206,8 @@ k_apply(const K2Params p) {
 int k2_blocks(int n) { return (n + K2_OBJ - 1) / K2_OBJ; }
 
 cudaError_t launch_k2(const K2Params& p, cudaStream_t s) {
-    const size_t smem = (p.nRB + 1) <= K2_WOFF_SMEM_MAX ? size_t(p.nRB + 1) * sizeof(int64_t) : 0;
+    const int tab = p.nRB + 1 + p.G + 1;
+    const size_t smem = tab <= K2_TAB_SMEM_MAX ? size_t(tab) * sizeof(int64_t) : 0;
     k_apply<<<p.nbx, K2_THREADS, smem, s>>>(p);
     return cudaGetLastError();
 }
@@ -206,21 +222,24 @@ __global__ void k_init(const InitParams p) {
         p.st->timeout_site = 0;
         p.st->stress = 0.0;
         *p.ticket = 0u;
+        if (p.bar) *p.bar = 0u;
     }
-    for (int e = tid; e < 2 * FJOFC_MAX_M * FJOFC_MAX_D; e += gridDim.x * blockDim.x) p.mu[e] = 0.0;
-    for (int I = tid; I <= p.nRB; I += gridDim.x * blockDim.x) {
+    for (int e = tid; e < 2 * FJOFC_MAX_M * FJOFC_MAX_D; e += gridDim.x * blockDim.x) p.mu[e] = 0.f;
+    for (int b = tid; b <= p.G; b += gridDim.x * blockDim.x) p.cta_start[b] = int64_t(b) * p.T / p.G;
+    for (int P = tid; P <= p.nRB; P += gridDim.x * blockDim.x) {
         int64_t s = 0;
-        for (int J = 0; J < I; ++J) {
-            const int64_t cols = int64_t(p.n) - int64_t(J) * p.RB;
+        for (int Q = 0; Q < P; ++Q) {
+            const int64_t cols = int64_t(p.n) - int64_t(walk_row(Q, p.nRB)) * p.RB;
             s += (cols + p.CW - 1) / p.CW;
         }
-        p.walk_off[I] = s;
+        p.walk_off[P] = s;
     }
 }
 
 cudaError_t launch_init(const InitParams& p, cudaStream_t s) {
     const int threads = 256;
-    const int blocks = (p.nRB + 1 + threads - 1) / threads;
+    const int mx = (p.nRB > p.G ? p.nRB : p.G) + 1;
+    const int blocks = (mx + threads - 1) / threads;
     k_init<<<blocks, threads, 0, s>>>(p);
     return cudaGetLastError();
 }
@@ -269,7 +288,7 @@ __global__ void k_oos_prep(const OOSPrepParams p) {
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
-        p.SX[j * p.d + kk] = t;
+        p.SX[j * p.d + kk] = float(t);
         if (blockIdx.x == 0) {
             *p.next_block = 0ull;
             p.st->done = 0;

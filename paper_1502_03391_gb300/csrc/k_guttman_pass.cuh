@@ -85,10 +85,11 @@ struct K1Shape {
                                    size_t(STAGES + 2 * SLOTS) * 8 + size_t(STAGES) * 4 + 128;
 };
 
-// Position of a sub-tile: modality l, row block I, walk position s (walk length L).
+// Position of a sub-tile: modality l, walk position wp visiting row block I, sub-tile s
+// of that walk (walk length L).
 struct Cursor {
     int64_t t;
-    int l, I, s, L;
+    int l, wp, I, s, L;
 };
 
 __device__ __forceinline__ void cursor_init(Cursor& c, int64_t t, const K1Params& p) {
@@ -100,7 +101,8 @@ __device__ __forceinline__ void cursor_init(Cursor& c, int64_t t, const K1Params
         const int mid = (lo + hi + 1) >> 1;
         if (__ldg(p.walk_off + mid) <= r) lo = mid; else hi = mid - 1;
     }
-    c.I = lo;
+    c.wp = lo;
+    c.I = walk_row(lo, p.nRB);
     c.s = static_cast<int>(r - __ldg(p.walk_off + lo));
     c.L = static_cast<int>(__ldg(p.walk_off + lo + 1) - __ldg(p.walk_off + lo));
 }
@@ -109,21 +111,62 @@ __device__ __forceinline__ void cursor_next(Cursor& c, const K1Params& p) {
     ++c.t;
     if (++c.s == c.L) {
         c.s = 0;
-        if (++c.I == p.nRB) { c.I = 0; ++c.l; }
-        if (c.l < p.m) c.L = static_cast<int>(__ldg(p.walk_off + c.I + 1) - __ldg(p.walk_off + c.I));
+        if (++c.wp == p.nRB) { c.wp = 0; ++c.l; }
+        c.I = walk_row(c.wp, p.nRB);
+        if (c.l < p.m) c.L = static_cast<int>(__ldg(p.walk_off + c.wp + 1) - __ldg(p.walk_off + c.wp));
     }
 }
 
-// Kahan-compensated float32 accumulator (fidelity of one modality within a CTA).
-struct Kahan {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v) {
-        const float y = v - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
+
+// The pairs of one RB x CW sub-tile owned by this thread: rows r0 + warp*R + r (x_i in
+// xi[r]), columns c0 + lane*C + c (x_j in xj[c]).  Adds b_ij (x_i - x_j) to racc[r], its
+// negative to the column accumulators (two interleaved chains by row parity) and
+// (s Delta_ij - d_ij)^2 to sf0/sf1.  MASKED: only pairs with i < j < n count (diagonal and
+// ragged sub-tiles); otherwise every pair of the sub-tile is valid.
+template <int D, typename TD, int R, int C, int CW, bool MASKED>
+__device__ __forceinline__ void subtile_pairs(const TD* tile, int warp, int lane, int r0, int c0, int n, float sc,
+                                              const float (&xi)[R][D], const float (&xj)[C][D],
+                                              float (&racc)[R][D], float (&cacc0)[C][D], float (&cacc1)[C][D],
+                                              float& sf0, float& sf1) {
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int k = 0; k < D; ++k) { cacc0[c][k] = 0.f; cacc1[c][k] = 0.f; }
+    sf0 = 0.f;
+    sf1 = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = r0 + warp * R + r;
+        float dl[C];
+        load_delta_row<TD, C>(tile + (warp * R + r) * CW + lane * C, dl);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            float diff[D];
+            float d2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                diff[k] = xi[r][k] - xj[c][k];
+                d2 = fmaf(diff[k], diff[k], d2);
+            }
+            const float rinv = rsqrt_approx(fmaxf(d2, FLT_MIN));
+            float bb = dl[c] * rinv;
+            float e = fmaf(sc, dl[c], -(d2 * rinv));
+            if (MASKED) {
+                const int j = c0 + lane * C + c;
+                const bool valid = (j > i) && (j < n);
+                bb = valid ? bb : 0.f;
+                e = valid ? e : 0.f;
+            }
+            if (r & 1) sf1 = fmaf(e, e, sf1); else sf0 = fmaf(e, e, sf0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                racc[r][k] = fmaf(bb, diff[k], racc[r][k]);
+                if (r & 1) cacc1[c][k] = fmaf(-bb, diff[k], cacc1[c][k]);
+                else cacc0[c][k] = fmaf(-bb, diff[k], cacc0[c][k]);
+            }
+        }
     }
-};
+}
 
 template <int D, typename TD>
 __global__ void __launch_bounds__(K1Shape<D, TD>::NT, 1)
@@ -141,7 +184,7 @@ k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
     uint64_t* rfull = full + STAGES;
     uint64_t* rempty = rfull + SLOTS;
     int* released = reinterpret_cast<int*>(rempty + SLOTS);       // [STAGES] releases so far (monotone)
-    __shared__ double s_red64[CWARPS];
+    __shared__ FF s_redff[CWARPS];
     __shared__ int s_abort;
     __shared__ int s_issued;                                       // sub-tiles issued so far
 
@@ -187,7 +230,7 @@ k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
     for (int q = 0; q < STAGES && q < nq; ++q) cursor_next(pc, p);
     __syncthreads();
     const volatile int* abort_flag = &s_abort;
-    double fid_total = 0.0;
+    FF fid_total{0.f, 0.f};
 
     {
         // ------------------------------------------------------------ compute
@@ -221,7 +264,7 @@ k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
         };
         load_rows(cc);
         load_cols(cn);
-        Kahan fid;
+        FF fid{0.f, 0.f};          // fidelity of the current modality (float-float)
         int cur_l = cc.l;
 
         // reduce this warp's share of the columns of sub-tile qq (deferred by one)
@@ -258,8 +301,8 @@ k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
                 load_cols(cn);
             }
             if (cc.l != cur_l) {        // modality changed inside this CTA's range
-                fid_total += double(p.wfid[cur_l]) * double(fid.s);
-                fid = Kahan();
+                fid_total = ff_add(fid_total, ff_mul(fid, p.wfid[cur_l]));
+                fid = FF{0.f, 0.f};
                 cur_l = cc.l;
             }
             const float sc = p.dscale[cc.l];
@@ -271,67 +314,11 @@ k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
             const TD* tile = stages + size_t(stage) * S::STAGE_ELEMS;
             const bool masked = (cc.s * CW < RB) || (c0 + CW > n);
             float cacc0[C][D], cacc1[C][D];
-#pragma unroll
-            for (int c = 0; c < C; ++c)
-#pragma unroll
-                for (int k = 0; k < D; ++k) { cacc0[c][k] = 0.f; cacc1[c][k] = 0.f; }
-            float sf0 = 0.f, sf1 = 0.f;
-            if (!masked) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    float dl[C];
-                    load_delta_row<TD, C>(tile + (warp * R + r) * CW + lane * C, dl);
-#pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        float diff[D];
-                        float d2 = 0.f;
-#pragma unroll
-                        for (int k = 0; k < D; ++k) {
-                            diff[k] = xi[r][k] - xj[c][k];
-                            d2 = fmaf(diff[k], diff[k], d2);
-                        }
-                        const float rinv = rsqrt_approx(fmaxf(d2, FLT_MIN));
-                        const float bb = dl[c] * rinv;
-                        const float e = fmaf(sc, dl[c], -(d2 * rinv));
-                        if (r & 1) sf1 = fmaf(e, e, sf1); else sf0 = fmaf(e, e, sf0);
-#pragma unroll
-                        for (int k = 0; k < D; ++k) {
-                            racc[r][k] = fmaf(bb, diff[k], racc[r][k]);
-                            if (r & 1) cacc1[c][k] = fmaf(-bb, diff[k], cacc1[c][k]);
-                            else cacc0[c][k] = fmaf(-bb, diff[k], cacc0[c][k]);
-                        }
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int i = r0 + warp * R + r;
-                    float dl[C];
-                    load_delta_row<TD, C>(tile + (warp * R + r) * CW + lane * C, dl);
-#pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        const int j = c0 + lane * C + c;
-                        const bool valid = (j > i) && (j < n);
-                        float diff[D];
-                        float d2 = 0.f;
-#pragma unroll
-                        for (int k = 0; k < D; ++k) {
-                            diff[k] = xi[r][k] - xj[c][k];
-                            d2 = fmaf(diff[k], diff[k], d2);
-                        }
-                        const float rinv = rsqrt_approx(fmaxf(d2, FLT_MIN));
-                        const float bb = valid ? dl[c] * rinv : 0.f;
-                        const float e = valid ? fmaf(sc, dl[c], -(d2 * rinv)) : 0.f;
-                        if (r & 1) sf1 = fmaf(e, e, sf1); else sf0 = fmaf(e, e, sf0);
-#pragma unroll
-                        for (int k = 0; k < D; ++k) {
-                            racc[r][k] = fmaf(bb, diff[k], racc[r][k]);
-                            if (r & 1) cacc1[c][k] = fmaf(-bb, diff[k], cacc1[c][k]);
-                            else cacc0[c][k] = fmaf(-bb, diff[k], cacc0[c][k]);
-                        }
-                    }
-                }
-            }
+            float sf0, sf1;
+            if (!masked)
+                subtile_pairs<D, TD, R, C, CW, false>(tile, warp, lane, r0, c0, n, sc, xi, xj, racc, cacc0, cacc1, sf0, sf1);
+            else
+                subtile_pairs<D, TD, R, C, CW, true>(tile, warp, lane, r0, c0, n, sc, xi, xj, racc, cacc0, cacc1, sf0, sf1);
             // release the stage; the last warp to do so refills it with sub-tile q + STAGES
             __syncwarp();
             if (lane == 0) {
@@ -343,7 +330,7 @@ k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
                 }
             }
             if (q + STAGES < nq) cursor_next(pc, p);
-            fid.add(sf0 + sf1);
+            fid = ff_add(fid, sf0 + sf1);
 
             // column partials of this sub-tile into its ring slot
             if (q >= SLOTS &&
@@ -390,7 +377,7 @@ k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
             atomicExch(&s_abort, 1);
             if (lane == 0) raise_error(p.st, FJOFC_ERR_TIMEOUT, 2);
         }
-        fid_total += double(p.wfid[cur_l]) * double(fid.s);
+        fid_total = ff_add(fid_total, ff_mul(fid, p.wfid[cur_l]));
     }
     __syncthreads();
     if (*abort_flag && tid == 0) {
@@ -401,15 +388,15 @@ k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
             (void)mbar_wait_bounded(smem_u32(&full[qq % STAGES]), uint32_t((qq / STAGES) & 1));
     }
 
-    // fidelity partial of this CTA (fixed-order float64 reduction)
-    const double ws = warp_sum_f64(fid_total);
-    if (lane == 0) s_red64[warp] = ws;
+    // fidelity partial of this CTA (fixed-order float-float reduction)
+    const FF ws = warp_sum_ff(fid_total);
+    if (lane == 0) s_redff[warp] = ws;
     __syncthreads();
     if (tid == 0) {
-        double tot = 0.0;
+        FF tot{0.f, 0.f};
 #pragma unroll
-        for (int w = 0; w < CWARPS; ++w) tot += s_red64[w];
-        p.fid[b] = tot;
+        for (int w = 0; w < CWARPS; ++w) tot = ff_add(tot, s_redff[w]);
+        p.fid[b] = make_float2(tot.hi, tot.lo);
     }
 }
 

@@ -141,10 +141,10 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
 #pragma unroll
                     for (int kk = 0; kk < D; ++kk) yr[r][kk] = ys[(r * FJOFC_MAX_M + j) * D + kk];
                 float bx[R][D], bs[R], f32[R];
-                double f64[R];
+                FF fff[R];                  // float-float fidelity (GB300's float64 rate is low)
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    bs[r] = 0.f; f32[r] = 0.f; f64[r] = 0.0;
+                    bs[r] = 0.f; f32[r] = 0.f; fff[r] = FF{0.f, 0.f};
 #pragma unroll
                     for (int kk = 0; kk < D; ++kk) bx[r][kk] = 0.f;
                 }
@@ -189,9 +189,9 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                             for (int kk = 0; kk < D; ++kk) bx[r][kk] = fmaf(bb, xp[c][kk], bx[r][kk]);
                         }
                     }
-                    if ((s & 7) == 7) {
+                    if ((s & 3) == 3) {
 #pragma unroll
-                        for (int r = 0; r < R; ++r) { f64[r] += double(f32[r]); f32[r] = 0.f; }
+                        for (int r = 0; r < R; ++r) { fff[r] = ff_add(fff[r], f32[r]); f32[r] = 0.f; }
                     }
                     __syncwarp();
                     ++q_cons;
@@ -206,11 +206,10 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                 // reduce this modality's sums over the warp
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    f64[r] += double(f32[r]);
-                    const double fr = warp_sum_f64(f64[r]);
+                    const FF fr = warp_sum_ff(ff_add(fff[r], f32[r]));
                     const float br = warp_sum_f32(bs[r]);
                     if (lane == 0) {
-                        fidj[r * FJOFC_MAX_M + j] = fr;
+                        fidj[r * FJOFC_MAX_M + j] = double(fr.hi) + double(fr.lo);
                         acc[(r * FJOFC_MAX_M + j) * (D + 1) + D] = br;
                     }
 #pragma unroll
@@ -256,15 +255,15 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
             for (int e = lane; e < R * m * D; e += 32) {
                 const int r = e / (m * D), rem = e - r * m * D, j = rem / D, kk = rem - j * D;
                 if (flags[r] != 0) continue;
-                double v = 0.0;
+                float v = 0.f;
                 for (int i2 = 0; i2 < m; ++i2) {
                     const float* a = acc + (r * FJOFC_MAX_M + i2) * (D + 1);
-                    const double wi = double(p.wfid[i2]), si = double(p.dscale[i2]);
-                    const double xi = wi * (p.SX[i2 * D + kk] - si * double(a[kk]));
-                    const double psi = wi * si * double(a[D]);
-                    v += p.winv[j][i2] * (xi + psi * double(ys[(r * FJOFC_MAX_M + i2) * D + kk]));
+                    const float wi = p.wfid[i2], si = p.dscale[i2];
+                    const float xi = wi * (p.SX[i2 * D + kk] - si * a[kk]);
+                    const float psi = wi * si * a[D];
+                    v = fmaf(p.winv[j][i2], fmaf(psi, ys[(r * FJOFC_MAX_M + i2) * D + kk], xi), v);
                 }
-                yn[(r * FJOFC_MAX_M + j) * D + kk] = float(v);
+                yn[(r * FJOFC_MAX_M + j) * D + kk] = v;
             }
             __syncwarp();
             for (int e = lane; e < R * m * D; e += 32) {

@@ -232,3 +232,24 @@ def test_padded_row_stride_is_transparent(fj):
         fj.embed(dev, prob.W, X, max_iter=8)
         outs.append(X.cpu().numpy())
     np.testing.assert_array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("m,n,d", [(2, 300, 3), (3, 257, 2), (2, 90, 10)])
+def test_persistent_and_per_pass_launches_agree(fj, m, n, d):
+    """The default path (one persistent cooperative kernel for the whole loop) and the
+    one-launch-per-pass path (profile=1) compute the same partials in the same order:
+    bitwise equal X, iteration counts and stress histories."""
+    import torch
+    prob = synthetic.make_insample(0, n=n, m=m, d=d, seed=81 + n)
+    dev = [fj.to_device_delta(D) for D in prob.deltas]
+    outs = []
+    for prof in (0, 1, 2):
+        X = torch.as_tensor(np.asarray(prob.X0, np.float32)).cuda()
+        r = fj.embed(dev, prob.W, X, max_iter=60, tol=1e-6, tol_mode="relative", profile=prof)
+        outs.append((X.cpu().numpy(), r))
+    for X, r in outs[1:]:
+        np.testing.assert_array_equal(X, outs[0][0])
+        assert r.iters == outs[0][1].iters
+        np.testing.assert_array_equal(r.history, outs[0][1].history)
+    assert outs[1][1].passes == outs[1][1].iters + 1 and outs[1][1].ms_pass > 0
+    assert outs[2][1].passes == outs[2][1].iters + 1 and outs[2][1].ms_pass > 0
