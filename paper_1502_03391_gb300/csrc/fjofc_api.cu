@@ -348,6 +348,8 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     const size_t o_st = cv.take<DevStatus>(1);
     const size_t o_hist = cv.take<double>(size_t(o.max_iter) + 2);
     const size_t o_fid2 = cv.take<float2>(2 * size_t(P.G));
+    const size_t o_cbase = cv.take<int64_t>(size_t(P.nRB));
+    const size_t o_contr = cv.take<int2>(size_t(m) * P.nRB);
     const size_t o_bar = cv.take<unsigned>(1);
     const size_t total = cv.off;
 
@@ -434,8 +436,17 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     }
 
     unsigned* bar = reinterpret_cast<unsigned*>(base + o_bar);
+    k2.tb.colpart = k1.colpart;
+    k2.tb.rowhead = k1.rowhead;
+    k2.tb.rowcont = k1.rowcont;
+    k2.tb.cbase = reinterpret_cast<int64_t*>(base + o_cbase);
+    k2.tb.cont = reinterpret_cast<int2*>(base + o_contr);
+    k2.tb.Tm = P.Tm;
+    k2.tb.d = d; k2.tb.RB = RB; k2.tb.CW = CW; k2.tb.rb_shift = k2.rb_shift; k2.tb.cw_shift = k2.cw_shift;
+    k2.tb.nRB = P.nRB;
     InitParams ip{st, k2.ticket, k2.mu, const_cast<int64_t*>(k1.walk_off), const_cast<int64_t*>(k2.cta_start),
-                  bar, int(n), RB, CW, P.nRB, P.G, P.T};
+                  bar, const_cast<int64_t*>(k2.tb.cbase), const_cast<int2*>(k2.tb.cont), m, int(n), RB, CW, P.nRB,
+                  P.G, P.T, P.Tm};
     FJ_CUDA(launch_init(ip, stream));
 
     float* bufs[3] = {X, buf1, buf2};
@@ -461,6 +472,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         pp.max_iter = o.max_iter; pp.tol_mode = o.tol_mode; pp.tol = o.tol; pp.npairs = k2.npairs;
         for (int j = 0; j < FJOFC_MAX_M; ++j)
             for (int l = 0; l < FJOFC_MAX_M; ++l) { pp.coef[j][l] = k2.coef[j][l]; pp.wcomm[j][l] = k2.wcomm[j][l]; }
+        pp.tb = k2.tb;
         if (o.profile == 2) {
             FJ_CUDA(cudaEventCreate(&pe0));
             FJ_CUDA(cudaEventCreate(&pe1));

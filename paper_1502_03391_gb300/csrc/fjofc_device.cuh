@@ -230,6 +230,19 @@ __device__ __forceinline__ FF warp_sum_ff(FF v) {
     return v;
 }
 
+// Float-float total of v[0], v[stride], ..., v[(count-1)*stride] by one warp: lane l sums
+// entries l, l+32, ... (loads issued together), then a fixed-order butterfly.  Used for the
+// per-pass totals, identically by the persistent kernel and by K2.
+__device__ __forceinline__ FF totals_ff(const float2* v, int stride, int count) {
+    const int lane = threadIdx.x & 31;
+    FF acc{0.f, 0.f};
+    for (int g = lane; g < count; g += 32) {
+        const float2 x = __ldcg(v + int64_t(g) * stride);
+        acc = ff_add(acc, FF{x.x, x.y});
+    }
+    return warp_sum_ff(acc);
+}
+
 // Full-warp float64 sum (xor butterfly, every lane gets the total).
 __device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll

@@ -53,6 +53,17 @@ struct K1Params {
 // CTAs of the K1 instantiation that fit on one SM.
 int k1_blocks_per_sm(int d, int dtype);
 
+// Tables written once per call by the initialisation kernel.
+struct BxTables {
+    const float* colpart;      // [T][d][CW]
+    const float* rowhead;      // [m][nRB][d][RB]
+    const float* rowcont;      // [G][d][RB]
+    const int64_t* cbase;      // [nRB]       first sub-tile (within a modality) of row block I's walk
+    const int2* cont;          // [m][nRB]    CTAs [x, y) whose range starts strictly inside that walk
+    int64_t Tm;
+    int d, RB, CW, rb_shift, cw_shift, nRB;
+};
+
 // ---------------------------------------------------------------------------
 // K2: apply Wmod^-1, centre, commensurability, stress, stopping test
 // ---------------------------------------------------------------------------
@@ -78,6 +89,7 @@ struct K2Params {
     double tol, npairs;        // tolerance, C(mn,2)
     float coef[FJOFC_MAX_M][FJOFC_MAX_M];    // [Wmod^-1]_{jl} * w_ll * s_l
     float wcomm[FJOFC_MAX_M][FJOFC_MAX_M];   // w_jl for j < l, else 0
+    BxTables tb;
 };
 
 cudaError_t launch_k2(const K2Params& p, cudaStream_t s);
@@ -98,6 +110,7 @@ struct PersistParams {
     double tol, npairs;
     float coef[FJOFC_MAX_M][FJOFC_MAX_M];
     float wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
+    BxTables tb;
 };
 
 struct InitParams {
@@ -107,8 +120,10 @@ struct InitParams {
     int64_t* walk_off;
     int64_t* cta_start;
     unsigned* bar;             // grid barrier counter of the persistent kernel (may be NULL)
-    int n, RB, CW, nRB, G;
-    int64_t T;
+    int64_t* cbase;            // [nRB]
+    int2* cont;                // [m][nRB]
+    int m, n, RB, CW, nRB, G;
+    int64_t T, Tm;
 };
 cudaError_t launch_init(const InitParams& p, cudaStream_t s);
 cudaError_t launch_finalize(float* Xout, const float* buf1, const float* buf2, int64_t count,

@@ -13,13 +13,12 @@
 //   * the column means of X_t (for the next centring) and, in the last CTA to finish,
 //     the stress history entry and the stopping test of Algorithm 1 (read as "continue
 //     while the decrease exceeds the tolerance").
-#include "fjofc_device.cuh"
+#include "k_apply_common.cuh"
 
 namespace fjofc {
 
 constexpr int K2_THREADS = 256;
 constexpr int K2_OBJ = 32;                 // objects per CTA (one per lane)
-constexpr int K2_TAB_SMEM_MAX = 4096;      // walk/CTA tables staged in shared memory up to this many
 
 // Fixed-order float-float sum over the CTA; every thread receives the total.
 __device__ __forceinline__ FF block_sum_ff(FF v, FF* sh) {
@@ -40,7 +39,6 @@ __device__ __forceinline__ FF block_sum_ff(FF v, FF* sh) {
 // is float32; cross-object sums are float-float (GB300's float64 rate is low).
 __global__ void __launch_bounds__(K2_THREADS)
 k_apply(const K2Params p) {
-    extern __shared__ int64_t s_tab[];          // walk_off [nRB+1] then cta_start [G+1]
     __shared__ float s_bx[FJOFC_MAX_M * FJOFC_MAX_D][K2_OBJ];
     __shared__ FF s_ff[K2_THREADS / 32];
     __shared__ FF s_part[FJOFC_MAX_M * FJOFC_MAX_D];
@@ -51,92 +49,27 @@ k_apply(const K2Params p) {
     const int m = p.m, n = p.n, d = p.d;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int i = blockIdx.x * K2_OBJ + lane;
-    const bool tab_smem = (p.nRB + 1 + p.G + 1) <= K2_TAB_SMEM_MAX;
-    const int64_t* woff = tab_smem ? s_tab : p.walk_off;
-    const int64_t* cstart = tab_smem ? s_tab + (p.nRB + 1) : p.cta_start;
-    if (tab_smem) {
-        for (int e = tid; e <= p.nRB; e += K2_THREADS) s_tab[e] = p.walk_off[e];
-        for (int e = tid; e <= p.G; e += K2_THREADS) s_tab[p.nRB + 1 + e] = p.cta_start[e];
-    }
-    __syncthreads();
-
     const float* mu_prev = p.mu + ((p.t - 1) & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
     float* mu_next = p.mu + (p.t & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
 
-    if (!p.final_pass) {
-        const int RB = p.RB, CW = p.CW, rbs = p.rb_shift, cws = p.cw_shift, nRB = p.nRB;
+    if (!p.final_pass)
         for (int lk = warp; lk < m * d; lk += K2_THREADS / 32) {
             const int l = lk / d, k = lk - l * d;
-            float acc = 0.f;
-            if (i < n) {
-                const int I = i >> rbs, ri = i & (RB - 1);
-                acc = p.rowhead[((int64_t(l) * nRB + I) * d + k) * RB + ri];
-                // continuation segments: CTAs whose range starts strictly inside this walk
-                const int P = walk_pos(I, nRB);
-                const int64_t ws = int64_t(l) * p.Tm + woff[P];
-                const int64_t we = int64_t(l) * p.Tm + woff[P + 1];
-                int lo = 0, hi = p.G;                 // first CTA b with cta_start[b] > ws
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (cstart[mid] > ws) hi = mid; else lo = mid + 1;
-                }
-                for (int b = lo; b < p.G && cstart[b] < we; ++b)
-                    acc += p.rowcont[(int64_t(b) * d + k) * RB + ri];
-                // column partials of the walks of row blocks 0..I: 16 independent loads in
-                // flight, summed in a fixed order
-                const float* cp = p.colpart + int64_t(l) * p.Tm * d * CW;
-                float csum = 0.f;
-                for (int J0 = 0; J0 <= I; J0 += 16) {
-                    float v[16];
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int J = J0 + u;
-                        v[u] = 0.f;
-                        if (J <= I) {
-                            const int rel = i - (J << rbs);
-                            const int sidx = rel >> cws, c = rel & (CW - 1);
-                            v[u] = cp[((woff[walk_pos(J, nRB)] + sidx) * d + k) * CW + c];
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) csum += v[u];
-                }
-                acc += csum;
-            }
-            s_bx[lk][lane] = acc;
+            s_bx[lk][lane] = (i < n) ? bx_partials(p.tb, l, k, i) : 0.f;
         }
-    }
     __syncthreads();
 
     FF comm{0.f, 0.f};
     for (int k = warp; k < d; k += K2_THREADS / 32) {
-        float xc[FJOFC_MAX_M];
-        float cm = 0.f;
-        if (i < n) {
-            // centre X_{t-1} (in place) and its commensurability term
-            for (int j = 0; j < m; ++j) {
-                const int64_t off = (int64_t(j) * n + i) * d + k;
-                xc[j] = p.Xprev[off] - mu_prev[j * FJOFC_MAX_D + k];
-                if (p.t > 1) p.Xprev[off] = xc[j];   // X_0 (mu_0 = 0) is left untouched
-            }
-            for (int j = 0; j < m; ++j)
-                for (int l = j + 1; l < m; ++l) {
-                    const float df = xc[j] - xc[l];
-                    cm = fmaf(p.wcomm[j][l] * df, df, cm);
-                }
-        }
+        float cm, xn[FJOFC_MAX_M];
+        mix_and_centre(p.Xprev, p.Xnext, m, n, d, i, k, p.t, p.final_pass != 0, mu_prev, p.coef, p.wcomm,
+                       &s_bx[k][lane], d * K2_OBJ, &cm, xn);
         comm = ff_add(comm, cm);
-        if (!p.final_pass) {
+        if (!p.final_pass)
             for (int j = 0; j < m; ++j) {
-                float v = 0.f;
-                if (i < n) {
-                    for (int l = 0; l < m; ++l) v = fmaf(p.coef[j][l], s_bx[l * d + k][lane], v);
-                    p.Xnext[(int64_t(j) * n + i) * d + k] = v;
-                }
-                const FF cs = warp_sum_ff(FF{v, 0.f});
+                const FF cs = warp_sum_ff(FF{xn[j], 0.f});
                 if (lane == 0) s_part[j * d + k] = cs;
             }
-        }
     }
     const FF ctot = block_sum_ff(comm, s_ff);
     const int npart = m * d + 1;
@@ -153,29 +86,16 @@ k_apply(const K2Params p) {
     if (!s_last) return;
     __threadfence();
 
-    // ---- last CTA: totals in a fixed order (per-thread strided sums, then a tree)
-    const int nblk = gridDim.x;
-    for (int e = 0; e < m * d; ++e) {
-        FF acc{0.f, 0.f};
-        for (int b = tid; b < nblk; b += K2_THREADS) {
-            const float2 v = __ldcg(p.bpart + int64_t(b) * npart + e);
-            acc = ff_add(acc, FF{v.x, v.y});
-        }
-        const FF tot = block_sum_ff(acc, s_ff);
-        if (tid == 0) mu_next[(e / d) * FJOFC_MAX_D + (e % d)] = (tot.hi + tot.lo) / float(n);
-    }
-    FF c{0.f, 0.f};
-    for (int b = tid; b < nblk; b += K2_THREADS) {
-        const float2 v = __ldcg(p.bpart + int64_t(b) * npart + m * d);
-        c = ff_add(c, FF{v.x, v.y});
-    }
-    const FF comm_tot = block_sum_ff(c, s_ff);
-    FF f{0.f, 0.f};
-    for (int e = tid; e < p.G; e += K2_THREADS) {
-        const float2 v = __ldcg(p.fid + e);
-        f = ff_add(f, FF{v.x, v.y});
-    }
-    const FF fid_tot = block_sum_ff(f, s_ff);
+    // ---- last CTA: totals in a fixed order (one warp per quantity; the persistent
+    // kernel's phase C computes them the same way)
+    __shared__ FF s_tot[FJOFC_MAX_M * FJOFC_MAX_D + 2];
+    for (int e = warp; e < npart + 1; e += K2_THREADS / 32)
+        s_tot[e] = (e < npart) ? totals_ff(p.bpart + e, npart, int(gridDim.x)) : totals_ff(p.fid, 1, p.G);
+    __syncthreads();
+    if (tid == 0)
+        for (int e = 0; e < m * d; ++e)
+            mu_next[(e / d) * FJOFC_MAX_D + (e % d)] = (s_tot[e].hi + s_tot[e].lo) / float(n);
+    const FF comm_tot = s_tot[npart - 1], fid_tot = s_tot[npart];
 
     if (tid == 0) {
         const double sigma = (double(fid_tot.hi) + double(fid_tot.lo)) + (double(comm_tot.hi) + double(comm_tot.lo));
@@ -206,9 +126,7 @@ k_apply(const K2Params p) {
 int k2_blocks(int n) { return (n + K2_OBJ - 1) / K2_OBJ; }
 
 cudaError_t launch_k2(const K2Params& p, cudaStream_t s) {
-    const int tab = p.nRB + 1 + p.G + 1;
-    const size_t smem = tab <= K2_TAB_SMEM_MAX ? size_t(tab) * sizeof(int64_t) : 0;
-    k_apply<<<p.nbx, K2_THREADS, smem, s>>>(p);
+    k_apply<<<p.nbx, K2_THREADS, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -226,19 +144,34 @@ __global__ void k_init(const InitParams p) {
     }
     for (int e = tid; e < 2 * FJOFC_MAX_M * FJOFC_MAX_D; e += gridDim.x * blockDim.x) p.mu[e] = 0.f;
     for (int b = tid; b <= p.G; b += gridDim.x * blockDim.x) p.cta_start[b] = int64_t(b) * p.T / p.G;
-    for (int P = tid; P <= p.nRB; P += gridDim.x * blockDim.x) {
+    auto walk_start = [&](int P) {           // prefix sum of the walk lengths before position P
         int64_t s = 0;
         for (int Q = 0; Q < P; ++Q) {
             const int64_t cols = int64_t(p.n) - int64_t(walk_row(Q, p.nRB)) * p.RB;
             s += (cols + p.CW - 1) / p.CW;
         }
-        p.walk_off[P] = s;
+        return s;
+    };
+    for (int P = tid; P <= p.nRB; P += gridDim.x * blockDim.x) p.walk_off[P] = walk_start(P);
+    for (int e = tid; e < p.m * p.nRB; e += gridDim.x * blockDim.x) {
+        const int l = e / p.nRB, I = e - l * p.nRB;
+        const int64_t base = walk_start(walk_pos(I, p.nRB));
+        if (l == 0) p.cbase[I] = base;
+        // CTAs b whose first sub-tile b*T/G lies strictly inside the walk [ws, we)
+        const int64_t ws = int64_t(l) * p.Tm + base;
+        const int64_t we = ws + (int64_t(p.n) - int64_t(I) * p.RB + p.CW - 1) / p.CW;
+        int64_t lo = ((ws + 1) * p.G + p.T - 1) / p.T;
+        int64_t hi = (we * p.G + p.T - 1) / p.T;
+        if (hi > p.G) hi = p.G;
+        if (lo > hi) lo = hi;
+        p.cont[e] = make_int2(int(lo), int(hi));
     }
 }
 
 cudaError_t launch_init(const InitParams& p, cudaStream_t s) {
     const int threads = 256;
-    const int mx = (p.nRB > p.G ? p.nRB : p.G) + 1;
+    int mx = (p.nRB > p.G ? p.nRB : p.G) + 1;
+    if (p.m * p.nRB > mx) mx = p.m * p.nRB;
     const int blocks = (mx + threads - 1) / threads;
     k_init<<<blocks, threads, 0, s>>>(p);
     return cudaGetLastError();

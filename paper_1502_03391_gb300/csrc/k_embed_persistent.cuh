@@ -20,6 +20,7 @@
 #pragma once
 
 #include "k_guttman_pass.cuh"
+#include "k_apply_common.cuh"
 
 namespace fjofc {
 
@@ -311,75 +312,23 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const PersistParams P) {
         float* Xnext = P.buf[t % 3];
         for (int g = b; g < P.ngroups; g += G) {
             const int i = g * GOBJ + lane;
-            if (!final_pass) {
-                const int rbs = P.rb_shift, cws = P.cw_shift, nRB = p.nRB;
+            if (!final_pass)
                 for (int lk = warp; lk < m * D; lk += CWARPS) {
                     const int l = lk / D, k = lk - l * D;
-                    float acc = 0.f;
-                    if (i < n) {
-                        const int I = i >> rbs, ri = i & (RB - 1);
-                        acc = __ldcg(p.rowhead + ((int64_t(l) * nRB + I) * D + k) * RB + ri);
-                        const int Pw = walk_pos(I, nRB);
-                        const int64_t ws = int64_t(l) * p.Tm + __ldg(p.walk_off + Pw);
-                        const int64_t we = int64_t(l) * p.Tm + __ldg(p.walk_off + Pw + 1);
-                        int lo = 0, hi = G;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (P.cta_start[mid] > ws) hi = mid; else lo = mid + 1;
-                        }
-                        for (int bb = lo; bb < G && P.cta_start[bb] < we; ++bb)
-                            acc += __ldcg(p.rowcont + (int64_t(bb) * D + k) * RB + ri);
-                        const float* cpl = p.colpart + int64_t(l) * p.Tm * D * CW;
-                        float csum = 0.f;
-                        for (int J0 = 0; J0 <= I; J0 += 16) {
-                            float v[16];
-#pragma unroll
-                            for (int u = 0; u < 16; ++u) {
-                                const int J = J0 + u;
-                                v[u] = 0.f;
-                                if (J <= I) {
-                                    const int rel = i - (J << rbs);
-                                    const int sidx = rel >> cws, c = rel & (CW - 1);
-                                    v[u] = __ldcg(cpl + ((__ldg(p.walk_off + walk_pos(J, nRB)) + sidx) * D + k) * CW + c);
-                                }
-                            }
-#pragma unroll
-                            for (int u = 0; u < 16; ++u) csum += v[u];
-                        }
-                        acc += csum;
-                    }
-                    s_bx[lk * GOBJ + lane] = acc;
+                    s_bx[lk * GOBJ + lane] = (i < n) ? bx_partials(P.tb, l, k, i) : 0.f;
                 }
-            }
             __syncthreads();
             FF comm{0.f, 0.f};
             for (int k = warp; k < D; k += CWARPS) {
-                float xc[FJOFC_MAX_M];
-                float cm = 0.f;
-                if (i < n) {
-                    for (int j = 0; j < m; ++j) {
-                        const int64_t off = (int64_t(j) * n + i) * D + k;
-                        xc[j] = __ldcg(Xprev + off) - s_mu[j * FJOFC_MAX_D + k];
-                        if (t > 1) Xprev[off] = xc[j];
-                    }
-                    for (int j = 0; j < m; ++j)
-                        for (int l = j + 1; l < m; ++l) {
-                            const float df = xc[j] - xc[l];
-                            cm = fmaf(P.wcomm[j][l] * df, df, cm);
-                        }
-                }
+                float cm, xn[FJOFC_MAX_M];
+                mix_and_centre(Xprev, Xnext, m, n, D, i, k, t, final_pass, s_mu, P.coef, P.wcomm,
+                               s_bx + k * GOBJ + lane, D * GOBJ, &cm, xn);
                 comm = ff_add(comm, cm);
-                if (!final_pass) {
+                if (!final_pass)
                     for (int j = 0; j < m; ++j) {
-                        float v = 0.f;
-                        if (i < n) {
-                            for (int l = 0; l < m; ++l) v = fmaf(P.coef[j][l], s_bx[(l * D + k) * GOBJ + lane], v);
-                            Xnext[(int64_t(j) * n + i) * D + k] = v;
-                        }
-                        const FF cs = warp_sum_ff(FF{v, 0.f});
+                        const FF cs = warp_sum_ff(FF{xn[j], 0.f});
                         if (lane == 0) s_part[j * D + k] = cs;
                     }
-                }
             }
             const FF cw = warp_sum_ff(comm);
             __syncthreads();
@@ -404,47 +353,19 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const PersistParams P) {
 
         // ================================================================ phase C
         {
+            // one warp per total: m*D column sums, commensurability, fidelity (all loads
+            // of a lane in one round); the same order in every CTA
             const int npart = m * D + 1;
-            for (int e = 0; e < m * D; ++e) {
-                FF acc{0.f, 0.f};
-                for (int g = tid; g < P.ngroups; g += NT) {
-                    const float2 v = __ldcg(P.bpart + int64_t(g) * npart + e);
-                    acc = ff_add(acc, FF{v.x, v.y});
-                }
-                const FF ws = warp_sum_ff(acc);
-                __syncthreads();
-                if (lane == 0) s_ff[warp] = ws;
-                __syncthreads();
-                if (tid == 0) {
-                    FF tot{0.f, 0.f};
-                    for (int w = 0; w < CWARPS; ++w) tot = ff_add(tot, s_ff[w]);
-                    s_mu[(e / D) * FJOFC_MAX_D + (e % D)] = final_pass ? 0.f : (tot.hi + tot.lo) / float(n);
-                }
-            }
-            FF cacc{0.f, 0.f}, facc{0.f, 0.f};
-            for (int g = tid; g < P.ngroups; g += NT) {
-                const float2 v = __ldcg(P.bpart + int64_t(g) * npart + m * D);
-                cacc = ff_add(cacc, FF{v.x, v.y});
-            }
-            for (int bb = tid; bb < G; bb += NT) {
-                const float2 v = __ldcg(P.fid2 + (t & 1) * G + bb);
-                facc = ff_add(facc, FF{v.x, v.y});
-            }
-            const FF wc = warp_sum_ff(cacc);
-            const FF wf = warp_sum_ff(facc);
-            __shared__ FF s_ff2[CWARPS];
-            __syncthreads();
-            if (lane == 0) {
-                s_ff[warp] = wc;
-                s_ff2[warp] = wf;
-            }
+            __shared__ FF s_tot[FJOFC_MAX_M * FJOFC_MAX_D + 2];
+            for (int e = warp; e < npart + 1; e += CWARPS)
+                s_tot[e] = (e < npart) ? totals_ff(P.bpart + e, npart, P.ngroups)
+                                       : totals_ff(P.fid2 + (t & 1) * G, 1, G);
             __syncthreads();
             if (tid == 0) {
-                FF ct{0.f, 0.f}, ft{0.f, 0.f};
-                for (int w = 0; w < CWARPS; ++w) {
-                    ct = ff_add(ct, s_ff[w]);
-                    ft = ff_add(ft, s_ff2[w]);
-                }
+                for (int e = 0; e < m * D; ++e)
+                    s_mu[(e / D) * FJOFC_MAX_D + (e % D)] =
+                        final_pass ? 0.f : (s_tot[e].hi + s_tot[e].lo) / float(n);
+                const FF ct = s_tot[npart - 1], ft = s_tot[npart];
                 const double sigma = (double(ft.hi) + double(ft.lo)) + (double(ct.hi) + double(ct.lo));
                 const int tp = t - 1;
                 int stop = final_pass ? 1 : 0;
