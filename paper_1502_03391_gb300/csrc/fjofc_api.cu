@@ -393,12 +393,16 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     k1.rowcont = reinterpret_cast<float*>(base + o_cont);
     k1.fid = reinterpret_cast<float2*>(base + o_fid);
     k1.walk_off = reinterpret_cast<int64_t*>(base + o_woff);
+    k1.cta_start = reinterpret_cast<int64_t*>(base + o_cta);
     k1.st = st;
     k1.m = m; k1.n = int(n); k1.d = d; k1.nRB = P.nRB; k1.G = P.G;
     k1.Tm = P.Tm; k1.T = P.T;
+    // K1 works in Delta's stored units (x / s_l), so its fidelity sum carries s_l^2
+    double dsc[FJOFC_MAX_M];
     for (int l = 0; l < FJOFC_MAX_M; ++l) {
-        k1.wfid[l] = l < m ? float(weights[l * m + l]) : 0.f;
-        k1.dscale[l] = (l < m && delta_scale) ? delta_scale[l] : 1.f;
+        dsc[l] = (l < m && delta_scale) ? double(delta_scale[l]) : 1.0;
+        k1.wfid[l] = l < m ? float(weights[l * m + l] * dsc[l] * dsc[l]) : 0.f;
+        k1.xscale[l] = float(1.0 / dsc[l]);
     }
 
     K2Params k2{};
@@ -424,7 +428,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     k2.npairs = double(m * n) * double(m * n - 1) / 2.0;
     for (int j = 0; j < m; ++j)
         for (int l = 0; l < m; ++l) {
-            k2.coef[j][l] = float(winv[j * m + l] * weights[l * m + l] * double(k1.dscale[l]));
+            k2.coef[j][l] = float(winv[j * m + l] * weights[l * m + l] * dsc[l]);
             k2.wcomm[j][l] = (j < l) ? float(weights[j * m + l]) : 0.f;
         }
 

@@ -43,11 +43,12 @@ struct K1Params {
     float* rowcont;            // [G][d][RB]   row partial of a CTA whose range starts mid-walk
     float2* fid;               // [G]          weighted fidelity partial per CTA (float-float)
     const int64_t* walk_off;   // [nRB+1]      prefix sums of the walk lengths, by walk position
+    const int64_t* cta_start;  // [G+1]        first sub-tile of every CTA's range
     DevStatus* st;
     int m, n, d, nRB, G;
     int64_t Tm, T;             // sub-tiles per modality, total
-    float wfid[FJOFC_MAX_M];   // w_ll: fidelity weight of modality l
-    float dscale[FJOFC_MAX_M]; // s_l: Delta scale of modality l
+    float wfid[FJOFC_MAX_M];   // w_ll s_l^2: weight of the fidelity sum in scaled units
+    float xscale[FJOFC_MAX_M]; // 1 / s_l: coordinates of modality l in Delta's stored units
 };
 
 // CTAs of the K1 instantiation that fit on one SM.

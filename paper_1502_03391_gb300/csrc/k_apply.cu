@@ -8,8 +8,9 @@
 //     L^+ = Wmod^-1 (x) I_n + Z (x) J_n, and the J_n part vanishes on B(X) X because the
 //     rows and columns of every B_l sum to zero, Sec. 2.1);
 //   * sigma(X_{t-1}) = (fidelity from K1) + sum_{j<l} w_jl ||X^(j) - X^(l)||^2 (Eq. stress,
-//     Remark faststress), with X_{t-1} first centred per modality in float64 (Guttman
-//     outputs are centred in exact arithmetic; this removes float32 drift);
+//     Remark faststress), with X_{t-1} first centred per modality by its float-float
+//     column means (Guttman outputs are centred in exact arithmetic; this removes
+//     float32 drift);
 //   * the column means of X_t (for the next centring) and, in the last CTA to finish,
 //     the stress history entry and the stopping test of Algorithm 1 (read as "continue
 //     while the decrease exceeds the tolerance").
@@ -18,66 +19,46 @@
 namespace fjofc {
 
 constexpr int K2_THREADS = 256;
-constexpr int K2_OBJ = 32;                 // objects per CTA (one per lane)
 
-// Fixed-order float-float sum over the CTA; every thread receives the total.
-__device__ __forceinline__ FF block_sum_ff(FF v, FF* sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum_ff(v);
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    FF t{0.f, 0.f};
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) t = ff_add(t, sh[w]);
-    return t;
-}
-
-// One CTA per 32 consecutive objects.  Phase 1: warp w sums the partials of (modality l,
-// coordinate k) pairs w, w+8, ... for its 32 objects (lane = object), 16 independent loads
-// in flight.  Phase 2: warp w handles coordinate k = w, w+8, ...: centre X_{t-1}, its
-// commensurability, the Wmod^-1 mix into X_t and the per-block column sums.  Arithmetic
-// is float32; cross-object sums are float-float (GB300's float64 rate is low).
+// One CTA per group of 32 consecutive objects (phase_b with a chunk of one group), then
+// the last CTA to finish forms the totals.  Arithmetic is float32; cross-object sums are
+// float-float (GB300's float64 rate is low).
 __global__ void __launch_bounds__(K2_THREADS)
 k_apply(const K2Params p) {
-    __shared__ float s_bx[FJOFC_MAX_M * FJOFC_MAX_D][K2_OBJ];
-    __shared__ FF s_ff[K2_THREADS / 32];
-    __shared__ FF s_part[FJOFC_MAX_M * FJOFC_MAX_D];
+    extern __shared__ float s_dyn[];             // phase_b_floats_per_group(m, d)
+    __shared__ float s_mu[FJOFC_MAX_M * FJOFC_MAX_D];
+    __shared__ float s_coef[FJOFC_MAX_M][FJOFC_MAX_M], s_wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
     __shared__ bool s_last;
 
     if (ld_volatile(&p.st->done)) return;
 
     const int m = p.m, n = p.n, d = p.d;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i = blockIdx.x * K2_OBJ + lane;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const float* mu_prev = p.mu + ((p.t - 1) & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
     float* mu_next = p.mu + (p.t & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
-
-    if (!p.final_pass)
-        for (int lk = warp; lk < m * d; lk += K2_THREADS / 32) {
-            const int l = lk / d, k = lk - l * d;
-            s_bx[lk][lane] = (i < n) ? bx_partials(p.tb, l, k, i) : 0.f;
-        }
+    for (int e = tid; e < FJOFC_MAX_M * FJOFC_MAX_D; e += K2_THREADS) s_mu[e] = mu_prev[e];
+    for (int e = tid; e < FJOFC_MAX_M * FJOFC_MAX_M; e += K2_THREADS) {
+        s_coef[e / FJOFC_MAX_M][e % FJOFC_MAX_M] = p.coef[e / FJOFC_MAX_M][e % FJOFC_MAX_M];
+        s_wcomm[e / FJOFC_MAX_M][e % FJOFC_MAX_M] = p.wcomm[e / FJOFC_MAX_M][e % FJOFC_MAX_M];
+    }
     __syncthreads();
 
-    FF comm{0.f, 0.f};
-    for (int k = warp; k < d; k += K2_THREADS / 32) {
-        float cm, xn[FJOFC_MAX_M];
-        mix_and_centre(p.Xprev, p.Xnext, m, n, d, i, k, p.t, p.final_pass != 0, mu_prev, p.coef, p.wcomm,
-                       &s_bx[k][lane], d * K2_OBJ, &cm, xn);
-        comm = ff_add(comm, cm);
-        if (!p.final_pass)
-            for (int j = 0; j < m; ++j) {
-                const FF cs = warp_sum_ff(FF{xn[j], 0.f});
-                if (lane == 0) s_part[j * d + k] = cs;
-            }
-    }
-    const FF ctot = block_sum_ff(comm, s_ff);
+    PhaseBArgs a;
+    a.tb = p.tb;
+    a.Xprev = p.Xprev;
+    a.Xnext = p.Xnext;
+    a.bpart = p.bpart;
+    a.mu_prev = s_mu;
+    a.coef = s_coef;
+    a.wcomm = s_wcomm;
+    a.m = m; a.n = n; a.d = d; a.t = p.t;
+    a.final_pass = p.final_pass != 0;
+    phase_b(a, blockIdx.x, gridDim.x, p.nbx, 1, s_dyn);
+
     const int npart = m * d + 1;
+    __threadfence();
+    __syncthreads();
     if (tid == 0) {
-        for (int e = 0; e < m * d; ++e)
-            p.bpart[int64_t(blockIdx.x) * npart + e] = p.final_pass ? make_float2(0.f, 0.f)
-                                                                     : make_float2(s_part[e].hi, s_part[e].lo);
-        p.bpart[int64_t(blockIdx.x) * npart + m * d] = make_float2(ctot.hi, ctot.lo);
         __threadfence();
         const unsigned prev = atomicAdd(p.ticket, 1u);
         s_last = (prev == gridDim.x - 1);
@@ -123,10 +104,11 @@ k_apply(const K2Params p) {
     }
 }
 
-int k2_blocks(int n) { return (n + K2_OBJ - 1) / K2_OBJ; }
+int k2_blocks(int n) { return (n + kGroupObjects - 1) / kGroupObjects; }
 
 cudaError_t launch_k2(const K2Params& p, cudaStream_t s) {
-    k_apply<<<p.nbx, K2_THREADS, 0, s>>>(p);
+    const size_t smem = size_t(phase_b_floats_per_group(p.m, p.d)) * sizeof(float);
+    k_apply<<<p.nbx, K2_THREADS, smem, s>>>(p);
     return cudaGetLastError();
 }
 

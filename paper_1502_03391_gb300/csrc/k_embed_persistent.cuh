@@ -2,12 +2,13 @@
 // cooperatively launched kernel: one CTA per SM, resident for every pass.
 //
 // Pass t (reads X_{t-1}, writes X_t):
-//   A. the fused all-pairs sub-tiles of this CTA's fixed range (same work, layout and
-//      partials as k_guttman_pass; see k_guttman_pass.cuh), fidelity partial -> fid[t&1][b];
+//   A. the fused all-pairs sub-tiles of this CTA's fixed range (phase_a, the same code as
+//      the standalone pass k_guttman_pass), fidelity partial -> fid[t&1][b];
 //   -- grid barrier --
-//   B. for object groups g = b, b+G, ... (32 objects each): sum the partials, centre
-//      X_{t-1} in place with the previous pass's means, its commensurability, the Wmod^-1
-//      mix into X_t (Eq. update / Cor. 1) and per-group float-float sums -> bpart[g];
+//   B. for object groups g = b, b+G, ... (32 objects each; phase_b, the same code as K2):
+//      sum the partials, centre X_{t-1} in place with the previous pass's means, its
+//      commensurability, the Wmod^-1 mix into X_t (Eq. update / Cor. 1) and per-group
+//      float-float sums -> bpart[g];
 //   -- grid barrier --
 //   C. every CTA reduces bpart and fid in the same fixed order, so all CTAs obtain the
 //      same means of X_t, sigma(X_{t-1}) and stopping decision (Algorithm 1 with the
@@ -59,27 +60,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
 
 template <int D, typename TD>
 __global__ void __launch_bounds__(K1Shape<D, TD>::NT, 1)
-k_embed_persistent(const __grid_constant__ TMaps tm, const PersistParams P) {
+k_embed_persistent(const __grid_constant__ TMaps tm, const __grid_constant__ PersistParams P) {
     using S = K1Shape<D, TD>;
-    constexpr int R = S::R, C = S::C, CWARPS = S::CWARPS, STAGES = S::STAGES, SLOTS = S::SLOTS;
-    constexpr int RB = S::RB, CW = S::CW, NT = S::NT;
-    constexpr int GOBJ = 32;
+    constexpr int CWARPS = S::CWARPS, NT = S::NT;
     const K1Params& p = P.k1;
 
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    TD* stages = reinterpret_cast<TD*>(smem);
-    float* red = reinterpret_cast<float*>(smem + size_t(STAGES) * S::STAGE_BYTES);   // [SLOTS][CWARPS][D][CW]
-    uint64_t* full = reinterpret_cast<uint64_t*>(red + S::RED_FLOATS);
-    uint64_t* rfull = full + STAGES;
-    uint64_t* rempty = rfull + SLOTS;
-    int* released = reinterpret_cast<int*>(rempty + SLOTS);
-    float* s_bx = red;                          // phase B overlay: [m*d][32] floats
-    static_assert(S::RED_FLOATS >= FJOFC_MAX_M * D * GOBJ, "phase-B overlay does not fit");
     __shared__ FF s_ff[CWARPS];
-    __shared__ FF s_part[FJOFC_MAX_M * FJOFC_MAX_D];
     __shared__ float s_mu[FJOFC_MAX_M * FJOFC_MAX_D];
+    __shared__ float s_coef[FJOFC_MAX_M][FJOFC_MAX_M], s_wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
     __shared__ int s_abort, s_issued, s_flag, s_stop, s_final;
     __shared__ double s_prev;
 
@@ -89,58 +78,27 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const PersistParams P) {
     const int passes = P.max_iter + 1;
     const int64_t t_begin = P.cta_start[b];
     const int nq = static_cast<int>(P.cta_start[b + 1] - t_begin);
-    const int64_t total_q = int64_t(passes) * nq;     // sub-tiles this CTA may ever issue
 
-    // issue the sub-tile with global index qg (pass-major; the range wraps every pass)
-    Cursor pc;
-    cursor_init(pc, t_begin, p);
-    int pc_local = 0;                                  // position of pc within the range
-    auto issue = [&](int64_t qg) {
-        const int stage = int(qg % STAGES);
-        atomicMax(&s_issued, int(qg + 1));
-        const uint32_t bar = smem_u32(&full[stage]);
-        mbar_arrive_expect_tx(bar, S::STAGE_BYTES);
-        tma_load_2d(smem_u32(stages + size_t(stage) * S::STAGE_ELEMS), &tm.map[pc.l], pc.I * RB + pc.s * CW,
-                    pc.I * RB, bar);
-    };
-    auto advance_pc = [&]() {
-        if (++pc_local == nq) {
-            pc_local = 0;
-            cursor_init(pc, t_begin, p);
-        } else {
-            cursor_next(pc, p);
-        }
-    };
+    K1Ring<D, TD> rg;
+    rg.carve(smem_raw);
+    // phase B reuses the column-partial ring (free between passes)
+    float* s_phb = rg.red;
+    const int bcap = int(S::RED_FLOATS / size_t(phase_b_floats_per_group(m, D)));
+    static_assert(S::RED_FLOATS >= size_t(phase_b_floats_per_group(FJOFC_MAX_M, D)), "phase-B overlay does not fit");
 
     if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(smem_u32(&full[s]), 1);
-            released[s] = 0;
-        }
-        for (int s = 0; s < SLOTS; ++s) {
-            mbar_init(smem_u32(&rfull[s]), CWARPS);
-            mbar_init(smem_u32(&rempty[s]), CWARPS);
-        }
-        s_abort = 0;
-        s_issued = 0;
         s_stop = 0;
         s_final = 0;
         s_prev = 0.0;
-        fence_barrier_init();
-        for (int l = 0; l < m; ++l) tma_prefetch_desc(&tm.map[l]);
     }
     for (int e = tid; e < FJOFC_MAX_M * FJOFC_MAX_D; e += NT) s_mu[e] = 0.f;
-    __syncthreads();
-    if (tid == 0) {
-        for (int64_t q = 0; q < STAGES && q < total_q; ++q) {
-            issue(q);
-            advance_pc();
-        }
+    for (int e = tid; e < FJOFC_MAX_M * FJOFC_MAX_M; e += NT) {
+        s_coef[e / FJOFC_MAX_M][e % FJOFC_MAX_M] = P.coef[e / FJOFC_MAX_M][e % FJOFC_MAX_M];
+        s_wcomm[e / FJOFC_MAX_M][e % FJOFC_MAX_M] = P.wcomm[e / FJOFC_MAX_M][e % FJOFC_MAX_M];
     }
-    // every thread keeps its own copy of the prefetch cursor STAGES ahead
-    if (tid != 0)
-        for (int64_t q = 0; q < STAGES && q < total_q; ++q) advance_pc();
-    __syncthreads();
+    // ring over every pass's sub-tiles; Delta does not change, so it prefetches the next
+    // pass's first sub-tiles while phases B and C run
+    rg.start(tm, p, t_begin, nq, int64_t(passes) * nq, &s_issued, &s_abort);
     const volatile int* abort_flag = &s_abort;
     unsigned bar_target = 0;
     bool ok = true;
@@ -149,145 +107,12 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const PersistParams P) {
 
     for (; t <= passes && ok; ++t) {
         const bool final_pass = (t == passes);
-        const float* X = P.buf[(t - 1) % 3];
-        const int64_t qbase = int64_t(t - 1) * nq;
+        float* Xprev = P.buf[(t - 1) % 3];
+        float* Xnext = P.buf[t % 3];
 
         // ================================================================ phase A
         FF fid_total{0.f, 0.f};
-        {
-            Cursor cc, cn;
-            cursor_init(cc, t_begin, p);
-            cn = cc;
-            bool seg_head = (cc.s == 0);
-            float xi[R][D], racc[R][D], xjn[C][D];
-            auto load_rows = [&](const Cursor& c) {
-                const float* Xl = X + int64_t(c.l) * n * D;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int i = c.I * RB + warp * R + r;
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        xi[r][k] = (i < n) ? __ldcg(Xl + int64_t(i) * D + k) : 0.f;
-                        racc[r][k] = 0.f;
-                    }
-                }
-            };
-            auto load_cols = [&](const Cursor& c) {
-                const float* Xl = X + int64_t(c.l) * n * D;
-                const int c0 = c.I * RB + c.s * CW + lane * C;
-#pragma unroll
-                for (int ci = 0; ci < C; ++ci)
-#pragma unroll
-                    for (int k = 0; k < D; ++k)
-                        xjn[ci][k] = (c0 + ci < n) ? __ldcg(Xl + int64_t(c0 + ci) * D + k) : 0.f;
-            };
-            load_rows(cc);
-            load_cols(cn);
-            FF fid{0.f, 0.f};
-            int cur_l = cc.l;
-
-            auto reduce_share = [&](int64_t qg, int64_t tglob) -> bool {
-                const int slot = int(qg % SLOTS);
-                if (!mbar_wait_or_abort(smem_u32(&rfull[slot]), uint32_t((qg / SLOTS) & 1), abort_flag)) return false;
-                const float* rb = red + size_t(slot) * CWARPS * D * CW;
-                float* cp = p.colpart + tglob * int64_t(D * CW);
-                constexpr int SHARE = (D * CW + CWARPS - 1) / CWARPS;
-                for (int e = warp * SHARE + lane; e < (warp + 1) * SHARE && e < D * CW; e += 32) {
-                    float v = 0.f;
-#pragma unroll
-                    for (int w = 0; w < CWARPS; ++w) v += rb[w * D * CW + e];
-                    cp[e] = v;
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&rempty[slot]));
-                return true;
-            };
-
-            for (int q = 0; q < nq && ok; ++q) {
-                const int64_t qg = qbase + q;
-                const int stage = int(qg % STAGES);
-                const int slot = int(qg % SLOTS);
-                const int r0 = cc.I * RB;
-                const int c0 = r0 + cc.s * CW;
-                float xj[C][D];
-#pragma unroll
-                for (int c = 0; c < C; ++c)
-#pragma unroll
-                    for (int k = 0; k < D; ++k) xj[c][k] = xjn[c][k];
-                if (q + 1 < nq) {
-                    cursor_next(cn, p);
-                    load_cols(cn);
-                }
-                if (cc.l != cur_l) {
-                    fid_total = ff_add(fid_total, ff_mul(fid, p.wfid[cur_l]));
-                    fid = FF{0.f, 0.f};
-                    cur_l = cc.l;
-                }
-                const float sc = p.dscale[cc.l];
-                if (!mbar_wait_or_abort(smem_u32(&full[stage]), uint32_t((qg / STAGES) & 1), abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                const TD* tile = stages + size_t(stage) * S::STAGE_ELEMS;
-                const bool masked = (cc.s * CW < RB) || (c0 + CW > n);
-                float cacc0[C][D], cacc1[C][D];
-                float sf0, sf1;
-                if (!masked)
-                    subtile_pairs<D, TD, R, C, CW, false>(tile, warp, lane, r0, c0, n, sc, xi, xj, racc, cacc0, cacc1,
-                                                          sf0, sf1);
-                else
-                    subtile_pairs<D, TD, R, C, CW, true>(tile, warp, lane, r0, c0, n, sc, xi, xj, racc, cacc0, cacc1,
-                                                         sf0, sf1);
-                // release the stage; the last warp to do so refills it (next pass wraps)
-                __syncwarp();
-                if (lane == 0) {
-                    __threadfence_block();
-                    if (atomicAdd(&released[stage], 1) == int(qg / STAGES + 1) * CWARPS - 1) {
-                        __threadfence_block();
-                        if (qg + STAGES < total_q) issue(qg + STAGES);
-                    }
-                }
-                if (qg + STAGES < total_q) advance_pc();
-                fid = ff_add(fid, sf0 + sf1);
-
-                if (qg >= SLOTS &&
-                    !mbar_wait_or_abort(smem_u32(&rempty[slot]), uint32_t(((qg / SLOTS) - 1) & 1), abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                float* rbuf = red + (size_t(slot) * CWARPS + warp) * D * CW;
-#pragma unroll
-                for (int k = 0; k < D; ++k)
-#pragma unroll
-                    for (int c = 0; c < C; ++c) rbuf[k * CW + lane * C + c] = cacc0[c][k] + cacc1[c][k];
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&rfull[slot]));
-                if (q >= 1 && !reduce_share(qg - 1, cc.t - 1)) {
-                    ok = false;
-                    break;
-                }
-                const bool walk_ends = (cc.s + 1 == cc.L);
-                const bool last = (q + 1 == nq);
-                if (walk_ends || last) {
-                    float* dst = seg_head ? p.rowhead + (int64_t(cc.l) * p.nRB + cc.I) * (D * RB)
-                                          : p.rowcont + int64_t(b) * (D * RB);
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-#pragma unroll
-                        for (int k = 0; k < D; ++k) {
-                            const float v = warp_sum_f32(racc[r][k]);
-                            if (lane == ((r * D + k) & 31)) dst[k * RB + warp * R + r] = v;
-                        }
-                }
-                cursor_next(cc, p);
-                if (walk_ends && !last) {
-                    seg_head = true;
-                    load_rows(cc);
-                }
-            }
-            if (ok) ok = reduce_share(qbase + nq - 1, t_begin + nq - 1);
-            fid_total = ff_add(fid_total, ff_mul(fid, p.wfid[cur_l]));
-        }
+        if (!phase_a<D, TD>(rg, tm, p, Xprev, int64_t(t - 1) * nq, b, fid_total)) ok = false;
         if (!ok) atomicExch(&s_abort, 1);
         {
             const FF ws = warp_sum_ff(fid_total);
@@ -308,42 +133,18 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const PersistParams P) {
         }
 
         // ================================================================ phase B
-        float* Xprev = P.buf[(t - 1) % 3];
-        float* Xnext = P.buf[t % 3];
-        for (int g = b; g < P.ngroups; g += G) {
-            const int i = g * GOBJ + lane;
-            if (!final_pass)
-                for (int lk = warp; lk < m * D; lk += CWARPS) {
-                    const int l = lk / D, k = lk - l * D;
-                    s_bx[lk * GOBJ + lane] = (i < n) ? bx_partials(P.tb, l, k, i) : 0.f;
-                }
-            __syncthreads();
-            FF comm{0.f, 0.f};
-            for (int k = warp; k < D; k += CWARPS) {
-                float cm, xn[FJOFC_MAX_M];
-                mix_and_centre(Xprev, Xnext, m, n, D, i, k, t, final_pass, s_mu, P.coef, P.wcomm,
-                               s_bx + k * GOBJ + lane, D * GOBJ, &cm, xn);
-                comm = ff_add(comm, cm);
-                if (!final_pass)
-                    for (int j = 0; j < m; ++j) {
-                        const FF cs = warp_sum_ff(FF{xn[j], 0.f});
-                        if (lane == 0) s_part[j * D + k] = cs;
-                    }
-            }
-            const FF cw = warp_sum_ff(comm);
-            __syncthreads();
-            if (lane == 0) s_ff[warp] = cw;
-            __syncthreads();
-            if (tid == 0) {
-                FF tot{0.f, 0.f};
-                for (int w = 0; w < CWARPS; ++w) tot = ff_add(tot, s_ff[w]);
-                const int npart = m * D + 1;
-                for (int e = 0; e < m * D; ++e)
-                    P.bpart[int64_t(g) * npart + e] =
-                        final_pass ? make_float2(0.f, 0.f) : make_float2(s_part[e].hi, s_part[e].lo);
-                P.bpart[int64_t(g) * npart + m * D] = make_float2(tot.hi, tot.lo);
-            }
-            __syncthreads();
+        {
+            PhaseBArgs a;
+            a.tb = P.tb;
+            a.Xprev = Xprev;
+            a.Xnext = Xnext;
+            a.bpart = P.bpart;
+            a.mu_prev = s_mu;
+            a.coef = s_coef;
+            a.wcomm = s_wcomm;
+            a.m = m; a.n = n; a.d = D; a.t = t;
+            a.final_pass = final_pass;
+            phase_b(a, b, G, P.ngroups, bcap, s_phb);
         }
         bar_target += unsigned(G);
         if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag)) {
@@ -356,7 +157,7 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const PersistParams P) {
             // one warp per total: m*D column sums, commensurability, fidelity (all loads
             // of a lane in one round); the same order in every CTA
             const int npart = m * D + 1;
-            __shared__ FF s_tot[FJOFC_MAX_M * FJOFC_MAX_D + 2];
+            FF* s_tot = reinterpret_cast<FF*>(rg.red);   // [MAX_M*MAX_D + 2], ring is idle here
             for (int e = warp; e < npart + 1; e += CWARPS)
                 s_tot[e] = (e < npart) ? totals_ff(P.bpart + e, npart, P.ngroups)
                                        : totals_ff(P.fid2 + (t & 1) * G, 1, G);
@@ -405,11 +206,7 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const PersistParams P) {
     }
     __syncthreads();
     // wait (bounded) for the sub-tiles prefetched for passes that did not run
-    if (tid == 0) {
-        const int hi = s_issued;
-        for (int qq = (hi > STAGES ? hi - STAGES : 0); qq < hi; ++qq)
-            (void)mbar_wait_bounded(smem_u32(&full[qq % STAGES]), uint32_t((qq / STAGES) & 1));
-    }
+    if (tid == 0) rg.drain();
     // the returned iterate (centred in place by the pass that computed its stress) goes
     // to the caller's buffer
     if (ok) {

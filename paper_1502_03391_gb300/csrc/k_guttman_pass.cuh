@@ -15,10 +15,11 @@
 // one 2-D TMA (cp.async.bulk.tensor) into a STAGES-deep ring completed on mbarriers;
 // the last warp to finish reading a stage (shared-memory counter) issues its refill.
 // Warp w owns R consecutive rows of the row block (x_i and the row accumulators stay in
-// registers for the whole walk segment); lane owns C consecutive columns of every
-// sub-tile.  Column accumulators go through a small ring of shared-memory slots; each
-// warp reduces its share of the previous sub-tile's columns in a fixed order and writes
-// one partial per (sub-tile, column).  Row accumulators are reduced across the warp at
+// registers for the whole walk segment; the next walk's x_i are fetched one sub-tile
+// ahead); lane owns C consecutive columns of every sub-tile.  Column accumulators go
+// through a small ring of shared-memory slots; each warp reduces its share of the
+// previous sub-tile's columns in a fixed order and writes one partial per (sub-tile,
+// column).  Row accumulators are reduced across the warp (reduce-scatter butterfly) at
 // walk-segment ends.  Warps never meet at a CTA-wide barrier inside the loop; they
 // synchronise only through mbarriers and the stage counters, with one sub-tile of
 // slack.  K2 sums every partial in a fixed order, so results are bitwise reproducible
@@ -53,7 +54,7 @@ template <int D> struct K1Cfg;
 FJOFC_K1CFG_X(1, FJOFC_SMALLD)    // default: 128 x 128 sub-tile, 64 KB at float32
 FJOFC_K1CFG_X(2, FJOFC_SMALLD)
 FJOFC_K1CFG_X(3, FJOFC_SMALLD)
-FJOFC_K1CFG_X(4, FJOFC_SMALLD)
+FJOFC_K1CFG(4, 16, 4, 8, 2)       // two stages: three and the staged rows exceed 227 KB
 FJOFC_K1CFG(5, 8, 4, 8, 3)        // 64 x 128, 32 KB
 FJOFC_K1CFG(6, 8, 4, 8, 3)
 FJOFC_K1CFG(7, 8, 2, 8, 5)        // 64 x 64, 16 KB
@@ -81,7 +82,9 @@ struct K1Shape {
     static constexpr int STAGE_ELEMS = RB * CW;
     static constexpr uint32_t STAGE_BYTES = STAGE_ELEMS * sizeof(TD);
     static constexpr size_t RED_FLOATS = size_t(SLOTS) * CWARPS * D * CW;
+    static constexpr int XROW_FLOATS = CWARPS * R * D;   // staged x_i of the next walk
     static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + RED_FLOATS * sizeof(float) +
+                                   size_t(XROW_FLOATS) * sizeof(float) +
                                    size_t(STAGES + 2 * SLOTS) * 8 + size_t(STAGES) * 4 + 128;
 };
 
@@ -117,14 +120,17 @@ __device__ __forceinline__ void cursor_next(Cursor& c, const K1Params& p) {
     }
 }
 
-
 // The pairs of one RB x CW sub-tile owned by this thread: rows r0 + warp*R + r (x_i in
-// xi[r]), columns c0 + lane*C + c (x_j in xj[c]).  Adds b_ij (x_i - x_j) to racc[r], its
-// negative to the column accumulators (two interleaved chains by row parity) and
-// (s Delta_ij - d_ij)^2 to sf0/sf1.  MASKED: only pairs with i < j < n count (diagonal and
+// xi[r]), columns c0 + lane*C + c (x_j in xj[c]).  Coordinates come in pre-divided by the
+// modality's Delta scale s (x' = x / s, so d' = d / s and b = Delta'/d' = Delta/d).
+// Adds b_ij (x'_i - x'_j) to racc[r], its negative to the column accumulators (two
+// interleaved chains by row parity) and (Delta'_ij - d'_ij)^2 to sf0/sf1.  The squared
+// distance starts from FLT_MIN instead of 0: this changes no d^2 above 2^-102 and keeps
+// rsqrt finite when x_i = x_j (then b (x_i - x_j) = 0, the d_ij = 0 rule of Eq. B, and
+// the fidelity term is Delta'^2).  MASKED: only pairs with i < j < n count (diagonal and
 // ragged sub-tiles); otherwise every pair of the sub-tile is valid.
 template <int D, typename TD, int R, int C, int CW, bool MASKED>
-__device__ __forceinline__ void subtile_pairs(const TD* tile, int warp, int lane, int r0, int c0, int n, float sc,
+__device__ __forceinline__ void subtile_pairs(const TD* tile, int warp, int lane, int r0, int c0, int n,
                                               const float (&xi)[R][D], const float (&xj)[C][D],
                                               float (&racc)[R][D], float (&cacc0)[C][D], float (&cacc1)[C][D],
                                               float& sf0, float& sf1) {
@@ -142,15 +148,15 @@ __device__ __forceinline__ void subtile_pairs(const TD* tile, int warp, int lane
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             float diff[D];
-            float d2 = 0.f;
+            float d2 = FLT_MIN;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 diff[k] = xi[r][k] - xj[c][k];
                 d2 = fmaf(diff[k], diff[k], d2);
             }
-            const float rinv = rsqrt_approx(fmaxf(d2, FLT_MIN));
+            const float rinv = rsqrt_approx(d2);
             float bb = dl[c] * rinv;
-            float e = fmaf(sc, dl[c], -(d2 * rinv));
+            float e = fmaf(-d2, rinv, dl[c]);
             if (MASKED) {
                 const int j = c0 + lane * C + c;
                 const bool valid = (j > i) && (j < n);
@@ -168,225 +174,366 @@ __device__ __forceinline__ void subtile_pairs(const TD* tile, int warp, int lane
     }
 }
 
+// Sum of v[0..V-1] over the 32 lanes as a reduce-scatter butterfly: at each level a lane
+// keeps half of its values (or all of them when the count is odd) and adds its partner's.
+// On return v[0..F-1] holds the totals of indices base .. base+F-1, and exactly one lane
+// per index has writer == true.  Every total is formed by the same pairing tree as
+// warp_sum_f32 (partners xor 16, 8, 4, 2, 1), with V/2 + V/4 + ... shuffles instead of 5V.
+template <int V, int OFF>
+struct WarpScatter {
+    static __device__ __forceinline__ void run(float* v, int lane, int& base, bool& writer) {
+        if constexpr (OFF > 0) {
+            if constexpr (V % 2 == 0) {
+                constexpr int H = V / 2;
+                const bool up = (lane & OFF) != 0;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const float send = up ? v[h] : v[h + H];
+                    const float keep = up ? v[h + H] : v[h];
+                    v[h] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+                }
+                if (up) base += H;
+                WarpScatter<H, OFF / 2>::run(v, lane, base, writer);
+            } else {
+#pragma unroll
+                for (int h = 0; h < V; ++h) v[h] += __shfl_xor_sync(0xffffffffu, v[h], OFF);
+                if (lane & OFF) writer = false;
+                WarpScatter<V, OFF / 2>::run(v, lane, base, writer);
+            }
+        }
+    }
+};
+template <int V, int OFF>
+struct WarpScatterCount {
+    static constexpr int value = OFF == 0 ? V : (V % 2 == 0 ? WarpScatterCount<V / 2, OFF / 2>::value
+                                                            : WarpScatterCount<V, OFF / 2>::value);
+};
+template <int V>
+struct WarpScatterCount<V, 0> {
+    static constexpr int value = V;
+};
+
+// Staging of the next walk's x_i: plain L2 loads (ld.global.cg; the iterate may have been
+// written earlier in the same launch) issued one sub-tile ahead into PER_LANE registers,
+// stored to this warp's shared-memory rows when the walk changes.
+template <int R, int D>
+struct RowStage {
+    static constexpr int PER_LANE = (R * D + 31) / 32;
+    float v[PER_LANE];
+};
+
+// Shared-memory carve-up and TMA ring state of one CTA of the all-pairs pass.  The ring
+// runs over a global sequence qg = 0, 1, ... of sub-tile uses; use qg is sub-tile
+// t_begin + (qg mod nq) of the CTA's range (the range repeats every pass).
+template <int D, typename TD>
+struct K1Ring {
+    using S = K1Shape<D, TD>;
+    TD* stages;
+    float* red;            // [SLOTS][CWARPS][D][CW] column accumulators
+    float* xrow;           // [CWARPS][R*D]          staged rows of the next walk
+    uint64_t* full;        // [STAGES]
+    uint64_t* rfull;       // [SLOTS]
+    uint64_t* rempty;      // [SLOTS]
+    int* released;         // [STAGES] releases so far (monotone)
+    int* issued;           // ring uses issued so far
+    int* abort_flag;       // set by a warp whose bounded wait gave up
+    Cursor pc;             // cursor of the next use to issue (every thread keeps a copy)
+    int pc_local;
+    int64_t t_begin;
+    int nq;
+    int64_t total_q;
+
+    __device__ __forceinline__ void carve(unsigned char* smem_raw) {
+        unsigned char* smem = reinterpret_cast<unsigned char*>(
+            (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+        stages = reinterpret_cast<TD*>(smem);
+        red = reinterpret_cast<float*>(smem + size_t(S::STAGES) * S::STAGE_BYTES);
+        xrow = red + S::RED_FLOATS;
+        full = reinterpret_cast<uint64_t*>(xrow + S::XROW_FLOATS);
+        rfull = full + S::STAGES;
+        rempty = rfull + S::SLOTS;
+        released = reinterpret_cast<int*>(rempty + S::SLOTS);
+    }
+
+    __device__ __forceinline__ void issue(const TMaps& tm, int64_t qg) {
+        const int stage = int(qg % S::STAGES);
+        atomicMax(issued, int(qg + 1));
+        const uint32_t bar = smem_u32(&full[stage]);
+        mbar_arrive_expect_tx(bar, S::STAGE_BYTES);
+        tma_load_2d(smem_u32(stages + size_t(stage) * S::STAGE_ELEMS), &tm.map[pc.l],
+                    pc.I * S::RB + pc.s * S::CW, pc.I * S::RB, bar);
+    }
+
+    __device__ __forceinline__ void advance(const K1Params& p) {
+        if (++pc_local == nq) {
+            pc_local = 0;
+            cursor_init(pc, t_begin, p);
+        } else {
+            cursor_next(pc, p);
+        }
+    }
+
+    // Barrier set-up and the first STAGES uses (thread 0 issues; every thread advances its
+    // cursor copy).  Ends with __syncthreads.
+    __device__ __forceinline__ void start(const TMaps& tm, const K1Params& p, int64_t t_begin_, int nq_,
+                                          int64_t total_q_, int* issued_, int* abort_) {
+        issued = issued_;
+        abort_flag = abort_;
+        t_begin = t_begin_;
+        nq = nq_;
+        total_q = total_q_;
+        pc_local = 0;
+        cursor_init(pc, t_begin, p);
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < S::STAGES; ++s) {
+                mbar_init(smem_u32(&full[s]), 1);
+                released[s] = 0;
+            }
+            for (int s = 0; s < S::SLOTS; ++s) {
+                mbar_init(smem_u32(&rfull[s]), S::CWARPS);
+                mbar_init(smem_u32(&rempty[s]), S::CWARPS);
+            }
+            *abort_flag = 0;
+            *issued = 0;
+            fence_barrier_init();
+            for (int l = 0; l < p.m; ++l) tma_prefetch_desc(&tm.map[l]);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int64_t q = 0; q < S::STAGES && q < total_q; ++q) {
+                issue(tm, q);
+                advance(p);
+            }
+        else
+            for (int64_t q = 0; q < S::STAGES && q < total_q; ++q) advance(p);
+        __syncthreads();
+    }
+
+    // After an abort: wait (bounded) for the copies that may still be in flight, the most
+    // recent use of every stage.  Thread 0 only.
+    __device__ __forceinline__ void drain() {
+        const int hi = *issued;
+        for (int qq = (hi > S::STAGES ? hi - S::STAGES : 0); qq < hi; ++qq)
+            (void)mbar_wait_bounded(smem_u32(&full[qq % S::STAGES]), uint32_t((qq / S::STAGES) & 1));
+    }
+};
+
+// One all-pairs pass over the CTA's range (ring uses qbase .. qbase + nq - 1) against the
+// iterate X.  Writes the column partials of every sub-tile, the row partials of every
+// walk segment and returns this thread's weighted fidelity in fid_total.  Returns false
+// if a bounded wait gave up (the caller raises the error and drains the ring).
+template <int D, typename TD>
+__device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, const K1Params& p, const float* X,
+                                        int64_t qbase, int b, FF& fid_total) {
+    using S = K1Shape<D, TD>;
+    constexpr int R = S::R, C = S::C, CWARPS = S::CWARPS, STAGES = S::STAGES, SLOTS = S::SLOTS;
+    constexpr int RB = S::RB, CW = S::CW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = p.n, nq = rg.nq;
+    const volatile int* abort_flag = rg.abort_flag;
+    fid_total = FF{0.f, 0.f};
+
+    Cursor cc, cn;
+    cursor_init(cc, rg.t_begin, p);
+    cn = cc;
+    bool seg_head = (cc.s == 0);
+    float xi[R][D], racc[R][D], xjn[C][D];
+    {
+        const float* Xl = X + int64_t(cc.l) * n * D;
+        const float xs = p.xscale[cc.l];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = cc.I * RB + warp * R + r;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                xi[r][k] = (i < n) ? __ldcg(Xl + int64_t(i) * D + k) * xs : 0.f;
+                racc[r][k] = 0.f;
+            }
+        }
+    }
+    auto load_cols = [&](const Cursor& c) {
+        const float* Xl = X + int64_t(c.l) * n * D;
+        const float xs = p.xscale[c.l];
+        const int c0 = c.I * RB + c.s * CW + lane * C;
+#pragma unroll
+        for (int ci = 0; ci < C; ++ci)
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                xjn[ci][k] = (c0 + ci < n) ? __ldcg(Xl + int64_t(c0 + ci) * D + k) * xs : 0.f;
+    };
+    load_cols(cn);
+    FF fid{0.f, 0.f};
+    int cur_l = cc.l;
+    float* xrow = rg.xrow + warp * (R * D);
+
+    // reduce this warp's share of the columns of ring use qg (deferred by one sub-tile)
+    auto reduce_share = [&](int64_t qg, int64_t tglob) -> bool {
+        const int slot = int(qg % SLOTS);
+        if (!mbar_wait_or_abort(smem_u32(&rg.rfull[slot]), uint32_t((qg / SLOTS) & 1), abort_flag)) return false;
+        const float* rb = rg.red + size_t(slot) * CWARPS * D * CW;
+        float* cp = p.colpart + tglob * int64_t(D * CW);
+        constexpr int SHARE = (D * CW + CWARPS - 1) / CWARPS;
+        for (int e = warp * SHARE + lane; e < (warp + 1) * SHARE && e < D * CW; e += 32) {
+            float v = 0.f;
+#pragma unroll
+            for (int w = 0; w < CWARPS; ++w) v += rb[w * D * CW + e];
+            cp[e] = v;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&rg.rempty[slot]));
+        return true;
+    };
+
+    for (int q = 0; q < nq; ++q) {
+        const int64_t qg = qbase + q;
+        const int stage = int(qg % STAGES);
+        const int slot = int(qg % SLOTS);
+        const int r0 = cc.I * RB;
+        const int c0 = r0 + cc.s * CW;
+        const bool walk_ends = (cc.s + 1 == cc.L);
+        const bool last = (q + 1 == nq);
+        float xj[C][D];
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int k = 0; k < D; ++k) xj[c][k] = xjn[c][k];
+        if (!last) {                // prefetch the next sub-tile's columns
+            cursor_next(cn, p);
+            load_cols(cn);
+        }
+        RowStage<R, D> rs;          // the next walk's rows, in flight during this sub-tile
+        if (walk_ends && !last) {
+            const float* src = X + (int64_t(cn.l) * n + int64_t(cn.I) * RB + warp * R) * D;
+            const int lim = (n - (cn.I * RB + warp * R)) * D;    // elements inside the modality
+#pragma unroll
+            for (int u = 0; u < RowStage<R, D>::PER_LANE; ++u) {
+                const int e = u * 32 + lane;
+                rs.v[u] = (e < R * D && e < lim) ? __ldcg(src + e) : 0.f;
+            }
+        }
+        if (cc.l != cur_l) {        // modality changed inside this CTA's range
+            fid_total = ff_add(fid_total, ff_mul(fid, p.wfid[cur_l]));
+            fid = FF{0.f, 0.f};
+            cur_l = cc.l;
+        }
+
+        if (!mbar_wait_or_abort(smem_u32(&rg.full[stage]), uint32_t((qg / STAGES) & 1), abort_flag)) return false;
+        const TD* tile = rg.stages + size_t(stage) * S::STAGE_ELEMS;
+        const bool masked = (cc.s * CW < RB) || (c0 + CW > n);
+        float cacc0[C][D], cacc1[C][D];
+        float sf0, sf1;
+        if (!masked)
+            subtile_pairs<D, TD, R, C, CW, false>(tile, warp, lane, r0, c0, n, xi, xj, racc, cacc0, cacc1, sf0, sf1);
+        else
+            subtile_pairs<D, TD, R, C, CW, true>(tile, warp, lane, r0, c0, n, xi, xj, racc, cacc0, cacc1, sf0, sf1);
+        // release the stage; the last warp to do so refills it with use qg + STAGES
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            // use k = qg / STAGES of this stage is fully released at count (k+1)*CWARPS
+            if (atomicAdd(&rg.released[stage], 1) == int(qg / STAGES + 1) * CWARPS - 1) {
+                __threadfence_block();
+                if (qg + STAGES < rg.total_q) rg.issue(tm, qg + STAGES);
+            }
+        }
+        if (qg + STAGES < rg.total_q) rg.advance(p);
+        fid = ff_add(fid, sf0 + sf1);
+
+        // column partials of this sub-tile into its ring slot
+        if (qg >= SLOTS &&
+            !mbar_wait_or_abort(smem_u32(&rg.rempty[slot]), uint32_t(((qg / SLOTS) - 1) & 1), abort_flag))
+            return false;
+        float* rbuf = rg.red + (size_t(slot) * CWARPS + warp) * D * CW;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if constexpr (C % 4 == 0) {
+#pragma unroll
+                for (int c = 0; c < C; c += 4)
+                    *reinterpret_cast<float4*>(rbuf + k * CW + lane * C + c) =
+                        make_float4(cacc0[c][k] + cacc1[c][k], cacc0[c + 1][k] + cacc1[c + 1][k],
+                                    cacc0[c + 2][k] + cacc1[c + 2][k], cacc0[c + 3][k] + cacc1[c + 3][k]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < C; ++c) rbuf[k * CW + lane * C + c] = cacc0[c][k] + cacc1[c][k];
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&rg.rfull[slot]));
+        if (q >= 1 && !reduce_share(qg - 1, cc.t - 1)) return false;
+
+        if (walk_ends || last) {
+            // row partials of this walk segment: reduce-scatter over the warp
+            float* dst = seg_head ? p.rowhead + (int64_t(cc.l) * p.nRB + cc.I) * (D * RB)
+                                  : p.rowcont + int64_t(b) * (D * RB);
+            float v[R * D];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int k = 0; k < D; ++k) v[r * D + k] = racc[r][k];
+            int base = 0;
+            bool writer = true;
+            WarpScatter<R * D, 16>::run(v, lane, base, writer);
+            constexpr int F = WarpScatterCount<R * D, 16>::value;
+            if (writer)
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    const int e = base + f, r = e / D, k = e - r * D;
+                    dst[k * RB + warp * R + r] = v[f];
+                }
+        }
+        cursor_next(cc, p);
+        if (walk_ends && !last) {
+            seg_head = true;
+            const float xs = p.xscale[cc.l];
+#pragma unroll
+            for (int u = 0; u < RowStage<R, D>::PER_LANE; ++u) {
+                const int e = u * 32 + lane;
+                if (e < R * D) xrow[e] = rs.v[u] * xs;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    xi[r][k] = xrow[r * D + k];
+                    racc[r][k] = 0.f;
+                }
+            __syncwarp();
+        }
+    }
+    if (!reduce_share(qbase + nq - 1, rg.t_begin + nq - 1)) return false;
+    fid_total = ff_add(fid_total, ff_mul(fid, p.wfid[cur_l]));
+    return true;
+}
+
+// Standalone pass (one launch per Guttman transform, used when the persistent kernel is
+// not: per-kernel timing).  Same ring, tiles and partials as the persistent kernel.
 template <int D, typename TD>
 __global__ void __launch_bounds__(K1Shape<D, TD>::NT, 1)
 k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
     using S = K1Shape<D, TD>;
-    constexpr int R = S::R, C = S::C, CWARPS = S::CWARPS, STAGES = S::STAGES, SLOTS = S::SLOTS;
-    constexpr int RB = S::RB, CW = S::CW;
-
+    constexpr int CWARPS = S::CWARPS;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    TD* stages = reinterpret_cast<TD*>(smem);
-    float* red = reinterpret_cast<float*>(smem + size_t(STAGES) * S::STAGE_BYTES);   // [SLOTS][CWARPS][D][CW]
-    uint64_t* full = reinterpret_cast<uint64_t*>(red + S::RED_FLOATS);
-    uint64_t* rfull = full + STAGES;
-    uint64_t* rempty = rfull + SLOTS;
-    int* released = reinterpret_cast<int*>(rempty + SLOTS);       // [STAGES] releases so far (monotone)
     __shared__ FF s_redff[CWARPS];
-    __shared__ int s_abort;
-    __shared__ int s_issued;                                       // sub-tiles issued so far
-
+    __shared__ int s_abort, s_issued;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b = blockIdx.x;
 
     if (ld_volatile(&p.st->done)) return;   // the loop has stopped: nothing to compute
 
-    const int64_t t_begin = int64_t(b) * p.T / p.G;
-    const int64_t t_end = int64_t(b + 1) * p.T / p.G;
-    const int nq = static_cast<int>(t_end - t_begin);   // >= 1 because G <= T
+    K1Ring<D, TD> rg;
+    rg.carve(smem_raw);
+    const int64_t t_begin = p.cta_start[b];
+    const int nq = static_cast<int>(p.cta_start[b + 1] - t_begin);   // >= 1 because G <= T
+    rg.start(tm, p, t_begin, nq, nq, &s_issued, &s_abort);
 
-    auto issue = [&](int q, const Cursor& c) {
-        const int stage = q % STAGES;
-        atomicMax(&s_issued, q + 1);
-        const uint32_t bar = smem_u32(&full[stage]);
-        mbar_arrive_expect_tx(bar, S::STAGE_BYTES);
-        tma_load_2d(smem_u32(stages + size_t(stage) * S::STAGE_ELEMS), &tm.map[c.l], c.I * RB + c.s * CW,
-                    c.I * RB, bar);
-    };
-
-    Cursor pc;   // cursor of the sub-tile STAGES ahead (every warp keeps its own copy)
-    cursor_init(pc, t_begin, p);
-    if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(smem_u32(&full[s]), 1);
-            released[s] = 0;
-        }
-        for (int s = 0; s < SLOTS; ++s) {
-            mbar_init(smem_u32(&rfull[s]), CWARPS);
-            mbar_init(smem_u32(&rempty[s]), CWARPS);
-        }
-        s_abort = 0;
-        s_issued = 0;
-        fence_barrier_init();
-        for (int l = 0; l < p.m; ++l) tma_prefetch_desc(&tm.map[l]);
-        Cursor c0 = pc;
-        for (int q = 0; q < STAGES && q < nq; ++q) {
-            issue(q, c0);
-            cursor_next(c0, p);
-        }
-    }
-    for (int q = 0; q < STAGES && q < nq; ++q) cursor_next(pc, p);
-    __syncthreads();
-    const volatile int* abort_flag = &s_abort;
     FF fid_total{0.f, 0.f};
-
-    {
-        // ------------------------------------------------------------ compute
-        const int n = p.n;
-        Cursor cc, cn;
-        cursor_init(cc, t_begin, p);
-        cn = cc;
-        bool seg_head = (cc.s == 0);
-        float xi[R][D], racc[R][D];
-        auto load_rows = [&](const Cursor& c) {
-            const float* Xl = p.X + int64_t(c.l) * n * D;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int i = c.I * RB + warp * R + r;
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    xi[r][k] = (i < n) ? __ldg(Xl + int64_t(i) * D + k) : 0.f;
-                    racc[r][k] = 0.f;
-                }
-            }
-        };
-        float xjn[C][D];
-        auto load_cols = [&](const Cursor& c) {
-            const float* Xl = p.X + int64_t(c.l) * n * D;
-            const int c0 = c.I * RB + c.s * CW + lane * C;
-#pragma unroll
-            for (int cidx = 0; cidx < C; ++cidx)
-#pragma unroll
-                for (int k = 0; k < D; ++k)
-                    xjn[cidx][k] = (c0 + cidx < n) ? __ldg(Xl + int64_t(c0 + cidx) * D + k) : 0.f;
-        };
-        load_rows(cc);
-        load_cols(cn);
-        FF fid{0.f, 0.f};          // fidelity of the current modality (float-float)
-        int cur_l = cc.l;
-
-        // reduce this warp's share of the columns of sub-tile qq (deferred by one)
-        auto reduce_share = [&](int qq) -> bool {
-            const int slot = qq % SLOTS;
-            if (!mbar_wait_or_abort(smem_u32(&rfull[slot]), uint32_t((qq / SLOTS) & 1), abort_flag)) return false;
-            const float* rb = red + size_t(slot) * CWARPS * D * CW;
-            float* cp = p.colpart + (t_begin + qq) * int64_t(D * CW);
-            constexpr int SHARE = (D * CW + CWARPS - 1) / CWARPS;
-            for (int e = warp * SHARE + lane; e < (warp + 1) * SHARE && e < D * CW; e += 32) {
-                float v = 0.f;
-#pragma unroll
-                for (int w = 0; w < CWARPS; ++w) v += rb[w * D * CW + e];
-                cp[e] = v;
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&rempty[slot]));
-            return true;
-        };
-
-        bool ok = true;
-        for (int q = 0; q < nq && ok; ++q) {
-            const int stage = q % STAGES;
-            const int slot = q % SLOTS;
-            const int r0 = cc.I * RB;
-            const int c0 = r0 + cc.s * CW;
-            float xj[C][D];
-#pragma unroll
-            for (int c = 0; c < C; ++c)
-#pragma unroll
-                for (int k = 0; k < D; ++k) xj[c][k] = xjn[c][k];
-            if (q + 1 < nq) {           // prefetch the next sub-tile's columns
-                cursor_next(cn, p);
-                load_cols(cn);
-            }
-            if (cc.l != cur_l) {        // modality changed inside this CTA's range
-                fid_total = ff_add(fid_total, ff_mul(fid, p.wfid[cur_l]));
-                fid = FF{0.f, 0.f};
-                cur_l = cc.l;
-            }
-            const float sc = p.dscale[cc.l];
-
-            if (!mbar_wait_or_abort(smem_u32(&full[stage]), uint32_t((q / STAGES) & 1), abort_flag)) {
-                ok = false;
-                break;
-            }
-            const TD* tile = stages + size_t(stage) * S::STAGE_ELEMS;
-            const bool masked = (cc.s * CW < RB) || (c0 + CW > n);
-            float cacc0[C][D], cacc1[C][D];
-            float sf0, sf1;
-            if (!masked)
-                subtile_pairs<D, TD, R, C, CW, false>(tile, warp, lane, r0, c0, n, sc, xi, xj, racc, cacc0, cacc1, sf0, sf1);
-            else
-                subtile_pairs<D, TD, R, C, CW, true>(tile, warp, lane, r0, c0, n, sc, xi, xj, racc, cacc0, cacc1, sf0, sf1);
-            // release the stage; the last warp to do so refills it with sub-tile q + STAGES
-            __syncwarp();
-            if (lane == 0) {
-                __threadfence_block();
-                // use k = q / STAGES of this stage is fully released at count (k+1)*CWARPS
-                if (atomicAdd(&released[stage], 1) == (q / STAGES + 1) * CWARPS - 1) {
-                    __threadfence_block();
-                    if (q + STAGES < nq) issue(q + STAGES, pc);
-                }
-            }
-            if (q + STAGES < nq) cursor_next(pc, p);
-            fid = ff_add(fid, sf0 + sf1);
-
-            // column partials of this sub-tile into its ring slot
-            if (q >= SLOTS &&
-                !mbar_wait_or_abort(smem_u32(&rempty[slot]), uint32_t(((q / SLOTS) - 1) & 1), abort_flag)) {
-                ok = false;
-                break;
-            }
-            float* rb = red + (size_t(slot) * CWARPS + warp) * D * CW;
-#pragma unroll
-            for (int k = 0; k < D; ++k)
-#pragma unroll
-                for (int c = 0; c < C; ++c) rb[k * CW + lane * C + c] = cacc0[c][k] + cacc1[c][k];
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&rfull[slot]));
-
-            if (q >= 1 && !reduce_share(q - 1)) {
-                ok = false;
-                break;
-            }
-
-            const bool walk_ends = (cc.s + 1 == cc.L);
-            const bool last = (q + 1 == nq);
-            if (walk_ends || last) {
-                // row partials of this walk segment: full-warp sum of each accumulator
-                float* dst = seg_head
-                    ? p.rowhead + (int64_t(cc.l) * p.nRB + cc.I) * (D * RB)
-                    : p.rowcont + int64_t(b) * (D * RB);
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        const float v = warp_sum_f32(racc[r][k]);
-                        if (lane == ((r * D + k) & 31)) dst[k * RB + warp * R + r] = v;
-                    }
-            }
-            cursor_next(cc, p);
-            if (walk_ends && !last) {
-                seg_head = true;
-                load_rows(cc);
-            }
-        }
-        if (ok) ok = reduce_share(nq - 1);
-        if (!ok) {
-            atomicExch(&s_abort, 1);
-            if (lane == 0) raise_error(p.st, FJOFC_ERR_TIMEOUT, 2);
-        }
-        fid_total = ff_add(fid_total, ff_mul(fid, p.wfid[cur_l]));
+    if (!phase_a<D, TD>(rg, tm, p, p.X, 0, b, fid_total)) {
+        atomicExch(&s_abort, 1);
+        if (lane == 0) raise_error(p.st, FJOFC_ERR_TIMEOUT, 2);
     }
     __syncthreads();
-    if (*abort_flag && tid == 0) {
-        // wait (bounded) for the copies this CTA may still have in flight: the most
-        // recent use of every stage
-        const int hi = s_issued;
-        for (int qq = (hi > STAGES ? hi - STAGES : 0); qq < hi; ++qq)
-            (void)mbar_wait_bounded(smem_u32(&full[qq % STAGES]), uint32_t((qq / STAGES) & 1));
-    }
+    if (s_abort && tid == 0) rg.drain();
 
     // fidelity partial of this CTA (fixed-order float-float reduction)
     const FF ws = warp_sum_ff(fid_total);
