@@ -426,6 +426,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     k2.Tm = P.Tm; k2.T = P.T;
     k2.tol_mode = o.tol_mode; k2.tol = o.tol;
     k2.npairs = double(m * n) * double(m * n - 1) / 2.0;
+    k2.inv_n = float(1.0 / double(n));
     for (int j = 0; j < m; ++j)
         for (int l = 0; l < m; ++l) {
             k2.coef[j][l] = float(winv[j * m + l] * weights[l * m + l] * dsc[l]);
@@ -473,7 +474,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         pp.hist = hist;
         pp.ngroups = P.nbx;
         pp.rb_shift = k2.rb_shift; pp.cw_shift = k2.cw_shift;
-        pp.max_iter = o.max_iter; pp.tol_mode = o.tol_mode; pp.tol = o.tol; pp.npairs = k2.npairs;
+        pp.max_iter = o.max_iter; pp.tol_mode = o.tol_mode; pp.tol = o.tol; pp.npairs = k2.npairs; pp.inv_n = k2.inv_n;
         for (int j = 0; j < FJOFC_MAX_M; ++j)
             for (int l = 0; l < FJOFC_MAX_M; ++l) { pp.coef[j][l] = k2.coef[j][l]; pp.wcomm[j][l] = k2.wcomm[j][l]; }
         pp.tb = k2.tb;

@@ -88,6 +88,7 @@ struct K2Params {
     int final_pass;            // 1: only sigma(X_{t-1}) and the centring
     int tol_mode;
     double tol, npairs;        // tolerance, C(mn,2)
+    float inv_n;               // 1 / n (column means)
     float coef[FJOFC_MAX_M][FJOFC_MAX_M];    // [Wmod^-1]_{jl} * w_ll * s_l
     float wcomm[FJOFC_MAX_M][FJOFC_MAX_M];   // w_jl for j < l, else 0
     BxTables tb;
@@ -109,6 +110,7 @@ struct PersistParams {
     int rb_shift, cw_shift;
     int max_iter, tol_mode;
     double tol, npairs;
+    float inv_n;
     float coef[FJOFC_MAX_M][FJOFC_MAX_M];
     float wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
     BxTables tb;

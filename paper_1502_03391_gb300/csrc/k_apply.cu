@@ -73,9 +73,7 @@ k_apply(const K2Params p) {
     for (int e = warp; e < npart + 1; e += K2_THREADS / 32)
         s_tot[e] = (e < npart) ? totals_ff(p.bpart + e, npart, int(gridDim.x)) : totals_ff(p.fid, 1, p.G);
     __syncthreads();
-    if (tid == 0)
-        for (int e = 0; e < m * d; ++e)
-            mu_next[(e / d) * FJOFC_MAX_D + (e % d)] = (s_tot[e].hi + s_tot[e].lo) / float(n);
+    if (tid < m * d) mu_next[(tid / d) * FJOFC_MAX_D + (tid % d)] = (s_tot[tid].hi + s_tot[tid].lo) * p.inv_n;
     const FF comm_tot = s_tot[npart - 1], fid_tot = s_tot[npart];
 
     if (tid == 0) {
@@ -94,7 +92,7 @@ k_apply(const K2Params p) {
                 const double prev = p.hist[tp - 1];
                 const double dec = prev - sigma;
                 const bool cont = (p.tol_mode == FJOFC_TOL_RELATIVE) ? (dec > p.tol * prev)
-                                                                     : (dec / p.npairs > p.tol);
+                                                                     : (dec > p.tol * p.npairs);
                 stop = !cont;
             }
             if (stop) st->done = 1;
@@ -112,9 +110,23 @@ cudaError_t launch_k2(const K2Params& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Per-call initialisation: status block, ticket, mu_0 = 0, walk offsets.
-__global__ void k_init(const InitParams p) {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+// Per-call initialisation (one CTA of kInitThreads): status block, ticket, mu_0 = 0, then
+//   walk_off[P]  = sub-tiles before walk position P (prefix sums of the walk lengths),
+//   cta_start[b] = first sub-tile of CTA b (b*T/G),
+//   cbase[I]     = first sub-tile (within a modality) of row block I's walk,
+//   cont[l][I]   = the CTAs whose range starts strictly inside that walk.
+// Each step reads only what earlier steps of this CTA wrote (global memory, ordered by
+// __syncthreads).
+constexpr int kInitThreads = 1024;
+
+__device__ __forceinline__ int64_t walk_len(int P, const InitParams& p) {
+    const int64_t cols = int64_t(p.n) - int64_t(walk_row(P, p.nRB)) * p.RB;
+    return (cols + p.CW - 1) / p.CW;
+}
+
+__global__ void __launch_bounds__(kInitThreads) k_init(const InitParams p) {
+    __shared__ int64_t s_part[kInitThreads];
+    const int tid = threadIdx.x;
     if (tid == 0) {
         p.st->done = 0;
         p.st->error = 0;
@@ -124,38 +136,62 @@ __global__ void k_init(const InitParams p) {
         *p.ticket = 0u;
         if (p.bar) *p.bar = 0u;
     }
-    for (int e = tid; e < 2 * FJOFC_MAX_M * FJOFC_MAX_D; e += gridDim.x * blockDim.x) p.mu[e] = 0.f;
-    for (int b = tid; b <= p.G; b += gridDim.x * blockDim.x) p.cta_start[b] = int64_t(b) * p.T / p.G;
-    auto walk_start = [&](int P) {           // prefix sum of the walk lengths before position P
-        int64_t s = 0;
-        for (int Q = 0; Q < P; ++Q) {
-            const int64_t cols = int64_t(p.n) - int64_t(walk_row(Q, p.nRB)) * p.RB;
-            s += (cols + p.CW - 1) / p.CW;
+    for (int e = tid; e < 2 * FJOFC_MAX_M * FJOFC_MAX_D; e += kInitThreads) p.mu[e] = 0.f;
+
+    // walk_off: block scan over contiguous chunks of positions
+    const int per = (p.nRB + kInitThreads - 1) / kInitThreads;
+    const int P0 = tid * per, P1 = min(P0 + per, p.nRB);
+    int64_t local = 0;
+    for (int P = P0; P < P1; ++P) local += walk_len(P, p);
+    s_part[tid] = local;
+    __syncthreads();
+    if (tid == 0) {
+        int64_t run = 0;
+        for (int e = 0; e < kInitThreads; ++e) {
+            const int64_t v = s_part[e];
+            s_part[e] = run;
+            run += v;
         }
-        return s;
-    };
-    for (int P = tid; P <= p.nRB; P += gridDim.x * blockDim.x) p.walk_off[P] = walk_start(P);
-    for (int e = tid; e < p.m * p.nRB; e += gridDim.x * blockDim.x) {
+    }
+    __syncthreads();
+    {
+        int64_t run = s_part[tid];
+        for (int P = P0; P < P1; ++P) {
+            p.walk_off[P] = run;
+            run += walk_len(P, p);
+        }
+        if (P1 == p.nRB && P0 < P1) p.walk_off[p.nRB] = run;
+    }
+    __syncthreads();
+
+    for (int b = tid; b <= p.G; b += kInitThreads) p.cta_start[b] = int64_t(b) * p.T / p.G;
+    __syncthreads();
+
+    // row-block tables
+    for (int e = tid; e < p.m * p.nRB; e += kInitThreads) {
         const int l = e / p.nRB, I = e - l * p.nRB;
-        const int64_t base = walk_start(walk_pos(I, p.nRB));
+        const int64_t base = p.walk_off[walk_pos(I, p.nRB)];
         if (l == 0) p.cbase[I] = base;
-        // CTAs b whose first sub-tile b*T/G lies strictly inside the walk [ws, we)
         const int64_t ws = int64_t(l) * p.Tm + base;
-        const int64_t we = ws + (int64_t(p.n) - int64_t(I) * p.RB + p.CW - 1) / p.CW;
-        int64_t lo = ((ws + 1) * p.G + p.T - 1) / p.T;
-        int64_t hi = (we * p.G + p.T - 1) / p.T;
-        if (hi > p.G) hi = p.G;
-        if (lo > hi) lo = hi;
-        p.cont[e] = make_int2(int(lo), int(hi));
+        const int64_t we = ws + walk_len(walk_pos(I, p.nRB), p);
+        // [lo, hi): CTAs b with ws < cta_start[b] < we
+        int lo = 0, hi = p.G;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (p.cta_start[mid] > ws) hi = mid; else lo = mid + 1;
+        }
+        const int c_lo = lo;
+        lo = c_lo; hi = p.G;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (p.cta_start[mid] >= we) hi = mid; else lo = mid + 1;
+        }
+        p.cont[e] = make_int2(c_lo, lo);
     }
 }
 
 cudaError_t launch_init(const InitParams& p, cudaStream_t s) {
-    const int threads = 256;
-    int mx = (p.nRB > p.G ? p.nRB : p.G) + 1;
-    if (p.m * p.nRB > mx) mx = p.m * p.nRB;
-    const int blocks = (mx + threads - 1) / threads;
-    k_init<<<blocks, threads, 0, s>>>(p);
+    k_init<<<1, kInitThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

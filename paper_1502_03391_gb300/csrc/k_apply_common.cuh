@@ -4,8 +4,7 @@
 //
 // Objects are handled in groups of 32 (lane = object).  For every group g the CTA
 //   1. sums (B'_l X_l)_{i,k} for all (l, k) from the K1 partials and stages x_{t-1} of the
-//      group in shared memory (one warp per (l, k) unit; every load of a unit is issued
-//      before the first add, so a unit costs one L2 round trip),
+//      group in shared memory (one warp per (l, k) unit),
 //   2. per coordinate k (one warp each): centres X_{t-1} with the previous pass's means,
 //      forms its commensurability, mixes X_t^(j) = sum_l coef[j][l] (B'_l X_l) and writes
 //      the float-float column sums of X_t -> bpart[g][j*d + k],
@@ -17,43 +16,32 @@
 namespace fjofc {
 
 constexpr int kGroupObjects = 32;
-constexpr int kBxBatch = 64;     // column partials issued per round
-constexpr int kBxConts = 4;      // continuation partials issued with them
+constexpr int kBxBatch = 16;     // column partials in flight per lane
 
 // (B'_l X_l)_{i,k}: the walk-head row partial of object i, the continuation row partials
 // in CTA order, then the column partials of the walks of row blocks 0..I(i) in order.
 // Data written earlier in the same launch is read through L2 (ld.global.cg); the tables
-// are read-only for the whole launch (ld.global.nc).
+// are read-only for the whole launch (ld.global.nc).  This code runs once per pass after
+// the long all-pairs loop, so it is kept small (rolled loops) to limit instruction-cache
+// refills; kBxBatch loads are issued before their sum.
 __device__ __forceinline__ float bx_sum(const BxTables& tb, int l, int k, int i) {
     const int d = tb.d, RB = tb.RB, CW = tb.CW, rbs = tb.rb_shift, cws = tb.cw_shift, nRB = tb.nRB;
     const int I = i >> rbs, ri = i & (RB - 1);
     const int2 cr = __ldg(tb.cont + int64_t(l) * nRB + I);
     const float* cp = tb.colpart + int64_t(l) * tb.Tm * d * CW;
-    auto col = [&](int J) {
-        const int rel = i - (J << rbs);
-        return __ldcg(cp + ((__ldg(tb.cbase + J) + (rel >> cws)) * d + k) * CW + (rel & (CW - 1)));
-    };
-    // first round: head, up to kBxConts continuations, up to kBxBatch column partials
-    const float head = __ldcg(tb.rowhead + ((int64_t(l) * nRB + I) * d + k) * RB + ri);
-    float cv[kBxConts];
-#pragma unroll
-    for (int u = 0; u < kBxConts; ++u)
-        cv[u] = (cr.x + u < cr.y) ? __ldcg(tb.rowcont + (int64_t(cr.x + u) * d + k) * RB + ri) : 0.f;
-    float v[kBxBatch];
-#pragma unroll
-    for (int u = 0; u < kBxBatch; ++u) v[u] = (u <= I) ? col(u) : 0.f;
-
-    float acc = head;
-#pragma unroll
-    for (int u = 0; u < kBxConts; ++u)
-        if (cr.x + u < cr.y) acc += cv[u];
-    for (int b = cr.x + kBxConts; b < cr.y; ++b) acc += __ldcg(tb.rowcont + (int64_t(b) * d + k) * RB + ri);
+    float acc = __ldcg(tb.rowhead + ((int64_t(l) * nRB + I) * d + k) * RB + ri);
+#pragma unroll 1
+    for (int b = cr.x; b < cr.y; ++b) acc += __ldcg(tb.rowcont + (int64_t(b) * d + k) * RB + ri);
     float csum = 0.f;
+#pragma unroll 1
+    for (int J0 = 0; J0 <= I; J0 += kBxBatch) {
+        float v[kBxBatch];
 #pragma unroll
-    for (int u = 0; u < kBxBatch; ++u) csum += v[u];
-    for (int J0 = kBxBatch; J0 <= I; J0 += kBxBatch) {
-#pragma unroll
-        for (int u = 0; u < kBxBatch; ++u) v[u] = (J0 + u <= I) ? col(J0 + u) : 0.f;
+        for (int u = 0; u < kBxBatch; ++u) {
+            const int J = J0 + u, rel = i - (J << rbs);
+            v[u] = (J <= I) ? __ldcg(cp + ((__ldg(tb.cbase + J) + (rel >> cws)) * d + k) * CW + (rel & (CW - 1)))
+                            : 0.f;
+        }
 #pragma unroll
         for (int u = 0; u < kBxBatch; ++u) csum += v[u];
     }
@@ -83,12 +71,14 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int g0, int gstride
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int m = a.m, n = a.n, d = a.d, md = m * d, npart = md + 1;
     const int mine = (g0 < ngroups) ? (ngroups - g0 + gstride - 1) / gstride : 0;
+#pragma unroll 1
     for (int c0 = 0; c0 < mine; c0 += cap) {
         const int nc = min(cap, mine - c0);
         float* s_bx = s;                                   // [nc][m][d][32]
         float* s_xp = s + nc * md * kGroupObjects;         // [nc][m][d][32]
         FF* s_comm = reinterpret_cast<FF*>(s + 2 * nc * md * kGroupObjects);   // [nc][d]
         // 1. partial sums and staged x_{t-1}, one (group, l, k) unit per warp
+#pragma unroll 1
         for (int u = warp; u < nc * md; u += nwarps) {
             const int gi = u / md, lk = u - gi * md, l = lk / d, k = lk - l * d;
             const int i = (g0 + (c0 + gi) * gstride) * kGroupObjects + lane;
@@ -98,6 +88,7 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int g0, int gstride
         }
         __syncthreads();
         // 2. per (group, coordinate): centre, commensurability, mix, column sums
+#pragma unroll 1
         for (int w = warp; w < nc * d; w += nwarps) {
             const int gi = w / d, k = w - gi * d;
             const int g = g0 + (c0 + gi) * gstride;

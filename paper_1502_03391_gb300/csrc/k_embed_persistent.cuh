@@ -162,10 +162,10 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const __grid_constant__ Per
                 s_tot[e] = (e < npart) ? totals_ff(P.bpart + e, npart, P.ngroups)
                                        : totals_ff(P.fid2 + (t & 1) * G, 1, G);
             __syncthreads();
+            if (tid < m * D)
+                s_mu[(tid / D) * FJOFC_MAX_D + (tid % D)] =
+                    final_pass ? 0.f : (s_tot[tid].hi + s_tot[tid].lo) * P.inv_n;
             if (tid == 0) {
-                for (int e = 0; e < m * D; ++e)
-                    s_mu[(e / D) * FJOFC_MAX_D + (e % D)] =
-                        final_pass ? 0.f : (s_tot[e].hi + s_tot[e].lo) / float(n);
                 const FF ct = s_tot[npart - 1], ft = s_tot[npart];
                 const double sigma = (double(ft.hi) + double(ft.lo)) + (double(ct.hi) + double(ct.lo));
                 const int tp = t - 1;
@@ -178,7 +178,7 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const __grid_constant__ Per
                     if (!stop && tp >= 1 && P.tol >= 0.0) {
                         const double dec = s_prev - sigma;
                         const bool cont = (P.tol_mode == FJOFC_TOL_RELATIVE) ? (dec > P.tol * s_prev)
-                                                                             : (dec / P.npairs > P.tol);
+                                                                             : (dec > P.tol * P.npairs);
                         if (!cont) stop = 1;
                     }
                     s_prev = sigma;

@@ -224,7 +224,9 @@ struct RowStage {
 
 // Shared-memory carve-up and TMA ring state of one CTA of the all-pairs pass.  The ring
 // runs over a global sequence qg = 0, 1, ... of sub-tile uses; use qg is sub-tile
-// t_begin + (qg mod nq) of the CTA's range (the range repeats every pass).
+// t_begin + (qg mod nq) of the CTA's range (the range repeats every pass).  The warp that
+// releases a stage last issues the use STAGES ahead, which at the end of a pass is one of
+// the next pass's first sub-tiles (Delta does not change between passes).
 template <int D, typename TD>
 struct K1Ring {
     using S = K1Shape<D, TD>;
@@ -427,16 +429,17 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
         else
             subtile_pairs<D, TD, R, C, CW, true>(tile, warp, lane, r0, c0, n, xi, xj, racc, cacc0, cacc1, sf0, sf1);
         // release the stage; the last warp to do so refills it with use qg + STAGES
+        const bool refill = qg + STAGES < rg.total_q;
         __syncwarp();
         if (lane == 0) {
             __threadfence_block();
             // use k = qg / STAGES of this stage is fully released at count (k+1)*CWARPS
             if (atomicAdd(&rg.released[stage], 1) == int(qg / STAGES + 1) * CWARPS - 1) {
                 __threadfence_block();
-                if (qg + STAGES < rg.total_q) rg.issue(tm, qg + STAGES);
+                if (refill) rg.issue(tm, qg + STAGES);
             }
         }
-        if (qg + STAGES < rg.total_q) rg.advance(p);
+        if (refill) rg.advance(p);
         fid = ff_add(fid, sf0 + sf1);
 
         // column partials of this sub-tile into its ring slot
