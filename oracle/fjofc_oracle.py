@@ -344,6 +344,37 @@ def guttman_step_closed_form(deltas: Sequence[np.ndarray], Wm: np.ndarray, X: np
     return out
 
 
+def guttman_rows(delta_rows: Sequence[np.ndarray], Wm: np.ndarray, X: np.ndarray, idx) -> np.ndarray:
+    """Rows ``idx`` of one Guttman transform L^+ B(X) X, for every modality, from the Delta
+    rows of those objects only (for problems too large for the dense step).
+
+    Eq. (update) / Cor. 1: row i of modality j is sum_l [Wmod^-1]_{jl} (B_l X^(l))_i with
+    (B_l X^(l))_i = sum_{j' != i, d != 0} w_ll Delta_l[i, j'] / d_ij' (x_i - x_j') (Eq. B).
+    The Z (x) J_n part of Cor. 1 adds sum_l Z_jl 1^T B_l X^(l), which is zero because every
+    column of B_l sums to zero (Sec. 2.1), so it is left out here; the test of this
+    function checks that claim against the full closed-form step.
+    ``delta_rows[l]`` is len(idx) x n (row a holds Delta_l[idx[a], :]).  Returns an
+    (m, len(idx), d) float64 array."""
+    Wm = np.asarray(Wm, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    m = Wm.shape[0]
+    n = X.shape[0] // m
+    idx = np.asarray(idx)
+    Winv = np.linalg.inv(modified_weight_matrix(Wm, n))
+    BX = np.zeros((m, len(idx), X.shape[1]))
+    for l in range(m):
+        Xl = X[l * n:(l + 1) * n]
+        for a, i in enumerate(idx):
+            diff = Xl[i][None, :] - Xl
+            dist = np.sqrt(np.einsum("jk,jk->j", diff, diff))
+            coef = np.zeros(n)
+            nz = dist != 0.0
+            nz[i] = False
+            coef[nz] = Wm[l, l] * np.asarray(delta_rows[l][a], dtype=np.float64)[nz] / dist[nz]
+            BX[l, a] = coef @ diff
+    return np.einsum("jl,lak->jak", Winv, BX)
+
+
 def stress_blocks(deltas: Sequence[np.ndarray], Wm: np.ndarray, X: np.ndarray, row_block: int = 1024) -> float:
     """Eq. (stress) summed block by block: sum_l w_ll sum_{i<j} (Delta_l,ij - d_ij(X^(l)))^2
     + sum_{i<j} w_ij ||X^(i) - X^(j)||_F^2 (the omnibus double sum restricted to its

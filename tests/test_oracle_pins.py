@@ -460,3 +460,24 @@ def test_pseudoinverse_moore_penrose_conditions(seed, m, n):
     assert np.abs(P @ L - (P @ L).T).max() <= 1e-10
     J = np.ones((N, N)) / N
     np.testing.assert_allclose(P, np.linalg.inv(L + J) - J, atol=1e-10 * np.abs(P).max())
+
+
+def test_guttman_rows_match_full_step():
+    """Sampled rows of one transform (no J_n term) equal the dense pinv step and the full
+    closed-form step (which keeps the J_n term) on a random problem with general W2
+    weights: pins that the column sums of B_l X^(l) vanish and that the row formula has
+    no dropped or transposed term."""
+    rng = np.random.default_rng(77)
+    m, n, d = 3, 23, 4
+    F = [rng.normal(size=(n, 3)) for _ in range(m)]
+    deltas = [np.sqrt(((f[:, None, :] - f[None, :, :]) ** 2).sum(-1)) for f in F]
+    Wm = rng.uniform(0.3, 1.7, size=(m, m))
+    Wm = (Wm + Wm.T) / 2
+    X = rng.normal(size=(m * n, d))
+    full = O.jofc_embed(deltas, Wm, X, max_iter=1).X
+    closed = O.guttman_step_closed_form(deltas, Wm, X)
+    idx = np.array([0, 5, 11, 22])
+    rows = O.guttman_rows([D[idx] for D in deltas], Wm, X, idx)
+    for j in range(m):
+        np.testing.assert_allclose(rows[j], full[j * n + idx], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(rows[j], closed[j * n + idx], rtol=1e-10, atol=1e-12)
