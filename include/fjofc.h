@@ -199,6 +199,73 @@ int fjofc_embed_noalloc(int32_t m, int64_t n, int32_t d,
                         const float* delta_scale, const double* weights,
                         float* X, const fjofc_opts* opts, fjofc_result* res, void* cuda_stream);
 
+/* ------------------------------------------------------------------------------------
+ * Learned warm start for fjofc_oos.  The paper has no counterpart: this is the learned
+ * form added beside the method.  A network with two hidden GELU layers
+ *     h1 = gelu(W1 x + b1), h2 = gelu(W2 h1 + b2), yhat = W3 h2 + b3,
+ * gelu(z) = z Phi(z), maps a new object's dissimilarities to in-sample landmarks to a
+ * start for the out-of-sample Guttman iterations of Sec. 3, which refine it: either
+ * every modality's position (n_out = m d, rows of the k x m x d layout of fjofc_oos) or
+ * one shared position yhat in R^d used as y_j(0) = yhat for every j (n_out = d).  Parameters are one flat float32 device vector:
+ * W1 (hidden x n_in), b1, W2 (hidden x hidden), b2, W3 (n_out x hidden), b3, matrices
+ * row-major.  Inputs x are IEEE binary16 (uint16_t bit patterns), count x n_in
+ * row-major; targets and outputs are float32 count x n_out.  All pointers except
+ * loss_history/loss/inv_mean are device pointers owned by the caller.  Scratch comes
+ * from the stream-ordered allocator.  Errors: FJOFC_ERR_ARG (sizes outside [1, 65536],
+ * NULL pointers, bad counts), FJOFC_ERR_NOMEM, FJOFC_ERR_CUDA.
+ * ------------------------------------------------------------------------------------ */
+
+/* Number of parameters (floats), or -1 for invalid sizes. */
+int64_t fjofc_mlp_param_count(int32_t n_in, int32_t hidden, int32_t n_out);
+
+/* Every weight and bias of a layer ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from a
+ * counter-based SplitMix64 stream keyed by seed (deterministic). */
+int fjofc_mlp_init(float* params, int32_t n_in, int32_t hidden, int32_t n_out, uint64_t seed, void* cuda_stream);
+
+/* Network inputs of k new objects: features[o][j*n_land + t] =
+ * binary16(delta_new[o][j][landmarks[t]] * inv_mean[j]); delta_new is the float32
+ * (k, m, ld) layout of fjofc_oos; landmarks: n_land device int32 in-sample indices;
+ * inv_mean: m host floats (1 / mean of Delta_j). */
+int fjofc_mlp_features(int32_t m, int64_t n, int64_t k, const float* delta_new, int64_t ld, const int32_t* landmarks,
+                       int32_t n_land, const float* inv_mean, uint16_t* features, void* cuda_stream);
+
+/* y = network(x) for count rows. */
+int fjofc_mlp_forward(const float* params, int32_t n_in, int32_t hidden, int32_t n_out, const uint16_t* x,
+                      int64_t count, float* y, void* cuda_stream);
+
+/* Gradient (P floats, device) and value (*loss, host, may be NULL) of
+ * L = 1/(2 count) sum_o ||network(x_o) - y_o||^2 over 1 <= count <= 8192 rows.
+ * Synchronises the stream. */
+int fjofc_mlp_gradient(const float* params, int32_t n_in, int32_t hidden, int32_t n_out, const uint16_t* x,
+                       const float* y, int64_t count, float* grad, double* loss, void* cuda_stream);
+
+/* The warm start y_j(0) = yhat for every modality: Y[o][j][:] = yhat[o][:] (Y is the
+ * k x m x d layout of fjofc_oos). */
+int fjofc_mlp_broadcast(int64_t k, int32_t m, int32_t d, const float* yhat, float* Y, void* cuda_stream);
+
+/* Fallback to the standard start: per object o, if s_warm[o] <= s_std[o] (stresses of the
+ * two starts, e.g. from fjofc_oos with max_iter = 0) Y[o] = Y_warm[o], else Y[o] keeps
+ * the standard start it holds on entry; used[o] (may be NULL) = 1 when the warm start
+ * was kept. */
+int fjofc_mlp_select(int64_t k, int32_t m, int32_t d, const float* Y_warm, const double* s_warm, const double* s_std,
+                     float* Y, int32_t* used, void* cuda_stream);
+
+typedef struct {
+    int32_t epochs;      /* passes over the training rows */
+    int32_t batch;       /* rows per Adam step (1..8192, <= count); the remainder is dropped */
+    float lr;            /* Adam step size (> 0) */
+    float beta1, beta2;  /* Adam moment decays; <= 0 selects 0.9 / 0.999 */
+    float eps;           /* Adam epsilon; <= 0 selects 1e-8 */
+    uint64_t seed;       /* epoch orders: row i -> (a i + c) mod count with gcd(a, count) = 1 */
+    int32_t reserved[4];
+} fjofc_mlp_train_opts;
+
+/* Adam on L over minibatches, in place on params (Adam moments start at zero).
+ * loss_history (host, may be NULL) receives each epoch's mean batch loss; when it is
+ * non-NULL the call synchronises the stream. */
+int fjofc_mlp_train(float* params, int32_t n_in, int32_t hidden, int32_t n_out, const uint16_t* x, const float* y,
+                    int64_t count, const fjofc_mlp_train_opts* opts, float* loss_history, void* cuda_stream);
+
 /* Message for a status code (static string). */
 const char* fjofc_strerror(int status);
 

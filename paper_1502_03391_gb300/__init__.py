@@ -34,7 +34,9 @@ TOL_ABS_NORMALIZED, TOL_RELATIVE = 0, 1
 MAX_M, MAX_D = 8, 16
 
 # Every symbol declared in include/fjofc.h.
-EXPORTS = ("fjofc_embed", "fjofc_embed_noalloc", "fjofc_stress", "fjofc_oos", "fjofc_strerror", "fjofc_version")
+EXPORTS = ("fjofc_embed", "fjofc_embed_noalloc", "fjofc_stress", "fjofc_oos", "fjofc_strerror", "fjofc_version",
+           "fjofc_mlp_param_count", "fjofc_mlp_init", "fjofc_mlp_features", "fjofc_mlp_forward", "fjofc_mlp_gradient",
+           "fjofc_mlp_train", "fjofc_mlp_broadcast", "fjofc_mlp_select")
 
 
 class FjofcError(RuntimeError):

@@ -28,7 +28,10 @@ def _declared_functions():
 
 def test_header_declares_expected_api():
     assert _declared_functions() == sorted(["fjofc_embed", "fjofc_embed_noalloc", "fjofc_stress", "fjofc_oos",
-                                            "fjofc_strerror", "fjofc_version"])
+                                            "fjofc_strerror", "fjofc_version", "fjofc_mlp_param_count",
+                                            "fjofc_mlp_init", "fjofc_mlp_features", "fjofc_mlp_forward",
+                                            "fjofc_mlp_gradient", "fjofc_mlp_train", "fjofc_mlp_broadcast",
+                                            "fjofc_mlp_select"])
 
 
 def test_library_loads_and_exports_every_declared_symbol():
