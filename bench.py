@@ -503,6 +503,103 @@ def run_oos(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_learned(args, rank, world, local_rank):
+    """Learned warm start on the out-of-sample workload: the m=2, n=10000, d=5 configuration,
+    a 512-512 GELU network (m*d outputs) trained on the method's own solutions for 20000
+    held-out objects, then 100000 test objects solved to relative stress change < 1e-6
+    from (a) the standard start and (b) the network's start with the per-object fallback.
+    Timed per step: (a) the solve; (b) features + network + fallback choice + solve.
+    value = object-solves per second of (b)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1502_03391_gb300 as fj
+    from paper_1502_03391_gb300 import learned as L
+    import synthetic
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(device)
+    prob = synthetic.make_insample(4, rep=rank, with_deltas=False)
+    m, n, d = prob.spec.m, prob.spec.n, prob.spec.d
+    deltas = []
+    for Fi in prob.F:
+        buf = fj.empty_delta(n, torch.float32, device)
+        buf.copy_(synthetic.torch_distances(Fi, device, torch.float32))
+        deltas.append(buf)
+    X = torch.as_tensor(np.asarray(prob.X0, np.float32), device=device)
+    fj.embed(deltas, prob.W, X, max_iter=200, tol=1e-7, tol_mode="relative", history=False)
+    inv_mean = [float(n * (n - 1)) / float(D.double().sum().item()) for D in deltas]
+    del deltas
+    lm = L.choose_landmarks(n, 256, seed=1)
+
+    def objects(count, stream_id):
+        F_new, _, Y0 = synthetic.make_oos_objects(prob, count, stream=stream_id, with_deltas=False)
+        dn = fj.empty_oos_delta(count, m, n, torch.float32, device)
+        for j in range(m):
+            dn[:, j, :].copy_(synthetic.torch_distances(F_new[j], device, torch.float32, G=prob.F[j]))
+        return dn, torch.as_tensor(np.asarray(Y0, np.float32), device=device).contiguous()
+
+    def solve(dn, Y, it, st):
+        fj.oos(X, dn, prob.W, Y, max_iter=500, tol=1e-6, tol_mode="relative", iters_out=it, stress_out=st)
+
+    ntr, kte = 20000, 100000
+    dtr, Ytr = objects(ntr, 1)
+    itr = torch.zeros(ntr, dtype=torch.int32, device=device)
+    str_ = torch.zeros(ntr, dtype=torch.float64, device=device)
+    solve(dtr, Ytr, itr, str_)
+    t0 = time.perf_counter()
+    net = L.WarmStartMLP(m * len(lm), 512, m * d, seed=3, device=device)
+    xtr = L.features(dtr, lm, inv_mean)
+    hist = net.train(xtr, Ytr.reshape(ntr, m * d).contiguous(), epochs=40, batch=256, lr=1e-3, seed=2)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del dtr, xtr
+    dte, Y0 = objects(kte, 2)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
+    it = torch.zeros(kte, dtype=torch.int32, device=device)
+    st = torch.zeros(kte, dtype=torch.float64, device=device)
+    Y = torch.empty_like(Y0)
+    res = {}
+
+    def plain():
+        Y.copy_(Y0)
+        solve(dte, Y, it, st)
+
+    def warm():
+        ws = net.warm_start(X, dte, prob.W, Y0, lm, inv_mean)
+        Y.copy_(ws.Y)
+        solve(dte, Y, it, st)
+        return ws
+
+    with ClockSampler(local_rank) as clk:
+        for name, fn in (("standard", plain), ("learned", warm)):
+            for _ in range(args.warmup):
+                fn()
+            ms, outs = _timed(torch, stream, fn, args.steps, flush)
+            res[name] = {"ms": sum(ms) / len(ms), "mean_iterations": float(it.double().mean().item()),
+                         "max_iterations": int(it.max().item()), "mean_final_stress": float(st.mean().item())}
+            if name == "learned":
+                res[name]["warm_start_kept"] = float(outs[-1].used_warm.double().mean().item())
+    clocks = clk.summary()
+    ratio = res["learned"]["mean_final_stress"] / res["standard"]["mean_final_stress"] - 1.0
+    if rank == 0:
+        line = {
+            "metric": "out-of-sample object solves/s (learned warm start)", "value": kte / (res["learned"]["ms"] / 1e3),
+            "unit": "objects/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["learned"]["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (float16 network inputs)", "data": "synthetic",
+            "config": {"workload": "learned-oos-m2-n10000-d5: 100000 new objects to relative stress change < 1e-6, "
+                                   "network 512-512-512-10 GELU trained on 20000 held-out objects' solutions",
+                       "k": kte, "m": m, "n": n, "d": d, "landmarks": len(lm), "train_objects": ntr,
+                       "l2": "delta_new 8 GB > L2; L2 flushed before every timed step"},
+            "forms": res, "speedup_vs_standard": res["standard"]["ms"] / res["learned"]["ms"],
+            "final_stress_rel_to_standard": ratio, "train_seconds": train_s,
+            "train_loss_first_last": [float(hist[0]), float(hist[-1])], "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -511,10 +608,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="insample", choices=["insample", "precision", "oos"],
+    ap.add_argument("--workload", default="insample", choices=["insample", "precision", "oos", "learned"],
                     help="insample: the headline line (m=2, n=5000, d=3); precision: m=3, n=20000, d=10 "
                          "with float16/bfloat16 Delta vs float32; oos: 100000 out-of-sample objects "
-                         "against the m=2, n=10000, d=5 configuration")
+                         "against the m=2, n=10000, d=5 configuration; learned: the same objects from the "
+                         "trained network's warm start vs the standard start")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -525,6 +623,8 @@ def main():
         run_precision(args, rank, world, local_rank)
     elif args.workload == "oos":
         run_oos(args, rank, world, local_rank)
+    elif args.workload == "learned":
+        run_learned(args, rank, world, local_rank)
     else:
         run_gpu(args, rank, world, local_rank)
 
