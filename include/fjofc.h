@@ -200,6 +200,52 @@ int fjofc_embed_noalloc(int32_t m, int64_t n, int32_t d,
                         float* X, const fjofc_opts* opts, fjofc_result* res, void* cuda_stream);
 
 /* ------------------------------------------------------------------------------------
+ * Batched in-sample embedding (the paper has no counterpart: a deployment form that
+ * runs many independent fJOFC problems, Algorithm 1 with Eq. update each, of uneven
+ * size together).  A plan fixes the problems' pointers, sizes, weights and the loop
+ * options (the same fjofc_opts for every problem; profile must be 0) and captures the
+ * whole computation into one CUDA graph: a per-problem set-up kernel, one cooperative
+ * launch per (d, delta_dtype) class in which every SM runs its list of problems (large
+ * problems on groups of SMs of their own), and a result gather.  fjofc_plan_run
+ * re-runs it from the current contents of every X (in X_0, out the returned X_T, as
+ * fjofc_embed).  Results are per problem, with the same status codes as fjofc_embed.
+ * The plan owns one device allocation (cudaMalloc) until fjofc_plan_destroy; Delta and
+ * X stay owned by the caller and must outlive the plan.
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    int32_t m;                  /* modalities, 1..FJOFC_MAX_M */
+    int64_t n;                  /* objects, >= 2 */
+    int32_t d;                  /* embedding dimension, 1..FJOFC_MAX_D */
+    const void* const* delta;   /* m device pointers to n x n Delta (as fjofc_embed); the
+                                   host array is read by fjofc_plan_create only */
+    int64_t ld;                 /* row stride of Delta in elements */
+    int32_t delta_dtype;        /* FJOFC_F32 / FJOFC_F16 / FJOFC_BF16 */
+    const float* delta_scale;   /* m host scales or NULL (read at create) */
+    const double* weights;      /* m x m host weights (read at create) */
+    float* X;                   /* device (m n) x d, in X_0, out X_T */
+} fjofc_problem;
+
+typedef struct fjofc_plan fjofc_plan;
+
+/* Validates every problem (FJOFC_ERR_ARG / _UNSUPPORTED as fjofc_embed), schedules and
+ * captures the plan; *plan receives it (NULL on error). */
+int fjofc_plan_create(const fjofc_problem* problems, int32_t count, const fjofc_opts* opts, fjofc_plan** plan);
+
+/* Enqueues the captured plan on the stream (no synchronisation). */
+int fjofc_plan_run(fjofc_plan* plan, void* cuda_stream);
+
+/* Per-problem results of the last run (host arrays of count entries, each may be NULL):
+ * status, iters (T of the returned X_T), stress sigma(X_T).  Synchronises the stream;
+ * returns the first non-zero status, else FJOFC_OK. */
+int fjofc_plan_results(const fjofc_plan* plan, int32_t* status, int32_t* iters, double* stress, void* cuda_stream);
+
+/* Schedule facts: groups[count] = SMs given to each problem (may be NULL), *graphed = 1
+ * when the plan runs as one CUDA graph, *launches = kernels per run. */
+int fjofc_plan_info(const fjofc_plan* plan, int32_t* groups, int32_t* graphed, int32_t* launches);
+
+void fjofc_plan_destroy(fjofc_plan* plan);
+
+/* ------------------------------------------------------------------------------------
  * Learned warm start for fjofc_oos.  The paper has no counterpart: this is the learned
  * form added beside the method.  A network with two hidden GELU layers
  *     h1 = gelu(W1 x + b1), h2 = gelu(W2 h1 + b2), yhat = W3 h2 + b3,

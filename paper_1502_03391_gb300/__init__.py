@@ -36,7 +36,8 @@ MAX_M, MAX_D = 8, 16
 # Every symbol declared in include/fjofc.h.
 EXPORTS = ("fjofc_embed", "fjofc_embed_noalloc", "fjofc_stress", "fjofc_oos", "fjofc_strerror", "fjofc_version",
            "fjofc_mlp_param_count", "fjofc_mlp_init", "fjofc_mlp_features", "fjofc_mlp_forward", "fjofc_mlp_gradient",
-           "fjofc_mlp_train", "fjofc_mlp_broadcast", "fjofc_mlp_select")
+           "fjofc_mlp_train", "fjofc_mlp_broadcast", "fjofc_mlp_select", "fjofc_plan_create", "fjofc_plan_run",
+           "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy")
 
 
 class FjofcError(RuntimeError):
@@ -57,6 +58,13 @@ class _Result(ctypes.Structure):
                 ("ms_apply", ctypes.c_float), ("launches", ctypes.c_int32)]
 
 
+class _Problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int64), ("d", ctypes.c_int32),
+                ("delta", ctypes.POINTER(ctypes.c_void_p)), ("ld", ctypes.c_int64), ("delta_dtype", ctypes.c_int32),
+                ("delta_scale", ctypes.POINTER(ctypes.c_float)), ("weights", ctypes.POINTER(ctypes.c_double)),
+                ("X", ctypes.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"fJOFC CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
@@ -71,6 +79,16 @@ def _load():
     lib.fjofc_oos.argtypes = [i32, i64, i32, i64, vp, vp, i64, i32, ctypes.POINTER(ctypes.c_float), dp, vp, vp, vp,
                               ctypes.POINTER(_Opts), ctypes.POINTER(_Result), vp]
     lib.fjofc_oos.restype = ctypes.c_int
+    lib.fjofc_plan_create.argtypes = [ctypes.POINTER(_Problem), i32, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
+    lib.fjofc_plan_create.restype = ctypes.c_int
+    lib.fjofc_plan_run.argtypes = [vp, vp]
+    lib.fjofc_plan_run.restype = ctypes.c_int
+    lib.fjofc_plan_results.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), dp, vp]
+    lib.fjofc_plan_results.restype = ctypes.c_int
+    lib.fjofc_plan_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.fjofc_plan_info.restype = ctypes.c_int
+    lib.fjofc_plan_destroy.argtypes = [vp]
+    lib.fjofc_plan_destroy.restype = None
     lib.fjofc_strerror.argtypes = [ctypes.c_int]
     lib.fjofc_strerror.restype = ctypes.c_char_p
     lib.fjofc_version.argtypes = []
@@ -289,3 +307,72 @@ def empty_oos_delta(k: int, m: int, n: int, dtype=None, device="cuda"):
     ld = padded_ld(n, dtype)
     buf = torch.zeros((k, m, ld), dtype=dtype, device=device)
     return buf[:, :, :n]
+
+
+# ------------------------------------------------------------------ batched plans
+
+@dataclasses.dataclass
+class PlanResults:
+    status: np.ndarray
+    iters: np.ndarray
+    stress: np.ndarray
+
+
+class Plan:
+    """Many independent in-sample problems run together (``fjofc_plan_*``).  ``problems``
+    is a sequence of (deltas, weights, X) or (deltas, weights, X, delta_scale) with the
+    same conventions as ``embed``; every problem gets the same loop options."""
+
+    def __init__(self, problems, max_iter: int, tol: float = -1.0, tol_mode: str = "relative"):
+        keep = []
+        arr = (_Problem * len(problems))()
+        for i, pr in enumerate(problems):
+            deltas, W, X = pr[0], pr[1], pr[2]
+            scale = pr[3] if len(pr) > 3 else None
+            m = len(deltas)
+            n = int(deltas[0].shape[0])
+            ld, code = _delta_layout(deltas, n)
+            ptrs = (ctypes.c_void_p * m)(*[D.data_ptr() for D in deltas])
+            Wn = _weights(W, m)
+            sc = _scales(scale, m)
+            keep += [ptrs, Wn, sc]
+            arr[i] = _Problem(m, n, int(X.shape[1]), ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p)), ld, code,
+                              ctypes.cast(sc, ctypes.POINTER(ctypes.c_float)) if sc is not None else None,
+                              Wn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(X.data_ptr()))
+        opts = _Opts(int(max_iter), float(tol), TOL_RELATIVE if tol_mode == "relative" else TOL_ABS_NORMALIZED)
+        h = ctypes.c_void_p()
+        _check(_lib.fjofc_plan_create(arr, len(problems), ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        self.count = len(problems)
+
+    def run(self, stream=None):
+        torch = _torch()
+        _check(_lib.fjofc_plan_run(self._h, _stream_handle(stream, torch.device("cuda"))))
+
+    def results(self, stream=None, check: bool = True) -> PlanResults:
+        torch = _torch()
+        st = (ctypes.c_int32 * self.count)()
+        it = (ctypes.c_int32 * self.count)()
+        sg = (ctypes.c_double * self.count)()
+        rc = _lib.fjofc_plan_results(self._h, st, it, sg, _stream_handle(stream, torch.device("cuda")))
+        if check:
+            _check(rc)
+        return PlanResults(np.array(st[:]), np.array(it[:]), np.array(sg[:]))
+
+    def info(self):
+        g = (ctypes.c_int32 * self.count)()
+        graphed = ctypes.c_int32(0)
+        launches = ctypes.c_int32(0)
+        _check(_lib.fjofc_plan_info(self._h, g, ctypes.byref(graphed), ctypes.byref(launches)))
+        return {"groups": np.array(g[:]), "graphed": bool(graphed.value), "launches": launches.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.fjofc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -241,12 +241,6 @@ int sm_count() {
     return sms > 0 ? sms : 1;
 }
 
-struct EmbedPlan {
-    K1Geom g;
-    int nRB = 0, G = 0, nbx = 0;
-    int64_t Tm = 0, T = 0;
-};
-
 bool cooperative_ok() {
     int dev = 0, coop = 0;
     cudaGetDevice(&dev);
@@ -259,7 +253,7 @@ int persist_blocks_per_sm(int d, int dtype) {
                                                                                : persist_bps_dt<__nv_bfloat16>(d);
 }
 
-EmbedPlan make_plan(int m, int64_t n, int d, int dtype, bool persistent) {
+EmbedPlan make_plan(int m, int64_t n, int d, int dtype, bool persistent, int G_override = 0) {
     EmbedPlan P;
     P.g = fjofc::k1_geometry(d, dtype);
     P.nRB = int((n + P.g.RB - 1) / P.g.RB);
@@ -268,7 +262,7 @@ EmbedPlan make_plan(int m, int64_t n, int d, int dtype, bool persistent) {
     P.Tm = Tm;
     P.T = Tm * m;
     const int bps = std::max(1, persistent ? persist_blocks_per_sm(d, dtype) : fjofc::k1_blocks_per_sm(d, dtype));
-    int64_t G = int64_t(bps) * sm_count();
+    int64_t G = G_override > 0 ? int64_t(G_override) : int64_t(bps) * sm_count();
     if (G > P.T) G = P.T;
     P.G = int(G);
     P.nbx = fjofc::k2_blocks(int(n));
@@ -293,6 +287,137 @@ int validate_insample(int32_t m, int64_t n, int32_t d, const void* const* delta,
 }
 
 }  // namespace
+
+namespace fjofc {
+
+int modified_weights_inverse(int m, int64_t n, const double* w, double* winv) { return weights_inverse(m, n, w, winv); }
+int tensor_map_encoder() { return get_encoder(); }
+
+int InsampleSetup::plan(int m_, int64_t n_, int d_, int dtype_, const fjofc_opts& opts, bool persistent,
+                        int G_override) {
+    m = m_; n = n_; d = d_; dtype = dtype_; o = opts;
+    P = make_plan(m, n, d, dtype, persistent, G_override);
+    if (P.g.RB == 0) {
+        snprintf(g_last_msg, sizeof(g_last_msg), "no kernel for d=%d", d);
+        return FJOFC_ERR_UNSUPPORTED;
+    }
+    const int RB = P.g.RB, CW = P.g.CW;
+    const int64_t mnd = int64_t(m) * n * d;
+    Carver cv;
+    o_buf1 = cv.take<float>(mnd);
+    o_buf2 = cv.take<float>(mnd);
+    o_col = cv.take<float>(size_t(P.T) * d * CW);
+    o_head = cv.take<float>(size_t(m) * P.nRB * d * RB);
+    o_cont = cv.take<float>(size_t(P.G) * d * RB);
+    o_fid = cv.take<float2>(P.G);
+    o_woff = cv.take<int64_t>(P.nRB + 1);
+    o_cta = cv.take<int64_t>(size_t(P.G) + 1);
+    o_mu = cv.take<float>(2 * FJOFC_MAX_M * FJOFC_MAX_D);
+    o_bpart = cv.take<float2>(size_t(P.nbx) * (size_t(m) * d + 1));
+    o_ticket = cv.take<unsigned>(1);
+    o_st = cv.take<DevStatus>(1);
+    o_hist = cv.take<double>(size_t(o.max_iter) + 2);
+    o_fid2 = cv.take<float2>(2 * size_t(P.G));
+    o_cbase = cv.take<int64_t>(size_t(P.nRB));
+    o_contr = cv.take<int2>(size_t(m) * P.nRB);
+    o_bar = cv.take<unsigned>(1);
+    bytes = (cv.off + 255) & ~size_t(255);
+    return FJOFC_OK;
+}
+
+int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const float* delta_scale,
+                        const double* weights, const double* winv, float* X) {
+    int rc;
+    const int RB = P.g.RB, CW = P.g.CW;
+    // TMA descriptors: Delta_l as a 2-D tensor {n cols, n rows}, box {CW, RB}
+    std::memset(&tm, 0, sizeof(tm));
+    for (int l = 0; l < m; ++l) {
+        const cuuint64_t dims[2] = {cuuint64_t(n), cuuint64_t(n)};
+        const cuuint64_t strides[1] = {cuuint64_t(ld) * dtype_size(dtype)};
+        const cuuint32_t box[2] = {cuuint32_t(CW), cuuint32_t(RB)};
+        if ((rc = encode_map(&tm.map[l], dtype, 2, delta[l], dims, strides, box))) return rc;
+    }
+    DevStatus* st = reinterpret_cast<DevStatus*>(base + o_st);
+    double* hist = reinterpret_cast<double*>(base + o_hist);
+    k1 = K1Params{};
+    k1.colpart = reinterpret_cast<float*>(base + o_col);
+    k1.rowhead = reinterpret_cast<float*>(base + o_head);
+    k1.rowcont = reinterpret_cast<float*>(base + o_cont);
+    k1.fid = reinterpret_cast<float2*>(base + o_fid);
+    k1.walk_off = reinterpret_cast<int64_t*>(base + o_woff);
+    k1.cta_start = reinterpret_cast<int64_t*>(base + o_cta);
+    k1.st = st;
+    k1.m = m; k1.n = int(n); k1.d = d; k1.nRB = P.nRB; k1.G = P.G;
+    k1.Tm = P.Tm; k1.T = P.T;
+    // the all-pairs pass works in Delta's stored units (x / s_l), so its fidelity sum
+    // carries s_l^2
+    double dsc[FJOFC_MAX_M];
+    for (int l = 0; l < FJOFC_MAX_M; ++l) {
+        dsc[l] = (l < m && delta_scale) ? double(delta_scale[l]) : 1.0;
+        k1.wfid[l] = l < m ? float(weights[l * m + l] * dsc[l] * dsc[l]) : 0.f;
+        k1.xscale[l] = float(1.0 / dsc[l]);
+    }
+
+    k2 = K2Params{};
+    k2.colpart = k1.colpart; k2.rowhead = k1.rowhead; k2.rowcont = k1.rowcont; k2.fid = k1.fid;
+    k2.walk_off = k1.walk_off;
+    k2.cta_start = k1.cta_start;
+    k2.mu = reinterpret_cast<float*>(base + o_mu);
+    k2.bpart = reinterpret_cast<float2*>(base + o_bpart);
+    k2.ticket = reinterpret_cast<unsigned*>(base + o_ticket);
+    k2.st = st;
+    k2.hist = hist;
+    k2.m = m; k2.n = int(n); k2.d = d; k2.RB = RB; k2.CW = CW; k2.nRB = P.nRB; k2.G = P.G; k2.nbx = P.nbx;
+    k2.rb_shift = 0;
+    while ((1 << k2.rb_shift) < RB) ++k2.rb_shift;
+    k2.cw_shift = 0;
+    while ((1 << k2.cw_shift) < CW) ++k2.cw_shift;
+    if ((1 << k2.rb_shift) != RB || (1 << k2.cw_shift) != CW) {
+        snprintf(g_last_msg, sizeof(g_last_msg), "internal: tile sizes must be powers of two");
+        return FJOFC_ERR_UNSUPPORTED;
+    }
+    k2.Tm = P.Tm; k2.T = P.T;
+    k2.tol_mode = o.tol_mode; k2.tol = o.tol;
+    k2.npairs = double(m * n) * double(m * n - 1) / 2.0;
+    k2.inv_n = float(1.0 / double(n));
+    for (int j = 0; j < m; ++j)
+        for (int l = 0; l < m; ++l) {
+            k2.coef[j][l] = float(winv[j * m + l] * weights[l * m + l] * dsc[l]);
+            k2.wcomm[j][l] = (j < l) ? float(weights[j * m + l]) : 0.f;
+        }
+    unsigned* bar = reinterpret_cast<unsigned*>(base + o_bar);
+    k2.tb.colpart = k1.colpart;
+    k2.tb.rowhead = k1.rowhead;
+    k2.tb.rowcont = k1.rowcont;
+    k2.tb.cbase = reinterpret_cast<int64_t*>(base + o_cbase);
+    k2.tb.cont = reinterpret_cast<int2*>(base + o_contr);
+    k2.tb.Tm = P.Tm;
+    k2.tb.d = d; k2.tb.RB = RB; k2.tb.CW = CW; k2.tb.rb_shift = k2.rb_shift; k2.tb.cw_shift = k2.cw_shift;
+    k2.tb.nRB = P.nRB;
+    ip = InitParams{st, k2.ticket, k2.mu, const_cast<int64_t*>(k1.walk_off), const_cast<int64_t*>(k2.cta_start),
+                    bar, const_cast<int64_t*>(k2.tb.cbase), const_cast<int2*>(k2.tb.cont), m, int(n), RB, CW,
+                    P.nRB, P.G, P.T, P.Tm};
+
+    pp = PersistParams{};
+    pp.k1 = k1;
+    pp.buf[0] = X;
+    pp.buf[1] = reinterpret_cast<float*>(base + o_buf1);
+    pp.buf[2] = reinterpret_cast<float*>(base + o_buf2);
+    pp.cta_start = k2.cta_start;
+    pp.fid2 = reinterpret_cast<float2*>(base + o_fid2);
+    pp.bpart = k2.bpart;
+    pp.bar = bar;
+    pp.hist = hist;
+    pp.ngroups = P.nbx;
+    pp.rb_shift = k2.rb_shift; pp.cw_shift = k2.cw_shift;
+    pp.max_iter = o.max_iter; pp.tol_mode = o.tol_mode; pp.tol = o.tol; pp.npairs = k2.npairs; pp.inv_n = k2.inv_n;
+    for (int j = 0; j < FJOFC_MAX_M; ++j)
+        for (int l = 0; l < FJOFC_MAX_M; ++l) { pp.coef[j][l] = k2.coef[j][l]; pp.wcomm[j][l] = k2.wcomm[j][l]; }
+    pp.tb = k2.tb;
+    return FJOFC_OK;
+}
+
+}  // namespace fjofc
 
 namespace {
 // The in-sample loop.  stress_only: sigma(X) of X only.  ext: run in a caller-supplied
@@ -327,31 +452,10 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     // One persistent cooperative launch runs the whole loop; profile == 1 (per-kernel
     // timing) uses one launch per all-pairs pass and per W^-1 pass instead.
     const bool persist = (o.profile != 1) && cooperative_ok() && persist_blocks_per_sm(d, dtype) >= 1;
-    const EmbedPlan P = make_plan(m, n, d, dtype, persist);
-    if (P.g.RB == 0) { snprintf(g_last_msg, sizeof(g_last_msg), "no kernel for d=%d", d); return FJOFC_ERR_UNSUPPORTED; }
-    const int RB = P.g.RB, CW = P.g.CW;
+    fjofc::InsampleSetup S;
+    if ((rc = S.plan(m, n, d, dtype, o, persist, 0))) return rc;
     const int64_t mnd = int64_t(m) * n * d;
-
-    // ---- scratch layout
-    Carver cv;
-    const size_t o_buf1 = cv.take<float>(mnd);
-    const size_t o_buf2 = cv.take<float>(mnd);
-    const size_t o_col = cv.take<float>(size_t(P.T) * d * CW);
-    const size_t o_head = cv.take<float>(size_t(m) * P.nRB * d * RB);
-    const size_t o_cont = cv.take<float>(size_t(P.G) * d * RB);
-    const size_t o_fid = cv.take<float2>(P.G);
-    const size_t o_woff = cv.take<int64_t>(P.nRB + 1);
-    const size_t o_cta = cv.take<int64_t>(size_t(P.G) + 1);
-    const size_t o_mu = cv.take<float>(2 * FJOFC_MAX_M * FJOFC_MAX_D);
-    const size_t o_bpart = cv.take<float2>(size_t(P.nbx) * (size_t(m) * d + 1));
-    const size_t o_ticket = cv.take<unsigned>(1);
-    const size_t o_st = cv.take<DevStatus>(1);
-    const size_t o_hist = cv.take<double>(size_t(o.max_iter) + 2);
-    const size_t o_fid2 = cv.take<float2>(2 * size_t(P.G));
-    const size_t o_cbase = cv.take<int64_t>(size_t(P.nRB));
-    const size_t o_contr = cv.take<int2>(size_t(m) * P.nRB);
-    const size_t o_bar = cv.take<unsigned>(1);
-    const size_t total = cv.off;
+    const size_t total = S.bytes;
 
     ScopedDeviceMem mem;
     mem.s = stream;
@@ -372,66 +476,15 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         }
         base = static_cast<char*>(mem.p);
     }
-    float* buf1 = reinterpret_cast<float*>(base + o_buf1);
-    float* buf2 = reinterpret_cast<float*>(base + o_buf2);
-    DevStatus* st = reinterpret_cast<DevStatus*>(base + o_st);
-    double* hist = reinterpret_cast<double*>(base + o_hist);
-
-    // ---- TMA descriptors: Delta_l as a 2-D tensor {n cols, n rows}, box {CW, RB}
-    TMaps tm;
-    std::memset(&tm, 0, sizeof(tm));
-    for (int l = 0; l < m; ++l) {
-        const cuuint64_t dims[2] = {cuuint64_t(n), cuuint64_t(n)};
-        const cuuint64_t strides[1] = {cuuint64_t(ld) * dtype_size(dtype)};
-        const cuuint32_t box[2] = {cuuint32_t(CW), cuuint32_t(RB)};
-        if ((rc = encode_map(&tm.map[l], dtype, 2, delta[l], dims, strides, box))) return rc;
-    }
-
-    K1Params k1{};
-    k1.colpart = reinterpret_cast<float*>(base + o_col);
-    k1.rowhead = reinterpret_cast<float*>(base + o_head);
-    k1.rowcont = reinterpret_cast<float*>(base + o_cont);
-    k1.fid = reinterpret_cast<float2*>(base + o_fid);
-    k1.walk_off = reinterpret_cast<int64_t*>(base + o_woff);
-    k1.cta_start = reinterpret_cast<int64_t*>(base + o_cta);
-    k1.st = st;
-    k1.m = m; k1.n = int(n); k1.d = d; k1.nRB = P.nRB; k1.G = P.G;
-    k1.Tm = P.Tm; k1.T = P.T;
-    // K1 works in Delta's stored units (x / s_l), so its fidelity sum carries s_l^2
-    double dsc[FJOFC_MAX_M];
-    for (int l = 0; l < FJOFC_MAX_M; ++l) {
-        dsc[l] = (l < m && delta_scale) ? double(delta_scale[l]) : 1.0;
-        k1.wfid[l] = l < m ? float(weights[l * m + l] * dsc[l] * dsc[l]) : 0.f;
-        k1.xscale[l] = float(1.0 / dsc[l]);
-    }
-
-    K2Params k2{};
-    k2.colpart = k1.colpart; k2.rowhead = k1.rowhead; k2.rowcont = k1.rowcont; k2.fid = k1.fid;
-    k2.walk_off = k1.walk_off;
-    k2.cta_start = reinterpret_cast<int64_t*>(base + o_cta);
-    k2.mu = reinterpret_cast<float*>(base + o_mu);
-    k2.bpart = reinterpret_cast<float2*>(base + o_bpart);
-    k2.ticket = reinterpret_cast<unsigned*>(base + o_ticket);
-    k2.st = st;
-    k2.hist = hist;
-    k2.m = m; k2.n = int(n); k2.d = d; k2.RB = RB; k2.CW = CW; k2.nRB = P.nRB; k2.G = P.G; k2.nbx = P.nbx;
-    k2.rb_shift = 0;
-    while ((1 << k2.rb_shift) < RB) ++k2.rb_shift;
-    k2.cw_shift = 0;
-    while ((1 << k2.cw_shift) < CW) ++k2.cw_shift;
-    if ((1 << k2.rb_shift) != RB || (1 << k2.cw_shift) != CW) {
-        snprintf(g_last_msg, sizeof(g_last_msg), "internal: tile sizes must be powers of two");
-        return FJOFC_ERR_UNSUPPORTED;
-    }
-    k2.Tm = P.Tm; k2.T = P.T;
-    k2.tol_mode = o.tol_mode; k2.tol = o.tol;
-    k2.npairs = double(m * n) * double(m * n - 1) / 2.0;
-    k2.inv_n = float(1.0 / double(n));
-    for (int j = 0; j < m; ++j)
-        for (int l = 0; l < m; ++l) {
-            k2.coef[j][l] = float(winv[j * m + l] * weights[l * m + l] * dsc[l]);
-            k2.wcomm[j][l] = (j < l) ? float(weights[j * m + l]) : 0.f;
-        }
+    if ((rc = S.bind(base, delta, ld, delta_scale, weights, winv, X))) return rc;
+    const EmbedPlan& P = S.P;
+    const TMaps& tm = S.tm;
+    K1Params& k1 = S.k1;
+    K2Params& k2 = S.k2;
+    float* buf1 = S.pp.buf[1];
+    float* buf2 = S.pp.buf[2];
+    DevStatus* st = k1.st;
+    double* hist = k2.hist;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (!ext) {
@@ -440,19 +493,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         FJ_CUDA(cudaEventRecord(ev0, stream));
     }
 
-    unsigned* bar = reinterpret_cast<unsigned*>(base + o_bar);
-    k2.tb.colpart = k1.colpart;
-    k2.tb.rowhead = k1.rowhead;
-    k2.tb.rowcont = k1.rowcont;
-    k2.tb.cbase = reinterpret_cast<int64_t*>(base + o_cbase);
-    k2.tb.cont = reinterpret_cast<int2*>(base + o_contr);
-    k2.tb.Tm = P.Tm;
-    k2.tb.d = d; k2.tb.RB = RB; k2.tb.CW = CW; k2.tb.rb_shift = k2.rb_shift; k2.tb.cw_shift = k2.cw_shift;
-    k2.tb.nRB = P.nRB;
-    InitParams ip{st, k2.ticket, k2.mu, const_cast<int64_t*>(k1.walk_off), const_cast<int64_t*>(k2.cta_start),
-                  bar, const_cast<int64_t*>(k2.tb.cbase), const_cast<int2*>(k2.tb.cont), m, int(n), RB, CW, P.nRB,
-                  P.G, P.T, P.Tm};
-    FJ_CUDA(launch_init(ip, stream));
+    FJ_CUDA(launch_init(S.ip, stream));
 
     float* bufs[3] = {X, buf1, buf2};
     const bool prof = o.profile == 1;
@@ -464,20 +505,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     int launches = 2;   // init + finalize (or init + the persistent kernel)
     cudaEvent_t pe0 = nullptr, pe1 = nullptr;
     if (persist) {
-        PersistParams pp{};
-        pp.k1 = k1;
-        pp.buf[0] = X; pp.buf[1] = buf1; pp.buf[2] = buf2;
-        pp.cta_start = k2.cta_start;
-        pp.fid2 = reinterpret_cast<float2*>(base + o_fid2);
-        pp.bpart = k2.bpart;
-        pp.bar = bar;
-        pp.hist = hist;
-        pp.ngroups = P.nbx;
-        pp.rb_shift = k2.rb_shift; pp.cw_shift = k2.cw_shift;
-        pp.max_iter = o.max_iter; pp.tol_mode = o.tol_mode; pp.tol = o.tol; pp.npairs = k2.npairs; pp.inv_n = k2.inv_n;
-        for (int j = 0; j < FJOFC_MAX_M; ++j)
-            for (int l = 0; l < FJOFC_MAX_M; ++l) { pp.coef[j][l] = k2.coef[j][l]; pp.wcomm[j][l] = k2.wcomm[j][l]; }
-        pp.tb = k2.tb;
+        const PersistParams& pp = S.pp;
         if (o.profile == 2) {
             FJ_CUDA(cudaEventCreate(&pe0));
             FJ_CUDA(cudaEventCreate(&pe1));

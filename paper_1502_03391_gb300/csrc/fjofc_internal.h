@@ -116,6 +116,14 @@ struct PersistParams {
     BxTables tb;
 };
 
+// One cooperative launch of many problems of the same embedding dimension and Delta type.
+struct BatchLaunch {
+    const TMaps* maps;            // [problems] tensor maps (global memory, 64-byte aligned)
+    const PersistParams* probs;   // [problems]
+    const int* cta_off;           // [grid + 1] offsets of every CTA's assignment list
+    const int2* assign;           // (problem, rank in the problem's CTA group)
+};
+
 struct InitParams {
     DevStatus* st;
     unsigned* ticket;
@@ -129,6 +137,8 @@ struct InitParams {
     int64_t T, Tm;
 };
 cudaError_t launch_init(const InitParams& p, cudaStream_t s);
+cudaError_t launch_init_batched(const InitParams* ps, int count, cudaStream_t s);
+cudaError_t launch_batch_results(const DevStatus* const* st, int count, int* out, double* stress, cudaStream_t s);
 cudaError_t launch_finalize(float* Xout, const float* buf1, const float* buf2, int64_t count,
                             const DevStatus* st, cudaStream_t s);
 
@@ -172,6 +182,39 @@ int run_insample(int32_t m, int64_t n, int32_t d, const void* const* delta, int6
                  const ExtScratch* ext);
 // Stores msg as the text fjofc_strerror returns for the next error; returns it.
 const char* set_message(const char* msg);
+
+// Geometry of one in-sample problem's all-pairs pass on G CTAs.
+struct EmbedPlan {
+    K1Geom g;
+    int nRB = 0, G = 0, nbx = 0;
+    int64_t Tm = 0, T = 0;
+};
+
+// Scratch layout and kernel parameters of one in-sample problem (shared by fjofc_embed
+// and the batched plans).  plan() sizes the scratch for G CTAs (G_override > 0: at most
+// that many, else one per SM times the resident CTAs per SM); bind() places it at base,
+// encodes the Delta tensor maps and fills the parameter blocks.
+struct InsampleSetup {
+    EmbedPlan P;
+    int m = 0, d = 0, dtype = 0;
+    int64_t n = 0;
+    fjofc_opts o{};
+    size_t o_buf1 = 0, o_buf2 = 0, o_col = 0, o_head = 0, o_cont = 0, o_fid = 0, o_woff = 0, o_cta = 0, o_mu = 0,
+           o_bpart = 0, o_ticket = 0, o_st = 0, o_hist = 0, o_fid2 = 0, o_cbase = 0, o_contr = 0, o_bar = 0;
+    size_t bytes = 0;
+    TMaps tm;
+    K1Params k1;
+    K2Params k2;
+    PersistParams pp;
+    InitParams ip;
+    int plan(int m, int64_t n, int d, int dtype, const fjofc_opts& opts, bool persistent, int G_override);
+    int bind(char* base, const void* const* delta, int64_t ld, const float* delta_scale, const double* weights,
+             const double* winv, float* X);
+};
+// Gauss-Jordan inverse of Wmod (Eq. modW) for the m x m weights; FJOFC_ERR_ARG if singular.
+int modified_weights_inverse(int m, int64_t n, const double* w, double* winv);
+// cuTensorMapEncodeTiled from the driver (once per process).
+int tensor_map_encoder();
 
 struct OOSPrepParams {
     const float* X;

@@ -13,4 +13,6 @@ template <int D, typename TD> K1Geom k1_geom_impl();
 namespace fjofc {
 template <int D, typename TD> cudaError_t persist_launch_impl(int grid, const TMaps& tm, const PersistParams& P, cudaStream_t s);
 template <int D, typename TD> int persist_bps_impl();
+template <int D, typename TD> cudaError_t batched_launch_impl(int grid, const BatchLaunch& bl, cudaStream_t s);
+template <int D, typename TD> int batched_bps_impl();
 }  // namespace fjofc

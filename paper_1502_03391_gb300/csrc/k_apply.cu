@@ -124,7 +124,7 @@ __device__ __forceinline__ int64_t walk_len(int P, const InitParams& p) {
     return (cols + p.CW - 1) / p.CW;
 }
 
-__global__ void __launch_bounds__(kInitThreads) k_init(const InitParams p) {
+__device__ __forceinline__ void init_problem(const InitParams& p) {
     __shared__ int64_t s_part[kInitThreads];
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -190,8 +190,36 @@ __global__ void __launch_bounds__(kInitThreads) k_init(const InitParams p) {
     }
 }
 
+__global__ void __launch_bounds__(kInitThreads) k_init(const InitParams p) { init_problem(p); }
+
+// One CTA per problem of a batch.
+__global__ void __launch_bounds__(kInitThreads) k_init_batched(const InitParams* __restrict__ ps) {
+    init_problem(ps[blockIdx.x]);
+}
+
 cudaError_t launch_init(const InitParams& p, cudaStream_t s) {
     k_init<<<1, kInitThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_batched(const InitParams* ps, int count, cudaStream_t s) {
+    if (count > 0) k_init_batched<<<count, kInitThreads, 0, s>>>(ps);
+    return cudaGetLastError();
+}
+
+// Per-problem results of a batch: out[3 p + 0] = error status, [3 p + 1] = final
+// iteration, and stress[p] = sigma of the returned iterate.
+__global__ void k_batch_results(const DevStatus* const* st, int count, int* out, double* stress) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    const DevStatus* s = st[e];
+    out[2 * e] = s->error;
+    out[2 * e + 1] = s->final_iter;
+    stress[e] = s->stress;
+}
+
+cudaError_t launch_batch_results(const DevStatus* const* st, int count, int* out, double* stress, cudaStream_t s) {
+    if (count > 0) k_batch_results<<<(count + 127) / 128, 128, 0, s>>>(st, count, out, stress);
     return cudaGetLastError();
 }
 

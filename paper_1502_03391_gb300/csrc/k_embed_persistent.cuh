@@ -32,10 +32,16 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     return v;
 }
 
-// Grid-wide barrier over a monotone counter: arrival k of every CTA waits for G*k
-// arrivals.  Bounded: returns false after kWaitLimitNs (or when *abort_flag is set).
+// Barrier of the G CTAs of one problem over a monotone counter: arrival k of every CTA
+// waits for G*k arrivals (G == 1: a CTA barrier).  Bounded: returns false after
+// kWaitLimitNs (or when *abort_flag is set).
 __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int* s_flag,
-                                             const volatile int* abort_flag) {
+                                             const volatile int* abort_flag, int G) {
+    if (G == 1) {
+        __threadfence();
+        __syncthreads();
+        return true;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -58,14 +64,14 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
     return *s_flag != 0;
 }
 
+// The whole loop of one problem on the CTA of rank b among its P.k1.G CTAs.
 template <int D, typename TD>
-__global__ void __launch_bounds__(K1Shape<D, TD>::NT, 1)
-k_embed_persistent(const __grid_constant__ TMaps tm, const __grid_constant__ PersistParams P) {
+__device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistParams& P, const int b,
+                                                unsigned char* smem_raw) {
     using S = K1Shape<D, TD>;
     constexpr int CWARPS = S::CWARPS, NT = S::NT;
     const K1Params& p = P.k1;
 
-    extern __shared__ unsigned char smem_raw[];
     __shared__ FF s_ff[CWARPS];
     __shared__ float s_mu[FJOFC_MAX_M * FJOFC_MAX_D];
     __shared__ float s_coef[FJOFC_MAX_M][FJOFC_MAX_M], s_wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
@@ -73,7 +79,7 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const __grid_constant__ Per
     __shared__ double s_prev;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int b = blockIdx.x, G = p.G;
+    const int G = p.G;
     const int m = p.m, n = p.n;
     const int passes = P.max_iter + 1;
     const int64_t t_begin = P.cta_start[b];
@@ -127,7 +133,7 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const __grid_constant__ Per
             }
         }
         bar_target += unsigned(G);
-        if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag) || *abort_flag) {
+        if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag, G) || *abort_flag) {
             ok = false;
             break;
         }
@@ -147,7 +153,7 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const __grid_constant__ Per
             phase_b(a, b, G, P.ngroups, bcap, s_phb);
         }
         bar_target += unsigned(G);
-        if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag)) {
+        if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag, G)) {
             ok = false;
             break;
         }
@@ -221,6 +227,65 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const __grid_constant__ Per
 }
 
 template <int D, typename TD>
+__global__ void __launch_bounds__(K1Shape<D, TD>::NT, 1)
+k_embed_persistent(const __grid_constant__ TMaps tm, const __grid_constant__ PersistParams P) {
+    extern __shared__ unsigned char smem_raw[];
+    persist_problem<D, TD>(tm, P, blockIdx.x, smem_raw);
+}
+
+// Many independent problems of one embedding dimension in one cooperative launch: CTA b
+// runs the problems of its list bl.assign[bl.cta_off[b] .. bl.cta_off[b+1]) one after the
+// other, each as rank `y` of that problem's CTA group.  A problem with a group of several
+// CTAs is first in all of their lists, so its ranks start together.  The problem's
+// parameters are copied to shared memory; its tensor maps stay in global memory.
+template <int D, typename TD>
+__global__ void __launch_bounds__(K1Shape<D, TD>::NT, 1)
+k_embed_batched(const __grid_constant__ BatchLaunch bl) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(16) PersistParams s_P;
+    static_assert(sizeof(PersistParams) % 4 == 0, "PersistParams copy");
+    const int b = blockIdx.x;
+    for (int a = bl.cta_off[b]; a < bl.cta_off[b + 1]; ++a) {
+        const int2 as = bl.assign[a];
+        const unsigned* src = reinterpret_cast<const unsigned*>(bl.probs + as.x);
+        unsigned* dst = reinterpret_cast<unsigned*>(&s_P);
+        for (int e = threadIdx.x; e < int(sizeof(PersistParams) / 4); e += blockDim.x) dst[e] = src[e];
+        __syncthreads();
+        persist_problem<D, TD>(bl.maps[as.x], s_P, as.y, smem_raw);
+        __syncthreads();
+    }
+}
+
+template <int D, typename TD>
+cudaError_t batched_launch_impl(int grid, const BatchLaunch& bl, cudaStream_t s) {
+    using S = K1Shape<D, TD>;
+    cudaError_t e = cudaFuncSetAttribute(k_embed_batched<D, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(S::SMEM));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(S::NT);
+    cfg.dynamicSmemBytes = S::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_embed_batched<D, TD>, bl);
+}
+
+template <int D, typename TD>
+int batched_bps_impl() {
+    using S = K1Shape<D, TD>;
+    cudaFuncSetAttribute(k_embed_batched<D, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::SMEM));
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_embed_batched<D, TD>, S::NT, S::SMEM) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+template <int D, typename TD>
 cudaError_t persist_launch_impl(int grid, const TMaps& tm, const PersistParams& P, cudaStream_t s) {
     using S = K1Shape<D, TD>;
     cudaError_t e = cudaFuncSetAttribute(k_embed_persistent<D, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -248,6 +313,12 @@ int persist_bps_impl() {
                                                                cudaStream_t);                            \
     template int persist_bps_impl<D, float>();                                                           \
     template int persist_bps_impl<D, __half>();                                                          \
-    template int persist_bps_impl<D, __nv_bfloat16>();
+    template int persist_bps_impl<D, __nv_bfloat16>();                                                   \
+    template cudaError_t batched_launch_impl<D, float>(int, const BatchLaunch&, cudaStream_t);             \
+    template cudaError_t batched_launch_impl<D, __half>(int, const BatchLaunch&, cudaStream_t);            \
+    template cudaError_t batched_launch_impl<D, __nv_bfloat16>(int, const BatchLaunch&, cudaStream_t);     \
+    template int batched_bps_impl<D, float>();                                                             \
+    template int batched_bps_impl<D, __half>();                                                            \
+    template int batched_bps_impl<D, __nv_bfloat16>();
 
 }  // namespace fjofc
