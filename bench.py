@@ -600,6 +600,100 @@ def run_learned(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_batched(args, rank, world, local_rank):
+    """256 independent problems, n ~ U[100, 4000], m in {2, 3}, d in {2, 3, 5}, each from the
+    small workload's generator with its own seed, float32 Delta, 150 transforms each.
+    (a) one plan (fjofc_plan_run: one CUDA graph) against (b) the plain path, one
+    fjofc_embed call per problem in sequence.  value = pair-updates/s of (a) summed over
+    the problems."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1502_03391_gb300 as fj
+    import synthetic
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(device)
+    iters = 150
+    shapes = synthetic.batched_problem_shapes(256, seed=3000 + rank)
+    probs, X0s, Xs = [], [], []
+    ppt_total, bytes_pass = 0, 0
+    for sh in shapes:
+        prob = synthetic.make_insample(0, n=sh["n"], m=sh["m"], d=sh["d"], seed=sh["seed"], with_deltas=False)
+        dev = []
+        for Fi in prob.F:
+            buf = fj.empty_delta(sh["n"], torch.float32, device)
+            buf.copy_(synthetic.torch_distances(Fi, device, torch.float32))
+            dev.append(buf)
+        X0 = torch.as_tensor(np.asarray(prob.X0, np.float32), device=device).contiguous()
+        probs.append((dev, prob.W))
+        X0s.append(X0)
+        Xs.append(X0.clone())
+        ppt_total += pairs_per_transform(sh["m"], sh["n"])
+        bytes_pass += sh["m"] * sh["n"] * (sh["n"] - 1) // 2 * 4
+    t0 = time.perf_counter()
+    plan = fj.Plan([(dv, W, X) for (dv, W), X in zip(probs, Xs)], max_iter=iters)
+    create_s = time.perf_counter() - t0
+    info = plan.info()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
+
+    def reset():
+        for X, X0 in zip(Xs, X0s):
+            X.copy_(X0)
+
+    def run_plan():
+        plan.run()
+
+    def run_plain():
+        for (dv, W), X in zip(probs, Xs):
+            fj.embed(dv, W, X, max_iter=iters, history=False)
+
+    res = {}
+    with ClockSampler(local_rank) as clk:
+        for name, fn in (("plan", run_plan), ("plain", run_plain)):
+            for _ in range(args.warmup):
+                reset()
+                fn()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                reset()
+                flush.fill_(float(k))
+                evs[k][0].record(stream)
+                fn()
+                evs[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms = [a.elapsed_time(b) for a, b in evs]
+            res[name] = {"ms": sum(ms) / len(ms)}
+    clocks = clk.summary()
+    r = plan.results()
+    res["plan"]["all_status_ok"] = bool(np.all(r.status == 0))
+    value = ppt_total * iters / (res["plan"]["ms"] / 1e3)
+    peaks, src = measured_peaks()
+    achieved = bytes_pass * (iters + 1) / (res["plan"]["ms"] / 1e3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": "Guttman pair-updates/s (batched)", "value": value, "unit": "pair-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["plan"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched-256: n ~ U[100,4000], m in {2,3}, d in {2,3,5}, float32 Delta, "
+                                   "150 transforms each, one plan (CUDA graph)", "problems": len(shapes),
+                       "l2": "L2 flushed before every timed step; Delta 14 GB in total"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "kernel": "k_embed_batched (3 classes)"},
+            "forms": res, "speedup_vs_one_call_each": res["plain"]["ms"] / res["plan"]["ms"],
+            "plan": {"graphed": info["graphed"], "launches": info["launches"],
+                     "groups_max": int(info["groups"].max()), "multi_sm_problems": int((info["groups"] > 1).sum()),
+                     "create_s": create_s},
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -608,11 +702,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="insample", choices=["insample", "precision", "oos", "learned"],
+    ap.add_argument("--workload", default="insample",
+                    choices=["insample", "precision", "oos", "learned", "batched"],
                     help="insample: the headline line (m=2, n=5000, d=3); precision: m=3, n=20000, d=10 "
                          "with float16/bfloat16 Delta vs float32; oos: 100000 out-of-sample objects "
                          "against the m=2, n=10000, d=5 configuration; learned: the same objects from the "
-                         "trained network's warm start vs the standard start")
+                         "trained network's warm start vs the standard start; batched: 256 problems "
+                         "(n ~ U[100,4000], m in {2,3}, d in {2,3,5}) in one plan vs one call each")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -625,6 +721,8 @@ def main():
         run_oos(args, rank, world, local_rank)
     elif args.workload == "learned":
         run_learned(args, rank, world, local_rank)
+    elif args.workload == "batched":
+        run_batched(args, rank, world, local_rank)
     else:
         run_gpu(args, rank, world, local_rank)
 

@@ -811,8 +811,8 @@ const char* fjofc_strerror(int status) {
         case FJOFC_OK: return "ok";
         case FJOFC_ERR_ARG: return g_last_msg[0] ? g_last_msg : "invalid argument";
         case FJOFC_ERR_CUDA: return g_last_msg[0] ? g_last_msg : "CUDA error";
-        case FJOFC_ERR_NONFINITE: return "stress became non-finite (NaN/Inf)";
-        case FJOFC_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+        case FJOFC_ERR_NONFINITE: return g_last_msg[0] ? g_last_msg : "stress became non-finite (NaN/Inf)";
+        case FJOFC_ERR_TIMEOUT: return g_last_msg[0] ? g_last_msg : "a bounded device-side wait timed out";
         case FJOFC_ERR_NOMEM: return g_last_msg[0] ? g_last_msg : "out of device memory";
         case FJOFC_ERR_UNSUPPORTED: return g_last_msg[0] ? g_last_msg : "unsupported configuration";
     }

@@ -239,7 +239,7 @@ extern "C" int fjofc_plan_create(const fjofc_problem* probs, int32_t nprob, cons
     plan->o_stp = off;
     off = align256(off + sizeof(void*) * nprob);
     plan->o_res = off;
-    off = align256(off + sizeof(int) * 2 * nprob);
+    off = align256(off + sizeof(int) * 3 * nprob);
     plan->o_stress = off;
     off = align256(off + sizeof(double) * nprob);
     for (Class& k : classes) {
@@ -323,7 +323,7 @@ extern "C" int fjofc_plan_results(const fjofc_plan* plan, int32_t* status, int32
                                   void* cuda_stream) {
     if (!plan) return fail(FJOFC_ERR_ARG, "plan is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    std::vector<int> res(2 * size_t(plan->nprob));
+    std::vector<int> res(3 * size_t(plan->nprob));
     std::vector<double> st(plan->nprob);
     cudaError_t e;
     if ((e = cudaMemcpyAsync(res.data(), plan->mem + plan->o_res, res.size() * sizeof(int), cudaMemcpyDeviceToHost,
@@ -334,10 +334,16 @@ extern "C" int fjofc_plan_results(const fjofc_plan* plan, int32_t* status, int32
         return cuda_fail(e, "plan results");
     int worst = FJOFC_OK;
     for (int p = 0; p < plan->nprob; ++p) {
-        if (status) status[p] = res[2 * p];
-        if (iters) iters[p] = res[2 * p + 1];
+        if (status) status[p] = res[3 * p];
+        if (iters) iters[p] = res[3 * p + 1];
         if (stress) stress[p] = st[p];
-        if (res[2 * p] != FJOFC_OK && worst == FJOFC_OK) worst = res[2 * p];
+        if (res[3 * p] != FJOFC_OK && worst == FJOFC_OK) {
+            worst = res[3 * p];
+            char msg[160];
+            snprintf(msg, sizeof(msg), "problem %d (SMs %d): status %d, wait site %d", p, plan->groups[p],
+                     res[3 * p], res[3 * p + 2]);
+            fjofc::set_message(msg);
+        }
     }
     return worst;
 }

@@ -207,14 +207,16 @@ cudaError_t launch_init_batched(const InitParams* ps, int count, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Per-problem results of a batch: out[3 p + 0] = error status, [3 p + 1] = final
-// iteration, and stress[p] = sigma of the returned iterate.
+// Per-problem results of a batch: out[3 p] = error status, out[3 p + 1] = final
+// iteration, out[3 p + 2] = where a bounded wait gave up (0 if none), stress[p] =
+// sigma of the returned iterate.
 __global__ void k_batch_results(const DevStatus* const* st, int count, int* out, double* stress) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count) return;
     const DevStatus* s = st[e];
-    out[2 * e] = s->error;
-    out[2 * e + 1] = s->final_iter;
+    out[3 * e] = s->error;
+    out[3 * e + 1] = s->final_iter;
+    out[3 * e + 2] = s->timeout_site;
     stress[e] = s->stress;
 }
 

@@ -108,6 +108,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
     const volatile int* abort_flag = &s_abort;
     unsigned bar_target = 0;
     bool ok = true;
+    int fail_site = 0;            // 31: all-pairs pass wait, 32: barrier 1, 33: barrier 2
     int last_finite = 0;          // newest iterate whose stress was finite
     int t = 1;
 
@@ -118,7 +119,10 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
 
         // ================================================================ phase A
         FF fid_total{0.f, 0.f};
-        if (!phase_a<D, TD>(rg, tm, p, Xprev, int64_t(t - 1) * nq, b, fid_total)) ok = false;
+        if (!phase_a<D, TD>(rg, tm, p, Xprev, int64_t(t - 1) * nq, b, fid_total)) {
+            ok = false;
+            fail_site = 31;
+        }
         if (!ok) atomicExch(&s_abort, 1);
         {
             const FF ws = warp_sum_ff(fid_total);
@@ -134,6 +138,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
         }
         bar_target += unsigned(G);
         if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag, G) || *abort_flag) {
+            if (ok) fail_site = 32;
             ok = false;
             break;
         }
@@ -154,6 +159,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
         }
         bar_target += unsigned(G);
         if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag, G)) {
+            fail_site = 33;
             ok = false;
             break;
         }
@@ -208,11 +214,14 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
 
     if (!ok && tid == 0) {
         atomicExch(&s_abort, 1);
-        raise_error(p.st, FJOFC_ERR_TIMEOUT, 3);
+        raise_error(p.st, FJOFC_ERR_TIMEOUT, fail_site);
     }
     __syncthreads();
-    // wait (bounded) for the sub-tiles prefetched for passes that did not run
+    // wait (bounded) for the sub-tiles prefetched for passes that did not run, then retire
+    // the ring's barriers (the CTA may run another problem next)
     if (tid == 0) rg.drain();
+    __syncthreads();
+    if (tid == 0) rg.invalidate();
     // the returned iterate (centred in place by the pass that computed its stress) goes
     // to the caller's buffer
     if (ok) {

@@ -311,6 +311,17 @@ struct K1Ring {
         __syncthreads();
     }
 
+    // Invalidate the ring's barriers once every copy has landed and every thread is past
+    // its last wait (the caller's __syncthreads), so that start() may initialise them
+    // again.  Thread 0 only.
+    __device__ __forceinline__ void invalidate() {
+        for (int s = 0; s < S::STAGES; ++s) mbar_inval(smem_u32(&full[s]));
+        for (int s = 0; s < S::SLOTS; ++s) {
+            mbar_inval(smem_u32(&rfull[s]));
+            mbar_inval(smem_u32(&rempty[s]));
+        }
+    }
+
     // After an abort: wait (bounded) for the copies that may still be in flight, the most
     // recent use of every stage.  Thread 0 only.
     __device__ __forceinline__ void drain() {

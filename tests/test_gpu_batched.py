@@ -2,8 +2,10 @@
 scheduled together (large ones on groups of SMs with their own barriers, small ones
 sharing an SM one after another), captured in one CUDA graph.
 
-* every problem's X after 20 transforms and its stress match the float64 oracle
-  (relative 1e-5 / 1e-6), including a float16-Delta problem in its own class;
+* every problem's X after 20 transforms matches the float64 oracle (relative 1e-5), and
+  its stress matches the oracle's stress of the same X (1e-6 relative plus the bound of
+  the float32 distance error, which matters only for small, well-fitted problems),
+  including a float16-Delta problem in its own class;
 * with the relative tolerance each problem stops on its own: the same transform count
   and, within float32 reduction-order differences, the same X as a single fjofc_embed;
 * re-running the plan from the same X_0 gives bitwise the same results;
@@ -42,6 +44,37 @@ SHAPES = [  # m, n, d, delta type
 ]
 
 
+RSQRT_EPS = 2.0 ** -22.9     # bound of the hardware reciprocal square root's relative error
+
+
+def _stress_tol(rounded, W, X):
+    """1e-6 relative, plus the float32 distance error the all-pairs pass cannot avoid:
+    each fidelity term (Delta - d)^2 moves by at most about 2 |Delta - d| d eps when d
+    carries the reciprocal square root's relative error eps, so small, well-fitted
+    problems (large sum |e| d / sum e^2) get that much more."""
+    X = np.asarray(X, np.float64)
+    m = len(rounded)
+    n = X.shape[0] // m
+    extra = 0.0
+    for l in range(m):
+        Xl = X[l * n:(l + 1) * n]
+        D = np.sqrt(((Xl[:, None, :] - Xl[None, :, :]) ** 2).sum(-1))
+        iu = np.triu_indices(n, 1)
+        extra += float(W[l][l]) * float(np.sum(np.abs(rounded[l][iu] - D[iu]) * D[iu]))
+    return 2.0 * RSQRT_EPS * extra
+
+
+def _check_stress(got, p, ref, where):
+    """The device's stress of its own X_T against the oracle's stress of that X_T (the
+    arithmetic: 1e-6 relative plus the float32 distance bound), and the oracle's stresses
+    of the device and oracle iterates against each other (1e-5 relative, as X)."""
+    Xg = p["X"].cpu().numpy().astype(np.float64)
+    s_dev_x = O.stress_blocks(p["rounded"], p["prob"].W, Xg)
+    tol = S_TOL * s_dev_x + _stress_tol(p["rounded"], p["prob"].W, Xg)
+    assert abs(got - s_dev_x) <= tol, where
+    assert abs(s_dev_x - ref.stress[-1]) <= X_TOL * ref.stress[-1], where
+
+
 def _problems(fj, shapes, seed0=500):
     import torch
     out = []
@@ -71,7 +104,7 @@ def test_mixed_batch_matches_oracle(fj):
         ref = O.jofc_embed(p["rounded"], p["prob"].W, p["X0"].astype(np.float64), max_iter=20)
         got = p["X"].cpu().numpy().astype(np.float64)
         assert _rel(got, ref.X) <= X_TOL, (i, SHAPES[i])
-        assert abs(res.stress[i] - ref.stress[-1]) <= S_TOL * max(ref.stress[-1], 1e-30), (i, SHAPES[i])
+        _check_stress(res.stress[i], p, ref, (SHAPES[i], i))
     plan.close()
 
 
@@ -106,11 +139,12 @@ def test_per_problem_stopping_matches_single_calls(fj):
             assert abs(res.stress[i] - r.stress) <= 1e-5 * r.stress
 
 
-def test_more_problems_than_sms_share_them(fj):
-    """400 small problems of one class (d = 2): every problem on one SM, two or three one
-    after another on each SM."""
-    rng = np.random.default_rng(3)
-    shapes = [(int(rng.integers(1, 3)), int(rng.integers(20, 60)), 2, "float32") for _ in range(400)]
+@pytest.mark.parametrize("d", [2, 3, 5])
+def test_more_problems_than_sms_share_them(fj, d):
+    """400 small problems of one class: every problem on one SM, two or three one after
+    another on each SM (the ring's barriers are retired and set up again in between)."""
+    rng = np.random.default_rng(3 + d)
+    shapes = [(int(rng.integers(1, 3)), int(rng.integers(20, 60)), d, "float32") for _ in range(400)]
     P = _problems(fj, shapes, seed0=1300)
     plan = fj.Plan([(p["dev"], p["prob"].W, p["X"], p["scales"]) for p in P], max_iter=12)
     info = plan.info()
@@ -121,4 +155,4 @@ def test_more_problems_than_sms_share_them(fj):
     for i, p in enumerate(P):
         ref = O.jofc_embed(p["rounded"], p["prob"].W, p["X0"].astype(np.float64), max_iter=12)
         assert _rel(p["X"].cpu().numpy(), ref.X) <= X_TOL, (i, shapes[i])
-        assert abs(res.stress[i] - ref.stress[-1]) <= S_TOL * max(ref.stress[-1], 1e-30), (i, shapes[i])
+        _check_stress(res.stress[i], p, ref, (shapes[i], i))
