@@ -603,9 +603,11 @@ def run_learned(args, rank, world, local_rank):
 def run_batched(args, rank, world, local_rank):
     """256 independent problems, n ~ U[100, 4000], m in {2, 3}, d in {2, 3, 5}, each from the
     small workload's generator with its own seed, float32 Delta, 150 transforms each.
-    (a) one plan (fjofc_plan_run: one CUDA graph) against (b) the plain path, one
-    fjofc_embed call per problem in sequence.  value = pair-updates/s of (a) summed over
-    the problems."""
+    (a) one autotuned plan (fjofc_plan_autotune: schedule constants chosen by timed
+    probes; fjofc_plan_run: one CUDA graph) against (b) the plain path, one fjofc_embed
+    call per problem in sequence; also reported: the plan whose tuner may store Delta as
+    float16.  value = pair-updates/s of (a) summed over the problems; every plan's final
+    configurations are re-scored with float32 Delta against the plain path's stress."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -633,8 +635,10 @@ def run_batched(args, rank, world, local_rank):
         ppt_total += pairs_per_transform(sh["m"], sh["n"])
         bytes_pass += sh["m"] * sh["n"] * (sh["n"] - 1) // 2 * 4
     t0 = time.perf_counter()
-    plan = fj.Plan([(dv, W, X) for (dv, W), X in zip(probs, Xs)], max_iter=iters)
+    plan = fj.Plan([(dv, W, X) for (dv, W), X in zip(probs, Xs)], max_iter=iters, autotune=True, probe_iters=8)
     create_s = time.perf_counter() - t0
+    plan16 = fj.Plan([(dv, W, X) for (dv, W), X in zip(probs, Xs)], max_iter=iters, autotune=True, probe_iters=8,
+                     allow_f16=True)
     info = plan.info()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
 
@@ -645,13 +649,18 @@ def run_batched(args, rank, world, local_rank):
     def run_plan():
         plan.run()
 
+    def run_plan16():
+        plan16.run()
+
+    plain_stress = [0.0] * len(probs)
+
     def run_plain():
-        for (dv, W), X in zip(probs, Xs):
-            fj.embed(dv, W, X, max_iter=iters, history=False)
+        for i, ((dv, W), X) in enumerate(zip(probs, Xs)):
+            plain_stress[i] = fj.embed(dv, W, X, max_iter=iters, history=False).stress
 
     res = {}
     with ClockSampler(local_rank) as clk:
-        for name, fn in (("plan", run_plan), ("plain", run_plain)):
+        for name, fn in (("plan", run_plan), ("plan_f16_allowed", run_plan16), ("plain", run_plain)):
             for _ in range(args.warmup):
                 reset()
                 fn()
@@ -668,8 +677,19 @@ def run_batched(args, rank, world, local_rank):
             ms = [a.elapsed_time(b) for a, b in evs]
             res[name] = {"ms": sum(ms) / len(ms)}
     clocks = clk.summary()
-    r = plan.results()
-    res["plan"]["all_status_ok"] = bool(np.all(r.status == 0))
+    # final stress of the plan's results, re-scored with the float32 Delta (the tuner may
+    # have chosen float16 storage), against the plain path's
+    for name, pl in (("plan", plan), ("plan_f16_allowed", plan16)):
+        for X, X0 in zip(Xs, X0s):
+            X.copy_(X0)
+        pl.run()
+        r = pl.results()
+        rescored = np.array([fj.stress(dv, W, X) for (dv, W), X in zip(probs, Xs)])
+        rel = np.abs(rescored - np.array(plain_stress)) / np.array(plain_stress)
+        res[name]["all_status_ok"] = bool(np.all(r.status == 0))
+        res[name]["final_stress_rel_to_plain_max"] = float(rel.max())
+        res[name]["final_stress_rel_to_plain_mean"] = float(rel.mean())
+        res[name]["tuning"] = pl.tuning
     value = ppt_total * iters / (res["plan"]["ms"] / 1e3)
     peaks, src = measured_peaks()
     achieved = bytes_pass * (iters + 1) / (res["plan"]["ms"] / 1e3) / 1e9
@@ -687,11 +707,12 @@ def run_batched(args, rank, world, local_rank):
             "forms": res, "speedup_vs_one_call_each": res["plain"]["ms"] / res["plan"]["ms"],
             "plan": {"graphed": info["graphed"], "launches": info["launches"],
                      "groups_max": int(info["groups"].max()), "multi_sm_problems": int((info["groups"] > 1).sum()),
-                     "create_s": create_s},
+                     "create_and_tune_s": create_s},
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     plan.close()
+    plan16.close()
 
 
 def main():

@@ -245,6 +245,30 @@ int fjofc_plan_info(const fjofc_plan* plan, int32_t* groups, int32_t* graphed, i
 
 void fjofc_plan_destroy(fjofc_plan* plan);
 
+typedef struct {
+    int32_t probe_iters;   /* transforms per timed probe run (<= 0: 8) */
+    int32_t allow_f16;     /* 1: float32 Delta may be stored as float16 (scaled by max/2^10) */
+    int32_t reserved[6];
+} fjofc_tune_opts;
+
+typedef struct {
+    float pass_cost;       /* chosen schedule constants (sub-tile units) */
+    float barrier_cost;
+    int32_t delta_dtype;   /* FJOFC_F16 when the float16 copies won, else -1 (as given) */
+    float probe_ms;        /* the winner's probe run */
+    int32_t candidates;    /* candidates timed */
+    int32_t reserved[3];
+} fjofc_tune_result;
+
+/* Autotuned plan: times a probe run (probe_iters transforms) of each candidate -- the
+ * schedule's cost constants, which fix how problems are cut into per-SM (problem,
+ * sub-tile range) work, and, when allowed, float16 storage of float32 Delta in
+ * plan-owned buffers -- and creates the plan of the fastest with opts.  Every problem's
+ * X is restored after each probe (X holds X_0 again on return).  result may be NULL. */
+int fjofc_plan_autotune(const fjofc_problem* problems, int32_t count, const fjofc_opts* opts,
+                        const fjofc_tune_opts* tune, fjofc_plan** plan, fjofc_tune_result* result,
+                        void* cuda_stream);
+
 /* ------------------------------------------------------------------------------------
  * Learned warm start for fjofc_oos.  The paper has no counterpart: this is the learned
  * form added beside the method.  A network with two hidden GELU layers

@@ -37,7 +37,7 @@ MAX_M, MAX_D = 8, 16
 EXPORTS = ("fjofc_embed", "fjofc_embed_noalloc", "fjofc_stress", "fjofc_oos", "fjofc_strerror", "fjofc_version",
            "fjofc_mlp_param_count", "fjofc_mlp_init", "fjofc_mlp_features", "fjofc_mlp_forward", "fjofc_mlp_gradient",
            "fjofc_mlp_train", "fjofc_mlp_broadcast", "fjofc_mlp_select", "fjofc_plan_create", "fjofc_plan_run",
-           "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy")
+           "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy", "fjofc_plan_autotune")
 
 
 class FjofcError(RuntimeError):
@@ -65,6 +65,15 @@ class _Problem(ctypes.Structure):
                 ("X", ctypes.c_void_p)]
 
 
+class _TuneOpts(ctypes.Structure):
+    _fields_ = [("probe_iters", ctypes.c_int32), ("allow_f16", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class _TuneResult(ctypes.Structure):
+    _fields_ = [("pass_cost", ctypes.c_float), ("barrier_cost", ctypes.c_float), ("delta_dtype", ctypes.c_int32),
+                ("probe_ms", ctypes.c_float), ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"fJOFC CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
@@ -87,6 +96,9 @@ def _load():
     lib.fjofc_plan_results.restype = ctypes.c_int
     lib.fjofc_plan_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.fjofc_plan_info.restype = ctypes.c_int
+    lib.fjofc_plan_autotune.argtypes = [ctypes.POINTER(_Problem), i32, ctypes.POINTER(_Opts),
+                                        ctypes.POINTER(_TuneOpts), ctypes.POINTER(vp), ctypes.POINTER(_TuneResult), vp]
+    lib.fjofc_plan_autotune.restype = ctypes.c_int
     lib.fjofc_plan_destroy.argtypes = [vp]
     lib.fjofc_plan_destroy.restype = None
     lib.fjofc_strerror.argtypes = [ctypes.c_int]
@@ -323,7 +335,11 @@ class Plan:
     is a sequence of (deltas, weights, X) or (deltas, weights, X, delta_scale) with the
     same conventions as ``embed``; every problem gets the same loop options."""
 
-    def __init__(self, problems, max_iter: int, tol: float = -1.0, tol_mode: str = "relative"):
+    def __init__(self, problems, max_iter: int, tol: float = -1.0, tol_mode: str = "relative",
+                 autotune: bool = False, probe_iters: int = 8, allow_f16: bool = False, stream=None):
+        """``autotune``: let ``fjofc_plan_autotune`` time candidate schedules (and float16
+        storage of float32 Delta when ``allow_f16``) on ``probe_iters`` transforms and keep
+        the fastest; the choice is in ``self.tuning``."""
         keep = []
         arr = (_Problem * len(problems))()
         for i, pr in enumerate(problems):
@@ -341,7 +357,18 @@ class Plan:
                               Wn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(X.data_ptr()))
         opts = _Opts(int(max_iter), float(tol), TOL_RELATIVE if tol_mode == "relative" else TOL_ABS_NORMALIZED)
         h = ctypes.c_void_p()
-        _check(_lib.fjofc_plan_create(arr, len(problems), ctypes.byref(opts), ctypes.byref(h)))
+        self.tuning = None
+        if autotune:
+            torch = _torch()
+            to = _TuneOpts(int(probe_iters), 1 if allow_f16 else 0)
+            tr = _TuneResult()
+            _check(_lib.fjofc_plan_autotune(arr, len(problems), ctypes.byref(opts), ctypes.byref(to), ctypes.byref(h),
+                                            ctypes.byref(tr), _stream_handle(stream, torch.device("cuda"))))
+            self.tuning = {"pass_cost": tr.pass_cost, "barrier_cost": tr.barrier_cost,
+                           "float16_delta": tr.delta_dtype == F16, "probe_ms": tr.probe_ms,
+                           "candidates": tr.candidates}
+        else:
+            _check(_lib.fjofc_plan_create(arr, len(problems), ctypes.byref(opts), ctypes.byref(h)))
         self._h = h
         self.count = len(problems)
 

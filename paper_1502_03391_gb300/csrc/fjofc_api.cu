@@ -291,6 +291,10 @@ int validate_insample(int32_t m, int64_t n, int32_t d, const void* const* delta,
 namespace fjofc {
 
 int modified_weights_inverse(int m, int64_t n, const double* w, double* winv) { return weights_inverse(m, n, w, winv); }
+int validate_problem(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t dtype,
+                     const float* delta_scale, const void* X) {
+    return validate_insample(m, n, d, delta, ld, dtype, delta_scale, X);
+}
 int tensor_map_encoder() { return get_encoder(); }
 
 int InsampleSetup::plan(int m_, int64_t n_, int d_, int dtype_, const fjofc_opts& opts, bool persistent,

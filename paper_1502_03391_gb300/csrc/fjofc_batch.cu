@@ -5,11 +5,12 @@
 // the class launches, the result gather) is captured once into a CUDA graph.
 //
 // Scheduling (host, once per plan): the cost of a problem is its sub-tiles per pass plus
-// a fixed per-pass cost (the per-object phase, totals and barriers, about kPassCost
-// sub-tiles; one more per pass for each group barrier) times its number of passes.
-// Problems costing more than the per-CTA average get a group of G >= 2 CTAs of their
-// own, placed first in those CTAs' lists so that all ranks start together; the others
-// go, largest first, to the least-loaded CTA (longest-processing-time rule).
+// a fixed per-pass cost (the per-object phase and totals, about kPassCost sub-tiles)
+// times its number of passes; a problem split over a group pays kBarrierCost per pass
+// on every rank for the group barriers.  A binary search finds the smallest per-CTA load
+// M such that every problem costing more than M gets a group of its own (ceil(cost /
+// (M - barrier cost)) CTAs, first in those CTAs' lists so that all ranks start
+// together) and the others fit, largest first, into the remaining capacity (first fit).
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -30,8 +31,8 @@ namespace {
 
 using fjofc::InsampleSetup;
 
-constexpr double kPassCost = 4.0;      // per-pass fixed cost, in sub-tiles
-constexpr double kBarrierCost = 1.0;   // per pass and group barrier pair, in sub-tiles
+constexpr double kPassCost = 4.0;      // default per-pass fixed cost, in sub-tiles
+constexpr double kBarrierCost = 1.0;   // default per pass and group barrier pair, in sub-tiles
 
 template <typename TD>
 cudaError_t batched_launch_dt(int d, int grid, const fjofc::BatchLaunch& bl, cudaStream_t s) {
@@ -92,6 +93,7 @@ struct fjofc_plan {
     std::vector<int> groups;           // CTAs per problem
     std::vector<Class> classes;
     char* mem = nullptr;               // one device allocation for everything
+    char* delta16 = nullptr;           // float16 copies of Delta chosen by the tuner (or NULL)
     size_t o_maps = 0, o_probs = 0, o_init = 0, o_stp = 0, o_res = 0, o_stress = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -118,11 +120,14 @@ struct fjofc_plan {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (mem) cudaFree(mem);
+        if (delta16) cudaFree(delta16);
     }
 };
 
-extern "C" int fjofc_plan_create(const fjofc_problem* probs, int32_t nprob, const fjofc_opts* opts,
-                                 fjofc_plan** out) {
+namespace {
+
+int create_plan(const fjofc_problem* probs, int32_t nprob, const fjofc_opts* opts, double pass_cost,
+                double barrier_cost, fjofc_plan** out) {
     if (!out) return fail(FJOFC_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!probs || nprob < 1) return fail(FJOFC_ERR_ARG, "need at least one problem");
@@ -156,9 +161,10 @@ extern "C" int fjofc_plan_create(const fjofc_problem* probs, int32_t nprob, cons
         if (!q.delta || !q.X || !q.weights) return fail(FJOFC_ERR_ARG, "problem with a NULL pointer");
         if (q.delta_dtype != FJOFC_F32 && q.delta_dtype != FJOFC_F16 && q.delta_dtype != FJOFC_BF16)
             return fail(FJOFC_ERR_ARG, "unknown delta_dtype");
+        if ((rc = fjofc::validate_problem(q.m, q.n, q.d, q.delta, q.ld, q.delta_dtype, q.delta_scale, q.X))) return rc;
         if ((rc = fjofc::modified_weights_inverse(q.m, q.n, q.weights, winv[p].data()))) return rc;
         if ((rc = S[p].plan(q.m, q.n, q.d, q.delta_dtype, o, true, 1))) return rc;
-        cost[p] = double(o.max_iter + 1) * (double(S[p].P.T) + kPassCost);
+        cost[p] = double(o.max_iter + 1) * (double(S[p].P.T) + pass_cost);
         int c = 0;
         while (c < int(classes.size()) && !(classes[c].d == q.d && classes[c].dtype == q.delta_dtype)) ++c;
         if (c == int(classes.size())) {
@@ -171,41 +177,60 @@ extern "C" int fjofc_plan_create(const fjofc_problem* probs, int32_t nprob, cons
         cls[p] = c;
     }
 
-    // ---- schedule every class onto its grid
+    // ---- schedule every class onto its grid: the smallest per-CTA load M (binary search)
+    // for which every problem costing more than M fits on a group of its own and the others
+    // fit, first-fit decreasing, into what is left
+    const double passes = double(o.max_iter + 1);
     std::vector<int> groups(nprob, 1);
     for (int c = 0; c < int(classes.size()); ++c) {
         Class& k = classes[c];
         std::vector<int> mine;
-        double total = 0.0;
+        double total = 0.0, lo = 0.0;
         for (int p = 0; p < nprob; ++p)
-            if (cls[p] == c) { mine.push_back(p); total += cost[p]; }
-        std::stable_sort(mine.begin(), mine.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-        const double target = total / k.grid;
-        std::vector<std::vector<int2>> lists(k.grid);
-        std::vector<double> load(k.grid, 0.0);
-        int fresh = 0;                                     // CTAs [fresh, grid) hold nothing yet
-        for (int p : mine) {
-            int G = 1;
-            if (cost[p] > 1.5 * target) {
-                G = int(std::ceil(cost[p] / target));
-                G = int(std::min<int64_t>(G, S[p].P.T));
-                G = std::min(G, k.grid - fresh);
-                if (G < 2) G = 1;
+            if (cls[p] == c) {
+                mine.push_back(p);
+                total += cost[p];
+                lo = std::max(lo, cost[p] / double(S[p].P.T) + passes * barrier_cost);
             }
-            if (G >= 2) {
-                for (int r = 0; r < G; ++r) {
-                    lists[fresh + r].push_back(make_int2(p, r));
-                    load[fresh + r] = (cost[p] + double(o.max_iter + 1) * kBarrierCost * G) / G;
+        std::stable_sort(mine.begin(), mine.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        lo = std::max(lo, total / k.grid);
+        std::vector<std::vector<int2>> lists;
+        std::vector<int> G(nprob, 1);
+        auto fits = [&](double M) {
+            lists.assign(k.grid, {});
+            std::vector<double> load(k.grid, 0.0);
+            int used = 0;
+            for (int p : mine) {
+                if (cost[p] <= M) continue;
+                const double room = M - passes * barrier_cost;
+                if (room <= 0.0) return false;
+                const int64_t g = int64_t(std::ceil(cost[p] / room));
+                if (g < 2 || g > S[p].P.T || used + g > k.grid) return false;
+                for (int r = 0; r < int(g); ++r) {
+                    lists[used + r].push_back(make_int2(p, r));
+                    load[used + r] = cost[p] / double(g) + passes * barrier_cost;
                 }
-                fresh += G;
-            } else {
-                const int b = int(std::min_element(load.begin(), load.end()) - load.begin());
+                G[p] = int(g);
+                used += int(g);
+            }
+            for (int p : mine) {
+                if (cost[p] > M) continue;
+                int b = 0;
+                while (b < k.grid && load[b] + cost[p] > M) ++b;
+                if (b == k.grid) return false;
                 lists[b].push_back(make_int2(p, 0));
                 load[b] += cost[p];
-                fresh = std::max(fresh, b + 1);
+                G[p] = 1;
             }
-            groups[p] = G;
+            return true;
+        };
+        double hi = std::max(lo, total) * 1.0001 + 1.0;
+        for (int it = 0; it < 60 && hi - lo > 1e-4 * hi; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (fits(mid)) hi = mid; else lo = mid;
         }
+        if (!fits(hi)) return fail(FJOFC_ERR_UNSUPPORTED, "internal: no schedule");
+        for (int p : mine) groups[p] = G[p];
         k.cta_off.assign(k.grid + 1, 0);
         for (int b = 0; b < k.grid; ++b) {
             k.cta_off[b + 1] = k.cta_off[b] + int(lists[b].size());
@@ -309,6 +334,13 @@ extern "C" int fjofc_plan_create(const fjofc_problem* probs, int32_t nprob, cons
     return FJOFC_OK;
 }
 
+}  // namespace
+
+extern "C" int fjofc_plan_create(const fjofc_problem* probs, int32_t nprob, const fjofc_opts* opts,
+                                 fjofc_plan** out) {
+    return create_plan(probs, nprob, opts, kPassCost, kBarrierCost, out);
+}
+
 extern "C" int fjofc_plan_run(fjofc_plan* plan, void* cuda_stream) {
     if (!plan) return fail(FJOFC_ERR_ARG, "plan is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -358,3 +390,165 @@ extern "C" int fjofc_plan_info(const fjofc_plan* plan, int32_t* groups, int32_t*
 }
 
 extern "C" void fjofc_plan_destroy(fjofc_plan* plan) { delete plan; }
+
+// ------------------------------------------------------------------ autotuner
+// Times a short run (probe_iters transforms, fixed count) of every candidate plan and
+// builds the plan of the fastest one with the caller's options.  Candidates: the
+// schedule's cost constants (how problems are cut into per-SM (problem, sub-tile range)
+// work) and, if the caller allows it, float16 storage of the float32 Delta (converted
+// into plan-owned buffers, scale max|Delta|/2^10 per matrix).  Every X is saved before
+// the probes and restored after each one.
+extern "C" int fjofc_plan_autotune(const fjofc_problem* probs, int32_t nprob, const fjofc_opts* opts,
+                                   const fjofc_tune_opts* topts, fjofc_plan** out, fjofc_tune_result* result,
+                                   void* cuda_stream) {
+    if (!out) return fail(FJOFC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!probs || nprob < 1 || !opts) return fail(FJOFC_ERR_ARG, "need problems and opts");
+    const int probe = (topts && topts->probe_iters > 0) ? topts->probe_iters : 8;
+    const bool allow16 = topts && topts->allow_f16;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e;
+
+    // save every X
+    std::vector<size_t> xoff(nprob + 1, 0);
+    for (int p = 0; p < nprob; ++p) xoff[p + 1] = xoff[p] + size_t(probs[p].m) * probs[p].n * probs[p].d;
+    float* xsave = nullptr;
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&xsave), std::max<size_t>(1, xoff[nprob]) * 4)) != cudaSuccess)
+        return cuda_fail(e, "tuner X backup");
+    struct Free {
+        void* p;
+        ~Free() { if (p) cudaFree(p); }
+    } fx{xsave};
+    auto copy_x = [&](bool save) -> cudaError_t {
+        for (int p = 0; p < nprob; ++p) {
+            const size_t bytes = (xoff[p + 1] - xoff[p]) * 4;
+            cudaError_t ee = save ? cudaMemcpyAsync(xsave + xoff[p], probs[p].X, bytes, cudaMemcpyDeviceToDevice, s)
+                                  : cudaMemcpyAsync(probs[p].X, xsave + xoff[p], bytes, cudaMemcpyDeviceToDevice, s);
+            if (ee != cudaSuccess) return ee;
+        }
+        return cudaSuccess;
+    };
+    if ((e = copy_x(true)) != cudaSuccess) return cuda_fail(e, "tuner X backup");
+
+    // float16 copies of the float32 Delta (only if allowed and useful)
+    std::vector<fjofc_problem> p16(probs, probs + nprob);
+    std::vector<std::vector<const void*>> ptr16(nprob);
+    std::vector<std::vector<float>> scale16(nprob);
+    char* d16 = nullptr;
+    bool have16 = false;
+    if (allow16) {
+        size_t bytes = 0;
+        std::vector<size_t> off16(nprob);
+        for (int p = 0; p < nprob; ++p) {
+            off16[p] = bytes;
+            if (probs[p].delta_dtype != FJOFC_F32) continue;
+            const int64_t ld16 = (probs[p].n + 7) / 8 * 8;
+            bytes = align256(bytes + size_t(probs[p].m) * probs[p].n * ld16 * 2);
+            have16 = true;
+        }
+        const size_t maxbytes = align256(bytes) + sizeof(unsigned) * 8 * size_t(nprob);
+        if (have16 && (e = cudaMalloc(reinterpret_cast<void**>(&d16), maxbytes)) != cudaSuccess)
+            return cuda_fail(e, "tuner float16 Delta");
+        if (have16) {
+            unsigned* mx = reinterpret_cast<unsigned*>(d16 + align256(bytes));
+            cudaMemsetAsync(mx, 0, sizeof(unsigned) * 8 * size_t(nprob), s);
+            for (int p = 0; p < nprob; ++p)
+                if (probs[p].delta_dtype == FJOFC_F32)
+                    for (int l = 0; l < probs[p].m; ++l)
+                        if ((e = fjofc::launch_absmax(static_cast<const float*>(probs[p].delta[l]), probs[p].n,
+                                                      probs[p].ld, mx + 8 * p + l, s)) != cudaSuccess) {
+                            cudaFree(d16);
+                            return cuda_fail(e, "tuner max");
+                        }
+            std::vector<unsigned> hm(8 * size_t(nprob));
+            cudaMemcpyAsync(hm.data(), mx, hm.size() * 4, cudaMemcpyDeviceToHost, s);
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+                cudaFree(d16);
+                return cuda_fail(e, "tuner max");
+            }
+            for (int p = 0; p < nprob; ++p) {
+                if (probs[p].delta_dtype != FJOFC_F32) continue;
+                const int64_t n = probs[p].n, ld16 = (n + 7) / 8 * 8;
+                ptr16[p].resize(probs[p].m);
+                scale16[p].resize(probs[p].m);
+                for (int l = 0; l < probs[p].m; ++l) {
+                    float mxv;
+                    std::memcpy(&mxv, &hm[8 * p + l], 4);
+                    const float sc = (mxv > 0.f && std::isfinite(mxv)) ? mxv / 1024.f : 1.f;
+                    const float base = probs[p].delta_scale ? probs[p].delta_scale[l] : 1.f;
+                    char* dst = d16 + off16[p] + size_t(l) * n * ld16 * 2;
+                    if ((e = fjofc::launch_to_half(static_cast<const float*>(probs[p].delta[l]), n, probs[p].ld,
+                                                   1.f / sc, dst, ld16, s)) != cudaSuccess) {
+                        cudaFree(d16);
+                        return cuda_fail(e, "tuner convert");
+                    }
+                    ptr16[p][l] = dst;
+                    scale16[p][l] = sc * base;
+                }
+                p16[p].delta = ptr16[p].data();
+                p16[p].ld = ld16;
+                p16[p].delta_dtype = FJOFC_F16;
+                p16[p].delta_scale = scale16[p].data();
+            }
+        }
+    }
+
+    struct Cand {
+        double pc, bc;
+        bool f16;
+    };
+    std::vector<Cand> cands;
+    const double pcs[4][2] = {{2.0, 0.5}, {4.0, 1.0}, {8.0, 2.0}, {4.0, 3.0}};
+    for (int f = 0; f < (have16 ? 2 : 1); ++f)
+        for (const auto& c : pcs) cands.push_back(Cand{c[0], c[1], f == 1});
+    fjofc_opts po = *opts;
+    po.max_iter = probe;
+    po.tol = -1.0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = -1;
+    float best_ms = 0.f;
+    int rc = FJOFC_OK;
+    for (int ci = 0; ci < int(cands.size()); ++ci) {
+        fjofc_plan* cand = nullptr;
+        rc = create_plan(cands[ci].f16 ? p16.data() : probs, nprob, &po, cands[ci].pc, cands[ci].bc, &cand);
+        if (rc) break;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && rc == FJOFC_OK; ++rep) {        // the first run warms up
+            cudaEventRecord(e0, s);
+            rc = fjofc_plan_run(cand, s);
+            cudaEventRecord(e1, s);
+            if (rc == FJOFC_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(e, "tuner probe");
+            if (rc == FJOFC_OK) cudaEventElapsedTime(&ms, e0, e1);
+            if (rc == FJOFC_OK && (e = copy_x(false)) != cudaSuccess) rc = cuda_fail(e, "tuner X restore");
+        }
+        if (rc == FJOFC_OK) rc = fjofc_plan_results(cand, nullptr, nullptr, nullptr, s);
+        delete cand;
+        if (rc) break;
+        if (best < 0 || ms < best_ms) {
+            best = ci;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == FJOFC_OK && (e = copy_x(false)) != cudaSuccess) rc = cuda_fail(e, "tuner X restore");
+    if (rc == FJOFC_OK) rc = create_plan(cands[best].f16 ? p16.data() : probs, nprob, opts, cands[best].pc,
+                                         cands[best].bc, out);
+    if (rc != FJOFC_OK) {
+        if (d16) cudaFree(d16);
+        return rc;
+    }
+    if (cands[best].f16) (*out)->delta16 = d16;      // the plan owns the float16 copies
+    else if (d16) cudaFree(d16);
+    if (result) {
+        std::memset(result, 0, sizeof(*result));
+        result->pass_cost = float(cands[best].pc);
+        result->barrier_cost = float(cands[best].bc);
+        result->delta_dtype = cands[best].f16 ? FJOFC_F16 : -1;
+        result->probe_ms = best_ms;
+        result->candidates = int(cands.size());
+    }
+    return FJOFC_OK;
+}

@@ -138,6 +138,11 @@ struct InitParams {
 };
 cudaError_t launch_init(const InitParams& p, cudaStream_t s);
 cudaError_t launch_init_batched(const InitParams* ps, int count, cudaStream_t s);
+// float32 Delta -> float16 storage for the batched tuner: largest |Delta| (float bits,
+// *out zeroed by the caller) and the scaled conversion.
+cudaError_t launch_absmax(const float* D, int64_t n, int64_t ld, unsigned* out, cudaStream_t s);
+cudaError_t launch_to_half(const float* D, int64_t n, int64_t ld, float inv_scale, void* out, int64_t ld16,
+                           cudaStream_t s);
 cudaError_t launch_batch_results(const DevStatus* const* st, int count, int* out, double* stress, cudaStream_t s);
 cudaError_t launch_finalize(float* Xout, const float* buf1, const float* buf2, int64_t count,
                             const DevStatus* st, cudaStream_t s);
@@ -213,6 +218,9 @@ struct InsampleSetup {
 };
 // Gauss-Jordan inverse of Wmod (Eq. modW) for the m x m weights; FJOFC_ERR_ARG if singular.
 int modified_weights_inverse(int m, int64_t n, const double* w, double* winv);
+// The argument checks of fjofc_embed for one problem.
+int validate_problem(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t dtype,
+                     const float* delta_scale, const void* X);
 // cuTensorMapEncodeTiled from the driver (once per process).
 int tensor_map_encoder();
 

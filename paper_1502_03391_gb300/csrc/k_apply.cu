@@ -317,3 +317,39 @@ cudaError_t launch_oos_summary(const int32_t* iters, const double* stress, int64
 }
 
 }  // namespace fjofc
+
+namespace fjofc {
+
+// Largest |Delta| of an n x n matrix (row stride ld) as float bits in *out (atomicMax on
+// the bit patterns, which order like the values for non-negative floats; *out starts at 0).
+__global__ void k_absmax(const float* __restrict__ D, int64_t n, int64_t ld, unsigned* out) {
+    float mx = 0.f;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n * n; e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = e / n, c = e - r * n;
+        mx = fmaxf(mx, fabsf(D[r * ld + c]));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
+}
+
+// out (row stride ld16) = half(D * inv_scale).
+__global__ void k_to_half(const float* __restrict__ D, int64_t n, int64_t ld, float inv_scale,
+                          __half* __restrict__ out, int64_t ld16) {
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n * n; e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = e / n, c = e - r * n;
+        out[r * ld16 + c] = __float2half_rn(D[r * ld + c] * inv_scale);
+    }
+}
+
+cudaError_t launch_absmax(const float* D, int64_t n, int64_t ld, unsigned* out, cudaStream_t s) {
+    k_absmax<<<256, 256, 0, s>>>(D, n, ld, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_half(const float* D, int64_t n, int64_t ld, float inv_scale, void* out, int64_t ld16,
+                           cudaStream_t s) {
+    k_to_half<<<512, 256, 0, s>>>(D, n, ld, inv_scale, static_cast<__half*>(out), ld16);
+    return cudaGetLastError();
+}
+
+}  // namespace fjofc

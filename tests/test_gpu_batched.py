@@ -156,3 +156,28 @@ def test_more_problems_than_sms_share_them(fj, d):
         ref = O.jofc_embed(p["rounded"], p["prob"].W, p["X0"].astype(np.float64), max_iter=12)
         assert _rel(p["X"].cpu().numpy(), ref.X) <= X_TOL, (i, shapes[i])
         _check_stress(res.stress[i], p, ref, (shapes[i], i))
+
+
+def test_autotuned_plan_matches_oracle_and_keeps_X0(fj):
+    """The tuner's probe runs leave every X at X_0; the tuned plan (float16 storage
+    allowed) gives oracle parity on the rounded Delta it chose."""
+    import torch
+    shapes = [(2, 300, 3, "float32"), (3, 180, 2, "float32"), (2, 640, 5, "float32"), (1, 90, 3, "float32")]
+    P = _problems(fj, shapes, seed0=1700)
+    plan = fj.Plan([(p["dev"], p["prob"].W, p["X"], p["scales"]) for p in P], max_iter=10, autotune=True,
+                   probe_iters=3, allow_f16=True)
+    assert plan.tuning["candidates"] == 8
+    for p in P:
+        assert bool((p["X"] == torch.as_tensor(p["X0"]).cuda()).all())
+    plan.run()
+    res = plan.results()
+    for i, p in enumerate(P):
+        deltas = p["rounded"]
+        if plan.tuning["float16_delta"]:
+            # the tuner's storage: Delta / s rounded to float16, s = max |Delta| / 2^10
+            deltas = []
+            for D in p["rounded"]:
+                s = np.float32(np.float32(D.max()) / np.float32(1024.0))
+                deltas.append((np.asarray(D, np.float32) * np.float32(1.0 / s)).astype(np.float16).astype(np.float64) * s)
+        ref = O.jofc_embed(deltas, p["prob"].W, p["X0"].astype(np.float64), max_iter=10)
+        assert _rel(p["X"].cpu().numpy(), ref.X) <= X_TOL, (i, shapes[i], plan.tuning)

@@ -32,7 +32,8 @@ def test_header_declares_expected_api():
                                             "fjofc_mlp_init", "fjofc_mlp_features", "fjofc_mlp_forward",
                                             "fjofc_mlp_gradient", "fjofc_mlp_train", "fjofc_mlp_broadcast",
                                             "fjofc_mlp_select", "fjofc_plan_create", "fjofc_plan_run",
-                                            "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy"])
+                                            "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy",
+                                            "fjofc_plan_autotune"])
 
 
 def test_library_loads_and_exports_every_declared_symbol():
