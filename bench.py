@@ -366,8 +366,9 @@ def run_precision(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     device = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(device)
-    prob = synthetic.make_insample(2, rep=rank, with_deltas=False)
+    prob = synthetic.make_insample(2, rep=rank, with_deltas=False, n=args.n or None)
     m, n, d = prob.spec.m, prob.spec.n, prob.spec.d
+    cap = args.max_iter or 300
     dev = {"f32": [], "f16": [], "bf16": []}
     scales = {"f32": None, "f16": [], "bf16": []}
     for Fi in prob.F:
@@ -389,7 +390,7 @@ def run_precision(args, rank, world, local_rank):
         for key in ("f32", "f16", "bf16"):
             def step():
                 X.copy_(X0)
-                return fj.embed(dev[key], prob.W, X, max_iter=300, tol=1e-7, tol_mode="relative", history=False,
+                return fj.embed(dev[key], prob.W, X, max_iter=cap, tol=1e-7, tol_mode="relative", history=False,
                                 delta_scale=scales[key], profile=2)
             for _ in range(args.warmup):
                 step()
@@ -723,6 +724,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=0, help="precision workload: objects (default 20000; a smaller "
+                                                       "case for profiling)")
+    ap.add_argument("--max-iter", type=int, default=0, help="precision workload: transform cap (default 300)")
     ap.add_argument("--workload", default="insample",
                     choices=["insample", "precision", "oos", "learned", "batched"],
                     help="insample: the headline line (m=2, n=5000, d=3); precision: m=3, n=20000, d=10 "

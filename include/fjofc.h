@@ -110,10 +110,11 @@ typedef struct fjofc_result {
  *                 commensurability weight of matched pairs across modalities i and j.
  *                 Eq. (W) is w_ii = 1, w_ij = w.
  *  X            : DEVICE float32 (m*n) x d row-major, rows modality-major (the n rows of
- *                 X^(1), then X^(2), ...).  In: X_0.  Out: the final iterate X_T, with
- *                 each modality block's column means removed in float64 (Guttman
- *                 outputs are centred in exact arithmetic, Sec. 1.2.2).  X_0 itself is
- *                 used as given (its stress is that of the uncentred input).
+ *                 X^(1), then X^(2), ...), 16-byte aligned.  In: X_0.  Out: the final
+ *                 iterate X_T, with each modality block's column means (float-float
+ *                 sums) removed (Guttman outputs are centred in exact arithmetic, Sec.
+ *                 1.2.2).  X_0 itself is used as given (its stress is that of the
+ *                 uncentred input).
  *  opts, res    : host; see above.  res may be NULL.
  *  cuda_stream  : cudaStream_t.
  *

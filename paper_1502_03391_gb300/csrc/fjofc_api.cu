@@ -280,6 +280,7 @@ int validate_insample(int32_t m, int64_t n, int32_t d, const void* const* delta,
     if (d > FJOFC_MAX_D) { snprintf(g_last_msg, sizeof(g_last_msg), "d > %d is not built", FJOFC_MAX_D); return FJOFC_ERR_UNSUPPORTED; }
     if (!delta) return arg_error("delta is NULL");
     if (!X) return arg_error("X is NULL");
+    if (reinterpret_cast<uintptr_t>(X) & 15u) return arg_error("X must be 16-byte aligned");
     if (delta_scale)
         for (int i = 0; i < m; ++i)
             if (!(delta_scale[i] > 0.f) || !std::isfinite(delta_scale[i])) return arg_error("delta_scale must be finite and > 0");

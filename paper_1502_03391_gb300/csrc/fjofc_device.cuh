@@ -65,6 +65,19 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared through L2 only (cp.async.cg); bytes < 16
+// reads that many and zero-fills the rest (0: reads nothing).  Both addresses 16-byte
+// aligned.
+__device__ __forceinline__ void cp_async_16(uint32_t dst, const void* src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+// Arrive on the mbarrier once this thread's earlier cp.async copies have landed (counts
+// as one of the barrier's expected arrivals).
+__device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" :: "r"(bar) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Invalidate an mbarrier before its memory is initialised again (a CTA that runs several
 // problems re-initialises its ring barriers for each one).
 __device__ __forceinline__ void mbar_inval(uint32_t bar) {

@@ -16,36 +16,59 @@
 namespace fjofc {
 
 constexpr int kGroupObjects = 32;
-constexpr int kBxBatch = 16;     // column partials in flight per lane
+constexpr int kBxBatch = 16;     // column partials in flight per lane (default)
 
-// (B'_l X_l)_{i,k}: the walk-head row partial of object i, the continuation row partials
-// in CTA order, then the column partials of the walks of row blocks 0..I(i) in order.
-// Data written earlier in the same launch is read through L2 (ld.global.cg); the tables
-// are read-only for the whole launch (ld.global.nc).  This code runs once per pass after
-// the long all-pairs loop, so it is kept small (rolled loops) to limit instruction-cache
-// refills; kBxBatch loads are issued before their sum.
-__device__ __forceinline__ float bx_sum(const BxTables& tb, int l, int k, int i) {
+// (B'_l X_l)_{i,k} for U units (l[u], k[u], object i[u]) at once: the walk-head row
+// partial of the object, the continuation row partials in CTA order, then the column
+// partials of the walks of row blocks 0..I(i) in order.  Every unit's loads of a round
+// (BATCH column partials each) are issued before any sum, so U units cost the latency of
+// one; each unit's sum is formed in the same order whatever U and BATCH are.  Data
+// written earlier in the same launch is read through L2 (ld.global.cg); the tables are
+// read-only for the whole launch (ld.global.nc).  This code runs once per pass after the
+// long all-pairs loop, so its loops stay rolled to limit instruction-cache refills.
+template <int BATCH, int U>
+__device__ __forceinline__ void bx_sum(const BxTables& tb, const int (&l)[U], const int (&k)[U], const int (&i)[U],
+                                       const bool (&on)[U], float (&out)[U]) {
     const int d = tb.d, RB = tb.RB, CW = tb.CW, rbs = tb.rb_shift, cws = tb.cw_shift, nRB = tb.nRB;
-    const int I = i >> rbs, ri = i & (RB - 1);
-    const int2 cr = __ldg(tb.cont + int64_t(l) * nRB + I);
-    const float* cp = tb.colpart + int64_t(l) * tb.Tm * d * CW;
-    float acc = __ldcg(tb.rowhead + ((int64_t(l) * nRB + I) * d + k) * RB + ri);
-#pragma unroll 1
-    for (int b = cr.x; b < cr.y; ++b) acc += __ldcg(tb.rowcont + (int64_t(b) * d + k) * RB + ri);
-    float csum = 0.f;
-#pragma unroll 1
-    for (int J0 = 0; J0 <= I; J0 += kBxBatch) {
-        float v[kBxBatch];
+    int I[U];
+    float acc[U], csum[U];
+    int Imax = -1;
 #pragma unroll
-        for (int u = 0; u < kBxBatch; ++u) {
-            const int J = J0 + u, rel = i - (J << rbs);
-            v[u] = (J <= I) ? __ldcg(cp + ((__ldg(tb.cbase + J) + (rel >> cws)) * d + k) * CW + (rel & (CW - 1)))
-                            : 0.f;
+    for (int u = 0; u < U; ++u) {
+        I[u] = on[u] ? (i[u] >> rbs) : -1;
+        Imax = max(Imax, I[u]);
+        acc[u] = on[u] ? __ldcg(tb.rowhead + ((int64_t(l[u]) * nRB + I[u]) * d + k[u]) * RB + (i[u] & (RB - 1))) : 0.f;
+        csum[u] = 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (!on[u]) continue;
+        const int2 cr = __ldg(tb.cont + int64_t(l[u]) * nRB + I[u]);
+#pragma unroll 1
+        for (int b = cr.x; b < cr.y; ++b)
+            acc[u] += __ldcg(tb.rowcont + (int64_t(b) * d + k[u]) * RB + (i[u] & (RB - 1)));
+    }
+#pragma unroll 1
+    for (int J0 = 0; J0 <= Imax; J0 += BATCH) {
+        float v[U][BATCH];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float* cp = tb.colpart + int64_t(l[u]) * tb.Tm * d * CW;
+#pragma unroll
+            for (int j = 0; j < BATCH; ++j) {
+                const int J = J0 + j, rel = i[u] - (J << rbs);
+                v[u][j] = (J <= I[u]) ? __ldcg(cp + ((__ldg(tb.cbase + J) + (rel >> cws)) * d + k[u]) * CW +
+                                               (rel & (CW - 1)))
+                                      : 0.f;
+            }
         }
 #pragma unroll
-        for (int u = 0; u < kBxBatch; ++u) csum += v[u];
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int j = 0; j < BATCH; ++j) csum[u] += v[u][j];
     }
-    return acc + csum;
+#pragma unroll
+    for (int u = 0; u < U; ++u) out[u] = acc[u] + csum[u];
 }
 
 // What phase B needs besides the partial tables.
@@ -67,6 +90,7 @@ __host__ __device__ constexpr int phase_b_floats_per_group(int m, int d) { retur
 // Phase B for the groups g = g0, g0 + gstride, ... (< ngroups), processed in chunks of at
 // most `cap` groups; s holds cap * phase_b_floats_per_group(m, d) floats (8-byte aligned).
 // Every thread of the CTA must call it.
+template <int BATCH = kBxBatch>
 __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int g0, int gstride, int ngroups, int cap, float* s) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int m = a.m, n = a.n, d = a.d, md = m * d, npart = md + 1;
@@ -77,14 +101,32 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int g0, int gstride
         float* s_bx = s;                                   // [nc][m][d][32]
         float* s_xp = s + nc * md * kGroupObjects;         // [nc][m][d][32]
         FF* s_comm = reinterpret_cast<FF*>(s + 2 * nc * md * kGroupObjects);   // [nc][d]
-        // 1. partial sums and staged x_{t-1}, one (group, l, k) unit per warp
+        // 1. partial sums and staged x_{t-1}: (group, l, k) units, two per warp per round
 #pragma unroll 1
-        for (int u = warp; u < nc * md; u += nwarps) {
-            const int gi = u / md, lk = u - gi * md, l = lk / d, k = lk - l * d;
-            const int i = (g0 + (c0 + gi) * gstride) * kGroupObjects + lane;
-            const bool in = i < n;
-            s_xp[u * kGroupObjects + lane] = in ? __ldcg(a.Xprev + (int64_t(l) * n + i) * d + k) : 0.f;
-            s_bx[u * kGroupObjects + lane] = (in && !a.final_pass) ? bx_sum(a.tb, l, k, i) : 0.f;
+        for (int u0 = warp; u0 < nc * md; u0 += 2 * nwarps) {
+            int uu[2], ll[2], kk[2], ii[2];
+            bool on[2], in[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uu[h] = u0 + h * nwarps;
+                const bool unit = uu[h] < nc * md;
+                const int gi = unit ? uu[h] / md : 0, lk = unit ? uu[h] - gi * md : 0;
+                ll[h] = lk / d;
+                kk[h] = lk - ll[h] * d;
+                ii[h] = (g0 + (c0 + gi) * gstride) * kGroupObjects + lane;
+                in[h] = unit && ii[h] < n;
+                on[h] = in[h] && !a.final_pass;
+            }
+            float xp[2], bx[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) xp[h] = in[h] ? __ldcg(a.Xprev + (int64_t(ll[h]) * n + ii[h]) * d + kk[h]) : 0.f;
+            bx_sum<BATCH, 2>(a.tb, ll, kk, ii, on, bx);
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (uu[h] < nc * md) {
+                    s_xp[uu[h] * kGroupObjects + lane] = xp[h];
+                    s_bx[uu[h] * kGroupObjects + lane] = on[h] ? bx[h] : 0.f;
+                }
         }
         __syncthreads();
         // 2. per (group, coordinate): centre, commensurability, mix, column sums

@@ -155,7 +155,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
             a.wcomm = s_wcomm;
             a.m = m; a.n = n; a.d = D; a.t = t;
             a.final_pass = final_pass;
-            phase_b(a, b, G, P.ngroups, bcap, s_phb);
+            phase_b<(D >= 5 ? 64 : kBxBatch)>(a, b, G, P.ngroups, bcap, s_phb);
         }
         bar_target += unsigned(G);
         if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag, G)) {
@@ -220,6 +220,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
     // wait (bounded) for the sub-tiles prefetched for passes that did not run, then retire
     // the ring's barriers (the CTA may run another problem next)
     if (tid == 0) rg.drain();
+    cp_async_wait_all();
     __syncthreads();
     if (tid == 0) rg.invalidate();
     // the returned iterate (centred in place by the pass that computed its stress) goes

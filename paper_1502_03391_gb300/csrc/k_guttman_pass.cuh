@@ -83,9 +83,13 @@ struct K1Shape {
     static constexpr uint32_t STAGE_BYTES = STAGE_ELEMS * sizeof(TD);
     static constexpr size_t RED_FLOATS = size_t(SLOTS) * CWARPS * D * CW;
     static constexpr int XROW_FLOATS = CWARPS * R * D;   // staged x_i of the next walk
+    // d >= 5: every sub-tile's x_j (CW columns x d, a 16-byte aligned window) staged in
+    // shared memory by the issuing warp (cp.async), STAGES uses ahead like Delta
+    static constexpr bool XSTAGE = D >= 5;
+    static constexpr int XS_FLOATS = XSTAGE ? CW * D + 8 : 0;
     static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + RED_FLOATS * sizeof(float) +
-                                   size_t(XROW_FLOATS) * sizeof(float) +
-                                   size_t(STAGES + 2 * SLOTS) * 8 + size_t(STAGES) * 4 + 128;
+                                   size_t(XROW_FLOATS) * sizeof(float) + size_t(STAGES) * XS_FLOATS * sizeof(float) +
+                                   size_t(2 * STAGES + 2 * SLOTS) * 8 + size_t(STAGES) * 4 + 128;
 };
 
 // Position of a sub-tile: modality l, walk position wp visiting row block I, sub-tile s
@@ -233,7 +237,9 @@ struct K1Ring {
     TD* stages;
     float* red;            // [SLOTS][CWARPS][D][CW] column accumulators
     float* xrow;           // [CWARPS][R*D]          staged rows of the next walk
+    float* xs;             // [STAGES][XS_FLOATS]    staged x_j (XSTAGE)
     uint64_t* full;        // [STAGES]
+    uint64_t* xfull;       // [STAGES] x_j landed (XSTAGE)
     uint64_t* rfull;       // [SLOTS]
     uint64_t* rempty;      // [SLOTS]
     int* released;         // [STAGES] releases so far (monotone)
@@ -251,8 +257,10 @@ struct K1Ring {
         stages = reinterpret_cast<TD*>(smem);
         red = reinterpret_cast<float*>(smem + size_t(S::STAGES) * S::STAGE_BYTES);
         xrow = red + S::RED_FLOATS;
-        full = reinterpret_cast<uint64_t*>(xrow + S::XROW_FLOATS);
-        rfull = full + S::STAGES;
+        xs = xrow + S::XROW_FLOATS;
+        full = reinterpret_cast<uint64_t*>(xs + size_t(S::STAGES) * S::XS_FLOATS);
+        xfull = full + S::STAGES;
+        rfull = xfull + S::STAGES;
         rempty = rfull + S::SLOTS;
         released = reinterpret_cast<int*>(rempty + S::SLOTS);
     }
@@ -264,6 +272,27 @@ struct K1Ring {
         mbar_arrive_expect_tx(bar, S::STAGE_BYTES);
         tma_load_2d(smem_u32(stages + size_t(stage) * S::STAGE_ELEMS), &tm.map[pc.l],
                     pc.I * S::RB + pc.s * S::CW, pc.I * S::RB, bar);
+    }
+
+    // x_j of use u (cursor c) into its stage, by all 32 lanes of one warp: the 16-byte
+    // aligned window of X (16-byte aligned) that holds the CW columns' coordinates, cut
+    // at the end of X; each lane arrives on xfull once its copies have landed.
+    __device__ __forceinline__ void issue_x(const K1Params& p, const float* X, int64_t u, const Cursor& c) {
+        const int lane = threadIdx.x & 31;
+        const int stage = int(u % S::STAGES);
+        const int64_t total = int64_t(p.m) * p.n * D;
+        const int64_t start = (int64_t(c.l) * p.n + c.I * S::RB + c.s * S::CW) * D;
+        const int64_t base = start & ~int64_t(3);
+        const int nch = (int(start - base) + S::CW * D + 3) / 4;
+        float* dst = xs + size_t(stage) * S::XS_FLOATS;
+        for (int k = lane; k < nch; k += 32) {
+            const int64_t f = base + 4 * int64_t(k);
+            const int64_t left = total - f;
+            const int bytes = left >= 4 ? 16 : (left > 0 ? int(left) * 4 : 0);
+            cp_async_16(smem_u32(dst + 4 * k), bytes ? static_cast<const void*>(X + f) : static_cast<const void*>(X),
+                        bytes);
+        }
+        cp_async_arrive_noinc(smem_u32(&xfull[stage]));
     }
 
     __device__ __forceinline__ void advance(const K1Params& p) {
@@ -289,6 +318,7 @@ struct K1Ring {
         if (threadIdx.x == 0) {
             for (int s = 0; s < S::STAGES; ++s) {
                 mbar_init(smem_u32(&full[s]), 1);
+                if (S::XSTAGE) mbar_init(smem_u32(&xfull[s]), 32);
                 released[s] = 0;
             }
             for (int s = 0; s < S::SLOTS; ++s) {
@@ -315,7 +345,10 @@ struct K1Ring {
     // its last wait (the caller's __syncthreads), so that start() may initialise them
     // again.  Thread 0 only.
     __device__ __forceinline__ void invalidate() {
-        for (int s = 0; s < S::STAGES; ++s) mbar_inval(smem_u32(&full[s]));
+        for (int s = 0; s < S::STAGES; ++s) {
+            mbar_inval(smem_u32(&full[s]));
+            if (S::XSTAGE) mbar_inval(smem_u32(&xfull[s]));
+        }
         for (int s = 0; s < S::SLOTS; ++s) {
             mbar_inval(smem_u32(&rfull[s]));
             mbar_inval(smem_u32(&rempty[s]));
@@ -350,7 +383,7 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
     cursor_init(cc, rg.t_begin, p);
     cn = cc;
     bool seg_head = (cc.s == 0);
-    float xi[R][D], racc[R][D], xjn[C][D];
+    float xi[R][D], racc[R][D], xjn[S::XSTAGE ? 1 : C][D];
     {
         const float* Xl = X + int64_t(cc.l) * n * D;
         const float xs = p.xscale[cc.l];
@@ -365,16 +398,30 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
         }
     }
     auto load_cols = [&](const Cursor& c) {
-        const float* Xl = X + int64_t(c.l) * n * D;
-        const float xs = p.xscale[c.l];
-        const int c0 = c.I * RB + c.s * CW + lane * C;
+        if constexpr (!S::XSTAGE) {
+            const float* Xl = X + int64_t(c.l) * n * D;
+            const float xs = p.xscale[c.l];
+            const int c0 = c.I * RB + c.s * CW + lane * C;
 #pragma unroll
-        for (int ci = 0; ci < C; ++ci)
+            for (int ci = 0; ci < C; ++ci)
 #pragma unroll
-            for (int k = 0; k < D; ++k)
-                xjn[ci][k] = (c0 + ci < n) ? __ldcg(Xl + int64_t(c0 + ci) * D + k) * xs : 0.f;
+                for (int k = 0; k < D; ++k)
+                    xjn[ci][k] = (c0 + ci < n) ? __ldcg(Xl + int64_t(c0 + ci) * D + k) * xs : 0.f;
+        }
     };
     load_cols(cn);
+    if constexpr (S::XSTAGE) {
+        // x_j of this pass's first uses (their Delta may have been issued during the
+        // previous pass, before this iterate existed)
+        if (warp == 0) {
+            Cursor c = cc;
+            const int k0 = nq < STAGES ? nq : STAGES;
+            for (int j = 0; j < k0; ++j) {
+                rg.issue_x(p, X, qbase + j, c);
+                if (j + 1 < k0) cursor_next(c, p);
+            }
+        }
+    }
     FF fid{0.f, 0.f};
     int cur_l = cc.l;
     float* xrow = rg.xrow + warp * (R * D);
@@ -397,19 +444,24 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
         return true;
     };
 
+    // ring position of use qbase: stage and use count of that stage, advanced incrementally
+    int stage = int(qbase % STAGES);
+    uint32_t kuse = uint32_t(qbase / STAGES);
     for (int q = 0; q < nq; ++q) {
         const int64_t qg = qbase + q;
-        const int stage = int(qg % STAGES);
-        const int slot = int(qg % SLOTS);
+        const int slot = int(qg & (SLOTS - 1));
+        static_assert((SLOTS & (SLOTS - 1)) == 0, "SLOTS must be a power of two");
         const int r0 = cc.I * RB;
         const int c0 = r0 + cc.s * CW;
         const bool walk_ends = (cc.s + 1 == cc.L);
         const bool last = (q + 1 == nq);
         float xj[C][D];
+        if constexpr (!S::XSTAGE) {
 #pragma unroll
-        for (int c = 0; c < C; ++c)
+            for (int c = 0; c < C; ++c)
 #pragma unroll
-            for (int k = 0; k < D; ++k) xj[c][k] = xjn[c][k];
+                for (int k = 0; k < D; ++k) xj[c][k] = xjn[c][k];
+        }
         if (!last) {                // prefetch the next sub-tile's columns
             cursor_next(cn, p);
             load_cols(cn);
@@ -430,7 +482,25 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
             cur_l = cc.l;
         }
 
-        if (!mbar_wait_or_abort(smem_u32(&rg.full[stage]), uint32_t((qg / STAGES) & 1), abort_flag)) return false;
+        if (!mbar_wait_or_abort(smem_u32(&rg.full[stage]), kuse & 1u, abort_flag)) return false;
+        if constexpr (S::XSTAGE) {
+            if (!mbar_wait_or_abort(smem_u32(&rg.xfull[stage]), kuse & 1u, abort_flag))
+                return false;
+            const int64_t start = (int64_t(cc.l) * n + c0) * D;
+            const float* xsrc = rg.xs + size_t(stage) * S::XS_FLOATS + int(start & 3) + lane * C * D;
+            const float xsc = p.xscale[cc.l];
+            if (c0 + CW <= n) {
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) xj[c][k] = xsrc[c * D + k] * xsc;
+            } else {                // ragged sub-tile: columns past n hold other data
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) xj[c][k] = (c0 + lane * C + c < n) ? xsrc[c * D + k] * xsc : 0.f;
+            }
+        }
         const TD* tile = rg.stages + size_t(stage) * S::STAGE_ELEMS;
         const bool masked = (cc.s * CW < RB) || (c0 + CW > n);
         float cacc0[C][D], cacc1[C][D];
@@ -442,13 +512,20 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
         // release the stage; the last warp to do so refills it with use qg + STAGES
         const bool refill = qg + STAGES < rg.total_q;
         __syncwarp();
+        int is_last = 0;
         if (lane == 0) {
             __threadfence_block();
             // use k = qg / STAGES of this stage is fully released at count (k+1)*CWARPS
-            if (atomicAdd(&rg.released[stage], 1) == int(qg / STAGES + 1) * CWARPS - 1) {
+            if (atomicAdd(&rg.released[stage], 1) == int(kuse + 1) * CWARPS - 1) {
                 __threadfence_block();
+                is_last = 1;
                 if (refill) rg.issue(tm, qg + STAGES);
             }
+        }
+        if constexpr (S::XSTAGE) {
+            // x_j of the refilled use, if it belongs to this pass (this iterate)
+            is_last = __shfl_sync(0xffffffffu, is_last, 0);
+            if (is_last && refill && q + STAGES < nq) rg.issue_x(p, X, qg + STAGES, rg.pc);
         }
         if (refill) rg.advance(p);
         fid = ff_add(fid, sf0 + sf1);
@@ -496,6 +573,10 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
                 }
         }
         cursor_next(cc, p);
+        if (++stage == STAGES) {
+            stage = 0;
+            ++kuse;
+        }
         if (walk_ends && !last) {
             seg_head = true;
             const float xs = p.xscale[cc.l];
@@ -546,6 +627,7 @@ k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
         atomicExch(&s_abort, 1);
         if (lane == 0) raise_error(p.st, FJOFC_ERR_TIMEOUT, 2);
     }
+    cp_async_wait_all();
     __syncthreads();
     if (s_abort && tid == 0) rg.drain();
 

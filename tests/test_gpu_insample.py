@@ -234,7 +234,7 @@ def test_padded_row_stride_is_transparent(fj):
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("m,n,d", [(2, 300, 3), (3, 257, 2), (2, 90, 10)])
+@pytest.mark.parametrize("m,n,d", [(2, 300, 3), (3, 257, 2), (2, 90, 10), (2, 2200, 9)])
 def test_persistent_and_per_pass_launches_agree(fj, m, n, d):
     """The default path (one persistent cooperative kernel for the whole loop) and the
     one-launch-per-pass path (profile=1) compute the same partials in the same order:
