@@ -457,7 +457,7 @@ def run_oos(args, rank, world, local_rank):
     X = torch.as_tensor(np.asarray(prob.X0, np.float32), device=device)
     fj.embed(deltas, prob.W, X, max_iter=200, tol=1e-7, tol_mode="relative", history=False)
     del deltas
-    k = 100000
+    k = args.k or 100000
     F_new, _, Y0 = synthetic.make_oos_objects(prob, k, stream=2, with_deltas=False)
     dnew = fj.empty_oos_delta(k, m, n, torch.float32, device)
     for j in range(m):
@@ -544,7 +544,7 @@ def run_learned(args, rank, world, local_rank):
     def solve(dn, Y, it, st):
         fj.oos(X, dn, prob.W, Y, max_iter=500, tol=1e-6, tol_mode="relative", iters_out=it, stress_out=st)
 
-    ntr, kte = 20000, 100000
+    ntr, kte = 20000, args.k or 100000
     dtr, Ytr = objects(ntr, 1)
     itr = torch.zeros(ntr, dtype=torch.int32, device=device)
     str_ = torch.zeros(ntr, dtype=torch.float64, device=device)
@@ -619,7 +619,7 @@ def run_batched(args, rank, world, local_rank):
     device = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(device)
     iters = 150
-    shapes = synthetic.batched_problem_shapes(256, seed=3000 + rank)
+    shapes = synthetic.batched_problem_shapes(args.problems or 256, seed=3000 + rank)
     probs, X0s, Xs = [], [], []
     ppt_total, bytes_pass = 0, 0
     for sh in shapes:
@@ -727,6 +727,8 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="precision workload: objects (default 20000; a smaller "
                                                        "case for profiling)")
     ap.add_argument("--max-iter", type=int, default=0, help="precision workload: transform cap (default 300)")
+    ap.add_argument("--k", type=int, default=0, help="oos / learned workloads: test objects (default 100000)")
+    ap.add_argument("--problems", type=int, default=0, help="batched workload: problems (default 256)")
     ap.add_argument("--workload", default="insample",
                     choices=["insample", "precision", "oos", "learned", "batched"],
                     help="insample: the headline line (m=2, n=5000, d=3); precision: m=3, n=20000, d=10 "

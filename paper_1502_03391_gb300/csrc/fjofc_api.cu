@@ -679,12 +679,12 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
     char* base = static_cast<char*>(mem.p);
     DevStatus* st = reinterpret_cast<DevStatus*>(base + o_st);
 
-    // delta_new as a 3-D tensor {n points, m modalities, k objects}, box {CW, 1, R}
+    // delta_new as a 3-D tensor {n points, m modalities, k objects}, box {CW, 1, 1}
     CUtensorMap tmap;
     {
         const cuuint64_t dims[3] = {cuuint64_t(n), cuuint64_t(m), cuuint64_t(k)};
         const cuuint64_t strides[2] = {cuuint64_t(ld) * dtype_size(dtype), cuuint64_t(ld) * m * dtype_size(dtype)};
-        const cuuint32_t box[3] = {cuuint32_t(g.CW), 1u, cuuint32_t(g.R)};
+        const cuuint32_t box[3] = {cuuint32_t(g.CW), 1u, 1u};
         if ((rc = encode_map(&tmap, dtype, 3, delta_new, dims, strides, box))) return rc;
     }
 

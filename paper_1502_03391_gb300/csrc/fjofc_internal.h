@@ -162,7 +162,7 @@ struct K3Params {
     float* Y;                  // k x m x d
     int32_t* iters_out;        // may be NULL
     double* stress_out;        // never NULL (internal buffer when the caller passes NULL)
-    unsigned long long* next_block;   // work counter (object groups)
+    unsigned long long* next_block;   // work counter (next new object)
     DevStatus* st;
     int m, n, nx, d, max_iter, tol_mode;
     int64_t k;

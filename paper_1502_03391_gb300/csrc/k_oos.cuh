@@ -11,12 +11,15 @@
 // Sec. 3; with general weights L22 is the modified weight matrix of Eq. modW) and the
 // stress is sum_j w_jj fid_j + sum_{i<j} w_ij ||y_i - y_j||^2 (Eq. joos).
 //
-// GB300 layout: a persistent grid; every warp takes groups of R new objects from an
-// atomic counter and iterates them until all R have stopped.  Each warp owns a
-// private STAGES-deep ring of TMA boxes {CW points, 1 modality, R objects} with its
-// own mbarriers, so warps never wait for one another.  Lanes own C consecutive
-// points of each box; X is read transposed ([m][d][n]) so the C points of a lane are
-// one vector load per coordinate.
+// GB300 layout: a persistent grid; every warp keeps R slots, each holding one new object
+// at its own pass.  A round is one pass of every occupied slot over all (modality,
+// sub-tile); a slot whose object stops is refilled from an atomic object counter at
+// the end of the round, so a warp never idles on objects that converged early.  Each
+// warp owns a private STAGES-deep ring; a stage holds one TMA box {CW points, 1
+// modality, 1 object} per occupied slot, all completing on the stage's mbarrier, so
+// warps never wait for one another (prefetch stays within a round).  Lanes own C
+// consecutive points of each box; X is read transposed ([m][d][n]) so the C points of
+// a lane are one vector load per coordinate, fetched one sub-tile ahead.
 #pragma once
 
 #include <float.h>
@@ -35,18 +38,21 @@ FJOFC_K3CFG(13, 2) FJOFC_K3CFG(14, 2) FJOFC_K3CFG(15, 2) FJOFC_K3CFG(16, 2)
 
 template <int D, typename TD>
 struct K3Shape {
-    static constexpr int R = K3Cfg<D>::R, C = 2, WARPS = 8, STAGES = 4;
+    // C points per lane (4 up to d = 8, 2 beyond: registers); stages keep about 16 KB of
+    // boxes in flight per warp (at least 4)
+    static constexpr int R = K3Cfg<D>::R, C = (D <= 8) ? 4 : 2, WARPS = 8;
     static constexpr int NT = WARPS * 32;
     static constexpr int CW = 32 * C;
     static constexpr int STAGE_ELEMS = R * CW;
     static constexpr uint32_t STAGE_BYTES = STAGE_ELEMS * sizeof(TD);
+    static constexpr int STAGES = (16384 / int(STAGE_BYTES)) < 4 ? 4 : ((16384 / int(STAGE_BYTES)) > 8 ? 8 : (16384 / int(STAGE_BYTES)));
     // per warp: ring, y state, reduced sums (sum b x: D, sum b: 1), fid (double)
     static constexpr size_t RING_BYTES = size_t(STAGES) * STAGE_BYTES;
     static constexpr size_t Y_FLOATS = size_t(R) * FJOFC_MAX_M * D;
     static constexpr size_t ACC_FLOATS = size_t(R) * FJOFC_MAX_M * (D + 1);
     static constexpr size_t WARP_BYTES =
         ((RING_BYTES + (2 * Y_FLOATS + ACC_FLOATS) * 4 + size_t(R) * FJOFC_MAX_M * 8 + 2 * R * 8 + R * 8 +
-          STAGES * 8) + 127) & ~size_t(127);
+          STAGES * 8 + R * 8 + R * 4) + 127) & ~size_t(127);
     static constexpr size_t SMEM = WARPS * WARP_BYTES + 128;
 };
 
@@ -68,14 +74,15 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
     double* fidj = reinterpret_cast<double*>(acc + S::ACC_FLOATS);       // [R][MAXM]
     double* sprev = fidj + R * FJOFC_MAX_M;                              // [R]
     double* scur = sprev + R;                                            // [R]
-    int* flags = reinterpret_cast<int*>(scur + R);                       // [R] done, [R] iters
+    int* flags = reinterpret_cast<int*>(scur + R);                       // [R] state, [R] iters
     uint64_t* full = reinterpret_cast<uint64_t*>(flags + 2 * R);         // [STAGES]
+    long long* slot_obj = reinterpret_cast<long long*>(full + STAGES);  // [R] object (-1: empty)
+    int* slot_pass = reinterpret_cast<int*>(slot_obj + R);               // [R] pass of the slot's object
 
     const int m = p.m, n = p.n;
     const int nsub = (n + CW - 1) / CW;
     const int passes = p.max_iter + 1;
     const int64_t per_pass = int64_t(m) * nsub;
-    const int64_t ngroups = (p.k + R - 1) / R;
 
     if (lane == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(smem_u32(&full[s]), 1);
@@ -84,55 +91,64 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
     }
     __syncwarp();
 
-    uint32_t q_cons = 0;   // sub-tiles consumed by this warp (all groups), drives stage/parity
+    uint32_t q_cons = 0;   // sub-tiles consumed by this warp, drives stage/parity
     uint32_t q_iss = 0;    // sub-tiles issued
+    const uint32_t box_bytes = uint32_t(CW * sizeof(TD));
+
+    // Slots: every slot holds one object (or none) and its own pass count; a slot whose
+    // object stops is refilled from the global object counter at the end of the round.
+    auto fetch = [&](int r) {              // lane 0: next object into slot r
+        const unsigned long long o = atomicAdd(p.next_block, 1ull);
+        slot_obj[r] = (int64_t(o) < p.k) ? (long long)o : -1ll;
+    };
+    auto init_slot = [&](int r) {          // all lanes: state of slot r's new object
+        const long long o = slot_obj[r];
+        for (int e = lane; e < m * D; e += 32) {
+            const int j = e / D, kk = e - j * D;
+            ys[(r * FJOFC_MAX_M + j) * D + kk] = (o >= 0) ? p.Y[(int64_t(o) * m + j) * D + kk] : 0.f;
+        }
+        if (lane == 0) {
+            flags[r] = (o >= 0) ? 0 : 1;   // 0 iterating, 1 empty
+            flags[R + r] = 0;
+            sprev[r] = 0.0;
+            slot_pass[r] = 1;
+        }
+    };
+    if (lane == 0)
+        for (int r = 0; r < R; ++r) fetch(r);
+    __syncwarp();
+    for (int r = 0; r < R; ++r) init_slot(r);
+    __syncwarp();
+
+    bool failed = false;
+    // sub-tile qq of a round: modality qq / nsub, points (qq % nsub) * CW; one box per
+    // occupied slot, all completing on the stage's mbarrier
+    auto issue_sub = [&](int64_t qq) {
+        const int j = int(qq / nsub), s = int(qq % nsub);
+        const int stage = int(q_iss % STAGES);
+        const uint32_t bar = smem_u32(&full[stage]);
+        int nact = 0;
+        for (int r = 0; r < R; ++r) nact += (slot_obj[r] >= 0);
+        mbar_arrive_expect_tx(bar, uint32_t(nact) * box_bytes);
+        for (int r = 0; r < R; ++r)
+            if (slot_obj[r] >= 0)
+                tma_load_3d(smem_u32(ring + size_t(stage) * S::STAGE_ELEMS + size_t(r) * CW), &tmap, s * CW, j,
+                            int(slot_obj[r]), bar);
+    };
 
     for (;;) {
-        int64_t g = 0;
-        if (lane == 0) g = static_cast<int64_t>(atomicAdd(p.next_block, 1ull));
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= ngroups) break;
+        // the round: one pass of every occupied slot over all (modality, sub-tile)
+        int any = 0;
+        if (lane < R) any = slot_obj[lane] >= 0;
+        if (!__any_sync(0xffffffffu, any)) break;
         if (ld_volatile(&p.st->error)) break;
-        const int64_t o0 = g * R;
-
-        // initial state of the R objects
-        for (int e = lane; e < R * m * D; e += 32) {
-            const int r = e / (m * D), rem = e - r * m * D, j = rem / D, kk = rem - j * D;
-            const int64_t o = o0 + r;
-            ys[(r * FJOFC_MAX_M + j) * D + kk] = (o < p.k) ? p.Y[(o * m + j) * D + kk] : 0.f;
+        int64_t issued_in_round = 0;
+        for (int e = 0; e < STAGES && issued_in_round < per_pass; ++e) {
+            if (lane == 0) issue_sub(issued_in_round);
+            ++issued_in_round;
+            ++q_iss;
         }
-        if (lane < R) {
-            flags[lane] = (o0 + lane < p.k) ? 0 : 1;   // objects past k start "done"
-            flags[R + lane] = 0;
-            sprev[lane] = 0.0;
-        }
-        __syncwarp();
-
-        // producer: sub-tile sequence (pass, j, s) of this group, in order
-        int64_t issued_in_group = 0;
-        const int64_t group_total = int64_t(passes) * per_pass;
-        auto issue_next = [&]() {
-            const int64_t qq = issued_in_group;
-            const int j = int((qq % per_pass) / nsub);
-            const int s = int(qq % nsub);
-            const int stage = int(q_iss % STAGES);
-            const uint32_t bar = smem_u32(&full[stage]);
-            mbar_arrive_expect_tx(bar, S::STAGE_BYTES);
-            tma_load_3d(smem_u32(ring + size_t(stage) * S::STAGE_ELEMS), &tmap, s * CW, j, int(o0), bar);
-        };
-        if (lane == 0) {
-            for (int e = 0; e < STAGES && issued_in_group < group_total; ++e) {
-                issue_next();
-                ++issued_in_group;
-                ++q_iss;
-            }
-        }
-        issued_in_group = __shfl_sync(0xffffffffu, issued_in_group, 0);
-        q_iss = __shfl_sync(0xffffffffu, q_iss, 0);
-
-        bool failed = false;
-        int pass = 1;
-        for (; pass <= passes; ++pass) {
+        {
             for (int j = 0; j < m; ++j) {
                 const float sc = p.dscale[j];
                 float yr[R][D];
@@ -149,19 +165,37 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                     for (int kk = 0; kk < D; ++kk) bx[r][kk] = 0.f;
                 }
                 const float* XTj = p.XT + int64_t(j) * D * p.nx;
+                // the C points of this lane in sub-tile s (X^T rows are padded to a multiple of
+                // 4 points, so whole vectors stay inside the row; points >= n are masked below)
+                auto load_xp = [&](int s, float (&xv)[C][D]) {
+                    const int pt = s * CW + lane * C;
+#pragma unroll
+                    for (int kk = 0; kk < D; ++kk) {
+                        const float* src = XTj + int64_t(kk) * p.nx + pt;
+                        if (pt + C <= p.nx) {
+                            if constexpr (C == 4) {
+                                const float4 v = __ldg(reinterpret_cast<const float4*>(src));
+                                xv[0][kk] = v.x; xv[1][kk] = v.y; xv[2][kk] = v.z; xv[3][kk] = v.w;
+                            } else {
+                                const float2 v = __ldg(reinterpret_cast<const float2*>(src));
+                                xv[0][kk] = v.x; xv[1][kk] = v.y;
+                            }
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < C; ++c) xv[c][kk] = 0.f;
+                        }
+                    }
+                };
+                float xpn[C][D];
+                load_xp(0, xpn);
                 for (int s = 0; s < nsub; ++s) {
                     const int pt0 = s * CW + lane * C;
                     float xp[C][D];
 #pragma unroll
-                    for (int kk = 0; kk < D; ++kk) {
-                        if (pt0 + 1 < n) {
-                            const float2 v = *reinterpret_cast<const float2*>(XTj + int64_t(kk) * p.nx + pt0);
-                            xp[0][kk] = v.x; xp[1][kk] = v.y;
-                        } else {
-                            xp[0][kk] = (pt0 < n) ? XTj[int64_t(kk) * p.nx + pt0] : 0.f;
-                            xp[1][kk] = 0.f;
-                        }
-                    }
+                    for (int c = 0; c < C; ++c)
+#pragma unroll
+                        for (int kk = 0; kk < D; ++kk) xp[c][kk] = xpn[c][kk];
+                    if (s + 1 < nsub) load_xp(s + 1, xpn);
                     const int stage = int(q_cons % STAGES);
                     const uint32_t par = (q_cons / STAGES) & 1u;
                     failed |= !mbar_wait_bounded(smem_u32(&full[stage]), par);
@@ -195,13 +229,11 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                     }
                     __syncwarp();
                     ++q_cons;
-                    if (lane == 0 && issued_in_group < group_total) {
-                        issue_next();
-                        ++issued_in_group;
+                    if (issued_in_round < per_pass) {
+                        if (lane == 0) issue_sub(issued_in_round);
+                        ++issued_in_round;
                         ++q_iss;
                     }
-                    issued_in_group = __shfl_sync(0xffffffffu, issued_in_group, 0);
-                    q_iss = __shfl_sync(0xffffffffu, q_iss, 0);
                 }
                 // reduce this modality's sums over the warp
 #pragma unroll
@@ -223,9 +255,10 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
             if (failed) break;
             __syncwarp();
 
-            // stress of y_{t-1} and the stopping test, one lane per object
-            if (lane < R && !flags[lane]) {
+            // stress of every occupied slot's y_{t-1} and its stopping test, one lane per slot
+            if (lane < R && flags[lane] == 0) {
                 const int r = lane;
+                const int pass = slot_pass[r];
                 double sig = 0.0;
                 for (int j = 0; j < m; ++j) sig += double(p.wfid[j]) * fidj[r * FJOFC_MAX_M + j];
                 for (int a = 0; a < m; ++a)
@@ -274,36 +307,39 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
             // outputs of the objects that stopped at this pass
             for (int e = lane; e < R * m * D; e += 32) {
                 const int r = e / (m * D), rem = e - r * m * D, j = rem / D, kk = rem - j * D;
-                if (flags[r] == 2) p.Y[((o0 + r) * m + j) * D + kk] = ys[(r * FJOFC_MAX_M + j) * D + kk];
+                if (flags[r] == 2) p.Y[(slot_obj[r] * m + j) * D + kk] = ys[(r * FJOFC_MAX_M + j) * D + kk];
             }
             __syncwarp();
-            int alldone = 1;
             if (lane < R) {
                 if (flags[lane] == 2) {
-                    const int64_t o = o0 + lane;
+                    const int64_t o = slot_obj[lane];
                     if (p.iters_out) p.iters_out[o] = flags[R + lane];
                     p.stress_out[o] = scur[lane];
                     if (!isfinite(scur[lane])) atomicCAS(&p.st->error, 0, FJOFC_ERR_NONFINITE);
-                    flags[lane] = 1;
+                } else if (flags[lane] == 0) {
+                    slot_pass[lane] += 1;
                 }
-                alldone = flags[lane] != 0;
             }
             __syncwarp();
-            if (__all_sync(0xffffffffu, alldone)) break;
-        }
-
-        // drain the sub-tiles issued ahead for passes that will not run
-        while (__shfl_sync(0xffffffffu, q_cons, 0) < q_iss) {
-            const int stage = int(q_cons % STAGES);
-            failed |= !mbar_wait_bounded(smem_u32(&full[stage]), (q_cons / STAGES) & 1u);
-            __syncwarp();
-            ++q_cons;
-        }
-        if (__any_sync(0xffffffffu, failed)) {
-            if (lane == 0) raise_error(p.st, FJOFC_ERR_TIMEOUT, 3);
-            return;
+            // refill the slots whose object stopped
+            for (int r = 0; r < R; ++r) {
+                if (flags[r] != 2) continue;       // uniform across the warp (shared memory)
+                if (lane == 0) fetch(r);
+                __syncwarp();
+                init_slot(r);
+                __syncwarp();
+            }
         }
     }
+
+    // drain the sub-tiles issued but not consumed (only after a failure)
+    while (q_cons < q_iss) {
+        const int stage = int(q_cons % STAGES);
+        failed |= !mbar_wait_bounded(smem_u32(&full[stage]), (q_cons / STAGES) & 1u);
+        __syncwarp();
+        ++q_cons;
+    }
+    if (__any_sync(0xffffffffu, failed) && lane == 0) raise_error(p.st, FJOFC_ERR_TIMEOUT, 3);
 }
 
 template <int D, typename TD>
