@@ -318,7 +318,7 @@ int InsampleSetup::plan(int m_, int64_t n_, int d_, int dtype_, const fjofc_opts
     o_woff = cv.take<int64_t>(P.nRB + 1);
     o_cta = cv.take<int64_t>(size_t(P.G) + 1);
     o_mu = cv.take<float>(2 * FJOFC_MAX_M * FJOFC_MAX_D);
-    o_bpart = cv.take<float2>(size_t(P.nbx) * (size_t(m) * d + 1));
+    o_bpart = cv.take<float2>(2 * size_t(P.nbx) * (size_t(m) * d + d));   // two pass parities
     o_ticket = cv.take<unsigned>(1);
     o_st = cv.take<DevStatus>(1);
     o_hist = cv.take<double>(size_t(o.max_iter) + 2);

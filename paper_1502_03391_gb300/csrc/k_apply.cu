@@ -20,12 +20,12 @@ namespace fjofc {
 
 constexpr int K2_THREADS = 256;
 
-// One CTA per group of 32 consecutive objects (phase_b with a chunk of one group), then
-// the last CTA to finish forms the totals.  Arithmetic is float32; cross-object sums are
+// One CTA per group of 32 consecutive objects (phase_b over its d units), then the last
+// CTA to finish forms the totals.  Arithmetic is float32; cross-object sums are
 // float-float (GB300's float64 rate is low).
 __global__ void __launch_bounds__(K2_THREADS)
 k_apply(const K2Params p) {
-    extern __shared__ float s_dyn[];             // phase_b_floats_per_group(m, d)
+    extern __shared__ float s_dyn[];             // d * phase_b_floats_per_unit(m)
     __shared__ float s_mu[FJOFC_MAX_M * FJOFC_MAX_D];
     __shared__ float s_coef[FJOFC_MAX_M][FJOFC_MAX_M], s_wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
     __shared__ bool s_last;
@@ -33,7 +33,7 @@ k_apply(const K2Params p) {
     if (ld_volatile(&p.st->done)) return;
 
     const int m = p.m, n = p.n, d = p.d;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const float* mu_prev = p.mu + ((p.t - 1) & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
     float* mu_next = p.mu + (p.t & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
     for (int e = tid; e < FJOFC_MAX_M * FJOFC_MAX_D; e += K2_THREADS) s_mu[e] = mu_prev[e];
@@ -53,9 +53,9 @@ k_apply(const K2Params p) {
     a.wcomm = s_wcomm;
     a.m = m; a.n = n; a.d = d; a.t = p.t;
     a.final_pass = p.final_pass != 0;
-    phase_b(a, blockIdx.x, gridDim.x, p.nbx, 1, s_dyn);
+    phase_b(a, int(blockIdx.x) * d, int(blockIdx.x + 1) * d, d, s_dyn);
 
-    const int npart = m * d + 1;
+    const int npart = phase_b_parts(m, d);
     __threadfence();
     __syncthreads();
     if (tid == 0) {
@@ -67,17 +67,15 @@ k_apply(const K2Params p) {
     if (!s_last) return;
     __threadfence();
 
-    // ---- last CTA: totals in a fixed order (one warp per quantity; the persistent
+    // ---- last CTA: totals in a fixed order (two quantities per warp; the persistent
     // kernel's phase C computes them the same way)
-    __shared__ FF s_tot[FJOFC_MAX_M * FJOFC_MAX_D + 2];
-    for (int e = warp; e < npart + 1; e += K2_THREADS / 32)
-        s_tot[e] = (e < npart) ? totals_ff(p.bpart + e, npart, int(gridDim.x)) : totals_ff(p.fid, 1, p.G);
+    __shared__ FF s_tot[FJOFC_MAX_M * FJOFC_MAX_D + FJOFC_MAX_D + 1];
+    pass_totals(p.bpart, npart, int(gridDim.x), p.fid, p.G, s_tot);
     __syncthreads();
     if (tid < m * d) mu_next[(tid / d) * FJOFC_MAX_D + (tid % d)] = (s_tot[tid].hi + s_tot[tid].lo) * p.inv_n;
-    const FF comm_tot = s_tot[npart - 1], fid_tot = s_tot[npart];
 
     if (tid == 0) {
-        const double sigma = (double(fid_tot.hi) + double(fid_tot.lo)) + (double(comm_tot.hi) + double(comm_tot.lo));
+        const double sigma = stress_from_totals(s_tot, s_tot[npart], m, d);
         const int tp = p.t - 1;                 // index of the iterate whose stress this is
         p.hist[tp] = sigma;
         DevStatus* st = p.st;
@@ -105,7 +103,7 @@ k_apply(const K2Params p) {
 int k2_blocks(int n) { return (n + kGroupObjects - 1) / kGroupObjects; }
 
 cudaError_t launch_k2(const K2Params& p, cudaStream_t s) {
-    const size_t smem = size_t(phase_b_floats_per_group(p.m, p.d)) * sizeof(float);
+    const size_t smem = size_t(p.d) * phase_b_floats_per_unit(p.m) * sizeof(float);
     k_apply<<<p.nbx, K2_THREADS, smem, s>>>(p);
     return cudaGetLastError();
 }

@@ -2,13 +2,14 @@
 // Remark faststress), shared by K2 (k_apply) and phase B of the persistent kernel so that
 // both paths sum every partial in exactly the same order (bitwise equal results).
 //
-// Objects are handled in groups of 32 (lane = object).  For every group g the CTA
-//   1. sums (B'_l X_l)_{i,k} for all (l, k) from the K1 partials and stages x_{t-1} of the
-//      group in shared memory (one warp per (l, k) unit),
-//   2. per coordinate k (one warp each): centres X_{t-1} with the previous pass's means,
-//      forms its commensurability, mixes X_t^(j) = sum_l coef[j][l] (B'_l X_l) and writes
-//      the float-float column sums of X_t -> bpart[g][j*d + k],
-//   3. sums the commensurability over k in order -> bpart[g][m*d].
+// Objects are handled in groups of 32 (lane = object) and per coordinate: a unit is one
+// (group g, coordinate k).  For every unit the CTA
+//   1. sums (B'_l X_l)_{i,k} for every modality l from the K1 partials and stages x_{t-1}
+//      of the group in shared memory (one warp per (unit, l)),
+//   2. (one warp per unit) centres X_{t-1} with the previous pass's means, forms its
+//      commensurability in coordinate k, mixes X_t^(j) = sum_l coef[j][l] (B'_l X_l) and
+//      writes the float-float sums of the group: column sums -> bpart[g][j*d + k],
+//      commensurability -> bpart[g][m*d + k].
 #pragma once
 
 #include "fjofc_device.cuh"
@@ -76,7 +77,7 @@ struct PhaseBArgs {
     BxTables tb;
     float* Xprev;                               // X_{t-1}, centred in place (t > 1)
     float* Xnext;                               // X_t
-    float2* bpart;                              // [ngroups][m*d + 1]
+    float2* bpart;                              // [ngroups][npart], npart = m*d + d
     const float* mu_prev;                       // [MAX_M][MAX_D] means of X_{t-1} (shared memory)
     const float (*coef)[FJOFC_MAX_M];           // Wmod^-1 w_ll s_l (shared memory)
     const float (*wcomm)[FJOFC_MAX_M];          // w_jl for j < l, else 0 (shared memory)
@@ -84,36 +85,43 @@ struct PhaseBArgs {
     bool final_pass;                            // only centre and score X_{t-1}
 };
 
-// Shared-memory floats phase B needs per group (staged values, then d float-float sums).
-__host__ __device__ constexpr int phase_b_floats_per_group(int m, int d) { return 2 * m * d * kGroupObjects + 2 * d; }
+// Per-group float-float sums written by phase B: the column sums of X_t^(j) for every
+// (j, k) at index j*d + k, then the commensurability of coordinate k at index m*d + k.
+__host__ __device__ constexpr int phase_b_parts(int m, int d) { return m * d + d; }
+// Shared-memory floats phase B needs per unit (staged partial sums and x_{t-1}).
+__host__ __device__ constexpr int phase_b_floats_per_unit(int m) { return 2 * m * kGroupObjects; }
 
-// Phase B for the groups g = g0, g0 + gstride, ... (< ngroups), processed in chunks of at
-// most `cap` groups; s holds cap * phase_b_floats_per_group(m, d) floats (8-byte aligned).
-// Every thread of the CTA must call it.
+// Phase B for the units u in [u0, u1), unit u = (group g = u / d, coordinate k = u % d),
+// processed in chunks of at most `cap` units; s holds cap * phase_b_floats_per_unit(m)
+// floats.  Every thread of the CTA must call it.
+//   1. one warp per (unit, modality l): (B'_l X_l)_{i,k} for the group's 32 objects (lane
+//      = object) from the partials, and x_{t-1}; two such at once per warp;
+//   2. one warp per unit: centre X_{t-1} with the previous pass's means (written back),
+//      its commensurability in coordinate k, the mix X_t^(j) = sum_l coef[j][l] (B'_l X_l)
+//      and the float-float sums of the group -> bpart[g].
 template <int BATCH = kBxBatch>
-__device__ __forceinline__ void phase_b(const PhaseBArgs& a, int g0, int gstride, int ngroups, int cap, float* s) {
+__device__ __forceinline__ void phase_b(const PhaseBArgs& a, int u0, int u1, int cap, float* s) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    const int m = a.m, n = a.n, d = a.d, md = m * d, npart = md + 1;
-    const int mine = (g0 < ngroups) ? (ngroups - g0 + gstride - 1) / gstride : 0;
+    const int m = a.m, n = a.n, d = a.d, md = m * d, npart = phase_b_parts(m, d);
 #pragma unroll 1
-    for (int c0 = 0; c0 < mine; c0 += cap) {
-        const int nc = min(cap, mine - c0);
-        float* s_bx = s;                                   // [nc][m][d][32]
-        float* s_xp = s + nc * md * kGroupObjects;         // [nc][m][d][32]
-        FF* s_comm = reinterpret_cast<FF*>(s + 2 * nc * md * kGroupObjects);   // [nc][d]
-        // 1. partial sums and staged x_{t-1}: (group, l, k) units, two per warp per round
+    for (int c0 = u0; c0 < u1; c0 += cap) {
+        const int nc = min(cap, u1 - c0);
+        float* s_bx = s;                                   // [nc][m][32]
+        float* s_xp = s + nc * m * kGroupObjects;          // [nc][m][32]
+        // 1. (unit, l) pairs, two per warp per round
 #pragma unroll 1
-        for (int u0 = warp; u0 < nc * md; u0 += 2 * nwarps) {
-            int uu[2], ll[2], kk[2], ii[2];
+        for (int w0 = warp; w0 < nc * m; w0 += 2 * nwarps) {
+            int ww[2], ll[2], kk[2], ii[2];
             bool on[2], in[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                uu[h] = u0 + h * nwarps;
-                const bool unit = uu[h] < nc * md;
-                const int gi = unit ? uu[h] / md : 0, lk = unit ? uu[h] - gi * md : 0;
-                ll[h] = lk / d;
-                kk[h] = lk - ll[h] * d;
-                ii[h] = (g0 + (c0 + gi) * gstride) * kGroupObjects + lane;
+                ww[h] = w0 + h * nwarps;
+                const bool unit = ww[h] < nc * m;
+                const int ui = unit ? ww[h] / m : 0;
+                ll[h] = unit ? ww[h] - ui * m : 0;
+                const int u = c0 + ui, g = u / d;
+                kk[h] = u - g * d;
+                ii[h] = g * kGroupObjects + lane;
                 in[h] = unit && ii[h] < n;
                 on[h] = in[h] && !a.final_pass;
             }
@@ -123,23 +131,22 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int g0, int gstride
             bx_sum<BATCH, 2>(a.tb, ll, kk, ii, on, bx);
 #pragma unroll
             for (int h = 0; h < 2; ++h)
-                if (uu[h] < nc * md) {
-                    s_xp[uu[h] * kGroupObjects + lane] = xp[h];
-                    s_bx[uu[h] * kGroupObjects + lane] = on[h] ? bx[h] : 0.f;
+                if (ww[h] < nc * m) {
+                    s_xp[ww[h] * kGroupObjects + lane] = xp[h];
+                    s_bx[ww[h] * kGroupObjects + lane] = on[h] ? bx[h] : 0.f;
                 }
         }
         __syncthreads();
-        // 2. per (group, coordinate): centre, commensurability, mix, column sums
+        // 2. per unit: centre, commensurability, mix, column sums
 #pragma unroll 1
-        for (int w = warp; w < nc * d; w += nwarps) {
-            const int gi = w / d, k = w - gi * d;
-            const int g = g0 + (c0 + gi) * gstride;
+        for (int ui = warp; ui < nc; ui += nwarps) {
+            const int u = c0 + ui, g = u / d, k = u - g * d;
             const int i = g * kGroupObjects + lane;
             const bool in = i < n;
             float xc[FJOFC_MAX_M];
             float c = 0.f;
             for (int j = 0; j < m; ++j) {
-                xc[j] = in ? s_xp[((gi * m + j) * d + k) * kGroupObjects + lane] - a.mu_prev[j * FJOFC_MAX_D + k] : 0.f;
+                xc[j] = in ? s_xp[(ui * m + j) * kGroupObjects + lane] - a.mu_prev[j * FJOFC_MAX_D + k] : 0.f;
                 if (in && a.t > 1) a.Xprev[(int64_t(j) * n + i) * d + k] = xc[j];
             }
             if (in)
@@ -149,11 +156,11 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int g0, int gstride
                         c = fmaf(a.wcomm[j][l] * df, df, c);
                     }
             const FF cw = warp_sum_ff(FF{c, 0.f});
-            if (lane == 0) s_comm[gi * d + k] = cw;
+            if (lane == 0) a.bpart[int64_t(g) * npart + md + k] = make_float2(cw.hi, cw.lo);
             for (int j = 0; j < m; ++j) {
                 float v = 0.f;
                 if (!a.final_pass && in) {
-                    for (int l = 0; l < m; ++l) v = fmaf(a.coef[j][l], s_bx[((gi * m + l) * d + k) * kGroupObjects + lane], v);
+                    for (int l = 0; l < m; ++l) v = fmaf(a.coef[j][l], s_bx[(ui * m + l) * kGroupObjects + lane], v);
                     a.Xnext[(int64_t(j) * n + i) * d + k] = v;
                 }
                 const FF cs = warp_sum_ff(FF{v, 0.f});
@@ -162,14 +169,68 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int g0, int gstride
             }
         }
         __syncthreads();
-        // 3. commensurability of each group, summed over k in order
-        for (int gi = threadIdx.x; gi < nc; gi += blockDim.x) {
-            FF tot{0.f, 0.f};
-            for (int k = 0; k < d; ++k) tot = ff_add(tot, s_comm[gi * d + k]);
-            a.bpart[int64_t(g0 + (c0 + gi) * gstride) * npart + md] = make_float2(tot.hi, tot.lo);
-        }
-        __syncthreads();
     }
+}
+
+// Float-float totals of two strided float2 sequences (p0[g*s0], g < c0 and p1[g*s1],
+// g < c1; c1 == 0: none) by one warp: lane l sums entries l, l+32, ... with 8 loads of
+// each in flight, then a fixed-order butterfly.  Every CTA that calls it gets the same
+// totals.
+__device__ __forceinline__ void totals2_ff(const float2* p0, int s0, int c0, const float2* p1, int s1, int c1,
+                                           FF& t0, FF& t1) {
+    const int lane = threadIdx.x & 31;
+    const int cmax = max(c0, c1);
+    FF a0{0.f, 0.f}, a1{0.f, 0.f};
+#pragma unroll 1
+    for (int g0 = lane; g0 < cmax; g0 += 8 * 32) {
+        float2 x0[8], x1[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int g = g0 + 32 * j;
+            x0[j] = g < c0 ? __ldcg(p0 + int64_t(g) * s0) : make_float2(0.f, 0.f);
+            x1[j] = g < c1 ? __ldcg(p1 + int64_t(g) * s1) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            a0 = ff_add(a0, FF{x0[j].x, x0[j].y});
+            a1 = ff_add(a1, FF{x1[j].x, x1[j].y});
+        }
+    }
+    t0 = warp_sum_ff(a0);
+    t1 = warp_sum_ff(a1);
+}
+
+// The per-pass totals in a fixed order, the same in every CTA that calls it (every thread
+// must call it): out[e] for e < npart = the float-float sum over the ngroups groups of
+// phase B's part e, out[npart] = the sum of the nfid fidelity partials.  Two totals per
+// warp at once.
+__device__ __forceinline__ void pass_totals(const float2* bpart, int npart, int ngroups, const float2* fid, int nfid,
+                                            FF* out) {
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nt = npart + 1;
+#pragma unroll 1
+    for (int e = warp; e < nt; e += 2 * nwarps) {
+        const int e1 = e + nwarps;
+        const float2* p0 = e < npart ? bpart + e : fid;
+        const int s0 = e < npart ? npart : 1, c0 = e < npart ? ngroups : nfid;
+        const float2* p1 = e1 < npart ? bpart + e1 : fid;
+        const int s1 = e1 < npart ? npart : 1, c1 = e1 < npart ? ngroups : (e1 == npart ? nfid : 0);
+        FF t0, t1;
+        totals2_ff(p0, s0, c0, p1, s1, c1, t0, t1);
+        if ((threadIdx.x & 31) == 0) {
+            out[e] = t0;
+            if (e1 < nt) out[e1] = t1;
+        }
+    }
+}
+
+// sigma from the pass totals (pass_totals' out) and the fidelity total of the same
+// iterate: the fidelity plus the commensurability of every coordinate, summed over k in
+// order.
+__device__ __forceinline__ double stress_from_totals(const FF* tot, FF fid, int m, int d) {
+    FF comm{0.f, 0.f};
+    for (int k = 0; k < d; ++k) comm = ff_add(comm, tot[m * d + k]);
+    return (double(fid.hi) + double(fid.lo)) + (double(comm.hi) + double(comm.lo));
 }
 
 }  // namespace fjofc

@@ -3,20 +3,22 @@
 //
 // Pass t (reads X_{t-1}, writes X_t):
 //   A. the fused all-pairs sub-tiles of this CTA's fixed range (phase_a, the same code as
-//      the standalone pass k_guttman_pass), fidelity partial -> fid[t&1][b];
+//      the standalone pass k_guttman_pass), fidelity partial -> fid2[t&1][b];
 //   -- grid barrier --
-//   B. for object groups g = b, b+G, ... (32 objects each; phase_b, the same code as K2):
-//      sum the partials, centre X_{t-1} in place with the previous pass's means, its
-//      commensurability, the Wmod^-1 mix into X_t (Eq. update / Cor. 1) and per-group
-//      float-float sums -> bpart[g];
+//   C. every CTA reduces the fidelity partials of pass t and phase B's per-group parts of
+//      pass t-1 in the same fixed order, so all CTAs obtain the same means of X_{t-1},
+//      sigma(X_{t-2}) and stopping decision about X_{t-2} (Algorithm 1 with the decrease
+//      reading); CTA 0 records the history;
+//   B. for the (group, coordinate) units of this CTA (phase_b, the same code as K2): sum
+//      the partials, centre X_{t-1} in place with its means, its commensurability, the
+//      Wmod^-1 mix into X_t (Eq. update / Cor. 1) and per-group float-float sums;
 //   -- grid barrier --
-//   C. every CTA reduces bpart and fid in the same fixed order, so all CTAs obtain the
-//      same means of X_t, sigma(X_{t-1}) and stopping decision (Algorithm 1 with the
-//      decrease reading); CTA 0 records the history.
+// The decision about an iterate is taken one pass after its stress is complete (the
+// all-pairs pass computed meanwhile is discarded at a stop).
 // Data written by other CTAs earlier in the same launch (iterates, partials) is read with
 // ld.global.cg (L2, never a possibly stale L1 line); the grid barrier orders the phases.
 // Delta does not change between passes, so the TMA ring keeps prefetching the next
-// pass's first sub-tiles while phases B and C run.  Grid barriers and every other wait
+// pass's first sub-tiles while phases C and B run.  Grid barriers and every other wait
 // are bounded (FJOFC_ERR_TIMEOUT instead of a hang).
 #pragma once
 
@@ -64,6 +66,30 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
     return *s_flag != 0;
 }
 
+// Per-phase clock stamps of passes 2..17 (instrumented builds, -DFJOFC_STAMPS): thread 0 of
+// every CTA records clock64 at the start of phase A, before and after the grid barrier,
+// after phase C and after phase B.
+#ifdef FJOFC_STAMPS
+constexpr int kStampPasses = 16, kStampCtas = 1024, kStampPoints = 5;
+static __device__ long long g_stamps[kStampPasses * kStampCtas * kStampPoints];
+#define FJ_STAMP(t, j)                                                                                   \
+    do {                                                                                                 \
+        if (threadIdx.x == 0 && (t) >= 2 && (t) < 2 + kStampPasses && b < kStampCtas)                   \
+            g_stamps[((int64_t((t) - 2) * kStampCtas + b) * kStampPoints) + (j)] = clock64();             \
+    } while (0)
+#else
+#define FJ_STAMP(t, j) do { } while (0)
+#endif
+
+// Column partials a lane of phase B keeps in flight (one round covers up to BATCH walks).
+#ifndef FJOFC_PHASEB_BATCH_SMALLD
+#define FJOFC_PHASEB_BATCH_SMALLD 16
+#endif
+template <int D>
+struct PhaseBBatch {
+    static constexpr int value = D >= 5 ? 64 : FJOFC_PHASEB_BATCH_SMALLD;
+};
+
 // The whole loop of one problem on the CTA of rank b among its P.k1.G CTAs.
 template <int D, typename TD>
 __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistParams& P, const int b,
@@ -73,6 +99,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
     const K1Params& p = P.k1;
 
     __shared__ FF s_ff[CWARPS];
+    __shared__ FF s_fidt[2];
     __shared__ float s_mu[FJOFC_MAX_M * FJOFC_MAX_D];
     __shared__ float s_coef[FJOFC_MAX_M][FJOFC_MAX_M], s_wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
     __shared__ int s_abort, s_issued, s_flag, s_stop, s_final;
@@ -84,13 +111,20 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
     const int passes = P.max_iter + 1;
     const int64_t t_begin = P.cta_start[b];
     const int nq = static_cast<int>(P.cta_start[b + 1] - t_begin);
+    const int npart = phase_b_parts(m, D);
+    // phase-B units (group, coordinate) of this CTA
+    const int64_t nunits = int64_t(P.ngroups) * D;
+    const int u0 = int(int64_t(b) * nunits / G), u1 = int(int64_t(b + 1) * nunits / G);
 
     K1Ring<D, TD> rg;
     rg.carve(smem_raw);
-    // phase B reuses the column-partial ring (free between passes)
+    // phases C and B reuse the column-partial ring (free between passes)
     float* s_phb = rg.red;
-    const int bcap = int(S::RED_FLOATS / size_t(phase_b_floats_per_group(m, D)));
-    static_assert(S::RED_FLOATS >= size_t(phase_b_floats_per_group(FJOFC_MAX_M, D)), "phase-B overlay does not fit");
+    FF* s_tot = reinterpret_cast<FF*>(rg.red);     // [MAX_M*MAX_D + MAX_D + 1], phase C only
+    static_assert(S::RED_FLOATS * sizeof(float) >= (FJOFC_MAX_M * FJOFC_MAX_D + FJOFC_MAX_D + 1) * sizeof(FF),
+                  "phase-C totals do not fit");
+    const int bcap = int(S::RED_FLOATS / size_t(phase_b_floats_per_unit(m)));
+    static_assert(S::RED_FLOATS >= size_t(phase_b_floats_per_unit(FJOFC_MAX_M)), "phase-B overlay does not fit");
 
     if (tid == 0) {
         s_stop = 0;
@@ -103,28 +137,38 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
         s_wcomm[e / FJOFC_MAX_M][e % FJOFC_MAX_M] = P.wcomm[e / FJOFC_MAX_M][e % FJOFC_MAX_M];
     }
     // ring over every pass's sub-tiles; Delta does not change, so it prefetches the next
-    // pass's first sub-tiles while phases B and C run
+    // pass's first sub-tiles while phase B runs
     rg.start(tm, p, t_begin, nq, int64_t(passes) * nq, &s_issued, &s_abort);
     const volatile int* abort_flag = &s_abort;
     unsigned bar_target = 0;
     bool ok = true;
-    int fail_site = 0;            // 31: all-pairs pass wait, 32: barrier 1, 33: barrier 2
+    int fail_site = 0;            // 31: all-pairs pass wait, 32: barrier after A, 33: barrier after B
     int last_finite = 0;          // newest iterate whose stress was finite
-    int t = 1;
 
-    for (; t <= passes && ok; ++t) {
-        const bool final_pass = (t == passes);
+    // Pass t (t = 1 .. passes) reads X_{t-1}; a last round t = passes + 1 only decides.
+    //   A(t): all pairs of X_{t-1} -> partials, fidelity of X_{t-1} -> fid2[t & 1]
+    //   -- grid barrier --
+    //   C(t): totals of fid2[t & 1] and of B(t-1)'s parts -> means of X_{t-1},
+    //         sigma(X_{t-2}) and the stopping decision about X_{t-2}
+    //   B(t): centre X_{t-1}, its commensurability, X_t (none in the final pass)
+    //   -- grid barrier --
+    // The decision comes one pass after the iterate it concerns (a stop discards the
+    // all-pairs pass computed meanwhile), so that the totals are formed right after the
+    // first barrier, next to phase B, instead of after the second one.
+    for (int t = 1; ok; ++t) {
+        const bool do_a = t <= passes;
         float* Xprev = P.buf[(t - 1) % 3];
         float* Xnext = P.buf[t % 3];
 
         // ================================================================ phase A
-        FF fid_total{0.f, 0.f};
-        if (!phase_a<D, TD>(rg, tm, p, Xprev, int64_t(t - 1) * nq, b, fid_total)) {
-            ok = false;
-            fail_site = 31;
-        }
-        if (!ok) atomicExch(&s_abort, 1);
-        {
+        FJ_STAMP(t, 0);
+        if (do_a) {
+            FF fid_total{0.f, 0.f};
+            if (!phase_a<D, TD>(rg, tm, p, Xprev, int64_t(t - 1) * nq, b, fid_total)) {
+                ok = false;
+                fail_site = 31;
+            }
+            if (!ok) atomicExch(&s_abort, 1);
             const FF ws = warp_sum_ff(fid_total);
             __syncthreads();
             if (lane == 0) s_ff[warp] = ws;
@@ -136,55 +180,34 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
                 P.fid2[(t & 1) * G + b] = make_float2(tot.hi, tot.lo);
             }
         }
+        FJ_STAMP(t, 1);
         bar_target += unsigned(G);
         if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag, G) || *abort_flag) {
             if (ok) fail_site = 32;
             ok = false;
             break;
         }
-
-        // ================================================================ phase B
-        {
-            PhaseBArgs a;
-            a.tb = P.tb;
-            a.Xprev = Xprev;
-            a.Xnext = Xnext;
-            a.bpart = P.bpart;
-            a.mu_prev = s_mu;
-            a.coef = s_coef;
-            a.wcomm = s_wcomm;
-            a.m = m; a.n = n; a.d = D; a.t = t;
-            a.final_pass = final_pass;
-            phase_b<(D >= 5 ? 64 : kBxBatch)>(a, b, G, P.ngroups, bcap, s_phb);
-        }
-        bar_target += unsigned(G);
-        if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag, G)) {
-            fail_site = 33;
-            ok = false;
-            break;
-        }
+        FJ_STAMP(t, 2);
 
         // ================================================================ phase C
-        {
-            // one warp per total: m*D column sums, commensurability, fidelity (all loads
-            // of a lane in one round); the same order in every CTA
-            const int npart = m * D + 1;
-            FF* s_tot = reinterpret_cast<FF*>(rg.red);   // [MAX_M*MAX_D + 2], ring is idle here
-            for (int e = warp; e < npart + 1; e += CWARPS)
-                s_tot[e] = (e < npart) ? totals_ff(P.bpart + e, npart, P.ngroups)
-                                       : totals_ff(P.fid2 + (t & 1) * G, 1, G);
-            __syncthreads();
-            if (tid < m * D)
-                s_mu[(tid / D) * FJOFC_MAX_D + (tid % D)] =
-                    final_pass ? 0.f : (s_tot[tid].hi + s_tot[tid].lo) * P.inv_n;
-            if (tid == 0) {
-                const FF ct = s_tot[npart - 1], ft = s_tot[npart];
-                const double sigma = (double(ft.hi) + double(ft.lo)) + (double(ct.hi) + double(ct.lo));
-                const int tp = t - 1;
-                int stop = final_pass ? 1 : 0;
+        // the same totals, in the same order, in every CTA
+        pass_totals(P.bpart + int64_t((t - 1) & 1) * P.ngroups * npart, npart, t >= 2 ? P.ngroups : 0,
+                    P.fid2 + (t & 1) * G, do_a ? G : 0, s_tot);
+        __syncthreads();
+        if (tid < m * D)
+            s_mu[(tid / D) * FJOFC_MAX_D + (tid % D)] =
+                (t >= 2 && t - 1 < passes) ? (s_tot[tid].hi + s_tot[tid].lo) * P.inv_n : 0.f;
+        if (tid == 0) {
+            if (do_a) s_fidt[t & 1] = s_tot[npart];          // fidelity of X_{t-1}, used at pass t+1
+            int stop = 0;
+            if (t >= 2) {
+                const int tp = t - 2;                        // the iterate decided about
+                // fidelity of X_{t-2}: from pass t-1's totals
+                const double sigma = stress_from_totals(s_tot, s_fidt[(t - 1) & 1], m, D);
+                stop = (tp == P.max_iter) ? 1 : 0;
                 if (b == 0) P.hist[tp] = sigma;
                 if (!isfinite(sigma)) {
-                    stop = 2;                         // non-finite: keep the last finite iterate
+                    stop = 2;                                // non-finite: keep the last finite iterate
                 } else {
                     last_finite = tp;
                     if (!stop && tp >= 1 && P.tol >= 0.0) {
@@ -195,8 +218,6 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
                     }
                     s_prev = sigma;
                 }
-                s_stop = stop;
-                s_final = last_finite;
                 if (b == 0) {
                     DevStatus* st = p.st;
                     if (stop == 2) st->error = FJOFC_ERR_NONFINITE;
@@ -207,8 +228,35 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
                     if (stop) st->done = 1;
                 }
             }
-            __syncthreads();
-            if (s_stop) break;
+            s_stop = stop;
+            s_final = last_finite;
+        }
+        __syncthreads();
+        FJ_STAMP(t, 3);
+        if (s_stop || !do_a) break;
+
+        // ================================================================ phase B
+        {
+            PhaseBArgs a;
+            a.tb = P.tb;
+            a.Xprev = Xprev;
+            a.Xnext = Xnext;
+            a.bpart = P.bpart + int64_t(t & 1) * P.ngroups * npart;
+            a.mu_prev = s_mu;
+            a.coef = s_coef;
+            a.wcomm = s_wcomm;
+            a.m = m; a.n = n; a.d = D; a.t = t;
+            a.final_pass = (t == passes);
+            phase_b<PhaseBBatch<D>::value>(a, u0, u1, bcap, s_phb);
+        }
+        FJ_STAMP(t, 4);
+        // X_t is complete, and every CTA is done with pass t's partial tables, before any
+        // CTA starts pass t+1
+        bar_target += unsigned(G);
+        if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag, G)) {
+            fail_site = 33;
+            ok = false;
+            break;
         }
     }
 

@@ -49,6 +49,11 @@ template <int D> struct K1Cfg;
 #ifndef FJOFC_K1_SMALLD_STAGES
 #define FJOFC_K1_SMALLD_STAGES 3
 #endif
+// smallest embedding dimension whose x_j are staged in shared memory per sub-tile
+// (below it every warp loads its columns' x_j from L2 one sub-tile ahead)
+#ifndef FJOFC_K1_XSTAGE_MIN_D
+#define FJOFC_K1_XSTAGE_MIN_D 1
+#endif
 #define FJOFC_SMALLD FJOFC_K1_SMALLD_R, FJOFC_K1_SMALLD_C, FJOFC_K1_SMALLD_WARPS, FJOFC_K1_SMALLD_STAGES
 #define FJOFC_K1CFG_X(...) FJOFC_K1CFG(__VA_ARGS__)
 FJOFC_K1CFG_X(1, FJOFC_SMALLD)    // default: 128 x 128 sub-tile, 64 KB at float32
@@ -70,11 +75,22 @@ FJOFC_K1CFG(16, 2, 2, 8, 8)
 #undef FJOFC_K1CFG_X
 #undef FJOFC_K1CFG
 
+// Rows of the walk in shared memory, per warp: row r's coordinates as (x_k, x_k) pairs,
+// XB = ceil(D/2) float4 per row ((x_0, x_0, x_1, x_1), (x_2, x_2, x_3, x_3), ...), so that a
+// packed (two-column) operation can take x_i as one operand; all lanes of the warp read
+// the same address (a broadcast).
+template <int D>
+struct XiBcast {
+    static constexpr int XB = (D + 1) / 2;
+};
+
+// Dynamic shared memory a CTA of the all-pairs kernels may use: the 227 KB per-CTA limit
+// less 2 KB for the kernels' static shared variables.
+constexpr size_t kK1SmemBudget = 232448 - 2048;
+
 template <int D, typename TD>
 struct K1Shape {
     static constexpr int R = K1Cfg<D>::R, C = K1Cfg<D>::C, CWARPS = K1Cfg<D>::CWARPS;
-    // 16-bit Delta halves the stage: keep about the same bytes in flight
-    static constexpr int STAGES = sizeof(TD) == 4 ? K1Cfg<D>::STAGES : 2 * K1Cfg<D>::STAGES;
     static constexpr int SLOTS = 2;                    // column-partial ring
     static constexpr int NT = CWARPS * 32;
     static constexpr int RB = CWARPS * R;
@@ -82,14 +98,23 @@ struct K1Shape {
     static constexpr int STAGE_ELEMS = RB * CW;
     static constexpr uint32_t STAGE_BYTES = STAGE_ELEMS * sizeof(TD);
     static constexpr size_t RED_FLOATS = size_t(SLOTS) * CWARPS * D * CW;
-    static constexpr int XROW_FLOATS = CWARPS * R * D;   // staged x_i of the next walk
-    // d >= 5: every sub-tile's x_j (CW columns x d, a 16-byte aligned window) staged in
-    // shared memory by the issuing warp (cp.async), STAGES uses ahead like Delta
-    static constexpr bool XSTAGE = D >= 5;
+    static constexpr int XROW_FLOATS = CWARPS * R * XiBcast<D>::XB * 4;   // x_i of the walk, broadcast pairs
+    // every sub-tile's x_j (CW columns x d, a 16-byte aligned window) staged in shared
+    // memory by the issuing warp (cp.async), STAGES uses ahead like Delta
+    static constexpr bool XSTAGE = D >= FJOFC_K1_XSTAGE_MIN_D;
     static constexpr int XS_FLOATS = XSTAGE ? CW * D + 8 : 0;
-    static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + RED_FLOATS * sizeof(float) +
-                                   size_t(XROW_FLOATS) * sizeof(float) + size_t(STAGES) * XS_FLOATS * sizeof(float) +
-                                   size_t(2 * STAGES + 2 * SLOTS) * 8 + size_t(STAGES) * 4 + 128;
+    static constexpr size_t smem_for(int stages) {
+        return size_t(stages) * STAGE_BYTES + RED_FLOATS * sizeof(float) + size_t(XROW_FLOATS) * sizeof(float) +
+               size_t(stages) * XS_FLOATS * sizeof(float) + size_t(2 * stages + 2 * SLOTS) * 8 +
+               size_t(stages) * 4 + 128;
+    }
+    // 16-bit Delta halves the stage: keep about the same bytes in flight, as many stages
+    // as fit in the budget
+    static constexpr int STAGES_WANTED = sizeof(TD) == 4 ? K1Cfg<D>::STAGES : 2 * K1Cfg<D>::STAGES;
+    static constexpr int fit_stages(int st) { return (st > 2 && smem_for(st) > kK1SmemBudget) ? fit_stages(st - 1) : st; }
+    static constexpr int STAGES = fit_stages(STAGES_WANTED);
+    static constexpr size_t SMEM = smem_for(STAGES);
+    static_assert(SMEM <= kK1SmemBudget, "all-pairs tile does not fit in shared memory");
 };
 
 // Position of a sub-tile: modality l, walk position wp visiting row block I, sub-tile s
@@ -124,55 +149,74 @@ __device__ __forceinline__ void cursor_next(Cursor& c, const K1Params& p) {
     }
 }
 
-// The pairs of one RB x CW sub-tile owned by this thread: rows r0 + warp*R + r (x_i in
-// xi[r]), columns c0 + lane*C + c (x_j in xj[c]).  Coordinates come in pre-divided by the
-// modality's Delta scale s (x' = x / s, so d' = d / s and b = Delta'/d' = Delta/d).
-// Adds b_ij (x'_i - x'_j) to racc[r], its negative to the column accumulators (two
-// interleaved chains by row parity) and (Delta'_ij - d'_ij)^2 to sf0/sf1.  The squared
-// distance starts from FLT_MIN instead of 0: this changes no d^2 above 2^-102 and keeps
-// rsqrt finite when x_i = x_j (then b (x_i - x_j) = 0, the d_ij = 0 rule of Eq. B, and
-// the fidelity term is Delta'^2).  MASKED: only pairs with i < j < n count (diagonal and
-// ragged sub-tiles); otherwise every pair of the sub-tile is valid.
+// The pairs of one RB x CW sub-tile owned by this thread: rows r0 + warp*R + r (x_i from
+// the warp's broadcast rows xib), columns c0 + lane*C + c (x_j, negated, in nxj: column
+// pair cp holds columns 2cp and 2cp+1 as the two halves of a float2).  Coordinates come
+// in pre-divided by the modality's Delta scale s (x' = x / s, so d' = d / s and
+// b = Delta'/d' = Delta/d).  Two columns are processed per instruction with Blackwell's
+// packed float32 operations (add/mul/fma .f32x2: same rounding per element as the
+// scalar operation, half the issue slots); the reciprocal square root stays scalar.
+// Adds b_ij (x'_i - x'_j) to racc[r] (scalar, columns in order), b_ij (x'_i - x'_j) to the
+// column accumulators (two interleaved chains by row parity; the caller negates them:
+// column j receives -b_ij (x'_i - x'_j)) and (Delta'_ij - d'_ij)^2 to sf0/sf1 (per
+// column parity halves).  The squared distance starts from FLT_MIN instead of 0: this
+// changes no d^2 above 2^-102 and keeps rsqrt finite when x_i = x_j (then
+// b (x_i - x_j) = 0, the d_ij = 0 rule of Eq. B, and the fidelity term is Delta'^2).
+// MASKED: only pairs with i < j < n count (diagonal and ragged sub-tiles); otherwise
+// every pair of the sub-tile is valid.
 template <int D, typename TD, int R, int C, int CW, bool MASKED>
 __device__ __forceinline__ void subtile_pairs(const TD* tile, int warp, int lane, int r0, int c0, int n,
-                                              const float (&xi)[R][D], const float (&xj)[C][D],
-                                              float (&racc)[R][D], float (&cacc0)[C][D], float (&cacc1)[C][D],
-                                              float& sf0, float& sf1) {
+                                              const float4* xib, const float2 (&nxj)[C / 2][D],
+                                              float (&racc)[R][D], float2 (&cacc0)[C / 2][D],
+                                              float2 (&cacc1)[C / 2][D], float2& sf0, float2& sf1) {
+    static_assert(C % 2 == 0, "columns are processed in pairs");
+    constexpr int CP = C / 2, XB = XiBcast<D>::XB;
 #pragma unroll
-    for (int c = 0; c < C; ++c)
+    for (int cp = 0; cp < CP; ++cp)
 #pragma unroll
-        for (int k = 0; k < D; ++k) { cacc0[c][k] = 0.f; cacc1[c][k] = 0.f; }
-    sf0 = 0.f;
-    sf1 = 0.f;
+        for (int k = 0; k < D; ++k) { cacc0[cp][k] = make_float2(0.f, 0.f); cacc1[cp][k] = make_float2(0.f, 0.f); }
+    sf0 = make_float2(0.f, 0.f);
+    sf1 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = r0 + warp * R + r;
+        float2 xb[2 * XB];
+#pragma unroll
+        for (int h = 0; h < XB; ++h) {
+            const float4 v = xib[r * XB + h];
+            xb[2 * h] = make_float2(v.x, v.y);
+            xb[2 * h + 1] = make_float2(v.z, v.w);
+        }
         float dl[C];
         load_delta_row<TD, C>(tile + (warp * R + r) * CW + lane * C, dl);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            float diff[D];
-            float d2 = FLT_MIN;
+        for (int cp = 0; cp < CP; ++cp) {
+            const float2 del = make_float2(dl[2 * cp], dl[2 * cp + 1]);
+            float2 diff[D];
+            float2 d2 = make_float2(FLT_MIN, FLT_MIN);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                diff[k] = xi[r][k] - xj[c][k];
-                d2 = fmaf(diff[k], diff[k], d2);
+                diff[k] = __fadd2_rn(xb[k], nxj[cp][k]);
+                d2 = __ffma2_rn(diff[k], diff[k], d2);
             }
-            const float rinv = rsqrt_approx(d2);
-            float bb = dl[c] * rinv;
-            float e = fmaf(-d2, rinv, dl[c]);
+            const float2 rinv = make_float2(rsqrt_approx(d2.x), rsqrt_approx(d2.y));
+            float2 bb = __fmul2_rn(del, rinv);
+            float2 e = __ffma2_rn(make_float2(-d2.x, -d2.y), rinv, del);
             if (MASKED) {
-                const int j = c0 + lane * C + c;
-                const bool valid = (j > i) && (j < n);
-                bb = valid ? bb : 0.f;
-                e = valid ? e : 0.f;
+                const int j = c0 + lane * C + 2 * cp;
+                const bool v0 = (j > i) && (j < n), v1 = (j + 1 > i) && (j + 1 < n);
+                bb.x = v0 ? bb.x : 0.f;
+                e.x = v0 ? e.x : 0.f;
+                bb.y = v1 ? bb.y : 0.f;
+                e.y = v1 ? e.y : 0.f;
             }
-            if (r & 1) sf1 = fmaf(e, e, sf1); else sf0 = fmaf(e, e, sf0);
+            if (r & 1) sf1 = __ffma2_rn(e, e, sf1); else sf0 = __ffma2_rn(e, e, sf0);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                racc[r][k] = fmaf(bb, diff[k], racc[r][k]);
-                if (r & 1) cacc1[c][k] = fmaf(-bb, diff[k], cacc1[c][k]);
-                else cacc0[c][k] = fmaf(-bb, diff[k], cacc0[c][k]);
+                racc[r][k] = fmaf(bb.x, diff[k].x, racc[r][k]);
+                racc[r][k] = fmaf(bb.y, diff[k].y, racc[r][k]);
+                if (r & 1) cacc1[cp][k] = __ffma2_rn(bb, diff[k], cacc1[cp][k]);
+                else cacc0[cp][k] = __ffma2_rn(bb, diff[k], cacc0[cp][k]);
             }
         }
     }
@@ -236,7 +280,7 @@ struct K1Ring {
     using S = K1Shape<D, TD>;
     TD* stages;
     float* red;            // [SLOTS][CWARPS][D][CW] column accumulators
-    float* xrow;           // [CWARPS][R*D]          staged rows of the next walk
+    float* xrow;           // [CWARPS][R][XB] float4 x_i of the current walk as (x_k, x_k) pairs
     float* xs;             // [STAGES][XS_FLOATS]    staged x_j (XSTAGE)
     uint64_t* full;        // [STAGES]
     uint64_t* xfull;       // [STAGES] x_j landed (XSTAGE)
@@ -383,30 +427,49 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
     cursor_init(cc, rg.t_begin, p);
     cn = cc;
     bool seg_head = (cc.s == 0);
-    float xi[R][D], racc[R][D], xjn[S::XSTAGE ? 1 : C][D];
-    {
-        const float* Xl = X + int64_t(cc.l) * n * D;
-        const float xs = p.xscale[cc.l];
+    constexpr int XB = XiBcast<D>::XB;
+    float racc[R][D], xjn[S::XSTAGE ? 1 : C][D];
+    float* xrow = rg.xrow + warp * (R * XB * 4);
+    // this warp's R rows of a walk (row block I of modality l) into its broadcast rows;
+    // element e = r*D + k of the R x D block comes from lane e % 32
+    auto put_rows = [&](const float (&v)[RowStage<R, D>::PER_LANE], float xs) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int i = cc.I * RB + warp * R + r;
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                xi[r][k] = (i < n) ? __ldcg(Xl + int64_t(i) * D + k) * xs : 0.f;
-                racc[r][k] = 0.f;
+        for (int u = 0; u < RowStage<R, D>::PER_LANE; ++u) {
+            const int e = u * 32 + lane;
+            if (e < R * D) {
+                const int r = e / D, k = e - r * D;
+                const float x = v[u] * xs;
+                *reinterpret_cast<float2*>(xrow + r * XB * 4 + 2 * k) = make_float2(x, x);
             }
         }
+        __syncwarp();
+    };
+    {
+        RowStage<R, D> rs0;
+        const float* src = X + (int64_t(cc.l) * n + int64_t(cc.I) * RB + warp * R) * D;
+        const int lim = (n - (cc.I * RB + warp * R)) * D;
+#pragma unroll
+        for (int u = 0; u < RowStage<R, D>::PER_LANE; ++u) {
+            const int e = u * 32 + lane;
+            rs0.v[u] = (e < R * D && e < lim) ? __ldcg(src + e) : 0.f;
+        }
+        __syncwarp();          // the previous pass's readers of xrow are done
+        put_rows(rs0.v, p.xscale[cc.l]);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k = 0; k < D; ++k) racc[r][k] = 0.f;
     }
     auto load_cols = [&](const Cursor& c) {
         if constexpr (!S::XSTAGE) {
             const float* Xl = X + int64_t(c.l) * n * D;
-            const float xs = p.xscale[c.l];
+            const float nxs = -p.xscale[c.l];      // -x_j in Delta's units
             const int c0 = c.I * RB + c.s * CW + lane * C;
 #pragma unroll
             for (int ci = 0; ci < C; ++ci)
 #pragma unroll
                 for (int k = 0; k < D; ++k)
-                    xjn[ci][k] = (c0 + ci < n) ? __ldcg(Xl + int64_t(c0 + ci) * D + k) * xs : 0.f;
+                    xjn[ci][k] = (c0 + ci < n) ? __ldcg(Xl + int64_t(c0 + ci) * D + k) * nxs : 0.f;
         }
     };
     load_cols(cn);
@@ -424,7 +487,6 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
     }
     FF fid{0.f, 0.f};
     int cur_l = cc.l;
-    float* xrow = rg.xrow + warp * (R * D);
 
     // reduce this warp's share of the columns of ring use qg (deferred by one sub-tile)
     auto reduce_share = [&](int64_t qg, int64_t tglob) -> bool {
@@ -455,12 +517,12 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
         const int c0 = r0 + cc.s * CW;
         const bool walk_ends = (cc.s + 1 == cc.L);
         const bool last = (q + 1 == nq);
-        float xj[C][D];
+        float2 nxj[C / 2][D];      // -x_j, column pairs
         if constexpr (!S::XSTAGE) {
 #pragma unroll
-            for (int c = 0; c < C; ++c)
+            for (int c = 0; c < C; c += 2)
 #pragma unroll
-                for (int k = 0; k < D; ++k) xj[c][k] = xjn[c][k];
+                for (int k = 0; k < D; ++k) nxj[c / 2][k] = make_float2(xjn[c][k], xjn[c + 1][k]);
         }
         if (!last) {                // prefetch the next sub-tile's columns
             cursor_next(cn, p);
@@ -488,27 +550,31 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
                 return false;
             const int64_t start = (int64_t(cc.l) * n + c0) * D;
             const float* xsrc = rg.xs + size_t(stage) * S::XS_FLOATS + int(start & 3) + lane * C * D;
-            const float xsc = p.xscale[cc.l];
+            const float nxsc = -p.xscale[cc.l];
             if (c0 + CW <= n) {
 #pragma unroll
-                for (int c = 0; c < C; ++c)
+                for (int c = 0; c < C; c += 2)
 #pragma unroll
-                    for (int k = 0; k < D; ++k) xj[c][k] = xsrc[c * D + k] * xsc;
+                    for (int k = 0; k < D; ++k)
+                        nxj[c / 2][k] = make_float2(xsrc[c * D + k] * nxsc, xsrc[(c + 1) * D + k] * nxsc);
             } else {                // ragged sub-tile: columns past n hold other data
 #pragma unroll
-                for (int c = 0; c < C; ++c)
+                for (int c = 0; c < C; c += 2)
 #pragma unroll
-                    for (int k = 0; k < D; ++k) xj[c][k] = (c0 + lane * C + c < n) ? xsrc[c * D + k] * xsc : 0.f;
+                    for (int k = 0; k < D; ++k)
+                        nxj[c / 2][k] = make_float2((c0 + lane * C + c < n) ? xsrc[c * D + k] * nxsc : 0.f,
+                                                    (c0 + lane * C + c + 1 < n) ? xsrc[(c + 1) * D + k] * nxsc : 0.f);
             }
         }
         const TD* tile = rg.stages + size_t(stage) * S::STAGE_ELEMS;
         const bool masked = (cc.s * CW < RB) || (c0 + CW > n);
-        float cacc0[C][D], cacc1[C][D];
-        float sf0, sf1;
+        float2 cacc0[C / 2][D], cacc1[C / 2][D];
+        float2 sf0, sf1;
+        const float4* xib = reinterpret_cast<const float4*>(xrow);
         if (!masked)
-            subtile_pairs<D, TD, R, C, CW, false>(tile, warp, lane, r0, c0, n, xi, xj, racc, cacc0, cacc1, sf0, sf1);
+            subtile_pairs<D, TD, R, C, CW, false>(tile, warp, lane, r0, c0, n, xib, nxj, racc, cacc0, cacc1, sf0, sf1);
         else
-            subtile_pairs<D, TD, R, C, CW, true>(tile, warp, lane, r0, c0, n, xi, xj, racc, cacc0, cacc1, sf0, sf1);
+            subtile_pairs<D, TD, R, C, CW, true>(tile, warp, lane, r0, c0, n, xib, nxj, racc, cacc0, cacc1, sf0, sf1);
         // release the stage; the last warp to do so refills it with use qg + STAGES
         const bool refill = qg + STAGES < rg.total_q;
         __syncwarp();
@@ -528,24 +594,28 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
             if (is_last && refill && q + STAGES < nq) rg.issue_x(p, X, qg + STAGES, rg.pc);
         }
         if (refill) rg.advance(p);
-        fid = ff_add(fid, sf0 + sf1);
+        fid = ff_add(fid, (sf0.x + sf0.y) + (sf1.x + sf1.y));
 
         // column partials of this sub-tile into its ring slot
         if (qg >= SLOTS &&
             !mbar_wait_or_abort(smem_u32(&rg.rempty[slot]), uint32_t(((qg / SLOTS) - 1) & 1), abort_flag))
             return false;
         float* rbuf = rg.red + (size_t(slot) * CWARPS + warp) * D * CW;
+        // column j receives -b_ij (x_i - x_j): the accumulators hold the sum of b_ij (x_i - x_j)
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             if constexpr (C % 4 == 0) {
 #pragma unroll
                 for (int c = 0; c < C; c += 4)
                     *reinterpret_cast<float4*>(rbuf + k * CW + lane * C + c) =
-                        make_float4(cacc0[c][k] + cacc1[c][k], cacc0[c + 1][k] + cacc1[c + 1][k],
-                                    cacc0[c + 2][k] + cacc1[c + 2][k], cacc0[c + 3][k] + cacc1[c + 3][k]);
+                        make_float4(-cacc0[c / 2][k].x - cacc1[c / 2][k].x, -cacc0[c / 2][k].y - cacc1[c / 2][k].y,
+                                    -cacc0[c / 2 + 1][k].x - cacc1[c / 2 + 1][k].x,
+                                    -cacc0[c / 2 + 1][k].y - cacc1[c / 2 + 1][k].y);
             } else {
 #pragma unroll
-                for (int c = 0; c < C; ++c) rbuf[k * CW + lane * C + c] = cacc0[c][k] + cacc1[c][k];
+                for (int c = 0; c < C; c += 2)
+                    *reinterpret_cast<float2*>(rbuf + k * CW + lane * C + c) =
+                        make_float2(-cacc0[c / 2][k].x - cacc1[c / 2][k].x, -cacc0[c / 2][k].y - cacc1[c / 2][k].y);
             }
         }
         __syncwarp();
@@ -579,21 +649,12 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
         }
         if (walk_ends && !last) {
             seg_head = true;
-            const float xs = p.xscale[cc.l];
-#pragma unroll
-            for (int u = 0; u < RowStage<R, D>::PER_LANE; ++u) {
-                const int e = u * 32 + lane;
-                if (e < R * D) xrow[e] = rs.v[u] * xs;
-            }
-            __syncwarp();
+            __syncwarp();          // every lane is done reading the old rows
+            put_rows(rs.v, p.xscale[cc.l]);
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    xi[r][k] = xrow[r * D + k];
-                    racc[r][k] = 0.f;
-                }
-            __syncwarp();
+                for (int k = 0; k < D; ++k) racc[r][k] = 0.f;
         }
     }
     if (!reduce_share(qbase + nq - 1, rg.t_begin + nq - 1)) return false;

@@ -6,3 +6,12 @@ FJOFC_INSTANTIATE_PERSIST(2)
 FJOFC_INSTANTIATE_PERSIST(3)
 FJOFC_INSTANTIATE_PERSIST(4)
 }  // namespace fjofc
+
+#ifdef FJOFC_STAMPS
+// Instrumented builds: copy the stamps of the last persistent launch (d <= 4) to host.
+extern "C" int fjofc_debug_stamps(long long* host, long long count) {
+    const long long cap = fjofc::kStampPasses * fjofc::kStampCtas * fjofc::kStampPoints;
+    if (count > cap) count = cap;
+    return cudaMemcpyFromSymbol(host, fjofc::g_stamps, size_t(count) * sizeof(long long)) == cudaSuccess ? 0 : -1;
+}
+#endif
