@@ -170,6 +170,64 @@ template <> struct DeltaLoad<__nv_bfloat16> {
     static __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
 };
 
+// Loads from the shared state space by 32-bit shared address (the compiler does not know
+// that the ring's generic pointers point into shared memory).
+__device__ __forceinline__ float4 lds_f4(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float2 lds_f2(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float lds_f1(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
+// C consecutive Delta values at shared address a (16-byte aligned for float32 C % 4 == 0)
+// as float.
+template <typename TD, int C>
+__device__ __forceinline__ void lds_delta_row(uint32_t a, float (&out)[C]) {
+    if constexpr (sizeof(TD) == 4) {
+        if constexpr (C % 4 == 0) {
+#pragma unroll
+            for (int c = 0; c < C; c += 4) {
+                const float4 v = lds_f4(a + 4 * c);
+                out[c] = v.x; out[c + 1] = v.y; out[c + 2] = v.z; out[c + 3] = v.w;
+            }
+        } else {
+            static_assert(C % 2 == 0, "even column count");
+#pragma unroll
+            for (int c = 0; c < C; c += 2) {
+                const float2 v = lds_f2(a + 4 * c);
+                out[c] = v.x; out[c + 1] = v.y;
+            }
+        }
+    } else {
+        static_assert(C % 2 == 0, "even column count");
+#pragma unroll
+        for (int c = 0; c < C; c += 2) {
+            const uint32_t w = lds_u32(a + 2 * c);
+            if constexpr (std::is_same<TD, __half>::value) {
+                const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w));
+                out[c] = v.x; out[c + 1] = v.y;
+            } else {
+                const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+                out[c] = v.x; out[c + 1] = v.y;
+            }
+        }
+    }
+}
+
 // Load C consecutive Delta values from shared memory (vectorised) as float.
 template <typename TD, int C>
 __device__ __forceinline__ void load_delta_row(const TD* p, float (&out)[C]) {

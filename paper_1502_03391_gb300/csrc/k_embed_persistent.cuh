@@ -67,10 +67,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
 }
 
 // Per-phase clock stamps of passes 2..17 (instrumented builds, -DFJOFC_STAMPS): thread 0 of
-// every CTA records clock64 at the start of phase A, before and after the grid barrier,
-// after phase C and after phase B.
+// every CTA records clock64 at the start of phase A, before and after the first grid
+// barrier, after phase C, after phase B and after phase C's totals.
 #ifdef FJOFC_STAMPS
-constexpr int kStampPasses = 16, kStampCtas = 1024, kStampPoints = 5;
+constexpr int kStampPasses = 16, kStampCtas = 1024, kStampPoints = 6;
 static __device__ long long g_stamps[kStampPasses * kStampCtas * kStampPoints];
 #define FJ_STAMP(t, j)                                                                                   \
     do {                                                                                                 \
@@ -194,6 +194,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
         pass_totals(P.bpart + int64_t((t - 1) & 1) * P.ngroups * npart, npart, t >= 2 ? P.ngroups : 0,
                     P.fid2 + (t & 1) * G, do_a ? G : 0, s_tot);
         __syncthreads();
+        FJ_STAMP(t, 5);
         if (tid < m * D)
             s_mu[(tid / D) * FJOFC_MAX_D + (tid % D)] =
                 (t >= 2 && t - 1 < passes) ? (s_tot[tid].hi + s_tot[tid].lo) * P.inv_n : 0.f;
@@ -285,7 +286,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
 }
 
 template <int D, typename TD>
-__global__ void __launch_bounds__(K1Shape<D, TD>::NT, 1)
+__global__ void __launch_bounds__(K1Shape<D, TD>::NT, FJOFC_K1_MINB)
 k_embed_persistent(const __grid_constant__ TMaps tm, const __grid_constant__ PersistParams P) {
     extern __shared__ unsigned char smem_raw[];
     persist_problem<D, TD>(tm, P, blockIdx.x, smem_raw);
@@ -297,7 +298,7 @@ k_embed_persistent(const __grid_constant__ TMaps tm, const __grid_constant__ Per
 // CTAs is first in all of their lists, so its ranks start together.  The problem's
 // parameters are copied to shared memory; its tensor maps stay in global memory.
 template <int D, typename TD>
-__global__ void __launch_bounds__(K1Shape<D, TD>::NT, 1)
+__global__ void __launch_bounds__(K1Shape<D, TD>::NT, FJOFC_K1_MINB)
 k_embed_batched(const __grid_constant__ BatchLaunch bl) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(16) PersistParams s_P;

@@ -54,6 +54,10 @@ template <int D> struct K1Cfg;
 #ifndef FJOFC_K1_XSTAGE_MIN_D
 #define FJOFC_K1_XSTAGE_MIN_D 1
 #endif
+// resident CTAs per SM the all-pairs kernels are compiled for (register budget)
+#ifndef FJOFC_K1_MINB
+#define FJOFC_K1_MINB 1
+#endif
 #define FJOFC_SMALLD FJOFC_K1_SMALLD_R, FJOFC_K1_SMALLD_C, FJOFC_K1_SMALLD_WARPS, FJOFC_K1_SMALLD_STAGES
 #define FJOFC_K1CFG_X(...) FJOFC_K1CFG(__VA_ARGS__)
 FJOFC_K1CFG_X(1, FJOFC_SMALLD)    // default: 128 x 128 sub-tile, 64 KB at float32
@@ -150,27 +154,30 @@ __device__ __forceinline__ void cursor_next(Cursor& c, const K1Params& p) {
 }
 
 // The pairs of one RB x CW sub-tile owned by this thread: rows r0 + warp*R + r (x_i from
-// the warp's broadcast rows xib), columns c0 + lane*C + c (x_j, negated, in nxj: column
-// pair cp holds columns 2cp and 2cp+1 as the two halves of a float2).  Coordinates come
-// in pre-divided by the modality's Delta scale s (x' = x / s, so d' = d / s and
-// b = Delta'/d' = Delta/d).  Two columns are processed per instruction with Blackwell's
-// packed float32 operations (add/mul/fma .f32x2: same rounding per element as the
-// scalar operation, half the issue slots); the reciprocal square root stays scalar.
-// Adds b_ij (x'_i - x'_j) to racc[r] (scalar, columns in order), b_ij (x'_i - x'_j) to the
-// column accumulators (two interleaved chains by row parity; the caller negates them:
-// column j receives -b_ij (x'_i - x'_j)) and (Delta'_ij - d'_ij)^2 to sf0/sf1 (per
+// the warp's broadcast rows at shared address xib), columns c0 + lane*C + c (x_j, negated,
+// in nxj: column pair cp holds columns 2cp and 2cp+1 as the two halves of a float2); the
+// sub-tile's Delta at shared address tile.  Coordinates come in pre-divided by the
+// modality's Delta scale s (x' = x / s, so d' = d / s and b = Delta'/d' = Delta/d).  Two
+// columns are processed per instruction with Blackwell's packed float32 operations
+// (add/mul/fma .f32x2: same rounding per element as the scalar operation, half the issue
+// slots); the reciprocal square root stays scalar.  With q = -b_ij and e' = d'_ij -
+// Delta'_ij (the packed forms take no negated operand, so the signs are arranged to need
+// one negation of Delta per column pair): adds -q (x'_i - x'_j) = b_ij (x'_i - x'_j) to
+// racc[r] (scalar, columns in order), q (x'_i - x'_j), the contribution to column j, to
+// the column accumulators (two interleaved chains by row parity) and e'^2 to sf0/sf1 (per
 // column parity halves).  The squared distance starts from FLT_MIN instead of 0: this
 // changes no d^2 above 2^-102 and keeps rsqrt finite when x_i = x_j (then
 // b (x_i - x_j) = 0, the d_ij = 0 rule of Eq. B, and the fidelity term is Delta'^2).
 // MASKED: only pairs with i < j < n count (diagonal and ragged sub-tiles); otherwise
 // every pair of the sub-tile is valid.
 template <int D, typename TD, int R, int C, int CW, bool MASKED>
-__device__ __forceinline__ void subtile_pairs(const TD* tile, int warp, int lane, int r0, int c0, int n,
-                                              const float4* xib, const float2 (&nxj)[C / 2][D],
+__device__ __forceinline__ void subtile_pairs(uint32_t tile, int warp, int lane, int r0, int c0, int n,
+                                              uint32_t xib, const float2 (&nxj)[C / 2][D],
                                               float (&racc)[R][D], float2 (&cacc0)[C / 2][D],
                                               float2 (&cacc1)[C / 2][D], float2& sf0, float2& sf1) {
     static_assert(C % 2 == 0, "columns are processed in pairs");
     constexpr int CP = C / 2, XB = XiBcast<D>::XB;
+    const float2 neg1 = make_float2(-1.f, -1.f);
 #pragma unroll
     for (int cp = 0; cp < CP; ++cp)
 #pragma unroll
@@ -183,15 +190,15 @@ __device__ __forceinline__ void subtile_pairs(const TD* tile, int warp, int lane
         float2 xb[2 * XB];
 #pragma unroll
         for (int h = 0; h < XB; ++h) {
-            const float4 v = xib[r * XB + h];
+            const float4 v = lds_f4(xib + 16 * (r * XB + h));
             xb[2 * h] = make_float2(v.x, v.y);
             xb[2 * h + 1] = make_float2(v.z, v.w);
         }
         float dl[C];
-        load_delta_row<TD, C>(tile + (warp * R + r) * CW + lane * C, dl);
+        lds_delta_row<TD, C>(tile + uint32_t(((warp * R + r) * CW + lane * C) * sizeof(TD)), dl);
 #pragma unroll
         for (int cp = 0; cp < CP; ++cp) {
-            const float2 del = make_float2(dl[2 * cp], dl[2 * cp + 1]);
+            const float2 ndel = __fmul2_rn(make_float2(dl[2 * cp], dl[2 * cp + 1]), neg1);
             float2 diff[D];
             float2 d2 = make_float2(FLT_MIN, FLT_MIN);
 #pragma unroll
@@ -200,23 +207,23 @@ __device__ __forceinline__ void subtile_pairs(const TD* tile, int warp, int lane
                 d2 = __ffma2_rn(diff[k], diff[k], d2);
             }
             const float2 rinv = make_float2(rsqrt_approx(d2.x), rsqrt_approx(d2.y));
-            float2 bb = __fmul2_rn(del, rinv);
-            float2 e = __ffma2_rn(make_float2(-d2.x, -d2.y), rinv, del);
+            float2 q = __fmul2_rn(ndel, rinv);            // -b
+            float2 e = __ffma2_rn(d2, rinv, ndel);        // d - Delta
             if (MASKED) {
                 const int j = c0 + lane * C + 2 * cp;
                 const bool v0 = (j > i) && (j < n), v1 = (j + 1 > i) && (j + 1 < n);
-                bb.x = v0 ? bb.x : 0.f;
+                q.x = v0 ? q.x : 0.f;
                 e.x = v0 ? e.x : 0.f;
-                bb.y = v1 ? bb.y : 0.f;
+                q.y = v1 ? q.y : 0.f;
                 e.y = v1 ? e.y : 0.f;
             }
             if (r & 1) sf1 = __ffma2_rn(e, e, sf1); else sf0 = __ffma2_rn(e, e, sf0);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                racc[r][k] = fmaf(bb.x, diff[k].x, racc[r][k]);
-                racc[r][k] = fmaf(bb.y, diff[k].y, racc[r][k]);
-                if (r & 1) cacc1[cp][k] = __ffma2_rn(bb, diff[k], cacc1[cp][k]);
-                else cacc0[cp][k] = __ffma2_rn(bb, diff[k], cacc0[cp][k]);
+                racc[r][k] = fmaf(-q.x, diff[k].x, racc[r][k]);
+                racc[r][k] = fmaf(-q.y, diff[k].y, racc[r][k]);
+                if (r & 1) cacc1[cp][k] = __ffma2_rn(q, diff[k], cacc1[cp][k]);
+                else cacc0[cp][k] = __ffma2_rn(q, diff[k], cacc0[cp][k]);
             }
         }
     }
@@ -549,28 +556,30 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
             if (!mbar_wait_or_abort(smem_u32(&rg.xfull[stage]), kuse & 1u, abort_flag))
                 return false;
             const int64_t start = (int64_t(cc.l) * n + c0) * D;
-            const float* xsrc = rg.xs + size_t(stage) * S::XS_FLOATS + int(start & 3) + lane * C * D;
+            const uint32_t xsrc = smem_u32(rg.xs + size_t(stage) * S::XS_FLOATS + int(start & 3) + lane * C * D);
             const float nxsc = -p.xscale[cc.l];
             if (c0 + CW <= n) {
 #pragma unroll
                 for (int c = 0; c < C; c += 2)
 #pragma unroll
                     for (int k = 0; k < D; ++k)
-                        nxj[c / 2][k] = make_float2(xsrc[c * D + k] * nxsc, xsrc[(c + 1) * D + k] * nxsc);
+                        nxj[c / 2][k] = make_float2(lds_f1(xsrc + 4 * (c * D + k)) * nxsc,
+                                                    lds_f1(xsrc + 4 * ((c + 1) * D + k)) * nxsc);
             } else {                // ragged sub-tile: columns past n hold other data
 #pragma unroll
                 for (int c = 0; c < C; c += 2)
 #pragma unroll
                     for (int k = 0; k < D; ++k)
-                        nxj[c / 2][k] = make_float2((c0 + lane * C + c < n) ? xsrc[c * D + k] * nxsc : 0.f,
-                                                    (c0 + lane * C + c + 1 < n) ? xsrc[(c + 1) * D + k] * nxsc : 0.f);
+                        nxj[c / 2][k] =
+                            make_float2((c0 + lane * C + c < n) ? lds_f1(xsrc + 4 * (c * D + k)) * nxsc : 0.f,
+                                        (c0 + lane * C + c + 1 < n) ? lds_f1(xsrc + 4 * ((c + 1) * D + k)) * nxsc : 0.f);
             }
         }
-        const TD* tile = rg.stages + size_t(stage) * S::STAGE_ELEMS;
+        const uint32_t tile = smem_u32(rg.stages + size_t(stage) * S::STAGE_ELEMS);
         const bool masked = (cc.s * CW < RB) || (c0 + CW > n);
         float2 cacc0[C / 2][D], cacc1[C / 2][D];
         float2 sf0, sf1;
-        const float4* xib = reinterpret_cast<const float4*>(xrow);
+        const uint32_t xib = smem_u32(xrow);
         if (!masked)
             subtile_pairs<D, TD, R, C, CW, false>(tile, warp, lane, r0, c0, n, xib, nxj, racc, cacc0, cacc1, sf0, sf1);
         else
@@ -601,21 +610,20 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
             !mbar_wait_or_abort(smem_u32(&rg.rempty[slot]), uint32_t(((qg / SLOTS) - 1) & 1), abort_flag))
             return false;
         float* rbuf = rg.red + (size_t(slot) * CWARPS + warp) * D * CW;
-        // column j receives -b_ij (x_i - x_j): the accumulators hold the sum of b_ij (x_i - x_j)
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             if constexpr (C % 4 == 0) {
 #pragma unroll
                 for (int c = 0; c < C; c += 4)
                     *reinterpret_cast<float4*>(rbuf + k * CW + lane * C + c) =
-                        make_float4(-cacc0[c / 2][k].x - cacc1[c / 2][k].x, -cacc0[c / 2][k].y - cacc1[c / 2][k].y,
-                                    -cacc0[c / 2 + 1][k].x - cacc1[c / 2 + 1][k].x,
-                                    -cacc0[c / 2 + 1][k].y - cacc1[c / 2 + 1][k].y);
+                        make_float4(cacc0[c / 2][k].x + cacc1[c / 2][k].x, cacc0[c / 2][k].y + cacc1[c / 2][k].y,
+                                    cacc0[c / 2 + 1][k].x + cacc1[c / 2 + 1][k].x,
+                                    cacc0[c / 2 + 1][k].y + cacc1[c / 2 + 1][k].y);
             } else {
 #pragma unroll
                 for (int c = 0; c < C; c += 2)
                     *reinterpret_cast<float2*>(rbuf + k * CW + lane * C + c) =
-                        make_float2(-cacc0[c / 2][k].x - cacc1[c / 2][k].x, -cacc0[c / 2][k].y - cacc1[c / 2][k].y);
+                        make_float2(cacc0[c / 2][k].x + cacc1[c / 2][k].x, cacc0[c / 2][k].y + cacc1[c / 2][k].y);
             }
         }
         __syncwarp();
@@ -665,7 +673,7 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
 // Standalone pass (one launch per Guttman transform, used when the persistent kernel is
 // not: per-kernel timing).  Same ring, tiles and partials as the persistent kernel.
 template <int D, typename TD>
-__global__ void __launch_bounds__(K1Shape<D, TD>::NT, 1)
+__global__ void __launch_bounds__(K1Shape<D, TD>::NT, FJOFC_K1_MINB)
 k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
     using S = K1Shape<D, TD>;
     constexpr int CWARPS = S::CWARPS;
