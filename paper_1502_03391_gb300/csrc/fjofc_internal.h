@@ -78,7 +78,7 @@ struct K2Params {
     const int64_t* walk_off;
     const int64_t* cta_start;  // [G+1] first sub-tile of every K1 CTA (b*T/G)
     float* mu;                 // [2][FJOFC_MAX_M][FJOFC_MAX_D] modality column means, by t parity
-    float2* bpart;             // [nbx][m*d+d] per-block float-float sums (column sums, commensurability)
+    float2* bpart;             // [m*d+d][nbx] per-group float-float sums (column sums, commensurability)
     unsigned* ticket;
     DevStatus* st;
     double* hist;              // sigma(X_0..X_max_iter)
@@ -103,7 +103,7 @@ struct PersistParams {
     float* buf[3];              // iterate t lives in buf[t % 3]; buf[0] is the caller's X
     const int64_t* cta_start;   // [G+1]
     float2* fid2;               // [2][G] fidelity partials by pass parity
-    float2* bpart;              // [2][ngroups][m*d+d] by pass parity
+    float2* bpart;              // [2][m*d+d][ngroups] by pass parity
     unsigned* bar;              // grid barrier counter (zeroed before launch)
     double* hist;               // sigma(X_0..X_max_iter)
     int ngroups;                // ceil(n / 32)

@@ -153,11 +153,11 @@ struct PhaseBArgs {
     BxTables tb;
     float* Xprev;                               // X_{t-1}, centred in place (t > 1)
     float* Xnext;                               // X_t
-    float2* bpart;                              // [ngroups][npart], npart = m*d + d
+    float2* bpart;                              // [npart][ngroups] (part-major), npart = m*d + d
     const float* mu_prev;                       // [MAX_M][MAX_D] means of X_{t-1} (shared memory)
     const float (*coef)[FJOFC_MAX_M];           // Wmod^-1 w_ll s_l (shared memory)
     const float (*wcomm)[FJOFC_MAX_M];          // w_jl for j < l, else 0 (shared memory)
-    int m, n, d, t;
+    int m, n, d, t, ngroups;
     bool final_pass;                            // only centre and score X_{t-1}
 };
 
@@ -248,7 +248,7 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int u0, int u1, int
                         c = fmaf(a.wcomm[j][l] * df, df, c);
                     }
             const FF cw = warp_sum_ff(FF{c, 0.f});
-            if (lane == 0) a.bpart[int64_t(g) * npart + md + k] = make_float2(cw.hi, cw.lo);
+            if (lane == 0) a.bpart[int64_t(md + k) * a.ngroups + g] = make_float2(cw.hi, cw.lo);
             for (int j = 0; j < m; ++j) {
                 float v = 0.f;
                 if (!a.final_pass && in) {
@@ -257,7 +257,8 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int u0, int u1, int
                 }
                 const FF cs = warp_sum_ff(FF{v, 0.f});
                 if (lane == 0)
-                    a.bpart[int64_t(g) * npart + j * d + k] = a.final_pass ? make_float2(0.f, 0.f) : make_float2(cs.hi, cs.lo);
+                    a.bpart[int64_t(j * d + k) * a.ngroups + g] =
+                        a.final_pass ? make_float2(0.f, 0.f) : make_float2(cs.hi, cs.lo);
             }
         }
         __syncthreads();
@@ -294,7 +295,8 @@ __device__ __forceinline__ void totals2_ff(const float2* p0, int s0, int c0, con
 
 // The per-pass totals in a fixed order, the same in every CTA that calls it (every thread
 // must call it): out[e] for e < npart = the float-float sum over the ngroups groups of
-// phase B's part e, out[npart] = the sum of the nfid fidelity partials.  Two totals per
+// phase B's part e (bpart is part-major), out[npart] = the sum of the nfid fidelity
+// partials.  Two totals per
 // warp at once.
 __device__ __forceinline__ void pass_totals(const float2* bpart, int npart, int ngroups, const float2* fid, int nfid,
                                             FF* out) {
@@ -303,12 +305,12 @@ __device__ __forceinline__ void pass_totals(const float2* bpart, int npart, int 
 #pragma unroll 1
     for (int e = warp; e < nt; e += 2 * nwarps) {
         const int e1 = e + nwarps;
-        const float2* p0 = e < npart ? bpart + e : fid;
-        const int s0 = e < npart ? npart : 1, c0 = e < npart ? ngroups : nfid;
-        const float2* p1 = e1 < npart ? bpart + e1 : fid;
-        const int s1 = e1 < npart ? npart : 1, c1 = e1 < npart ? ngroups : (e1 == npart ? nfid : 0);
+        const float2* p0 = e < npart ? bpart + int64_t(e) * ngroups : fid;
+        const int c0 = e < npart ? ngroups : nfid;
+        const float2* p1 = e1 < npart ? bpart + int64_t(e1) * ngroups : fid;
+        const int c1 = e1 < npart ? ngroups : (e1 == npart ? nfid : 0);
         FF t0, t1;
-        totals2_ff(p0, s0, c0, p1, s1, c1, t0, t1);
+        totals2_ff(p0, 1, c0, p1, 1, c1, t0, t1);
         if ((threadIdx.x & 31) == 0) {
             out[e] = t0;
             if (e1 < nt) out[e1] = t1;

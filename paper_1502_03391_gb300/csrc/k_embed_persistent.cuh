@@ -246,7 +246,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
             a.mu_prev = s_mu;
             a.coef = s_coef;
             a.wcomm = s_wcomm;
-            a.m = m; a.n = n; a.d = D; a.t = t;
+            a.m = m; a.n = n; a.d = D; a.t = t; a.ngroups = P.ngroups;
             a.final_pass = (t == passes);
             phase_b<PhaseBBatch<D>::value>(a, u0, u1, bcap, s_phb);
         }
