@@ -170,6 +170,12 @@ __device__ __forceinline__ void cursor_next(Cursor& c, const K1Params& p) {
 // b (x_i - x_j) = 0, the d_ij = 0 rule of Eq. B, and the fidelity term is Delta'^2).
 // MASKED: only pairs with i < j < n count (diagonal and ragged sub-tiles); otherwise
 // every pair of the sub-tile is valid.
+// Rows processed together by subtile_pairs: each step of the computation is written for
+// RI rows side by side, so that the independent rows' dependency chains are interleaved.
+#ifndef FJOFC_ROW_INTERLEAVE
+#define FJOFC_ROW_INTERLEAVE 2
+#endif
+
 template <int D, typename TD, int R, int C, int CW, bool MASKED>
 __device__ __forceinline__ void subtile_pairs(uint32_t tile, int warp, int lane, int r0, int c0, int n,
                                               uint32_t xib, const float2 (&nxj)[C / 2][D],
@@ -177,6 +183,7 @@ __device__ __forceinline__ void subtile_pairs(uint32_t tile, int warp, int lane,
                                               float2 (&cacc1)[C / 2][D], float2& sf0, float2& sf1) {
     static_assert(C % 2 == 0, "columns are processed in pairs");
     constexpr int CP = C / 2, XB = XiBcast<D>::XB;
+    constexpr int RI = (R % FJOFC_ROW_INTERLEAVE == 0) ? FJOFC_ROW_INTERLEAVE : 1;
     const float2 neg1 = make_float2(-1.f, -1.f);
 #pragma unroll
     for (int cp = 0; cp < CP; ++cp)
@@ -185,46 +192,65 @@ __device__ __forceinline__ void subtile_pairs(uint32_t tile, int warp, int lane,
     sf0 = make_float2(0.f, 0.f);
     sf1 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = r0 + warp * R + r;
-        float2 xb[2 * XB];
+    for (int rb = 0; rb < R; rb += RI) {
+        float2 xb[RI][2 * XB];
+        float dl[RI][C];
 #pragma unroll
-        for (int h = 0; h < XB; ++h) {
-            const float4 v = lds_f4(xib + 16 * (r * XB + h));
-            xb[2 * h] = make_float2(v.x, v.y);
-            xb[2 * h + 1] = make_float2(v.z, v.w);
+        for (int h = 0; h < RI; ++h) {
+            const int r = rb + h;
+#pragma unroll
+            for (int x = 0; x < XB; ++x) {
+                const float4 v = lds_f4(xib + 16 * (r * XB + x));
+                xb[h][2 * x] = make_float2(v.x, v.y);
+                xb[h][2 * x + 1] = make_float2(v.z, v.w);
+            }
+            lds_delta_row<TD, C>(tile + uint32_t(((warp * R + r) * CW + lane * C) * sizeof(TD)), dl[h]);
         }
-        float dl[C];
-        lds_delta_row<TD, C>(tile + uint32_t(((warp * R + r) * CW + lane * C) * sizeof(TD)), dl);
 #pragma unroll
         for (int cp = 0; cp < CP; ++cp) {
-            const float2 ndel = __fmul2_rn(make_float2(dl[2 * cp], dl[2 * cp + 1]), neg1);
-            float2 diff[D];
-            float2 d2 = make_float2(FLT_MIN, FLT_MIN);
+            float2 ndel[RI], diff[RI][D], d2[RI], rinv[RI], q[RI], e[RI];
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                diff[k] = __fadd2_rn(xb[k], nxj[cp][k]);
-                d2 = __ffma2_rn(diff[k], diff[k], d2);
+            for (int h = 0; h < RI; ++h) {
+                ndel[h] = __fmul2_rn(make_float2(dl[h][2 * cp], dl[h][2 * cp + 1]), neg1);
+                d2[h] = make_float2(FLT_MIN, FLT_MIN);
             }
-            const float2 rinv = make_float2(rsqrt_approx(d2.x), rsqrt_approx(d2.y));
-            float2 q = __fmul2_rn(ndel, rinv);            // -b
-            float2 e = __ffma2_rn(d2, rinv, ndel);        // d - Delta
-            if (MASKED) {
-                const int j = c0 + lane * C + 2 * cp;
-                const bool v0 = (j > i) && (j < n), v1 = (j + 1 > i) && (j + 1 < n);
-                q.x = v0 ? q.x : 0.f;
-                e.x = v0 ? e.x : 0.f;
-                q.y = v1 ? q.y : 0.f;
-                e.y = v1 ? e.y : 0.f;
-            }
-            if (r & 1) sf1 = __ffma2_rn(e, e, sf1); else sf0 = __ffma2_rn(e, e, sf0);
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                racc[r][k] = fmaf(-q.x, diff[k].x, racc[r][k]);
-                racc[r][k] = fmaf(-q.y, diff[k].y, racc[r][k]);
-                if (r & 1) cacc1[cp][k] = __ffma2_rn(q, diff[k], cacc1[cp][k]);
-                else cacc0[cp][k] = __ffma2_rn(q, diff[k], cacc0[cp][k]);
+            for (int k = 0; k < D; ++k)
+#pragma unroll
+                for (int h = 0; h < RI; ++h) {
+                    diff[h][k] = __fadd2_rn(xb[h][k], nxj[cp][k]);
+                    d2[h] = __ffma2_rn(diff[h][k], diff[h][k], d2[h]);
+                }
+#pragma unroll
+            for (int h = 0; h < RI; ++h) rinv[h] = make_float2(rsqrt_approx(d2[h].x), rsqrt_approx(d2[h].y));
+#pragma unroll
+            for (int h = 0; h < RI; ++h) {
+                q[h] = __fmul2_rn(ndel[h], rinv[h]);             // -b
+                e[h] = __ffma2_rn(d2[h], rinv[h], ndel[h]);      // d - Delta
+                if (MASKED) {
+                    const int i = r0 + warp * R + rb + h;
+                    const int j = c0 + lane * C + 2 * cp;
+                    const bool v0 = (j > i) && (j < n), v1 = (j + 1 > i) && (j + 1 < n);
+                    q[h].x = v0 ? q[h].x : 0.f;
+                    e[h].x = v0 ? e[h].x : 0.f;
+                    q[h].y = v1 ? q[h].y : 0.f;
+                    e[h].y = v1 ? e[h].y : 0.f;
+                }
             }
+#pragma unroll
+            for (int h = 0; h < RI; ++h) {
+                if ((rb + h) & 1) sf1 = __ffma2_rn(e[h], e[h], sf1); else sf0 = __ffma2_rn(e[h], e[h], sf0);
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+#pragma unroll
+                for (int h = 0; h < RI; ++h) {
+                    const int r = rb + h;
+                    racc[r][k] = fmaf(-q[h].x, diff[h][k].x, racc[r][k]);
+                    racc[r][k] = fmaf(-q[h].y, diff[h][k].y, racc[r][k]);
+                    if (r & 1) cacc1[cp][k] = __ffma2_rn(q[h], diff[h][k], cacc1[cp][k]);
+                    else cacc0[cp][k] = __ffma2_rn(q[h], diff[h][k], cacc0[cp][k]);
+                }
         }
     }
 }
@@ -415,6 +441,19 @@ struct K1Ring {
     }
 };
 
+// Instrumented builds (-DFJOFC_STAMPS): clock cycles warp 0 of every CTA spends in the
+// ring's waits (rfull, full, xfull, rempty) and the number of passes, summed over every
+// launch of the process.
+#ifdef FJOFC_STAMPS
+static __device__ unsigned long long g_waitcyc[1024][5];
+#define FJ_WAIT_T0() const long long fj_w0 = clock64()
+#define FJ_WAIT_ADD(which_) \
+    do { if (threadIdx.x == 0 && blockIdx.x < 1024) fj_wait[which_] += (unsigned long long)(clock64() - fj_w0); } while (0)
+#else
+#define FJ_WAIT_T0() do { } while (0)
+#define FJ_WAIT_ADD(which_) do { } while (0)
+#endif
+
 // One all-pairs pass over the CTA's range (ring uses qbase .. qbase + nq - 1) against the
 // iterate X.  Writes the column partials of every sub-tile, the row partials of every
 // walk segment and returns this thread's weighted fidelity in fid_total.  Returns false
@@ -494,11 +533,16 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
     }
     FF fid{0.f, 0.f};
     int cur_l = cc.l;
+#ifdef FJOFC_STAMPS
+    unsigned long long fj_wait[4] = {0, 0, 0, 0};
+#endif
 
     // reduce this warp's share of the columns of ring use qg (deferred by one sub-tile)
     auto reduce_share = [&](int64_t qg, int64_t tglob) -> bool {
         const int slot = int(qg % SLOTS);
+        FJ_WAIT_T0();
         if (!mbar_wait_or_abort(smem_u32(&rg.rfull[slot]), uint32_t((qg / SLOTS) & 1), abort_flag)) return false;
+        FJ_WAIT_ADD(0);
         const float* rb = rg.red + size_t(slot) * CWARPS * D * CW;
         float* cp = p.colpart + tglob * int64_t(D * CW);
         constexpr int SHARE = (D * CW + CWARPS - 1) / CWARPS;
@@ -551,10 +595,16 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
             cur_l = cc.l;
         }
 
-        if (!mbar_wait_or_abort(smem_u32(&rg.full[stage]), kuse & 1u, abort_flag)) return false;
+        {
+            FJ_WAIT_T0();
+            if (!mbar_wait_or_abort(smem_u32(&rg.full[stage]), kuse & 1u, abort_flag)) return false;
+            FJ_WAIT_ADD(1);
+        }
         if constexpr (S::XSTAGE) {
+            FJ_WAIT_T0();
             if (!mbar_wait_or_abort(smem_u32(&rg.xfull[stage]), kuse & 1u, abort_flag))
                 return false;
+            FJ_WAIT_ADD(2);
             const int64_t start = (int64_t(cc.l) * n + c0) * D;
             const uint32_t xsrc = smem_u32(rg.xs + size_t(stage) * S::XS_FLOATS + int(start & 3) + lane * C * D);
             const float nxsc = -p.xscale[cc.l];
@@ -606,9 +656,13 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
         fid = ff_add(fid, (sf0.x + sf0.y) + (sf1.x + sf1.y));
 
         // column partials of this sub-tile into its ring slot
-        if (qg >= SLOTS &&
-            !mbar_wait_or_abort(smem_u32(&rg.rempty[slot]), uint32_t(((qg / SLOTS) - 1) & 1), abort_flag))
-            return false;
+        {
+            FJ_WAIT_T0();
+            if (qg >= SLOTS &&
+                !mbar_wait_or_abort(smem_u32(&rg.rempty[slot]), uint32_t(((qg / SLOTS) - 1) & 1), abort_flag))
+                return false;
+            FJ_WAIT_ADD(3);
+        }
         float* rbuf = rg.red + (size_t(slot) * CWARPS + warp) * D * CW;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -667,6 +721,12 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
     }
     if (!reduce_share(qbase + nq - 1, rg.t_begin + nq - 1)) return false;
     fid_total = ff_add(fid_total, ff_mul(fid, p.wfid[cur_l]));
+#ifdef FJOFC_STAMPS
+    if (threadIdx.x == 0 && blockIdx.x < 1024) {
+        for (int x = 0; x < 4; ++x) atomicAdd(&g_waitcyc[blockIdx.x][x], fj_wait[x]);
+        atomicAdd(&g_waitcyc[blockIdx.x][4], 1ull);
+    }
+#endif
     return true;
 }
 

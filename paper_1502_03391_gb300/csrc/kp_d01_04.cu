@@ -14,4 +14,9 @@ extern "C" int fjofc_debug_stamps(long long* host, long long count) {
     if (count > cap) count = cap;
     return cudaMemcpyFromSymbol(host, fjofc::g_stamps, size_t(count) * sizeof(long long)) == cudaSuccess ? 0 : -1;
 }
+// Wait cycles of warp 0 per CTA in the ring's waits (rfull, full, xfull, rempty) and the
+// number of all-pairs passes, summed over the process (d <= 4 persistent kernels).
+extern "C" int fjofc_debug_waits(unsigned long long* host) {
+    return cudaMemcpyFromSymbol(host, fjofc::g_waitcyc, sizeof(fjofc::g_waitcyc)) == cudaSuccess ? 0 : -1;
+}
 #endif
