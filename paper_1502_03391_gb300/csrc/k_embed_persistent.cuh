@@ -4,11 +4,12 @@
 // Pass t (reads X_{t-1}, writes X_t):
 //   A. the fused all-pairs sub-tiles of this CTA's fixed range (phase_a, the same code as
 //      the standalone pass k_guttman_pass), fidelity partial -> fid2[t&1][b];
-//   -- grid barrier --
-//   C. every CTA reduces the fidelity partials of pass t and phase B's per-group parts of
-//      pass t-1 in the same fixed order, so all CTAs obtain the same means of X_{t-1},
-//      sigma(X_{t-2}) and stopping decision about X_{t-2} (Algorithm 1 with the decrease
-//      reading); CTA 0 records the history;
+//   -- grid barrier (arrival) --
+//   C. while waiting for the slowest CTA, every CTA reduces the fidelity partials of pass
+//      t-1 and phase B's per-group parts of pass t-1 in the same fixed order, so all CTAs
+//      obtain the same means of X_{t-1}, sigma(X_{t-2}) and stopping decision about
+//      X_{t-2} (Algorithm 1 with the decrease reading); CTA 0 records the history;
+//   -- grid barrier (completion) --
 //   B. for the (group, coordinate) units of this CTA (phase_b, the same code as K2): sum
 //      the partials, centre X_{t-1} in place with its means, its commensurability, the
 //      Wmod^-1 mix into X_t (Eq. update / Cor. 1) and per-group float-float sums;
@@ -66,6 +67,43 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
     return *s_flag != 0;
 }
 
+// The same barrier in two halves, so that a CTA can work between its arrival and the
+// completion: grid_arrive (every thread; the CTA's earlier writes are published before
+// the arrival) and grid_wait (every thread; bounded like grid_barrier).
+__device__ __forceinline__ void grid_arrive(unsigned* ctr, int G) {
+    __syncthreads();
+    if (G > 1 && threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+    }
+}
+__device__ __forceinline__ bool grid_wait(unsigned* ctr, unsigned target, int* s_flag, const volatile int* abort_flag,
+                                          int G) {
+    if (G == 1) {
+        __threadfence();
+        __syncthreads();
+        return true;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        if (ld_acquire_gpu(ctr) < target) {
+            const uint64_t t0 = globaltimer_ns();
+            for (uint32_t it = 1;; ++it) {
+                if (ld_acquire_gpu(ctr) >= target) break;
+                if ((it & 63u) == 0u && (*abort_flag || globaltimer_ns() - t0 > kWaitLimitNs)) {
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *s_flag = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
 // Per-phase clock stamps of passes 2..17 (instrumented builds, -DFJOFC_STAMPS): thread 0 of
 // every CTA records clock64 at the start of phase A, before and after the first grid
 // barrier, after phase C, after phase B and after phase C's totals.
@@ -99,7 +137,6 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
     const K1Params& p = P.k1;
 
     __shared__ FF s_ff[CWARPS];
-    __shared__ FF s_fidt[2];
     __shared__ float s_mu[FJOFC_MAX_M * FJOFC_MAX_D];
     __shared__ float s_coef[FJOFC_MAX_M][FJOFC_MAX_M], s_wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
     __shared__ int s_abort, s_issued, s_flag, s_stop, s_final;
@@ -147,14 +184,15 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
 
     // Pass t (t = 1 .. passes) reads X_{t-1}; a last round t = passes + 1 only decides.
     //   A(t): all pairs of X_{t-1} -> partials, fidelity of X_{t-1} -> fid2[t & 1]
-    //   -- grid barrier --
-    //   C(t): totals of fid2[t & 1] and of B(t-1)'s parts -> means of X_{t-1},
+    //   -- grid barrier, arrival --
+    //   C(t): totals of fid2[(t-1) & 1] and of B(t-1)'s parts -> means of X_{t-1},
     //         sigma(X_{t-2}) and the stopping decision about X_{t-2}
+    //   -- grid barrier, wait --
     //   B(t): centre X_{t-1}, its commensurability, X_t (none in the final pass)
     //   -- grid barrier --
     // The decision comes one pass after the iterate it concerns (a stop discards the
-    // all-pairs pass computed meanwhile), so that the totals are formed right after the
-    // first barrier, next to phase B, instead of after the second one.
+    // all-pairs pass computed meanwhile), so that the totals are formed while the CTA
+    // waits for the slowest one to finish phase A.
     for (int t = 1; ok; ++t) {
         const bool do_a = t <= passes;
         float* Xprev = P.buf[(t - 1) % 3];
@@ -182,29 +220,25 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
         }
         FJ_STAMP(t, 1);
         bar_target += unsigned(G);
-        if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag, G) || *abort_flag) {
-            if (ok) fail_site = 32;
-            ok = false;
-            break;
-        }
-        FJ_STAMP(t, 2);
+        grid_arrive(P.bar, G);
 
         // ================================================================ phase C
-        // the same totals, in the same order, in every CTA
+        // While the other CTAs finish phase A: the totals of pass t-1 (phase B's parts and
+        // the fidelity partials of A(t-1), complete since the previous barriers), the same
+        // in every CTA and in the same order -> means of X_{t-1}, sigma(X_{t-2}) and the
+        // stopping decision about X_{t-2}
         pass_totals(P.bpart + int64_t((t - 1) & 1) * P.ngroups * npart, npart, t >= 2 ? P.ngroups : 0,
-                    P.fid2 + (t & 1) * G, do_a ? G : 0, s_tot);
+                    P.fid2 + ((t - 1) & 1) * G, t >= 2 ? G : 0, s_tot);
         __syncthreads();
         FJ_STAMP(t, 5);
         if (tid < m * D)
             s_mu[(tid / D) * FJOFC_MAX_D + (tid % D)] =
                 (t >= 2 && t - 1 < passes) ? (s_tot[tid].hi + s_tot[tid].lo) * P.inv_n : 0.f;
         if (tid == 0) {
-            if (do_a) s_fidt[t & 1] = s_tot[npart];          // fidelity of X_{t-1}, used at pass t+1
             int stop = 0;
             if (t >= 2) {
                 const int tp = t - 2;                        // the iterate decided about
-                // fidelity of X_{t-2}: from pass t-1's totals
-                const double sigma = stress_from_totals(s_tot, s_fidt[(t - 1) & 1], m, D);
+                const double sigma = stress_from_totals(s_tot, s_tot[npart], m, D);
                 stop = (tp == P.max_iter) ? 1 : 0;
                 if (b == 0) P.hist[tp] = sigma;
                 if (!isfinite(sigma)) {
@@ -232,8 +266,15 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
             s_stop = stop;
             s_final = last_finite;
         }
-        __syncthreads();
         FJ_STAMP(t, 3);
+        // every CTA has finished phase A (its partial tables are complete) and no CTA still
+        // reads X_{t-1} for phase A
+        if (!grid_wait(P.bar, bar_target, &s_flag, abort_flag, G) || *abort_flag) {
+            if (ok) fail_site = 32;
+            ok = false;
+            break;
+        }
+        FJ_STAMP(t, 2);
         if (s_stop || !do_a) break;
 
         // ================================================================ phase B
