@@ -8,8 +8,9 @@
 //      of the group in shared memory (one warp per (unit, l)),
 //   2. (one warp per unit) centres X_{t-1} with the previous pass's means, forms its
 //      commensurability in coordinate k, mixes X_t^(j) = sum_l coef[j][l] (B'_l X_l) and
-//      writes the float-float sums of the group: column sums -> bpart[g][j*d + k],
-//      commensurability -> bpart[g][m*d + k].
+//      writes the group's sums (part-major bpart): column sums of X_t (float32; they only
+//      feed the next centring) -> part j*d + k, commensurability (float-float) -> part
+//      m*d + k.
 #pragma once
 
 #include "fjofc_device.cuh"
@@ -159,6 +160,9 @@ struct PhaseBArgs {
     const float (*wcomm)[FJOFC_MAX_M];          // w_jl for j < l, else 0 (shared memory)
     int m, n, d, t, ngroups;
     bool final_pass;                            // only centre and score X_{t-1}
+#ifdef FJOFC_STAMPS
+    long long* stamp = nullptr;                 // instrumented builds: clock after step 1
+#endif
 };
 
 // Per-group float-float sums written by phase B: the column sums of X_t^(j) for every
@@ -174,7 +178,7 @@ __host__ __device__ constexpr int phase_b_floats_per_unit(int m) { return 2 * m 
 //      = object) from the partials, and x_{t-1}; two such at once per warp;
 //   2. one warp per unit: centre X_{t-1} with the previous pass's means (written back),
 //      its commensurability in coordinate k, the mix X_t^(j) = sum_l coef[j][l] (B'_l X_l)
-//      and the float-float sums of the group -> bpart[g].
+//      and the group's sums -> bpart.
 template <int BATCH = kBxBatch>
 __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int u0, int u1, int cap, float* s) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -229,36 +233,53 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int u0, int u1, int
         }
         }
         __syncthreads();
-        // 2. per unit: centre, commensurability, mix, column sums
+#ifdef FJOFC_STAMPS
+        if (a.stamp && threadIdx.x == 0 && c0 == u0) *a.stamp = clock64();
+#endif
+        // 2. per unit: centre, commensurability, mix, column sums.  The group's column
+        //    sums of X_t (used only for the next centring) are float32 butterflies; the
+        //    commensurability (part of sigma) is float-float; all m+1 in one butterfly.
 #pragma unroll 1
         for (int ui = warp; ui < nc; ui += nwarps) {
             const int u = c0 + ui, g = u / d, k = u - g * d;
             const int i = g * kGroupObjects + lane;
             const bool in = i < n;
-            float xc[FJOFC_MAX_M];
+            float xc[FJOFC_MAX_M], cs[FJOFC_MAX_M];
             float c = 0.f;
-            for (int j = 0; j < m; ++j) {
-                xc[j] = in ? s_xp[(ui * m + j) * kGroupObjects + lane] - a.mu_prev[j * FJOFC_MAX_D + k] : 0.f;
-                if (in && a.t > 1) a.Xprev[(int64_t(j) * n + i) * d + k] = xc[j];
+#pragma unroll
+            for (int j = 0; j < FJOFC_MAX_M; ++j) {
+                xc[j] = (j < m && in) ? s_xp[(ui * m + j) * kGroupObjects + lane] - a.mu_prev[j * FJOFC_MAX_D + k] : 0.f;
+                if (j < m && in && a.t > 1) a.Xprev[(int64_t(j) * n + i) * d + k] = xc[j];
             }
-            if (in)
-                for (int j = 0; j < m; ++j)
-                    for (int l = j + 1; l < m; ++l) {
+#pragma unroll
+            for (int j = 0; j < FJOFC_MAX_M; ++j)
+#pragma unroll
+                for (int l = j + 1; l < FJOFC_MAX_M; ++l)
+                    if (l < m) {
                         const float df = xc[j] - xc[l];
                         c = fmaf(a.wcomm[j][l] * df, df, c);
                     }
-            const FF cw = warp_sum_ff(FF{c, 0.f});
-            if (lane == 0) a.bpart[int64_t(md + k) * a.ngroups + g] = make_float2(cw.hi, cw.lo);
-            for (int j = 0; j < m; ++j) {
+#pragma unroll
+            for (int j = 0; j < FJOFC_MAX_M; ++j) {
                 float v = 0.f;
-                if (!a.final_pass && in) {
+                if (j < m && !a.final_pass && in) {
                     for (int l = 0; l < m; ++l) v = fmaf(a.coef[j][l], s_bx[(ui * m + l) * kGroupObjects + lane], v);
                     a.Xnext[(int64_t(j) * n + i) * d + k] = v;
                 }
-                const FF cs = warp_sum_ff(FF{v, 0.f});
-                if (lane == 0)
-                    a.bpart[int64_t(j * d + k) * a.ngroups + g] =
-                        a.final_pass ? make_float2(0.f, 0.f) : make_float2(cs.hi, cs.lo);
+                cs[j] = v;
+            }
+            FF cw{c, 0.f};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const FF w{__shfl_xor_sync(0xffffffffu, cw.hi, o), __shfl_xor_sync(0xffffffffu, cw.lo, o)};
+                cw = ((lane & o) == 0) ? ff_add(cw, w) : ff_add(w, cw);
+#pragma unroll
+                for (int j = 0; j < FJOFC_MAX_M; ++j) cs[j] += __shfl_xor_sync(0xffffffffu, cs[j], o);
+            }
+            if (lane == 0) {
+                a.bpart[int64_t(md + k) * a.ngroups + g] = make_float2(cw.hi, cw.lo);
+                for (int j = 0; j < m; ++j)
+                    a.bpart[int64_t(j * d + k) * a.ngroups + g] = make_float2(a.final_pass ? 0.f : cs[j], 0.f);
             }
         }
         __syncthreads();

@@ -108,7 +108,7 @@ __device__ __forceinline__ bool grid_wait(unsigned* ctr, unsigned target, int* s
 // every CTA records clock64 at the start of phase A, before and after the first grid
 // barrier, after phase C, after phase B and after phase C's totals.
 #ifdef FJOFC_STAMPS
-constexpr int kStampPasses = 16, kStampCtas = 1024, kStampPoints = 6;
+constexpr int kStampPasses = 16, kStampCtas = 1024, kStampPoints = 7;
 static __device__ long long g_stamps[kStampPasses * kStampCtas * kStampPoints];
 #define FJ_STAMP(t, j)                                                                                   \
     do {                                                                                                 \
@@ -289,6 +289,10 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
             a.wcomm = s_wcomm;
             a.m = m; a.n = n; a.d = D; a.t = t; a.ngroups = P.ngroups;
             a.final_pass = (t == passes);
+#ifdef FJOFC_STAMPS
+            if (t >= 2 && t < 2 + kStampPasses && b < kStampCtas)
+                a.stamp = &g_stamps[((int64_t(t - 2) * kStampCtas + b) * kStampPoints) + 6];
+#endif
             phase_b<PhaseBBatch<D>::value>(a, u0, u1, bcap, s_phb);
         }
         FJ_STAMP(t, 4);
