@@ -52,7 +52,8 @@ def measured_peaks():
 def kernel_source_sha():
     h = hashlib.sha256()
     for rel in ("paper_1502_03391_gb300/csrc/k_guttman_pass.cuh", "paper_1502_03391_gb300/csrc/fjofc_device.cuh",
-                "paper_1502_03391_gb300/csrc/k_embed_persistent.cuh", "paper_1502_03391_gb300/csrc/kp_d01_04.cu"):
+                "paper_1502_03391_gb300/csrc/k_embed_persistent.cuh", "paper_1502_03391_gb300/csrc/k_apply_common.cuh",
+                "paper_1502_03391_gb300/csrc/kp_d01_04.cu"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -157,7 +157,7 @@ struct K3Geom {
 
 struct K3Params {
     const float* X;            // in-sample (m*n) x d
-    const float* XT;           // in-sample transposed: [m][d][nx] (nx = n rounded up to 4)
+    const float* XT;           // in-sample transposed and negated, -X^T: [m][d][nx] (nx = n rounded up to 4)
     const float* SX;           // [m][d] column sums of each X^(j)
     float* Y;                  // k x m x d
     int32_t* iters_out;        // may be NULL

@@ -258,7 +258,7 @@ __global__ void k_oos_prep(const OOSPrepParams p) {
     double s = 0.0;
     for (int i = threadIdx.x; i < p.nx; i += blockDim.x) {
         const float v = (i < p.n) ? p.X[(int64_t(j) * p.n + i) * p.d + kk] : 0.f;
-        p.XT[(int64_t(j) * p.d + kk) * p.nx + i] = v;
+        p.XT[(int64_t(j) * p.d + kk) * p.nx + i] = -v;       // K3 works with -x
         s += double(v);
     }
     s = warp_sum_f64(s);

@@ -162,8 +162,9 @@ __device__ __forceinline__ void cursor_next(Cursor& c, const K1Params& p) {
 // (add/mul/fma .f32x2: same rounding per element as the scalar operation, half the issue
 // slots); the reciprocal square root stays scalar.  With q = -b_ij and e' = d'_ij -
 // Delta'_ij (the packed forms take no negated operand, so the signs are arranged to need
-// one negation of Delta per column pair): adds -q (x'_i - x'_j) = b_ij (x'_i - x'_j) to
-// racc[r] (scalar, columns in order), q (x'_i - x'_j), the contribution to column j, to
+// one negation of Delta per column pair): adds q (x'_i - x'_j) = -b_ij (x'_i - x'_j) to
+// racc[r] (scalar, columns in order; the row flush negates it), q (x'_i - x'_j), the
+// contribution to column j, to
 // the column accumulators (two interleaved chains by row parity) and e'^2 to sf0/sf1 (per
 // column parity halves).  The squared distance starts from FLT_MIN instead of 0: this
 // changes no d^2 above 2^-102 and keeps rsqrt finite when x_i = x_j (then
@@ -246,8 +247,8 @@ __device__ __forceinline__ void subtile_pairs(uint32_t tile, int warp, int lane,
 #pragma unroll
                 for (int h = 0; h < RI; ++h) {
                     const int r = rb + h;
-                    racc[r][k] = fmaf(-q[h].x, diff[h][k].x, racc[r][k]);
-                    racc[r][k] = fmaf(-q[h].y, diff[h][k].y, racc[r][k]);
+                    racc[r][k] = fmaf(q[h].x, diff[h][k].x, racc[r][k]);
+                    racc[r][k] = fmaf(q[h].y, diff[h][k].y, racc[r][k]);
                     if (r & 1) cacc1[cp][k] = __ffma2_rn(q[h], diff[h][k], cacc1[cp][k]);
                     else cacc0[cp][k] = __ffma2_rn(q[h], diff[h][k], cacc0[cp][k]);
                 }
@@ -692,7 +693,7 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
-                for (int k = 0; k < D; ++k) v[r * D + k] = racc[r][k];
+                for (int k = 0; k < D; ++k) v[r * D + k] = -racc[r][k];   // racc holds -sum b (x_i - x_j)
             int base = 0;
             bool writer = true;
             WarpScatter<R * D, 16>::run(v, lane, base, writer);

@@ -50,9 +50,12 @@ struct K3Shape {
     static constexpr size_t RING_BYTES = size_t(STAGES) * STAGE_BYTES;
     static constexpr size_t Y_FLOATS = size_t(R) * FJOFC_MAX_M * D;
     static constexpr size_t ACC_FLOATS = size_t(R) * FJOFC_MAX_M * (D + 1);
+    // y_j of the slots as (y, y) pairs: YB float4 per slot
+    static constexpr int YB = (D + 1) / 2;
+    static constexpr size_t YB_FLOATS = size_t(R) * YB * 4;
     static constexpr size_t WARP_BYTES =
-        ((RING_BYTES + (2 * Y_FLOATS + ACC_FLOATS) * 4 + size_t(R) * FJOFC_MAX_M * 8 + 2 * R * 8 + R * 8 +
-          STAGES * 8 + R * 8 + R * 4) + 127) & ~size_t(127);
+        ((RING_BYTES + YB_FLOATS * 4 + (2 * Y_FLOATS + ACC_FLOATS) * 4 + size_t(R) * FJOFC_MAX_M * 8 + 2 * R * 8 +
+          R * 8 + STAGES * 8 + R * 8 + R * 4) + 127) & ~size_t(127);
     static constexpr size_t SMEM = WARPS * WARP_BYTES + 128;
 };
 
@@ -60,7 +63,8 @@ template <int D, typename TD>
 __global__ void __launch_bounds__(K3Shape<D, TD>::NT, 1)
 k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
     using S = K3Shape<D, TD>;
-    constexpr int R = S::R, C = S::C, STAGES = S::STAGES, CW = S::CW;
+    constexpr int R = S::R, C = S::C, STAGES = S::STAGES, CW = S::CW, YB = S::YB;
+    static_assert(C % 2 == 0, "points are processed in pairs");
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -68,7 +72,8 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* wb = smem + size_t(warp) * S::WARP_BYTES;
     TD* ring = reinterpret_cast<TD*>(wb);
-    float* ys = reinterpret_cast<float*>(wb + S::RING_BYTES);          // [R][MAXM][D]  y_{t-1}
+    float* yb = reinterpret_cast<float*>(wb + S::RING_BYTES);          // [R][YB] float4 (y, y) pairs
+    float* ys = yb + S::YB_FLOATS;                                       // [R][MAXM][D]  y_{t-1}
     float* yn = ys + S::Y_FLOATS;                                        // [R][MAXM][D]  y_t
     float* acc = yn + S::Y_FLOATS;                                       // [R][MAXM][D+1]
     double* fidj = reinterpret_cast<double*>(acc + S::ACC_FLOATS);       // [R][MAXM]
@@ -150,24 +155,28 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
         }
         {
             for (int j = 0; j < m; ++j) {
-                const float sc = p.dscale[j];
-                float yr[R][D];
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-#pragma unroll
-                    for (int kk = 0; kk < D; ++kk) yr[r][kk] = ys[(r * FJOFC_MAX_M + j) * D + kk];
-                float bx[R][D], bs[R], f32[R];
-                FF fff[R];                  // float-float fidelity (GB300's float64 rate is low)
+                // the slots' y_j as (y, y) pairs (one packed operand for two points), read
+                // by every lane from the same address
+                for (int e = lane; e < R * D; e += 32) {
+                    const int r = e / D, kk = e - r * D;
+                    const float y = ys[(r * FJOFC_MAX_M + j) * D + kk];
+                    *reinterpret_cast<float2*>(yb + (r * YB + kk / 2) * 4 + 2 * (kk & 1)) = make_float2(y, y);
+                }
+                __syncwarp();
+                const float2 nsc = make_float2(-p.dscale[j], -p.dscale[j]);
+                float2 bx[R][D], bs[R], f2[R];   // per point-parity halves; bx holds -sum b x
+                FF fff[R];                        // float-float fidelity (GB300's float64 rate is low)
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    bs[r] = 0.f; f32[r] = 0.f; fff[r] = FF{0.f, 0.f};
+                    bs[r] = make_float2(0.f, 0.f); f2[r] = make_float2(0.f, 0.f); fff[r] = FF{0.f, 0.f};
 #pragma unroll
-                    for (int kk = 0; kk < D; ++kk) bx[r][kk] = 0.f;
+                    for (int kk = 0; kk < D; ++kk) bx[r][kk] = make_float2(0.f, 0.f);
                 }
                 const float* XTj = p.XT + int64_t(j) * D * p.nx;
-                // the C points of this lane in sub-tile s (X^T rows are padded to a multiple of
-                // 4 points, so whole vectors stay inside the row; points >= n are masked below)
-                auto load_xp = [&](int s, float (&xv)[C][D]) {
+                // -x of the C points of this lane in sub-tile s as point pairs (X^T holds -x;
+                // its rows are padded to a multiple of 4 points, so whole vectors stay inside
+                // the row; points >= n are masked below)
+                auto load_xp = [&](int s, float2 (&xv)[C / 2][D]) {
                     const int pt = s * CW + lane * C;
 #pragma unroll
                     for (int kk = 0; kk < D; ++kk) {
@@ -175,57 +184,73 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                         if (pt + C <= p.nx) {
                             if constexpr (C == 4) {
                                 const float4 v = __ldg(reinterpret_cast<const float4*>(src));
-                                xv[0][kk] = v.x; xv[1][kk] = v.y; xv[2][kk] = v.z; xv[3][kk] = v.w;
+                                xv[0][kk] = make_float2(v.x, v.y);
+                                xv[1][kk] = make_float2(v.z, v.w);
                             } else {
-                                const float2 v = __ldg(reinterpret_cast<const float2*>(src));
-                                xv[0][kk] = v.x; xv[1][kk] = v.y;
+                                xv[0][kk] = __ldg(reinterpret_cast<const float2*>(src));
                             }
                         } else {
 #pragma unroll
-                            for (int c = 0; c < C; ++c) xv[c][kk] = 0.f;
+                            for (int c = 0; c < C / 2; ++c) xv[c][kk] = make_float2(0.f, 0.f);
                         }
                     }
                 };
-                float xpn[C][D];
+                float2 xpn[C / 2][D];
                 load_xp(0, xpn);
+                const uint32_t ybs = smem_u32(yb);
                 for (int s = 0; s < nsub; ++s) {
                     const int pt0 = s * CW + lane * C;
-                    float xp[C][D];
+                    float2 xp[C / 2][D];
 #pragma unroll
-                    for (int c = 0; c < C; ++c)
+                    for (int c = 0; c < C / 2; ++c)
 #pragma unroll
                         for (int kk = 0; kk < D; ++kk) xp[c][kk] = xpn[c][kk];
                     if (s + 1 < nsub) load_xp(s + 1, xpn);
                     const int stage = int(q_cons % STAGES);
                     const uint32_t par = (q_cons / STAGES) & 1u;
                     failed |= !mbar_wait_bounded(smem_u32(&full[stage]), par);
-                    const TD* tile = ring + size_t(stage) * S::STAGE_ELEMS;
+                    const uint32_t tile = smem_u32(ring + size_t(stage) * S::STAGE_ELEMS);
                     const bool ragged = (s * CW + CW > n);
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
-                        float dl[C];
-                        load_delta_row<TD, C>(tile + r * CW + lane * C, dl);
+                        float2 y2[2 * YB];
 #pragma unroll
-                        for (int c = 0; c < C; ++c) {
-                            float d2 = 0.f;
+                        for (int h = 0; h < YB; ++h) {
+                            const float4 v = lds_f4(ybs + 16 * (r * YB + h));
+                            y2[2 * h] = make_float2(v.x, v.y);
+                            y2[2 * h + 1] = make_float2(v.z, v.w);
+                        }
+                        float dl[C];
+                        lds_delta_row<TD, C>(tile + uint32_t((r * CW + lane * C) * sizeof(TD)), dl);
+#pragma unroll
+                        for (int cp = 0; cp < C / 2; ++cp) {
+                            const float2 del = make_float2(dl[2 * cp], dl[2 * cp + 1]);
+                            float2 d2 = make_float2(0.f, 0.f);
 #pragma unroll
                             for (int kk = 0; kk < D; ++kk) {
-                                const float df = yr[r][kk] - xp[c][kk];
-                                d2 = fmaf(df, df, d2);
+                                const float2 df = __fadd2_rn(y2[kk], xp[cp][kk]);
+                                d2 = __ffma2_rn(df, df, d2);
                             }
-                            const float rinv = (d2 > 0.f) ? rsqrt_approx(d2) : 0.f;
-                            float bb = dl[c] * rinv;
-                            float e = fmaf(sc, dl[c], -(d2 * rinv));
-                            if (ragged && pt0 + c >= n) { bb = 0.f; e = 0.f; }
-                            bs[r] += bb;
-                            f32[r] = fmaf(e, e, f32[r]);
+                            const float2 rinv = make_float2((d2.x > 0.f) ? rsqrt_approx(d2.x) : 0.f,
+                                                            (d2.y > 0.f) ? rsqrt_approx(d2.y) : 0.f);
+                            float2 bb = __fmul2_rn(del, rinv);
+                            float2 e = __ffma2_rn(nsc, del, __fmul2_rn(d2, rinv));    // d - s delta
+                            if (ragged) {
+                                if (pt0 + 2 * cp >= n) { bb.x = 0.f; e.x = 0.f; }
+                                if (pt0 + 2 * cp + 1 >= n) { bb.y = 0.f; e.y = 0.f; }
+                            }
+                            bs[r] = __fadd2_rn(bs[r], bb);
+                            f2[r] = __ffma2_rn(e, e, f2[r]);
 #pragma unroll
-                            for (int kk = 0; kk < D; ++kk) bx[r][kk] = fmaf(bb, xp[c][kk], bx[r][kk]);
+                            for (int kk = 0; kk < D; ++kk) bx[r][kk] = __ffma2_rn(bb, xp[cp][kk], bx[r][kk]);
                         }
                     }
                     if ((s & 3) == 3) {
 #pragma unroll
-                        for (int r = 0; r < R; ++r) { fff[r] = ff_add(fff[r], f32[r]); f32[r] = 0.f; }
+                        for (int r = 0; r < R; ++r) {
+                            fff[r] = ff_add(fff[r], f2[r].x + f2[r].y);
+                            f2[r] = make_float2(0.f, 0.f);
+                        }
                     }
                     __syncwarp();
                     ++q_cons;
@@ -238,18 +263,19 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                 // reduce this modality's sums over the warp
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const FF fr = warp_sum_ff(ff_add(fff[r], f32[r]));
-                    const float br = warp_sum_f32(bs[r]);
+                    const FF fr = warp_sum_ff(ff_add(fff[r], f2[r].x + f2[r].y));
+                    const float br = warp_sum_f32(bs[r].x + bs[r].y);
                     if (lane == 0) {
                         fidj[r * FJOFC_MAX_M + j] = double(fr.hi) + double(fr.lo);
                         acc[(r * FJOFC_MAX_M + j) * (D + 1) + D] = br;
                     }
 #pragma unroll
                     for (int kk = 0; kk < D; ++kk) {
-                        const float v = warp_sum_f32(bx[r][kk]);
+                        const float v = warp_sum_f32(bx[r][kk].x + bx[r][kk].y);
                         if (lane == ((r * D + kk) & 31)) acc[(r * FJOFC_MAX_M + j) * (D + 1) + kk] = v;
                     }
                 }
+                __syncwarp();
             }
             failed = __any_sync(0xffffffffu, failed);
             if (failed) break;
@@ -292,7 +318,7 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                 for (int i2 = 0; i2 < m; ++i2) {
                     const float* a = acc + (r * FJOFC_MAX_M + i2) * (D + 1);
                     const float wi = p.wfid[i2], si = p.dscale[i2];
-                    const float xi = wi * (p.SX[i2 * D + kk] - si * a[kk]);
+                    const float xi = wi * fmaf(si, a[kk], p.SX[i2 * D + kk]);   // a[kk] = -sum_k b_k x_k
                     const float psi = wi * si * a[D];
                     v = fmaf(p.winv[j][i2], fmaf(psi, ys[(r * FJOFC_MAX_M + i2) * D + kk], xi), v);
                 }
