@@ -32,6 +32,10 @@ Readings of the paper taken here (each is listed in the design doc):
   modality j has weight ``w_jj`` to the in-sample points of modality j and weight
   ``w_ij`` to the new point of modality i.  For Eq. (W) this is the paper's W^(o).
 * Several new objects are independent problems (Sec. 3, last paragraph).
+* Relaxed updates (the Conclusion's suggested acceleration): ``X_t = X_{t-1} + r
+  (L^+ B(X_{t-1}) X_{t-1} - X_{t-1})`` with ``0 <= r <= 2``, applied to the iterates as
+  they are (no centring step: the plain transform's output is centred by itself, a
+  relaxed one keeps ``(1 - r)`` times the previous iterate's column means).
 """
 from __future__ import annotations
 
@@ -189,12 +193,26 @@ def guttman_step(X: np.ndarray, Lp: np.ndarray, W: np.ndarray, Delta: np.ndarray
     return Lp @ (guttman_B(X, W, Delta) @ X)
 
 
+def relaxed_step(X: np.ndarray, Lp: np.ndarray, W: np.ndarray, Delta: np.ndarray, relax: float) -> np.ndarray:
+    """The relaxed update of iterative majorization that the paper names as the next
+    acceleration of fJOFC (Conclusion, with de Leeuw and Heiser's relaxed updates):
+    move from ``X`` towards the Guttman transform and ``relax`` times as far,
+    ``X + relax (L^+ B(X) X - X)``.  ``relax = 1`` is the plain transform.  For
+    ``0 <= relax <= 2`` the result stays inside the majorizing quadratic's level set of
+    ``X`` (Eq. major: tau(., X) is a quadratic in the new configuration, minimised by
+    the Guttman transform, and the relaxed point mirrors ``X`` about that minimiser at
+    most), so the stress does not increase."""
+    G = guttman_step(X, Lp, W, Delta)
+    return X + relax * (G - X)
+
+
 def jofc_embed(deltas: Sequence[np.ndarray], Wm: np.ndarray, X0: np.ndarray, max_iter: int,
                tol: float = -1.0, tol_mode: str = "relative", keep_iterates: bool = False,
-               Lp: Optional[np.ndarray] = None) -> EmbedResult:
+               Lp: Optional[np.ndarray] = None, relax: float = 1.0) -> EmbedResult:
     """Algorithm 1 from a given ``X_0`` (its cMDS initialisation is not part of the
-    loop): compute sigma(X_0); then repeat ``X_t = L^+ B(X_{t-1}) X_{t-1}`` and
-    sigma(X_t) until the stopping test fails or ``max_iter`` transforms are done."""
+    loop): compute sigma(X_0); then repeat ``X_t = L^+ B(X_{t-1}) X_{t-1}`` (or, with
+    ``relax != 1``, the relaxed update ``relaxed_step``) and sigma(X_t) until the
+    stopping test fails or ``max_iter`` transforms are done."""
     m = len(deltas)
     n = np.asarray(deltas[0]).shape[0]
     W = omnibus_weights(Wm, n)
@@ -207,7 +225,7 @@ def jofc_embed(deltas: Sequence[np.ndarray], Wm: np.ndarray, X0: np.ndarray, max
     its = [X.copy()] if keep_iterates else None
     t = 0
     while t < max_iter:
-        X = guttman_step(X, Lp, W, Delta)
+        X = guttman_step(X, Lp, W, Delta) if relax == 1.0 else relaxed_step(X, Lp, W, Delta, relax)
         t += 1
         hist.append(raw_stress(X, W, Delta))
         if keep_iterates:

@@ -249,6 +249,62 @@ def test_monotone_descent_and_centering():
         np.testing.assert_allclose(Xt.mean(0), 0, atol=1e-12)
 
 
+@pytest.mark.parametrize("m,w", [(2, 0.5), (3, 1.2)])
+def test_relaxed_update_stays_in_the_majorizer_level_set(m, w):
+    """Relaxed updates (the Conclusion's suggested acceleration): tau(., X) of Eq. (major)
+    is a quadratic in the new configuration minimised by the Guttman transform G, so at
+    X + r (G - X) it equals tau(G, X) + (1 - r)^2 (sigma(X) - tau(G, X)), and
+    sigma(X_r) <= tau(X_r, X) <= sigma(X) exactly when 0 <= r <= 2."""
+    n = 11
+    deltas, Wm, X = _small_problem(m, n, 2, seed=40 + m, w=w)
+    W = O.omnibus_weights(Wm, n)
+    D = O.omnibus_dissimilarity(deltas)
+    L = O.laplacian(W)
+    Lp = _lp(Wm, n)
+    BX = O.guttman_B(X, W, D) @ X
+    iu = np.triu_indices(m * n, 1)
+    c = np.sum(W[iu] * D[iu] ** 2)
+
+    def tau(Y):
+        return c + np.trace(Y.T @ L @ Y) - 2 * np.trace(Y.T @ BX)
+
+    sX = O.raw_stress(X, W, D)
+    np.testing.assert_allclose(tau(X), sX, rtol=1e-12)
+    G = O.guttman_step(X, Lp, W, D)
+    tG = tau(G)
+    for r in (0.0, 0.5, 1.0, 1.5, 2.0, 2.5):
+        Xr = O.relaxed_step(X, Lp, W, D, r)
+        np.testing.assert_allclose(tau(Xr), tG + (1 - r) ** 2 * (sX - tG), rtol=1e-10, atol=1e-10 * sX)
+        if r <= 2.0:
+            assert O.raw_stress(Xr, W, D) <= tau(Xr) + 1e-10 * sX
+            assert tau(Xr) <= sX + 1e-10 * sX
+        else:
+            assert tau(Xr) > sX
+
+
+def test_relaxed_loop_descends_keeps_fixed_points_and_r0_stays():
+    """With 0 < r <= 2 the relaxed loop's stress never increases; r = 0 leaves X_0 in
+    place; a zero-stress configuration is a fixed point of the relaxed map too."""
+    deltas, Wm, X0 = _small_problem(2, 20, 2, seed=31)
+    for r in (1.5, 1.9, 2.0):
+        res = O.jofc_embed(deltas, Wm, X0, max_iter=60, relax=r)
+        st = np.array(res.stress)
+        assert np.all(np.diff(st) <= 1e-12 * st[:-1]), r
+        assert st[-1] < st[0]
+    res0 = O.jofc_embed(deltas, Wm, X0, max_iter=5, relax=0.0)
+    np.testing.assert_array_equal(res0.X, X0)
+    rng = np.random.default_rng(12)
+    n = 12
+    Y = rng.standard_normal((n, 2))
+    Y -= Y.mean(0)
+    Dy = np.sqrt(((Y[:, None] - Y[None]) ** 2).sum(-1))
+    Wm2 = _eqW(2, 0.5)
+    X = np.vstack([Y, Y])
+    W = O.omnibus_weights(Wm2, n)
+    D = O.omnibus_dissimilarity([Dy, Dy])
+    np.testing.assert_allclose(O.relaxed_step(X, _lp(Wm2, n), W, D, 1.7), X, atol=1e-12)
+
+
 def test_exact_configuration_fixed_point_and_recovery():
     """When every Delta_i holds the distances of one configuration Y, X = [Y; Y] has
     zero stress and is a fixed point; from a perturbed start stress falls to ~0."""
