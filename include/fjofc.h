@@ -73,7 +73,15 @@ typedef struct fjofc_opts {
                              1: one launch per all-pairs pass (K1) and per W^-1 pass (K2),
                                 each timed with CUDA events on cuda_stream (ms_pass, ms_apply).
                              2: the persistent kernel, its launch timed (ms_pass). */
-    int32_t reserved[4];  /* must be zero */
+    float   relax;        /* relaxed updates (the Conclusion's suggested acceleration of the
+                             majorization): X_t = X_{t-1} + relax (L^+ B(X_{t-1}) X_{t-1} -
+                             X_{t-1}).  0 or 1: the plain Guttman transform.  Otherwise in
+                             (0, 2]: the stress still does not increase (the relaxed point
+                             stays inside the majorizer's level set).  With relax != 1 the
+                             iterates are not centred (the oracle's definition: a relaxed
+                             iterate keeps (1 - relax) times the previous one's column
+                             means).  FJOFC_ERR_ARG outside [0, 2]. */
+    int32_t reserved[3];  /* must be zero */
 } fjofc_opts;
 
 typedef struct fjofc_result {
@@ -111,10 +119,10 @@ typedef struct fjofc_result {
  *                 Eq. (W) is w_ii = 1, w_ij = w.
  *  X            : DEVICE float32 (m*n) x d row-major, rows modality-major (the n rows of
  *                 X^(1), then X^(2), ...), 16-byte aligned.  In: X_0.  Out: the final
- *                 iterate X_T, with each modality block's column means (float-float
- *                 sums) removed (Guttman outputs are centred in exact arithmetic, Sec.
- *                 1.2.2).  X_0 itself is used as given (its stress is that of the
- *                 uncentred input).
+ *                 iterate X_T, with each modality block's column means removed (Guttman
+ *                 outputs are centred in exact arithmetic, Sec. 1.2.2; not with
+ *                 relaxed updates, see opts.relax).  X_0 itself is used as given (its
+ *                 stress is that of the uncentred input).
  *  opts, res    : host; see above.  res may be NULL.
  *  cuda_stream  : cudaStream_t.
  *

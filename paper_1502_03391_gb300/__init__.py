@@ -48,7 +48,7 @@ class FjofcError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("tol_mode", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("profile", ctypes.c_int32), ("relax", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
 
 
 class _Result(ctypes.Structure):
@@ -224,11 +224,12 @@ class EmbedResult:
 
 def embed(deltas: Sequence, weights, X, max_iter: int, tol: float = -1.0, tol_mode: str = "relative",
           delta_scale=None, stream=None, history: bool = True, check: bool = True,
-          profile: int = 0) -> EmbedResult:
+          profile: int = 0, relax: float = 1.0) -> EmbedResult:
     """In-sample fJOFC from ``X`` (in place).  ``deltas``: m CUDA n x n views (float32,
     float16 or bfloat16; row stride a multiple of 16 bytes); ``weights``: m x m;
     ``X``: contiguous float32 CUDA tensor of shape (m*n, d).  ``profile``: 0 none, 1 one
-    launch per pass with per-kernel timing, 2 the persistent loop kernel timed.  See
+    launch per pass with per-kernel timing, 2 the persistent loop kernel timed.
+    ``relax``: relaxed updates (1 = the plain Guttman transform, up to 2).  See
     ``fjofc_embed``."""
     m = len(deltas)
     n = int(deltas[0].shape[0])
@@ -239,7 +240,7 @@ def embed(deltas: Sequence, weights, X, max_iter: int, tol: float = -1.0, tol_mo
     ptrs = (ctypes.c_void_p * m)(*[D.data_ptr() for D in deltas])
     Wn = _weights(weights, m)
     opts = _Opts(int(max_iter), float(tol), TOL_RELATIVE if tol_mode == "relative" else TOL_ABS_NORMALIZED,
-                 int(profile))
+                 int(profile), float(relax))
     hist = np.zeros(int(max_iter) + 1, dtype=np.float64) if history else None
     res = _Result()
     if hist is not None:

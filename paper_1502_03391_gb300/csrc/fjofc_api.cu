@@ -383,6 +383,9 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
     }
     k2.Tm = P.Tm; k2.T = P.T;
     k2.tol_mode = o.tol_mode; k2.tol = o.tol;
+    // relaxed updates: 0 and 1 are the plain transform, whose iterates are centred
+    k2.relax = (o.relax == 0.f) ? 1.f : o.relax;
+    k2.centre = (k2.relax == 1.f) ? 1 : 0;
     k2.npairs = double(m * n) * double(m * n - 1) / 2.0;
     k2.inv_n = float(1.0 / double(n));
     for (int j = 0; j < m; ++j)
@@ -416,6 +419,7 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
     pp.ngroups = P.nbx;
     pp.rb_shift = k2.rb_shift; pp.cw_shift = k2.cw_shift;
     pp.max_iter = o.max_iter; pp.tol_mode = o.tol_mode; pp.tol = o.tol; pp.npairs = k2.npairs; pp.inv_n = k2.inv_n;
+    pp.relax = k2.relax; pp.centre = k2.centre;
     for (int j = 0; j < FJOFC_MAX_M; ++j)
         for (int l = 0; l < FJOFC_MAX_M; ++l) { pp.coef[j][l] = k2.coef[j][l]; pp.wcomm[j][l] = k2.wcomm[j][l]; }
     pp.tb = k2.tb;
@@ -441,7 +445,8 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         if (o.tol_mode != FJOFC_TOL_ABS_NORMALIZED && o.tol_mode != FJOFC_TOL_RELATIVE) return arg_error("unknown tol_mode");
         if (std::isnan(o.tol)) return arg_error("tol is NaN");
         if (o.profile < 0 || o.profile > 2) return arg_error("profile must be 0, 1 or 2");
-        for (int r = 0; r < 4; ++r)
+        if (!(o.relax >= 0.f && o.relax <= 2.f)) return arg_error("relax must be in [0, 2]");
+        for (int r = 0; r < 3; ++r)
             if (o.reserved[r] != 0) return arg_error("opts.reserved must be zero");
     } else {
         o.max_iter = 0;

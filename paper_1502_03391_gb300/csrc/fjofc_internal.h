@@ -89,6 +89,8 @@ struct K2Params {
     int tol_mode;
     double tol, npairs;        // tolerance, C(mn,2)
     float inv_n;               // 1 / n (column means)
+    float relax;               // relaxed update factor (1: the plain Guttman transform)
+    int centre;                // 1: centre X_{t-1} in place with its column means (relax == 1)
     float coef[FJOFC_MAX_M][FJOFC_MAX_M];    // [Wmod^-1]_{jl} * w_ll * s_l
     float wcomm[FJOFC_MAX_M][FJOFC_MAX_M];   // w_jl for j < l, else 0
     BxTables tb;
@@ -111,6 +113,8 @@ struct PersistParams {
     int max_iter, tol_mode;
     double tol, npairs;
     float inv_n;
+    float relax;                // relaxed update factor (1: the plain Guttman transform)
+    int centre;                 // 1: centre X_{t-1} in place with its column means
     float coef[FJOFC_MAX_M][FJOFC_MAX_M];
     float wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
     BxTables tb;

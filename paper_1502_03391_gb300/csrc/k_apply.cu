@@ -52,6 +52,8 @@ k_apply(const K2Params p) {
     a.coef = s_coef;
     a.wcomm = s_wcomm;
     a.m = m; a.n = n; a.d = d; a.t = p.t; a.ngroups = p.nbx;
+    a.centre = p.centre != 0;
+    a.relax = p.relax;
     a.final_pass = p.final_pass != 0;
     phase_b(a, int(blockIdx.x) * d, int(blockIdx.x + 1) * d, d, s_dyn);
 

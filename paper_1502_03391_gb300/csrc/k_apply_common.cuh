@@ -6,8 +6,9 @@
 // (group g, coordinate k).  For every unit the CTA
 //   1. sums (B'_l X_l)_{i,k} for every modality l from the K1 partials and stages x_{t-1}
 //      of the group in shared memory (one warp per (unit, l)),
-//   2. (one warp per unit) centres X_{t-1} with the previous pass's means, forms its
-//      commensurability in coordinate k, mixes X_t^(j) = sum_l coef[j][l] (B'_l X_l) and
+//   2. (one warp per unit) centres X_{t-1} with the previous pass's means (plain
+//      transform only), forms its commensurability in coordinate k, mixes
+//      X_t^(j) = sum_l coef[j][l] (B'_l X_l) (relaxed: X_{t-1} + relax (that - X_{t-1})) and
 //      writes the group's sums (part-major bpart): column sums of X_t (float32; they only
 //      feed the next centring) -> part j*d + k, commensurability (float-float) -> part
 //      m*d + k.
@@ -160,6 +161,8 @@ struct PhaseBArgs {
     const float (*wcomm)[FJOFC_MAX_M];          // w_jl for j < l, else 0 (shared memory)
     int m, n, d, t, ngroups;
     bool final_pass;                            // only centre and score X_{t-1}
+    bool centre;                                // centre X_{t-1} in place (plain transform)
+    float relax;                                // X_t = X_{t-1} + relax (G - X_{t-1})
 #ifdef FJOFC_STAMPS
     long long* stamp = nullptr;                 // instrumented builds: clock after step 1
 #endif
@@ -248,8 +251,10 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int u0, int u1, int
             float c = 0.f;
 #pragma unroll
             for (int j = 0; j < FJOFC_MAX_M; ++j) {
-                xc[j] = (j < m && in) ? s_xp[(ui * m + j) * kGroupObjects + lane] - a.mu_prev[j * FJOFC_MAX_D + k] : 0.f;
-                if (j < m && in && a.t > 1) a.Xprev[(int64_t(j) * n + i) * d + k] = xc[j];
+                xc[j] = (j < m && in) ? s_xp[(ui * m + j) * kGroupObjects + lane] -
+                                            (a.centre ? a.mu_prev[j * FJOFC_MAX_D + k] : 0.f)
+                                      : 0.f;
+                if (j < m && in && a.centre && a.t > 1) a.Xprev[(int64_t(j) * n + i) * d + k] = xc[j];
             }
 #pragma unroll
             for (int j = 0; j < FJOFC_MAX_M; ++j)
@@ -264,6 +269,7 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int u0, int u1, int
                 float v = 0.f;
                 if (j < m && !a.final_pass && in) {
                     for (int l = 0; l < m; ++l) v = fmaf(a.coef[j][l], s_bx[(ui * m + l) * kGroupObjects + lane], v);
+                    if (a.relax != 1.f) v = fmaf(1.f - a.relax, xc[j], a.relax * v);   // relaxed update
                     a.Xnext[(int64_t(j) * n + i) * d + k] = v;
                 }
                 cs[j] = v;

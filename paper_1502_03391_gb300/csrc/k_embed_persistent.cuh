@@ -288,6 +288,8 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
             a.coef = s_coef;
             a.wcomm = s_wcomm;
             a.m = m; a.n = n; a.d = D; a.t = t; a.ngroups = P.ngroups;
+            a.centre = P.centre != 0;
+            a.relax = P.relax;
             a.final_pass = (t == passes);
 #ifdef FJOFC_STAMPS
             if (t >= 2 && t < 2 + kStampPasses && b < kStampCtas)

@@ -253,3 +253,43 @@ def test_persistent_and_per_pass_launches_agree(fj, m, n, d):
         np.testing.assert_array_equal(r.history, outs[0][1].history)
     assert outs[1][1].passes == outs[1][1].iters + 1 and outs[1][1].ms_pass > 0
     assert outs[2][1].passes == outs[2][1].iters + 1 and outs[2][1].ms_pass > 0
+
+
+@pytest.mark.parametrize("m,n,d,relax", [(2, 150, 3, 1.5), (3, 129, 2, 2.0), (2, 300, 5, 1.8)])
+def test_relaxed_updates_match_oracle(fj, m, n, d, relax):
+    """Relaxed updates (opts.relax, the Conclusion's suggested acceleration) against the
+    oracle's relaxed loop: X after 20 transforms within 1e-5, every stress within 1e-6;
+    no centring of the iterates (the oracle's definition), and the persistent and
+    per-pass launches agree bit for bit."""
+    import torch
+    prob = synthetic.make_insample(0, n=n, m=m, d=d, seed=91 + n)
+    ref = _oracle(prob.deltas, prob.W, prob.X0, 20, relax=relax)
+    dev = [fj.to_device_delta(D) for D in prob.deltas]
+    outs = []
+    for prof in (0, 1):
+        X = torch.as_tensor(np.asarray(prob.X0, np.float32)).cuda()
+        r = fj.embed(dev, prob.W, X, max_iter=20, profile=prof, relax=relax)
+        outs.append((X.cpu().numpy(), r))
+    X, r = outs[0]
+    assert r.status == 0 and r.iters == 20
+    assert _rel(X, ref.X) <= X_TOL
+    np.testing.assert_allclose(r.history, ref.stress, rtol=S_TOL)
+    np.testing.assert_array_equal(outs[1][0], X)
+    np.testing.assert_array_equal(outs[1][1].history, r.history)
+
+
+def test_relaxed_updates_reach_tolerance_in_fewer_transforms(fj):
+    """Over-relaxation shortens the run to a relative stress change of 1e-6 on the m=2,
+    n=400, d=2 generator, and the final stress is no worse than the plain run's (within
+    1e-3 relative): what the relaxed updates are for."""
+    import torch
+    prob = synthetic.make_insample(0, n=400, seed=97)
+    dev = [fj.to_device_delta(D) for D in prob.deltas]
+    runs = {}
+    for relax in (1.0, 1.9):
+        X = torch.as_tensor(np.asarray(prob.X0, np.float32)).cuda()
+        runs[relax] = fj.embed(dev, prob.W, X, max_iter=3000, tol=1e-6, tol_mode="relative", relax=relax)
+    assert runs[1.9].iters < runs[1.0].iters
+    assert runs[1.9].stress <= runs[1.0].stress * (1 + 1e-3)
+    st = np.asarray(runs[1.9].history)
+    assert np.all(np.diff(st) <= 1e-6 * st[:-1])       # float32 rounding aside, no increase

@@ -57,11 +57,11 @@ class _Call:
         self.lib.fjofc_embed.restype = ctypes.c_int
 
     def embed(self, m=2, n=8, d=2, ld=8, dtype=0, W=None, ptr=4096, X=8192, max_iter=5, tol_mode=1,
-              scales=None):
+              scales=None, relax=0.0):
         fj = self.fj
         W = np.array([[1.0, 0.5], [0.5, 1.0]]) if W is None else np.asarray(W, dtype=np.float64)
         ptrs = (ctypes.c_void_p * max(m, 1))(*([ptr] * max(m, 1)))
-        opts = fj._Opts(max_iter, -1.0, tol_mode)
+        opts = fj._Opts(max_iter, -1.0, tol_mode, 0, relax)
         sc = None if scales is None else (ctypes.c_float * m)(*scales)
         return self.lib.fjofc_embed(ctypes.c_int32(m), ctypes.c_int64(n), ctypes.c_int32(d), ptrs,
                                     ctypes.c_int64(ld), ctypes.c_int32(dtype), sc,
@@ -93,6 +93,9 @@ def call():
     (dict(W=[[np.nan, 0.5], [0.5, 1.0]]), -1),
     (dict(scales=[1.0, 0.0]), -1),
     (dict(dtype=1, n=8, ld=12), -1),        # f16 rows of 24 bytes
+    (dict(relax=2.5), -1),                  # relaxed updates only up to 2
+    (dict(relax=-0.5), -1),
+    (dict(relax=float("nan")), -1),
 ])
 def test_invalid_arguments_rejected_before_cuda(call, kw, code):
     assert call.embed(**kw) == code
