@@ -482,6 +482,73 @@ def run_relaxed(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_paper(args, rank, world, local_rank):
+    """The paper's run-time experiment (Sec. 4.3), synthetic from its own generator
+    (Y ~ N((5,5), I_2), modality i = Y + U(-z/50, z/50) jitter, Delta_i its distances;
+    Eq. W with w = 0.5, d = 2, X0 seeded N(0, I)): time per Guttman transform of
+    fjofc_embed (100 transforms per call) for m = 2..6 at n = 400 and for n = 200..1000
+    at m = 3, beside the float64 dense Algorithm 1 of the oracle (JOFC with an explicit
+    pseudoinverse, timed per transform after its pinv, on the host cores; 3 transforms).
+    value = GPU transforms per second at m = 6, n = 400."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1502_03391_gb300 as fj
+    import synthetic
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
+    rows = []
+    cases = [(m, 400) for m in (2, 3, 4, 5, 6)] + [(3, n) for n in (200, 600, 800, 1000)]
+    with ClockSampler(local_rank) as clk:
+        for m, n in cases:
+            deltas = synthetic.paper_jitter_modalities(n=n, m=m, dim=2, seed=4300 + 10 * m + n)
+            W = synthetic.weights_matrix(m, 1.0, 0.5)
+            X0n = np.random.default_rng(4400 + m + n).standard_normal((m * n, 2))
+            dev = [fj.to_device_delta(D) for D in deltas]
+            X0 = torch.as_tensor(np.asarray(X0n, np.float32), device=device)
+            X = torch.empty_like(X0)
+
+            def step():
+                X.copy_(X0)
+                return fj.embed(dev, W, X, max_iter=100, history=False, profile=2)
+            for _ in range(args.warmup):
+                step()
+            ms, outs = _timed(torch, stream, step, args.steps, flush)
+            us_gpu = 1e3 * sum(ms) / sum(r.iters for r in outs)
+            us_kernel = 1e3 * sum(r.ms_pass for r in outs) / sum(r.passes for r in outs)
+            row = {"m": m, "n": n, "gpu_us_per_transform": us_gpu, "kernel_us_per_pass": us_kernel}
+            if rank == 0 and not args.no_cpu_baseline:
+                from oracle import fjofc_oracle as O
+                Wo = O.omnibus_weights(W, n)
+                Do = O.omnibus_dissimilarity(deltas)
+                Lp = O.pseudoinverse(O.laplacian(Wo))
+                Xc = X0n.copy()
+                t0 = time.perf_counter()
+                for _ in range(3):
+                    Xc = O.guttman_step(Xc, Lp, Wo, Do)
+                row["oracle_ms_per_transform"] = (time.perf_counter() - t0) / 3 * 1e3
+                row["oracle_over_gpu"] = row["oracle_ms_per_transform"] * 1e3 / us_gpu
+            rows.append(row)
+    if rank == 0:
+        top = [r for r in rows if r["m"] == 6][0]
+        line = {
+            "metric": "Guttman transforms/s (paper-shaped workload, m=6, n=400, d=2)",
+            "value": 1e6 / top["gpu_us_per_transform"], "unit": "transforms/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": top["gpu_us_per_transform"] * 100 / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (the paper's Sec. 4.3 generator)",
+            "config": {"workload": "paper-4.3: m = 2..6 at n = 400 and n = 200..1000 at m = 3, d = 2, Eq. W "
+                                   "w = 0.5, 100 transforms per call", "cpu_cores": os.cpu_count()},
+            "cases": rows, "clocks": clk.summary(),
+            "paper_context": "the paper's per-iteration JOFC/fJOFC ratios (serial CPU): 2.86-10.71 for m = 2..6, "
+                             "2.10-12.63 for n = 200..1000",
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_oos(args, rank, world, local_rank):
     """Out-of-sample batch: the m=2, n=10000, d=5 in-sample configuration (200 transforms or
     relative change < 1e-7), then 100000 new objects (float32 dissimilarities to all
@@ -781,14 +848,15 @@ def main():
     ap.add_argument("--k", type=int, default=0, help="oos / learned workloads: test objects (default 100000)")
     ap.add_argument("--problems", type=int, default=0, help="batched workload: problems (default 256)")
     ap.add_argument("--workload", default="insample",
-                    choices=["insample", "precision", "oos", "learned", "batched", "relaxed"],
+                    choices=["insample", "precision", "oos", "learned", "batched", "relaxed", "paper"],
                     help="insample: the headline line (m=2, n=5000, d=3); precision: m=3, n=20000, d=10 "
                          "with float16/bfloat16 Delta vs float32; oos: 100000 out-of-sample objects "
                          "against the m=2, n=10000, d=5 configuration; learned: the same objects from the "
                          "trained network's warm start vs the standard start; batched: 256 problems "
                          "(n ~ U[100,4000], m in {2,3}, d in {2,3,5}) in one plan vs one call each; relaxed: "
                          "the headline workload to a relative stress change of 1e-6 with relaxed updates "
-                         "(relax 1.9, 2) vs the plain transform")
+                         "(relax 1.9, 2) vs the plain transform; paper: the paper's Sec. 4.3 run-time "
+                         "experiment (m = 2..6, n = 200..1000) beside the dense float64 Algorithm 1")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -805,6 +873,8 @@ def main():
         run_batched(args, rank, world, local_rank)
     elif args.workload == "relaxed":
         run_relaxed(args, rank, world, local_rank)
+    elif args.workload == "paper":
+        run_paper(args, rank, world, local_rank)
     else:
         run_gpu(args, rank, world, local_rank)
 

@@ -16,7 +16,10 @@ eye:
 * Algorithm 1's loop ``X_t = L^+ B(X_{t-1}) X_{t-1}`` with ``L^+`` the
   Moore-Penrose pseudoinverse from ``numpy.linalg.pinv`` (SVD, rank-revealing cutoff),
 * the out-of-sample Guttman transform of Eq. (joosupdate) with the dense blocks
-  ``L_12, L_22, B_12, B_22`` of Sec. 3 and ``numpy.linalg.inv(L_22)``.
+  ``L_12, L_22, B_12, B_22`` of Sec. 3 and ``numpy.linalg.inv(L_22)``,
+* Algorithm 2's initialisation: classical MDS (``numpy.linalg.eigh`` of the
+  double-centred squared dissimilarities) and the orthogonal Procrustes fit
+  (``numpy.linalg.svd``).
 
 Readings of the paper taken here (each is listed in the design doc):
 
@@ -32,6 +35,10 @@ Readings of the paper taken here (each is listed in the design doc):
   modality j has weight ``w_jj`` to the in-sample points of modality j and weight
   ``w_ij`` to the new point of modality i.  For Eq. (W) this is the paper's W^(o).
 * Several new objects are independent problems (Sec. 3, last paragraph).
+* Initialisation (Algorithm 2, lines 1-7): the Procrustes fit of ``xi_i`` onto
+  ``xi_0`` is ``xi_i V U'`` for ``xi_0' xi_i = U S V'`` (the printed ``xi_i U V'`` is
+  the inverse rotation); cMDS eigenvectors get a sign convention (largest-magnitude
+  entry positive).
 * Relaxed updates (the Conclusion's suggested acceleration): ``X_t = X_{t-1} + r
   (L^+ B(X_{t-1}) X_{t-1} - X_{t-1})`` with ``0 <= r <= 2``, applied to the iterates as
   they are (no centring step: the plain transform's output is centred by itself, a
@@ -233,6 +240,56 @@ def jofc_embed(deltas: Sequence[np.ndarray], Wm: np.ndarray, X0: np.ndarray, max
         if not continue_iterating(hist[-2], hist[-1], tol, tol_mode, n_pairs):
             break
     return EmbedResult(X=X, iters=t, stress=hist, iterates=its)
+
+
+# ---------------------------------------------------------------------------
+# Initialisation (Algorithm 2, lines 1-7)
+# ---------------------------------------------------------------------------
+
+def cmds(D: np.ndarray, d: int) -> np.ndarray:
+    """Classical MDS (Torgerson; Algorithm 1, step 1) of an n x n dissimilarity matrix:
+    the double-centred matrix ``-1/2 J D^2 J`` (``J = I - 11'/n``, ``D^2`` elementwise)
+    by ``numpy.linalg.eigh``, its d largest eigenpairs, coordinates ``v_k sqrt(max(l_k,
+    0))``.  Sign convention (eigenvectors are defined up to sign): in every column the
+    entry of largest magnitude is positive."""
+    D = np.asarray(D, dtype=np.float64)
+    n = D.shape[0]
+    J = np.eye(n) - np.ones((n, n)) / n
+    S = -0.5 * J @ (D * D) @ J
+    lam, V = np.linalg.eigh(S)
+    top = np.argsort(lam)[::-1][:d]
+    xi = V[:, top] * np.sqrt(np.maximum(lam[top], 0.0))
+    for k in range(xi.shape[1]):
+        if xi[np.argmax(np.abs(xi[:, k])), k] < 0:
+            xi[:, k] = -xi[:, k]
+    return xi
+
+
+def procrustes_fit(xi: np.ndarray, xi0: np.ndarray) -> np.ndarray:
+    """The orthogonal Procrustes fit of ``xi`` onto ``xi0`` (Algorithm 2, line 4): the
+    rotation R (orthogonal d x d) minimising ||xi R - xi0||_F.  With ``T = xi0' xi =
+    U S V'`` this is ``R = V U'``; the printed ``xi U V'`` is the inverse rotation (read
+    as a transposition slip: the text asks for the fit of xi onto xi0)."""
+    T = np.asarray(xi0, dtype=np.float64).T @ np.asarray(xi, dtype=np.float64)
+    U, _, Vt = np.linalg.svd(T)
+    return xi @ (Vt.T @ U.T)
+
+
+def initial_configuration(deltas: Sequence[np.ndarray], d: int) -> np.ndarray:
+    """Algorithm 2, lines 1-7: ``xi_0`` = cMDS of the average dissimilarity ``sum_i
+    Delta_i / m``, centred; for every modality ``xi_i`` = cMDS of ``Delta_i``, centred,
+    and ``X^(i)_(0)`` its Procrustes fit onto ``xi_0``; the rows stacked modality-major
+    into the (m n) x d ``X_(0)``."""
+    m = len(deltas)
+    avg = sum(np.asarray(D, dtype=np.float64) for D in deltas) / m
+    xi0 = cmds(avg, d)
+    xi0 = xi0 - xi0.mean(0)
+    blocks = []
+    for D in deltas:
+        xi = cmds(D, d)
+        xi = xi - xi.mean(0)
+        blocks.append(procrustes_fit(xi, xi0))
+    return np.vstack(blocks)
 
 
 # ---------------------------------------------------------------------------

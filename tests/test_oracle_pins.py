@@ -305,6 +305,55 @@ def test_relaxed_loop_descends_keeps_fixed_points_and_r0_stays():
     np.testing.assert_allclose(O.relaxed_step(X, _lp(Wm2, n), W, D, 1.7), X, atol=1e-12)
 
 
+def test_cmds_recovers_a_euclidean_configuration():
+    """Torgerson's theorem: cMDS of the distance matrix of a centred Y in R^d returns Y up
+    to an orthogonal transform (equal Gram matrices), centred, with the eigenvalues the
+    squared singular values of Y; cMDS to fewer dimensions keeps the d' leading ones."""
+    rng = np.random.default_rng(5)
+    n, d = 30, 3
+    Y = rng.standard_normal((n, d)) @ np.diag([3.0, 2.0, 1.0])
+    Y -= Y.mean(0)
+    D = np.sqrt(((Y[:, None] - Y[None]) ** 2).sum(-1))
+    xi = O.cmds(D, d)
+    np.testing.assert_allclose(xi @ xi.T, Y @ Y.T, atol=1e-9)
+    np.testing.assert_allclose(xi.mean(0), 0, atol=1e-12)
+    np.testing.assert_allclose(np.sort((xi ** 2).sum(0))[::-1], np.linalg.svd(Y, compute_uv=False) ** 2, rtol=1e-9)
+    U, sv, Vt = np.linalg.svd(Y, full_matrices=False)
+    np.testing.assert_allclose(np.abs(O.cmds(D, 1)[:, 0]), np.abs(U[:, 0] * sv[0]), atol=1e-9)
+    k = np.argmax(np.abs(xi), axis=0)
+    assert np.all(xi[k, np.arange(d)] > 0)
+
+
+def test_procrustes_fit_undoes_a_rotation():
+    """The fit of xi = xi0 Q (Q orthogonal, a reflection included) onto xi0 is xi0 itself;
+    the printed xi U V' (the inverse rotation) would give xi0 Q^2."""
+    rng = np.random.default_rng(6)
+    xi0 = rng.standard_normal((25, 3))
+    for Q in (np.linalg.qr(rng.standard_normal((3, 3)))[0], np.diag([1.0, -1.0, 1.0])):
+        xi = xi0 @ Q
+        np.testing.assert_allclose(O.procrustes_fit(xi, xi0), xi0, atol=1e-10)
+    th = 0.7
+    Q = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    xi0 = rng.standard_normal((20, 2))
+    U, _, Vt = np.linalg.svd(xi0.T @ (xi0 @ Q))
+    assert np.linalg.norm((xi0 @ Q) @ (U @ Vt) - xi0) > 0.1      # the printed form does not fit
+
+
+def test_initial_configuration_of_identical_modalities():
+    """With Delta_i = D(Y) for every i the initialisation puts every modality on the same
+    configuration (commensurability 0) that cMDS gives for D(Y), and it is centred."""
+    rng = np.random.default_rng(7)
+    n, m, d = 18, 3, 2
+    Y = rng.standard_normal((n, d)) * np.array([2.0, 1.0])
+    Y -= Y.mean(0)
+    D = np.sqrt(((Y[:, None] - Y[None]) ** 2).sum(-1))
+    X = O.initial_configuration([D] * m, d)
+    for i in range(m):
+        np.testing.assert_allclose(X[i * n:(i + 1) * n], X[:n], atol=1e-10)
+    np.testing.assert_allclose(X[:n] @ X[:n].T, Y @ Y.T, atol=1e-9)
+    np.testing.assert_allclose(X.reshape(m, n, d).mean(1), 0, atol=1e-12)
+
+
 def test_exact_configuration_fixed_point_and_recovery():
     """When every Delta_i holds the distances of one configuration Y, X = [Y; Y] has
     zero stress and is a fixed point; from a perturbed start stress falls to ~0."""
