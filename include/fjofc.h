@@ -138,6 +138,39 @@ int fjofc_embed(int32_t m, int64_t n, int32_t d,
                 float* X, const fjofc_opts* opts, fjofc_result* res, void* cuda_stream);
 
 /*
+ * fjofc_init_cmds -- Algorithm 2's initial configuration X_(0) (lines 1-7): xi_0 = classical
+ * MDS of the average dissimilarity (sum_i Delta_i)/m, centred; for every modality i,
+ * xi_i = classical MDS of Delta_i, centred, and X^(i)_(0) = its orthogonal Procrustes fit
+ * onto xi_0 (the rotation R minimising ||xi_i R - xi_0||_F; with xi_0' xi_i = U S V',
+ * R = V U' -- the printed xi_i U V' is the inverse rotation).  Classical MDS (Torgerson,
+ * Algorithm 1 step 1): the d leading eigenpairs of -1/2 J D2 J (D2 the elementwise squared
+ * dissimilarities), coordinates v_k sqrt(max(lambda_k, 0)), each column's entry of largest
+ * magnitude made positive.  Eigenpairs by subspace iteration on the device (one pass over
+ * Delta per iteration, p = min(2d + 4, n) vectors) until the d leading Ritz values change
+ * by less than opts->tol (relative).
+ *
+ *  m, n, d, delta, ld, delta_dtype, delta_scale : as in fjofc_embed.
+ *  X          : DEVICE float32 (m*n) x d, 16-byte aligned; out: X_(0), rows modality-major.
+ *  opts       : host, may be NULL (max_iter 200, tol 1e-6); max_iter <= 0 and tol <= 0
+ *               select those defaults; reserved must be zero.
+ *  iters_out  : host array of m + 1 ints or NULL: subspace iterations of the average's and
+ *               of every modality's eigenproblem.
+ *  cuda_stream: cudaStream_t.  Synchronises the stream (the small eigenproblems are solved
+ *               on the host between device passes); allocates its scratch with the
+ *               stream-ordered allocator.
+ * Errors as fjofc_embed (FJOFC_ERR_ARG for invalid arguments).
+ */
+typedef struct fjofc_init_opts {
+    int32_t max_iter;     /* subspace iterations per eigenproblem (<= 0: 200) */
+    double  tol;          /* relative change of the d leading Ritz values to stop (<= 0: 1e-6) */
+    int32_t reserved[4];  /* must be zero */
+} fjofc_init_opts;
+
+int fjofc_init_cmds(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t delta_dtype,
+                    const float* delta_scale, float* X, const fjofc_init_opts* opts, int32_t* iters_out,
+                    void* cuda_stream);
+
+/*
  * fjofc_stress -- the raw stress sigma(X) of Eq. (stress) for a configuration X, by the
  * same all-pairs pass (fidelity over the upper triangle of each Delta_i, Remark
  * faststress) plus the commensurability term.  Arguments as in fjofc_embed; X is

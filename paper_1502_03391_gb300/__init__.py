@@ -37,7 +37,7 @@ MAX_M, MAX_D = 8, 16
 EXPORTS = ("fjofc_embed", "fjofc_embed_noalloc", "fjofc_stress", "fjofc_oos", "fjofc_strerror", "fjofc_version",
            "fjofc_mlp_param_count", "fjofc_mlp_init", "fjofc_mlp_features", "fjofc_mlp_forward", "fjofc_mlp_gradient",
            "fjofc_mlp_train", "fjofc_mlp_broadcast", "fjofc_mlp_select", "fjofc_plan_create", "fjofc_plan_run",
-           "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy", "fjofc_plan_autotune")
+           "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy", "fjofc_plan_autotune", "fjofc_init_cmds")
 
 
 class FjofcError(RuntimeError):
@@ -74,6 +74,10 @@ class _TuneResult(ctypes.Structure):
                 ("probe_ms", ctypes.c_float), ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
+class _InitOpts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("reserved", ctypes.c_int32 * 4)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"fJOFC CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
@@ -101,6 +105,9 @@ def _load():
     lib.fjofc_plan_autotune.restype = ctypes.c_int
     lib.fjofc_plan_destroy.argtypes = [vp]
     lib.fjofc_plan_destroy.restype = None
+    lib.fjofc_init_cmds.argtypes = [i32, i64, i32, ctypes.POINTER(vp), i64, i32, ctypes.POINTER(ctypes.c_float),
+                                    vp, ctypes.POINTER(_InitOpts), ctypes.POINTER(i32), vp]
+    lib.fjofc_init_cmds.restype = ctypes.c_int
     lib.fjofc_strerror.argtypes = [ctypes.c_int]
     lib.fjofc_strerror.restype = ctypes.c_char_p
     lib.fjofc_version.argtypes = []
@@ -271,6 +278,29 @@ def stress(deltas: Sequence, weights, X, delta_scale=None, stream=None) -> float
                            ctypes.byref(out), _stream_handle(stream, X.device))
     _check(st)
     return out.value
+
+
+def init_cmds(deltas: Sequence, d: int, X=None, max_iter: int = 0, tol: float = 0.0, delta_scale=None,
+              stream=None):
+    """Algorithm 2's initial configuration X_(0) (classical MDS of the average and of
+    every Delta_i, Procrustes onto the average's); see ``fjofc_init_cmds``.  ``X``: a
+    contiguous float32 (m*n, d) CUDA tensor to write (allocated if None).  Returns
+    ``(X, iters)`` with the subspace iterations of the m + 1 eigenproblems."""
+    torch = _torch()
+    m = len(deltas)
+    n = int(deltas[0].shape[0])
+    ld, code = _delta_layout(deltas, n)
+    if X is None:
+        X = torch.empty((m * n, d), dtype=torch.float32, device=deltas[0].device)
+    if X.dtype != torch.float32 or not X.is_contiguous() or X.dim() != 2 or X.shape != (m * n, d):
+        raise ValueError("X must be a contiguous float32 (m*n, d) CUDA tensor")
+    ptrs = (ctypes.c_void_p * m)(*[D.data_ptr() for D in deltas])
+    opts = _InitOpts(int(max_iter), float(tol))
+    iters = (ctypes.c_int32 * (m + 1))()
+    st = _lib.fjofc_init_cmds(m, n, d, ptrs, ld, code, _scales(delta_scale, m), ctypes.c_void_p(X.data_ptr()),
+                              ctypes.byref(opts), iters, _stream_handle(stream, X.device))
+    _check(st)
+    return X, [int(v) for v in iters]
 
 
 @dataclasses.dataclass

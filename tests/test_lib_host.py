@@ -33,7 +33,7 @@ def test_header_declares_expected_api():
                                             "fjofc_mlp_gradient", "fjofc_mlp_train", "fjofc_mlp_broadcast",
                                             "fjofc_mlp_select", "fjofc_plan_create", "fjofc_plan_run",
                                             "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy",
-                                            "fjofc_plan_autotune"])
+                                            "fjofc_plan_autotune", "fjofc_init_cmds"])
 
 
 def test_library_loads_and_exports_every_declared_symbol():
@@ -107,6 +107,25 @@ def test_error_messages_name_the_problem(call):
     assert "16 bytes" in call.fj.strerror(-1)
     assert call.embed(W=[[1.0, 0.5], [0.4, 1.0]]) == -1
     assert "symmetric" in call.fj.strerror(-1)
+
+
+def test_init_argument_validation(call):
+    fj = call.fj
+    lib = call.lib
+    lib.fjofc_init_cmds.restype = ctypes.c_int
+
+    def init(m=2, n=8, d=2, ld=8, ptr=4096, X=8192, max_iter=0, tol=0.0):
+        ptrs = (ctypes.c_void_p * m)(*([ptr] * m))
+        opts = fj._InitOpts(max_iter, tol)
+        return lib.fjofc_init_cmds(ctypes.c_int32(m), ctypes.c_int64(n), ctypes.c_int32(d), ptrs, ctypes.c_int64(ld),
+                                   ctypes.c_int32(0), None, ctypes.c_void_p(X), ctypes.byref(opts), None, None)
+
+    assert init(n=5, ld=6) == -1          # rows not 16-byte aligned
+    assert init(X=0) == -1
+    assert init(X=8196) == -1             # X not 16-byte aligned
+    assert init(d=17) == -6
+    assert init(max_iter=-1) == -1
+    assert init(tol=-1.0) == -1
 
 
 def test_oos_argument_validation(call):
