@@ -74,37 +74,22 @@ __device__ __forceinline__ void bx_sum(const BxTables& tb, const int (&l)[U], co
     for (int u = 0; u < U; ++u) out[u] = acc[u] + csum[u];
 }
 
-// v[0..31] of every lane -> lane o returns the sum over the 32 lanes of v[o]: a
-// reduce-scatter butterfly (partners xor 16, 8, 4, 2, 1; at each level a lane keeps the
-// half of its values that its own lane bit selects), the same pairing tree for every o.
-__device__ __forceinline__ float warp_transpose_sum32(float (&v)[32], int lane) {
-#pragma unroll
-    for (int off = 16, h = 16; off > 0; off >>= 1, h >>= 1) {
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            if (e < h) {
-                const float send = up ? v[e] : v[e + h];
-                const float keep = up ? v[e + h] : v[e];
-                v[e] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-            }
-        }
-    }
-    return v[0];
-}
-
-// Walks whose column partials one warp gathers in a round of bx_sum_wide (two per lane).
-constexpr int kWideWalksPerRound = 64;
+// Walks whose column partials one warp gathers in a round of bx_sum_wide: 8 lanes read
+// one walk's 128-byte row (16 bytes each), so a load instruction covers 4 walks; 12
+// loads per lane in flight.
+constexpr int kWideUnroll = 12;
+constexpr int kWideWalksPerRound = 4 * kWideUnroll;
 
 // (B'_l X_l)_{i,k} for the 32 objects i = 32g + lane of one group (all in row block I):
 // the walk-head row partial and the continuation row partials of each object (lane =
-// object), plus the column partials of the walks of row blocks 0..I gathered with lane =
-// walk: lane L reads the 32 objects' partials of walks L, L+32, ... (one 128-byte row
-// each, 16-byte loads, all of a round in flight), adds them per object, and a transposing
-// butterfly leaves object o's total in lane o.  The order of every sum is fixed.
-// Requires RB >= 32 (a group inside one row block).  Every lane of the warp must call it.
+// object), plus the column partials of the walks of row blocks 0..I: lane (q, s) of the
+// four 8-lane groups q reads objects 4s..4s+3 of walks q, q+4, q+8, ... (fully coalesced
+// 128-byte rows), adds them in walk order, the four groups are combined by a fixed
+// butterfly and a gather leaves object o's total in lane o.  The order of every sum is
+// fixed.  Requires RB >= 32 (a group inside one row block).  Every lane of the warp must
+// call it.
 __device__ __forceinline__ float bx_sum_wide(const BxTables& tb, int l, int k, int g, bool on) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, q = lane >> 3, sq = lane & 7;
     const int d = tb.d, RB = tb.RB, CW = tb.CW, rbs = tb.rb_shift, cws = tb.cw_shift, nRB = tb.nRB;
     const int i0 = g * kGroupObjects, i = i0 + lane;
     const int I = i0 >> rbs;
@@ -115,39 +100,46 @@ __device__ __forceinline__ float bx_sum_wide(const BxTables& tb, int l, int k, i
 #pragma unroll 1
         for (int b = cr.x; b < cr.y; ++b) head += __ldcg(tb.rowcont + (int64_t(b) * d + k) * RB + (i & (RB - 1)));
     }
-    float acc[32];
-#pragma unroll
-    for (int e = 0; e < 32; ++e) acc[e] = 0.f;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     const float* cp = tb.colpart + int64_t(l) * tb.Tm * d * CW;
     const int nJ = on ? I + 1 : 0;
 #pragma unroll 1
     for (int J0 = 0; J0 < nJ; J0 += kWideWalksPerRound) {
-        float4 v[2][8];
+        float4 v[kWideUnroll];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int J = J0 + h * 32 + lane;
+        for (int u = 0; u < kWideUnroll; ++u) {
+            const int J = J0 + 4 * u + q;
             if (J < nJ) {
                 const int rel0 = i0 - (J << rbs);
-                const float4* src = reinterpret_cast<const float4*>(
-                    cp + ((__ldg(tb.cbase + J) + (rel0 >> cws)) * d + k) * CW + (rel0 & (CW - 1)));
-#pragma unroll
-                for (int q = 0; q < 8; ++q) v[h][q] = __ldcg(src + q);
+                v[u] = __ldcg(reinterpret_cast<const float4*>(
+                                  cp + ((__ldg(tb.cbase + J) + (rel0 >> cws)) * d + k) * CW + (rel0 & (CW - 1))) +
+                              sq);
             } else {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) v[h][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                acc[4 * q] += v[h][q].x;
-                acc[4 * q + 1] += v[h][q].y;
-                acc[4 * q + 2] += v[h][q].z;
-                acc[4 * q + 3] += v[h][q].w;
-            }
+        for (int u = 0; u < kWideUnroll; ++u) {
+            acc.x += v[u].x;
+            acc.y += v[u].y;
+            acc.z += v[u].z;
+            acc.w += v[u].w;
+        }
     }
-    return head + warp_transpose_sum32(acc, lane);
+    // combine the four walk groups (partners xor 8, then xor 16; every lane gets the sum)
+#pragma unroll
+    for (int o = 8; o <= 16; o <<= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+        acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+    }
+    // object o = lane sits in component o & 3 of lane o >> 2
+    const int src = lane >> 2, comp = lane & 3;
+    const float cx = __shfl_sync(0xffffffffu, acc.x, src), cy = __shfl_sync(0xffffffffu, acc.y, src);
+    const float cz = __shfl_sync(0xffffffffu, acc.z, src), cw = __shfl_sync(0xffffffffu, acc.w, src);
+    const float col = comp == 0 ? cx : (comp == 1 ? cy : (comp == 2 ? cz : cw));
+    return head + col;
 }
 
 // What phase B needs besides the partial tables.
@@ -192,9 +184,9 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int u0, int u1, int
         float* s_bx = s;                                   // [nc][m][32]
         float* s_xp = s + nc * m * kGroupObjects;          // [nc][m][32]
         // 1. (unit, l) pairs: one per warp per round, column partials gathered by walk
-        //    (bx_sum_wide) when a round or two covers every walk, else two per warp per
-        //    round with lane = object (bx_sum)
-        if (a.tb.RB >= kGroupObjects && a.tb.nRB <= 2 * kWideWalksPerRound) {
+        //    rows (bx_sum_wide) when up to three rounds cover every walk, else two per
+        //    warp per round with lane = object (bx_sum)
+        if (a.tb.RB >= kGroupObjects && a.tb.nRB <= 3 * kWideWalksPerRound) {
 #pragma unroll 1
             for (int w = warp; w < nc * m; w += nwarps) {
                 const int ui = w / m, l = w - ui * m;
