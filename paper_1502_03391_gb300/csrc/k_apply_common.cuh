@@ -79,6 +79,11 @@ __device__ __forceinline__ void bx_sum(const BxTables& tb, const int (&l)[U], co
 // loads per lane in flight.
 constexpr int kWideUnroll = 12;
 constexpr int kWideWalksPerRound = 4 * kWideUnroll;
+// largest number of walks (row blocks) for which phase B gathers by rows (beyond it: lane
+// = object, for any walk count the row gather measured faster)
+#ifndef FJOFC_WIDE_MAX_WALKS
+#define FJOFC_WIDE_MAX_WALKS (1 << 30)
+#endif
 
 // (B'_l X_l)_{i,k} for the 32 objects i = 32g + lane of one group (all in row block I):
 // the walk-head row partial and the continuation row partials of each object (lane =
@@ -184,9 +189,9 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int u0, int u1, int
         float* s_bx = s;                                   // [nc][m][32]
         float* s_xp = s + nc * m * kGroupObjects;          // [nc][m][32]
         // 1. (unit, l) pairs: one per warp per round, column partials gathered by walk
-        //    rows (bx_sum_wide) when up to three rounds cover every walk, else two per
-        //    warp per round with lane = object (bx_sum)
-        if (a.tb.RB >= kGroupObjects && a.tb.nRB <= 3 * kWideWalksPerRound) {
+        //    rows (bx_sum_wide; RB >= 32), else two per warp per round with lane = object
+        //    (bx_sum)
+        if (a.tb.RB >= kGroupObjects && a.tb.nRB <= FJOFC_WIDE_MAX_WALKS) {
 #pragma unroll 1
             for (int w = warp; w < nc * m; w += nwarps) {
                 const int ui = w / m, l = w - ui * m;
@@ -272,7 +277,8 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int u0, int u1, int
                 const FF w{__shfl_xor_sync(0xffffffffu, cw.hi, o), __shfl_xor_sync(0xffffffffu, cw.lo, o)};
                 cw = ((lane & o) == 0) ? ff_add(cw, w) : ff_add(w, cw);
 #pragma unroll
-                for (int j = 0; j < FJOFC_MAX_M; ++j) cs[j] += __shfl_xor_sync(0xffffffffu, cs[j], o);
+                for (int j = 0; j < FJOFC_MAX_M; ++j)
+                    if (j < m) cs[j] += __shfl_xor_sync(0xffffffffu, cs[j], o);     // m is warp-uniform
             }
             if (lane == 0) {
                 a.bpart[int64_t(md + k) * a.ngroups + g] = make_float2(cw.hi, cw.lo);

@@ -31,7 +31,11 @@ namespace fjofc {
 template <int D> struct K3Cfg;
 #define FJOFC_K3CFG(D_, R_) template <> struct K3Cfg<D_> { static constexpr int R = R_; };
 FJOFC_K3CFG(1, 8) FJOFC_K3CFG(2, 8) FJOFC_K3CFG(3, 8) FJOFC_K3CFG(4, 8)
-FJOFC_K3CFG(5, 4) FJOFC_K3CFG(6, 4) FJOFC_K3CFG(7, 4) FJOFC_K3CFG(8, 4)
+#ifndef FJOFC_K3_R_D5_8
+#define FJOFC_K3_R_D5_8 8
+#endif
+FJOFC_K3CFG(5, FJOFC_K3_R_D5_8) FJOFC_K3CFG(6, FJOFC_K3_R_D5_8) FJOFC_K3CFG(7, FJOFC_K3_R_D5_8)
+FJOFC_K3CFG(8, FJOFC_K3_R_D5_8)
 FJOFC_K3CFG(9, 2) FJOFC_K3CFG(10, 2) FJOFC_K3CFG(11, 2) FJOFC_K3CFG(12, 2)
 FJOFC_K3CFG(13, 2) FJOFC_K3CFG(14, 2) FJOFC_K3CFG(15, 2) FJOFC_K3CFG(16, 2)
 #undef FJOFC_K3CFG
