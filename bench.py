@@ -37,6 +37,19 @@ WORKLOAD = dict(k=1, m=2, n=5000, d=3, max_iter=200, tol=1e-7, tol_mode="relativ
 CPU_SAMPLE = dict(n=1000, iters=30)
 
 
+def aggregate_ranks(dist, device, elapsed_ms, work):
+    """Whole-job figures of independent replicas: the slowest rank's time (max over
+    ranks) and the work of all ranks (sum).  ``dist`` None: one process."""
+    if dist is None:
+        return float(elapsed_ms), float(work)
+    import torch
+    t = torch.tensor([float(elapsed_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(work)], device=device, dtype=torch.float64)
+    dist.all_reduce(w)
+    return float(t.item()), float(w.item())
+
+
 def pairs_per_transform(m, n):
     return m * n * (n - 1) // 2 + (m * (m - 1) // 2) * n
 
@@ -231,16 +244,7 @@ def run_gpu(args, rank, world, local_rank):
             passes += r.passes
             launches += r.launches
         barrier()
-    elapsed_ms = sum(a.elapsed_time(b) for a, b in step_ev)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-        it = torch.tensor([iters], device=device, dtype=torch.float64)
-        dist.all_reduce(it)
-        total_iters = float(it.item())
-    else:
-        total_iters = float(iters)
+    elapsed_ms, total_iters = aggregate_ranks(dist, device, sum(a.elapsed_time(b) for a, b in step_ev), iters)
     ppt = pairs_per_transform(m, n)
     value = ppt * total_iters / (elapsed_ms / 1e3)
 
@@ -289,14 +293,7 @@ def run_gpu(args, rank, world, local_rank):
             it2 += r.iters
         e1.record(stream)
         barrier()
-        ems = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ems], device=device)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-            itt = torch.tensor([it2], device=device, dtype=torch.float64)
-            dist.all_reduce(itt)
-            it2 = float(itt.item())
+        ems, it2 = aggregate_ranks(dist, device, e0.elapsed_time(e1), it2)
         h2d = sum(dd.numel() * dd.element_size() for dd in hostD) + hostX0.numel() * 4
         e2e = {"value": ppt * it2 / (ems / 1e3), "unit": "pair-updates/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(hostX.numel() * 4 + 8 + 4)}
