@@ -605,7 +605,8 @@ extern "C" int fjofc_init_cmds(int32_t m, int64_t n, int32_t d, const void* cons
     if (n > (int64_t(1) << 24)) { set_message("n too large for the initialisation"); return FJOFC_ERR_UNSUPPORTED; }
     const int nn = int(n);
     const int p = int(std::min<int64_t>(2 * int64_t(d) + 4, n));
-    const int P = p <= 8 ? 8 : (p <= 16 ? 16 : 32);
+    const int pw = std::max(p, int(d));                 // the width holds d columns even when n < d
+    const int P = pw <= 8 ? 8 : (pw <= 16 ? 16 : 32);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const int nb = (nn + kRedRows - 1) / kRedRows;
     const size_t nP = size_t(nn) * P, nd = size_t(nn) * d;

@@ -37,7 +37,8 @@ def _f32(a):
     return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
-@pytest.mark.parametrize("m,n,d,latent", [(2, 200, 2, 5), (3, 150, 3, 5), (2, 300, 5, 10), (2, 1000, 3, 10)])
+@pytest.mark.parametrize("m,n,d,latent", [(2, 200, 2, 5), (3, 150, 3, 5), (2, 300, 5, 10), (2, 1000, 3, 10),
+                                          (2, 9, 3, 5)])
 def test_init_matches_oracle(fj, m, n, d, latent):
     prob = synthetic.make_insample(0, n=n, m=m, d=d, latent=latent, seed=300 + n + m)
     dev = [fj.to_device_delta(D) for D in prob.deltas]
