@@ -138,12 +138,12 @@ int fjofc_embed(int32_t m, int64_t n, int32_t d,
                 float* X, const fjofc_opts* opts, fjofc_result* res, void* cuda_stream);
 
 /*
- * fjofc_init_cmds -- Algorithm 2's initial configuration X_(0) (lines 1-7): xi_0 = classical
+ * fjofc_init_cmds -- Algorithm 2's initial configuration X_(0): xi_0 = classical
  * MDS of the average dissimilarity (sum_i Delta_i)/m, centred; for every modality i,
  * xi_i = classical MDS of Delta_i, centred, and X^(i)_(0) = its orthogonal Procrustes fit
  * onto xi_0 (the rotation R minimising ||xi_i R - xi_0||_F; with xi_0' xi_i = U S V',
- * R = V U' -- the printed xi_i U V' is the inverse rotation).  Classical MDS (Torgerson,
- * Algorithm 1 step 1): the d leading eigenpairs of -1/2 J D2 J (D2 the elementwise squared
+ * R = V U' -- the printed xi_i U V' is the inverse rotation).  Classical MDS (Torgerson, the
+ * initialisation of Algorithm 1): the d leading eigenpairs of -1/2 J D2 J (D2 the elementwise squared
  * dissimilarities), coordinates v_k sqrt(max(lambda_k, 0)), each column's entry of largest
  * magnitude made positive.  Eigenpairs by subspace iteration on the device (one pass over
  * Delta per iteration, p = min(2d + 4, n) vectors) until the d leading Ritz values change

@@ -35,7 +35,7 @@ Readings of the paper taken here (each is listed in the design doc):
   modality j has weight ``w_jj`` to the in-sample points of modality j and weight
   ``w_ij`` to the new point of modality i.  For Eq. (W) this is the paper's W^(o).
 * Several new objects are independent problems (Sec. 3, last paragraph).
-* Initialisation (Algorithm 2, lines 1-7): the Procrustes fit of ``xi_i`` onto
+* Initialisation (Algorithm 2): the Procrustes fit of ``xi_i`` onto
   ``xi_0`` is ``xi_i V U'`` for ``xi_0' xi_i = U S V'`` (the printed ``xi_i U V'`` is
   the inverse rotation); cMDS eigenvectors get a sign convention (largest-magnitude
   entry positive).
@@ -243,11 +243,11 @@ def jofc_embed(deltas: Sequence[np.ndarray], Wm: np.ndarray, X0: np.ndarray, max
 
 
 # ---------------------------------------------------------------------------
-# Initialisation (Algorithm 2, lines 1-7)
+# Initialisation (Algorithm 2)
 # ---------------------------------------------------------------------------
 
 def cmds(D: np.ndarray, d: int) -> np.ndarray:
-    """Classical MDS (Torgerson; Algorithm 1, step 1) of an n x n dissimilarity matrix:
+    """Classical MDS (Torgerson; the initialisation of Algorithm 1) of an n x n dissimilarity matrix:
     the double-centred matrix ``-1/2 J D^2 J`` (``J = I - 11'/n``, ``D^2`` elementwise)
     by ``numpy.linalg.eigh``, its d largest eigenpairs, coordinates ``v_k sqrt(max(l_k,
     0))``.  Sign convention (eigenvectors are defined up to sign): in every column the
@@ -266,8 +266,8 @@ def cmds(D: np.ndarray, d: int) -> np.ndarray:
 
 
 def procrustes_fit(xi: np.ndarray, xi0: np.ndarray) -> np.ndarray:
-    """The orthogonal Procrustes fit of ``xi`` onto ``xi0`` (Algorithm 2, line 4): the
-    rotation R (orthogonal d x d) minimising ||xi R - xi0||_F.  With ``T = xi0' xi =
+    """The orthogonal Procrustes fit of ``xi`` onto ``xi0`` (Algorithm 2's Procrustes
+    step): the rotation R (orthogonal d x d) minimising ||xi R - xi0||_F.  With ``T = xi0' xi =
     U S V'`` this is ``R = V U'``; the printed ``xi U V'`` is the inverse rotation (read
     as a transposition slip: the text asks for the fit of xi onto xi0)."""
     T = np.asarray(xi0, dtype=np.float64).T @ np.asarray(xi, dtype=np.float64)
@@ -276,7 +276,7 @@ def procrustes_fit(xi: np.ndarray, xi0: np.ndarray) -> np.ndarray:
 
 
 def initial_configuration(deltas: Sequence[np.ndarray], d: int) -> np.ndarray:
-    """Algorithm 2, lines 1-7: ``xi_0`` = cMDS of the average dissimilarity ``sum_i
+    """Algorithm 2's initialisation: ``xi_0`` = cMDS of the average dissimilarity ``sum_i
     Delta_i / m``, centred; for every modality ``xi_i`` = cMDS of ``Delta_i``, centred,
     and ``X^(i)_(0)`` its Procrustes fit onto ``xi_0``; the rows stacked modality-major
     into the (m n) x d ``X_(0)``."""

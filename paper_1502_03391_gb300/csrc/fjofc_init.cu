@@ -1,11 +1,11 @@
-// Algorithm 2, lines 1-7: the initial configuration X_(0) of fJOFC.
+// Algorithm 2's initialisation: the initial configuration X_(0) of fJOFC.
 //
 //   xi_0 = cMDS of the average dissimilarity (sum_i Delta_i) / m, centred;
 //   for every modality i: xi_i = cMDS of Delta_i, centred, and X^(i)_(0) its orthogonal
 //   Procrustes fit onto xi_0 (the rotation R minimising ||xi_i R - xi_0||: with
 //   xi_0' xi_i = U S V', R = V U'; the printed xi_i U V' is the inverse rotation).
 //
-// Classical MDS (Torgerson; Algorithm 1, step 1) takes the d leading eigenpairs of
+// Classical MDS (Torgerson; the initialisation of Algorithm 1) takes the d leading eigenpairs of
 // S = -1/2 J D2 J (D2 the elementwise squared dissimilarities, J = I - 11'/n) and
 // returns v_k sqrt(max(lambda_k, 0)), each column's largest-magnitude entry made
 // positive.  The eigenpairs come from subspace iteration with p = 2d + 4 vectors:
