@@ -65,6 +65,16 @@ extern "C" {
 #define FJOFC_TOL_ABS_NORMALIZED 0
 #define FJOFC_TOL_RELATIVE       1
 
+/* Out-of-sample kernel forms (fjofc_opts.oos_form).  STREAMING: every object is one warp
+ * slot of a persistent kernel that streams its dissimilarities from memory every
+ * iteration (any m, n, d; built for many objects).  RESIDENT: one CTA per object with
+ * -X^T and the object's dissimilarities held in shared memory for all its iterations
+ * (d <= 8 and 4 m ceil4(n) (d + 1) <= 200 KB; built for few objects against a small
+ * in-sample set); FJOFC_ERR_UNSUPPORTED when it does not fit. */
+#define FJOFC_OOS_AUTO 0
+#define FJOFC_OOS_STREAMING 1
+#define FJOFC_OOS_RESIDENT 2
+
 typedef struct fjofc_opts {
     int32_t max_iter;     /* maximum number of Guttman transforms (>= 0) */
     double  tol;          /* tolerance of the stopping rule; < 0 = run max_iter transforms */
@@ -81,7 +91,10 @@ typedef struct fjofc_opts {
                              iterates are not centred (the oracle's definition: a relaxed
                              iterate keeps (1 - relax) times the previous one's column
                              means).  FJOFC_ERR_ARG outside [0, 2]. */
-    int32_t reserved[3];  /* must be zero */
+    int32_t oos_form;     /* fjofc_oos only (other entry points ignore it): FJOFC_OOS_*.
+                             FJOFC_OOS_AUTO picks the resident form when it fits and every
+                             object gets its own CTA in one wave, else the streaming form. */
+    int32_t reserved[2];  /* must be zero */
 } fjofc_opts;
 
 typedef struct fjofc_result {

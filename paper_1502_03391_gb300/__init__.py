@@ -48,7 +48,8 @@ class FjofcError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("tol_mode", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("relax", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
+                ("profile", ctypes.c_int32), ("relax", ctypes.c_float), ("oos_form", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class _Result(ctypes.Structure):
@@ -311,13 +312,17 @@ class OOSResult:
     ms: float
 
 
+_OOS_FORMS = {"auto": 0, "streaming": 1, "resident": 2}
+
+
 def oos(X, delta_new, weights, Y, max_iter: int, tol: float = -1.0, tol_mode: str = "relative",
-        iters_out=None, stress_out=None, delta_scale=None, stream=None, check: bool = True) -> OOSResult:
+        iters_out=None, stress_out=None, delta_scale=None, stream=None, check: bool = True,
+        form: str = "auto") -> OOSResult:
     """Out-of-sample embedding of k new objects (in place in ``Y``).  ``X``: float32 CUDA
     (m*n, d) in-sample configuration; ``delta_new``: CUDA (k, m, n) view with unit stride in
     the last dimension, row stride ``ld`` = stride(1), stride(0) = m*ld; ``Y``: contiguous
     float32 CUDA (k, m, d).  ``iters_out`` (int32 [k]) and ``stress_out`` (float64 [k]) are
-    optional CUDA outputs."""
+    optional CUDA outputs.  ``form``: "auto", "streaming" or "resident" (``fjofc_opts.oos_form``)."""
     torch = _torch()
     k, m, n = (int(s) for s in delta_new.shape)
     d = int(X.shape[1])
@@ -331,6 +336,7 @@ def oos(X, delta_new, weights, Y, max_iter: int, tol: float = -1.0, tol_mode: st
     code = _dtype_code(delta_new)
     Wn = _weights(weights, m)
     opts = _Opts(int(max_iter), float(tol), TOL_RELATIVE if tol_mode == "relative" else TOL_ABS_NORMALIZED)
+    opts.oos_form = _OOS_FORMS[form]
     res = _Result()
     ip = ctypes.c_void_p(iters_out.data_ptr()) if iters_out is not None else None
     sp = ctypes.c_void_p(stress_out.data_ptr()) if stress_out is not None else None

@@ -217,6 +217,25 @@ K3Geom k3_geom_dt(int d) {
     return K3Geom{};
 }
 
+template <typename TD>
+cudaError_t k3r_launch_dt(int d, int grid, const K3Params& p, cudaStream_t s) {
+    switch (d) {
+#define C_(D) case D: return k3r_launch_impl<D, TD>(grid, p, s);
+        C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8)
+#undef C_
+    }
+    return cudaErrorInvalidValue;
+}
+template <typename TD>
+int k3r_bps_dt(int d, size_t smem) {
+    switch (d) {
+#define C_(D) case D: return k3r_bps_impl<D, TD>(smem);
+        C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8)
+#undef C_
+    }
+    return 0;
+}
+
 // ------------------------------------------------------------------ device scratch
 // One stream-ordered allocation per call, carved into 256-byte aligned pieces.
 struct Carver {
@@ -446,7 +465,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         if (std::isnan(o.tol)) return arg_error("tol is NaN");
         if (o.profile < 0 || o.profile > 2) return arg_error("profile must be 0, 1 or 2");
         if (!(o.relax >= 0.f && o.relax <= 2.f)) return arg_error("relax must be in [0, 2]");
-        for (int r = 0; r < 3; ++r)
+        for (int r = 0; r < 2; ++r)
             if (o.reserved[r] != 0) return arg_error("opts.reserved must be zero");
     } else {
         o.max_iter = 0;
@@ -649,6 +668,16 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
     if (delta_scale)
         for (int i = 0; i < m; ++i)
             if (!(delta_scale[i] > 0.f) || !std::isfinite(delta_scale[i])) return arg_error("delta_scale must be finite and > 0");
+    if (o.oos_form != FJOFC_OOS_AUTO && o.oos_form != FJOFC_OOS_STREAMING && o.oos_form != FJOFC_OOS_RESIDENT)
+        return arg_error("unknown oos_form");
+    const int nx = int((n + 3) / 4 * 4);
+    const bool resident_fits = k3r_fits(m, nx, d);
+    if (o.oos_form == FJOFC_OOS_RESIDENT && !resident_fits) {
+        snprintf(g_last_msg, sizeof(g_last_msg),
+                 "the resident out-of-sample form needs d <= %d and %zu bytes of shared memory (at most %zu)", kK3rMaxD,
+                 k3r_smem_bytes(m, nx, d), kK3rSmemBudget);
+        return FJOFC_ERR_UNSUPPORTED;
+    }
     int rc;
     if (k > 0) {
         const void* ptrs[1] = {delta_new};
@@ -660,10 +689,22 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
         if (res) { res->status = 0; res->iters = 0; res->stress = 0.0; res->stress_normalized = 0.0; res->ms_total = 0.f; }
         return FJOFC_OK;
     }
+    // the form: resident when asked, or (auto) when it fits and every object gets its own
+    // CTA in one wave; otherwise streaming
+    const size_t r_smem = k3r_smem_bytes(m, nx, d);
+    int r_bps = 0;
+    if (resident_fits && o.oos_form != FJOFC_OOS_STREAMING)
+        r_bps = (dtype == FJOFC_F32) ? k3r_bps_dt<float>(d, r_smem) : (dtype == FJOFC_F16) ? k3r_bps_dt<__half>(d, r_smem)
+                                                                                         : k3r_bps_dt<__nv_bfloat16>(d, r_smem);
+    const bool resident = (o.oos_form == FJOFC_OOS_RESIDENT) ||
+                          (o.oos_form == FJOFC_OOS_AUTO && resident_fits && r_bps > 0 && k <= int64_t(r_bps) * sm_count());
+    if (o.oos_form == FJOFC_OOS_RESIDENT && r_bps < 1) {
+        snprintf(g_last_msg, sizeof(g_last_msg), "the resident out-of-sample form cannot be launched (%zu bytes of shared memory)", r_smem);
+        return FJOFC_ERR_UNSUPPORTED;
+    }
     if ((rc = get_encoder())) return rc;
     const K3Geom g = (dtype == FJOFC_F32) ? k3_geom_dt<float>(d) : (dtype == FJOFC_F16) ? k3_geom_dt<__half>(d)
                                                                                       : k3_geom_dt<__nv_bfloat16>(d);
-    const int nx = int((n + 3) / 4 * 4);
 
     Carver cv;
     const size_t o_xt = cv.take<float>(size_t(m) * d * nx);
@@ -685,8 +726,9 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
     DevStatus* st = reinterpret_cast<DevStatus*>(base + o_st);
 
     // delta_new as a 3-D tensor {n points, m modalities, k objects}, box {CW, 1, 1}
+    // (the streaming form's TMA source)
     CUtensorMap tmap;
-    {
+    if (!resident) {
         const cuuint64_t dims[3] = {cuuint64_t(n), cuuint64_t(m), cuuint64_t(k)};
         const cuuint64_t strides[2] = {cuuint64_t(ld) * dtype_size(dtype), cuuint64_t(ld) * m * dtype_size(dtype)};
         const cuuint32_t box[3] = {cuuint32_t(g.CW), 1u, 1u};
@@ -698,6 +740,8 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
     p.XT = reinterpret_cast<float*>(base + o_xt);
     p.SX = reinterpret_cast<float*>(base + o_sx);
     p.Y = Y;
+    p.delta_new = delta_new;
+    p.ld = ld;
     p.iters_out = iters_out ? iters_out : reinterpret_cast<int32_t*>(base + o_it);
     p.stress_out = stress_out ? stress_out : reinterpret_cast<double*>(base + o_sig);
     p.next_block = reinterpret_cast<unsigned long long*>(base + o_ctr);
@@ -721,16 +765,25 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
     FJ_CUDA(cudaEventRecord(ev0, stream));
     OOSPrepParams pp{X, const_cast<float*>(p.XT), const_cast<float*>(p.SX), m, int(n), nx, d, p.next_block, st};
     FJ_CUDA(launch_oos_prep(pp, stream));
-    const int bps = std::max(1, (dtype == FJOFC_F32) ? k3_bps_dt<float>(d) : (dtype == FJOFC_F16) ? k3_bps_dt<__half>(d)
-                                                                                              : k3_bps_dt<__nv_bfloat16>(d));
-    const int64_t groups = (k + g.R - 1) / g.R;
-    int64_t grid = int64_t(bps) * sm_count();
-    const int64_t need = (groups + g.WARPS - 1) / g.WARPS;
-    if (grid > need) grid = need;
-    if (grid < 1) grid = 1;
-    cudaError_t e = (dtype == FJOFC_F32) ? k3_launch_dt<float>(d, int(grid), tmap, p, stream)
-                  : (dtype == FJOFC_F16) ? k3_launch_dt<__half>(d, int(grid), tmap, p, stream)
-                                         : k3_launch_dt<__nv_bfloat16>(d, int(grid), tmap, p, stream);
+    cudaError_t e;
+    if (resident) {
+        // one CTA per object, at most one wave; CTAs take further objects from the counter
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(k, int64_t(r_bps) * sm_count()));
+        e = (dtype == FJOFC_F32) ? k3r_launch_dt<float>(d, int(grid), p, stream)
+          : (dtype == FJOFC_F16) ? k3r_launch_dt<__half>(d, int(grid), p, stream)
+                                 : k3r_launch_dt<__nv_bfloat16>(d, int(grid), p, stream);
+    } else {
+        const int bps = std::max(1, (dtype == FJOFC_F32) ? k3_bps_dt<float>(d) : (dtype == FJOFC_F16) ? k3_bps_dt<__half>(d)
+                                                                                                  : k3_bps_dt<__nv_bfloat16>(d));
+        const int64_t groups = (k + g.R - 1) / g.R;
+        int64_t grid = int64_t(bps) * sm_count();
+        const int64_t need = (groups + g.WARPS - 1) / g.WARPS;
+        if (grid > need) grid = need;
+        if (grid < 1) grid = 1;
+        e = (dtype == FJOFC_F32) ? k3_launch_dt<float>(d, int(grid), tmap, p, stream)
+          : (dtype == FJOFC_F16) ? k3_launch_dt<__half>(d, int(grid), tmap, p, stream)
+                                 : k3_launch_dt<__nv_bfloat16>(d, int(grid), tmap, p, stream);
+    }
     FJ_CUDA(e);
     double* sums = reinterpret_cast<double*>(base + o_sum);
     FJ_CUDA(launch_oos_summary(p.iters_out, p.stress_out, k, reinterpret_cast<int32_t*>(sums + 1), sums, stream));

@@ -139,7 +139,7 @@ int create_plan(const fjofc_problem* probs, int32_t nprob, const fjofc_opts* opt
     if (std::isnan(o.tol)) return fail(FJOFC_ERR_ARG, "tol is NaN");
     if (o.profile != 0) return fail(FJOFC_ERR_ARG, "profile must be 0 for a plan");
     if (!(o.relax >= 0.f && o.relax <= 2.f)) return fail(FJOFC_ERR_ARG, "relax must be in [0, 2]");
-    for (int r = 0; r < 3; ++r)
+    for (int r = 0; r < 2; ++r)
         if (o.reserved[r] != 0) return fail(FJOFC_ERR_ARG, "opts.reserved must be zero");
     int rc;
     if ((rc = fjofc::tensor_map_encoder())) return rc;

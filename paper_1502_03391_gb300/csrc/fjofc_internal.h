@@ -164,6 +164,8 @@ struct K3Params {
     const float* XT;           // in-sample transposed and negated, -X^T: [m][d][nx] (nx = n rounded up to 4)
     const float* SX;           // [m][d] column sums of each X^(j)
     float* Y;                  // k x m x d
+    const void* delta_new;     // k x m x n, row stride ld elements (the resident form reads it directly)
+    int64_t ld;
     int32_t* iters_out;        // may be NULL
     double* stress_out;        // never NULL (internal buffer when the caller passes NULL)
     unsigned long long* next_block;   // work counter (next new object)

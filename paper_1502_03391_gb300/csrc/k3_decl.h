@@ -8,4 +8,21 @@ namespace fjofc {
 template <int D, typename TD> cudaError_t k3_launch_impl(int grid, const CUtensorMap& tmap, const K3Params& p, cudaStream_t s);
 template <int D, typename TD> int k3_bps_impl();
 template <int D, typename TD> K3Geom k3_geom_impl();
+
+// The resident out-of-sample form (k_oos_resident.cuh): one CTA per object, -X^T and the
+// object's dissimilarities in shared memory ([m][d][nx] + [m][nx] float32).
+constexpr int kK3rThreads = 256;
+constexpr int kK3rWarps = kK3rThreads / 32;
+constexpr int kK3rMaxD = 8;                       // instantiated for d = 1..8
+// dynamic shared memory the resident form may use (its static arrays and the alignment
+// stay inside the 227 KB per CTA)
+constexpr size_t kK3rSmemBudget = size_t(200) * 1024;
+inline size_t k3r_smem_bytes(int m, int64_t nx, int d) {
+    return size_t(m) * size_t(nx) * size_t(d + 1) * sizeof(float);
+}
+inline bool k3r_fits(int m, int64_t nx, int d) {
+    return d >= 1 && d <= kK3rMaxD && k3r_smem_bytes(m, nx, d) <= kK3rSmemBudget;
+}
+template <int D, typename TD> cudaError_t k3r_launch_impl(int grid, const K3Params& p, cudaStream_t s);
+template <int D, typename TD> int k3r_bps_impl(size_t smem);
 }  // namespace fjofc

@@ -5,6 +5,9 @@ after T transforms must match the oracle's dense Eq. (joosupdate) iteration (sma
 its pinned O(nmd) form (large n) within relative error 1e-5 per object, stresses within
 1e-6.  Cases: k not a multiple of the object group, n not a multiple of the point tile,
 general weights, float16 delta, per-object stopping, exact-configuration fixed points.
+Each case runs both kernel forms: the streaming one (one warp slot per object, the
+dissimilarities streamed every iteration) and the resident one (one CTA per object with
+-X^T and the object's dissimilarities in shared memory; d <= 8).
 """
 import numpy as np
 import pytest
@@ -49,19 +52,28 @@ def _setup(m, n, d, k, seed, w=0.5):
     return prob, X, dnew, Y0
 
 
+FORMS = ["streaming", "resident"]
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("m,n,d,k", [(2, 10, 2, 1), (2, 63, 3, 7), (3, 64, 2, 33), (2, 65, 5, 9),
-                                     (2, 200, 3, 17), (3, 130, 10, 5), (2, 40, 16, 3), (1, 50, 2, 4)])
-def test_oos_parity_fixed_iterations(fj, m, n, d, k):
+                                     (2, 200, 3, 17), (3, 130, 10, 5), (2, 40, 16, 3), (1, 50, 2, 4),
+                                     (8, 301, 3, 3), (4, 257, 8, 2)])
+def test_oos_parity_fixed_iterations(fj, m, n, d, k, form):
+    if form == "resident" and d > 8:
+        pytest.skip("the resident form is built for d <= 8")
     T = 15
     prob, X, dnew, Y0 = _setup(m, n, d, k, seed=300 + n + m + d)
     dn, Xd, Yd, it, st = _device_inputs(fj, X, dnew, Y0)
-    res = fj.oos(Xd, dn, prob.W, Yd, max_iter=T, iters_out=it, stress_out=st)
+    res = fj.oos(Xd, dn, prob.W, Yd, max_iter=T, iters_out=it, stress_out=st, form=form)
     assert res.status == 0 and res.max_iters == T
     Y = Yd.cpu().numpy()
     sig = st.cpu().numpy()
     assert np.all(it.cpu().numpy() == T)
+    # the dense Eq. (joosupdate) oracle; its pinned O(nmd) form above m n = 1000 (time)
+    oracle = O.oos_embed if m * n <= 1000 else O.oos_embed_closed_form
     for o in range(k):
-        ref = O.oos_embed(X, _f32(dnew[o]), _f32(Y0[o]), prob.W, max_iter=T)
+        ref = oracle(X, _f32(dnew[o]), _f32(Y0[o]), prob.W, max_iter=T)
         err = np.linalg.norm(Y[o] - ref.y) / np.linalg.norm(ref.y)
         assert err <= 1e-5, (o, err)
         assert abs(sig[o] - ref.stress[-1]) <= 1e-6 * ref.stress[-1]
@@ -85,7 +97,8 @@ def test_oos_full_size_workload(fj):
         assert abs(sig[o] - ref.stress[-1]) <= 1e-6 * ref.stress[-1]
 
 
-def test_oos_general_weights_and_half_delta(fj):
+@pytest.mark.parametrize("form", FORMS)
+def test_oos_general_weights_and_half_delta(fj, form):
     import torch
     rng = np.random.default_rng(3)
     m, n, d, k = 3, 77, 3, 6
@@ -94,7 +107,7 @@ def test_oos_general_weights_and_half_delta(fj):
     W = np.triu(A) + np.triu(A, 1).T
     scale = [float(dnew[:, j].max()) / 32 for j in range(m)]
     dn, Xd, Yd, it, st = _device_inputs(fj, X, dnew, Y0, dtype=torch.float16, scale=scale)
-    fj.oos(Xd, dn, W, Yd, max_iter=12, delta_scale=scale, stress_out=st)
+    fj.oos(Xd, dn, W, Yd, max_iter=12, delta_scale=scale, stress_out=st, form=form)
     Y = Yd.cpu().numpy()
     rounded = dn.double().cpu().numpy() * np.asarray(scale)[None, :, None]
     for o in range(k):
@@ -102,12 +115,14 @@ def test_oos_general_weights_and_half_delta(fj):
         assert np.linalg.norm(Y[o] - ref.y) / np.linalg.norm(ref.y) <= 1e-5
 
 
-def test_oos_per_object_stopping(fj):
+@pytest.mark.parametrize("form", FORMS)
+def test_oos_per_object_stopping(fj, form):
     m, n, d, k = 2, 90, 2, 12
     prob, X, dnew, Y0 = _setup(m, n, d, k, seed=501)
     tol = 1e-5
     dn, Xd, Yd, it, st = _device_inputs(fj, X, dnew, Y0)
-    fj.oos(Xd, dn, prob.W, Yd, max_iter=300, tol=tol, tol_mode="relative", iters_out=it, stress_out=st)
+    fj.oos(Xd, dn, prob.W, Yd, max_iter=300, tol=tol, tol_mode="relative", iters_out=it, stress_out=st,
+           form=form)
     iters = it.cpu().numpy()
     Y = Yd.cpu().numpy()
     assert iters.min() >= 1 and iters.max() < 300
@@ -121,7 +136,8 @@ def test_oos_per_object_stopping(fj):
         assert (h[-2] - h[-1]) <= tol * h[-2] * 1.5 + 1e-9 * h[-2]
 
 
-def test_oos_exact_configuration_fixed_point(fj):
+@pytest.mark.parametrize("form", FORMS)
+def test_oos_exact_configuration_fixed_point(fj, form):
     """A new object that repeats in-sample object j of a zero-stress embedding stays at
     X_j (Sec. 3 fixed point)."""
     rng = np.random.default_rng(9)
@@ -136,6 +152,29 @@ def test_oos_exact_configuration_fixed_point(fj):
     dnew = np.stack([np.stack([Dy[j], Dy[j]]) for j in idx])
     Y0 = np.stack([np.stack([Yc[j], Yc[j]]) for j in idx])
     dn, Xd, Yd, it, st = _device_inputs(fj, X, dnew, Y0)
-    fj.oos(Xd, dn, W, Yd, max_iter=5, stress_out=st)
+    fj.oos(Xd, dn, W, Yd, max_iter=5, stress_out=st, form=form)
     np.testing.assert_allclose(Yd.cpu().numpy(), Y0, atol=2e-5)
     assert float(st.max()) < 1e-6
+
+
+def test_oos_forms_agree_and_auto_picks_resident_for_few_objects(fj):
+    """Both forms on the same inputs (one object per CTA against a small in-sample set, 60
+    transforms): results within float32 reduction-order noise; the automatic choice (few
+    objects, small in-sample set) equals the resident result bit for bit."""
+    import torch
+    m, n, d, k = 3, 400, 3, 5
+    prob, X, dnew, Y0 = _setup(m, n, d, k, seed=777)
+    outs = {}
+    for form in ("streaming", "resident", "auto"):
+        dn, Xd, Yd, it, st = _device_inputs(fj, X, dnew, Y0)
+        fj.oos(Xd, dn, prob.W, Yd, max_iter=60, iters_out=it, stress_out=st, form=form)
+        torch.cuda.synchronize()
+        outs[form] = (Yd.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy())
+    Ys, its, ss = outs["streaming"]
+    Yr, itr, sr = outs["resident"]
+    assert np.all(its == 60) and np.all(itr == 60)
+    for o in range(k):
+        assert np.linalg.norm(Yr[o] - Ys[o]) / np.linalg.norm(Ys[o]) <= 1e-5, o
+    np.testing.assert_allclose(sr, ss, rtol=1e-6)
+    np.testing.assert_array_equal(outs["auto"][0], Yr)
+    np.testing.assert_array_equal(outs["auto"][2], sr)

@@ -148,3 +148,17 @@ def test_oos_argument_validation(call):
     assert oos(d=17) == -6
     assert oos(W=[[1.0, 0.5], [0.3, 1.0]]) == -1
     assert oos(k=0) == 0          # nothing to embed: success without touching the GPU
+
+    def oos_form(form, m=2, n=8, d=2):
+        o = fj._Opts(3, -1.0, 1)
+        o.oos_form = form
+        Wm = np.eye(m) + 0.5 * (1 - np.eye(m))
+        return lib.fjofc_oos(ctypes.c_int32(m), ctypes.c_int64(n), ctypes.c_int32(d), ctypes.c_int64(4),
+                             ctypes.c_void_p(8192), ctypes.c_void_p(4096), ctypes.c_int64(n), ctypes.c_int32(0), None,
+                             Wm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(12288), None, None,
+                             ctypes.byref(o), None, None)
+
+    assert oos_form(3) == -1                      # unknown form
+    assert oos_form(2, d=9) == -6                 # resident form: d <= 8
+    assert oos_form(2, n=100000) == -6            # resident form: does not fit in shared memory
+    assert "shared memory" in fj.strerror(-6)
