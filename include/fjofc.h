@@ -209,7 +209,9 @@ int fjofc_stress(int32_t m, int64_t n, int32_t d,
  *  iters_out  : DEVICE int32[k] or NULL: transforms applied per object.
  *  stress_out : DEVICE float64[k] or NULL: final out-of-sample stress (Eq. joos).
  *  opts       : max_iter and the stopping rule, applied per object; the normalised
- *               mode divides by the number of weighted terms m*n + C(m,2).
+ *               mode divides by the number of weighted terms m*n + C(m,2).  oos_form
+ *               picks the kernel form (FJOFC_OOS_*); both give the same results up to
+ *               float32 summation order.
  *  res        : res->iters receives the largest per-object count, res->stress the sum
  *               of the final stresses.  May be NULL.
  */
