@@ -564,6 +564,22 @@ def _loglog_slope(xs, ys):
     return float(np.polyfit(np.log(np.asarray(xs, float)), np.log(np.asarray(ys, float)), 1)[0])
 
 
+def held_out_rows(m, n):
+    """Mask over the m*n modality-major rows of a configuration: False at the last
+    object (row j*n + n-1) of every modality j."""
+    import numpy as np
+    keep = np.ones(m * n, dtype=bool)
+    keep[n - 1::n] = False
+    return keep
+
+
+def procrustes_rotation(A, B):
+    """The orthogonal R minimising ||A R - B||_F (from the SVD of A'B)."""
+    import numpy as np
+    U, _, Vt = np.linalg.svd(np.asarray(A, np.float64).T @ np.asarray(B, np.float64))
+    return U @ Vt
+
+
 def run_paper_oos(args, rank, world, local_rank):
     """The paper's out-of-sample experiment (Sec. 4.4) with its Sec. 4.3 generator in three
     dimensions (d = 3, Eq. W with w = 0.5): Algorithm 2 in-sample (fjofc_init_cmds, then
@@ -598,8 +614,7 @@ def run_paper_oos(args, rank, world, local_rank):
             deltas = synthetic.paper_jitter_modalities(n=n, m=m, dim=3, seed=4500 + 10 * m + n)
             W = synthetic.weights_matrix(m, 1.0, 0.5)
             y0 = np.random.default_rng(4700 + m + n).standard_normal((1, m, d)).astype(np.float32)
-            keep = np.ones(m * n, dtype=bool)
-            keep[n - 1::n] = False                      # row j*n + n-1: object n in modality j
+            keep = held_out_rows(m, n)
             full = [fj.to_device_delta(D) for D in deltas]
             part = [fj.to_device_delta(np.ascontiguousarray(D[:n - 1, :n - 1])) for D in deltas]
             dnew = fj.empty_oos_delta(1, m, n - 1, torch.float32, device)
@@ -635,8 +650,7 @@ def run_paper_oos(args, rank, world, local_rank):
             Xp_h = Xp.cpu().numpy().astype(np.float64)
             Y_h = Y.cpu().numpy().astype(np.float64)[0]
             Xk = Xf_h.reshape(m * n, d)[keep]
-            U, _, Vt = np.linalg.svd(Xp_h.T @ Xk)
-            R = U @ Vt                                  # orthogonal Procrustes: Xp R ~ Xf without object n
+            R = procrustes_rotation(Xp_h, Xk)           # Xp R ~ Xf without object n
             row = {"m": m, "n": n,
                    "insample_ms": float(np.median(ms_full)), "insample_transforms": int(it_full[-1]),
                    "insample_minus_one_ms": float(np.median(ms_part)), "insample_minus_one_transforms": int(it_part[-1]),
