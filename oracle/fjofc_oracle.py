@@ -247,8 +247,8 @@ def jofc_embed(deltas: Sequence[np.ndarray], Wm: np.ndarray, X0: np.ndarray, max
 # ---------------------------------------------------------------------------
 
 def cmds(D: np.ndarray, d: int) -> np.ndarray:
-    """Classical MDS (Torgerson; the initialisation of Algorithm 1) of an n x n dissimilarity matrix:
-    the double-centred matrix ``-1/2 J D^2 J`` (``J = I - 11'/n``, ``D^2`` elementwise)
+    """Classical MDS (Torgerson; the initialisation of Algorithm 1) of an n x n
+    dissimilarity matrix: the double-centred matrix ``-1/2 J D^2 J`` (``J = I - 11'/n``, ``D^2`` elementwise)
     by ``numpy.linalg.eigh``, its d largest eigenpairs, coordinates ``v_k sqrt(max(l_k,
     0))``.  Sign convention (eigenvectors are defined up to sign): in every column the
     entry of largest magnitude is positive."""

@@ -5,8 +5,8 @@
 //   Procrustes fit onto xi_0 (the rotation R minimising ||xi_i R - xi_0||: with
 //   xi_0' xi_i = U S V', R = V U'; the printed xi_i U V' is the inverse rotation).
 //
-// Classical MDS (Torgerson; the initialisation of Algorithm 1) takes the d leading eigenpairs of
-// S = -1/2 J D2 J (D2 the elementwise squared dissimilarities, J = I - 11'/n) and
+// Classical MDS (Torgerson; the initialisation of Algorithm 1) takes the d leading
+// eigenpairs of S = -1/2 J D2 J (D2 the elementwise squared dissimilarities, J = I - 11'/n) and
 // returns v_k sqrt(max(lambda_k, 0)), each column's largest-magnitude entry made
 // positive.  The eigenpairs come from subspace iteration with p = 2d + 4 vectors:
 // Y = S V by one pass over Delta (the average and its square formed on the fly, no n x n
