@@ -21,7 +21,7 @@ eye:
   double-centred squared dissimilarities) and the orthogonal Procrustes fit
   (``numpy.linalg.svd``).
 
-Readings of the paper taken here (each is listed in the design doc):
+Readings of the paper taken here:
 
 * stopping rule: Algorithm 1 prints ``sigma(X_t) - sigma(X_{t-1}) > eps``, which a
   descent method never satisfies; the loop continues while the *decrease*

@@ -84,7 +84,7 @@ def test_full_size_one_transform_sampled_rows(fj, full_problem, dt):
     got = np.stack([X1[j * n + idx] for j in range(m)])
     assert _rel(got, want) <= X_TOL
     if dt != "float32":
-        # input error of the 16-bit storage (stated in the design doc; loose gate)
+        # input error of the 16-bit storage (the rounding of Delta; loose gate)
         exact = [synthetic.euclidean_distances(prob.F[l][idx], prob.F[l]) for l in range(m)]
         err = _rel(got, O.guttman_rows(exact, prob.W, X0.astype(np.float64), idx))
         print(f"{dt}: one transform vs exact-Delta oracle, sampled rows: {err:.3e}")

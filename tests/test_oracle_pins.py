@@ -128,7 +128,7 @@ def _small_problem(m=2, n=12, d=2, seed=3, w=0.5):
 
 @pytest.mark.parametrize("m,n,d,w", [(2, 12, 2, 0.5), (3, 9, 3, 2.0), (4, 7, 1, 0.1)])
 def test_fast_update_equals_dense_step(m, n, d, w):
-    """Eq. (update) with the c4 reading of Algorithm 2's coefficients: the oracle's
+    """Eq. (update) with the reading of Algorithm 2's coefficient typo: the oracle's
     pinv(L) B(X) X equals (1/(n+mw)) B_j X^(j) + (w/(n(n+mw))) sum_l B_l X^(l), with the
     B_l the diagonal blocks of B(X) built from a plain per-modality loop."""
     deltas, Wm, X = _small_problem(m, n, d, seed=10 + m, w=w)
@@ -192,6 +192,35 @@ def test_m1_is_textbook_smacof():
                 dij = np.sqrt(np.sum((X[i] - X[j]) ** 2))
                 exp[i] += deltas[0][i, j] / dij * (X[i] - X[j])
     np.testing.assert_allclose(Xn, exp / n, rtol=1e-12, atol=1e-13)
+
+
+def test_commensurability_weight_extremes():
+    """Sec. 1.2.1 on the weight w of Eq. W: w = 0 embeds every Delta_i on its own (each
+    block of one transform is the unit-weight SMACOF update of its modality, written as
+    an explicit loop), and a large w forces the modalities' configurations together
+    (after one transform the blocks differ by O(1/w))."""
+    m, n, d = 2, 9, 2
+    deltas, _, X = _small_problem(m, n, d, seed=12)
+    D = O.omnibus_dissimilarity(deltas)
+    W0 = _eqW(m, 0.0)
+    Xn = O.guttman_step(X, _lp(W0, n), O.omnibus_weights(W0, n), D)
+    for l in range(m):
+        Xl = X[l * n:(l + 1) * n]
+        exp = np.zeros_like(Xl)
+        for i in range(n):
+            for j in range(n):
+                if i != j:
+                    dij = np.sqrt(np.sum((Xl[i] - Xl[j]) ** 2))
+                    exp[i] += deltas[l][i, j] / dij * (Xl[i] - Xl[j])
+        # w = 0 leaves the blocks disconnected: L^+ acts per block, and each block of
+        # B(X) X is centred, so the step is the per-modality update
+        np.testing.assert_allclose(Xn[l * n:(l + 1) * n], exp / n, rtol=1e-10, atol=1e-12)
+    gaps = []
+    for w in (1e2, 1e4):
+        Ww = _eqW(m, w)
+        Xw = O.guttman_step(X, _lp(Ww, n), O.omnibus_weights(Ww, n), D)
+        gaps.append(np.linalg.norm(Xw[:n] - Xw[n:]) / np.linalg.norm(Xw))
+    assert gaps[1] < 1e-3 and 0.5e2 < gaps[0] / gaps[1] < 2e2, gaps
 
 
 # ---------------------------------------------------------------- stress identities
