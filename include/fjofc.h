@@ -94,7 +94,25 @@ typedef struct fjofc_opts {
     int32_t oos_form;     /* fjofc_oos only (other entry points ignore it): FJOFC_OOS_*.
                              FJOFC_OOS_AUTO picks the resident form when it fits and every
                              object gets its own CTA in one wave, else the streaming form. */
-    int32_t reserved[2];  /* must be zero */
+    int32_t check_inputs; /* in-sample entry points: 1 = one extra pass over every Delta_i
+                             before the loop checks that it is a dissimilarity (Sec. 1.2):
+                             every entry finite and >= 0 and Delta[a][b] == Delta[b][a]
+                             exactly (the diagonal is not read).  A violation returns
+                             FJOFC_ERR_ARG naming the modality and the entry; X is left
+                             as given.  0 = no check (the kernels then read only the strict
+                             upper triangle, so an asymmetric input is used through it). */
+    int32_t deterministic;/* 0 or 1.  Every reduction of every entry point runs in a fixed
+                             order (no floating-point atomics), so results are bitwise
+                             reproducible run to run on the same GPU model whatever this
+                             is set to; the field records the caller's requirement and is
+                             checked for a valid value only. */
+    int32_t wait_limit_us;/* bound of the in-sample loop's grid-wide waits, microseconds
+                             (0 = 2 000 000, i.e. 2 s).  A wait that does not complete in
+                             time ends the kernel with FJOFC_ERR_TIMEOUT instead of
+                             spinning; X then holds X_0 or an earlier iterate of the call
+                             (the loop keeps every third iterate in the caller's buffer),
+                             X_0 as given when the first pass timed out. */
+    int32_t reserved[3];  /* must be zero */
 } fjofc_opts;
 
 typedef struct fjofc_result {
@@ -224,27 +242,37 @@ int fjofc_oos(int32_t m, int64_t n, int32_t d, int64_t k,
 /*
  * fjofc_embed_noalloc -- fjofc_embed without any allocation at call time.
  *
- * Some callers cannot allocate device memory while they run: code that runs inside a
- * host callback or a driver-managed context where cudaMalloc/cudaMallocAsync is not
- * allowed, real-time loops that must not enter an allocator (CUDA's or a framework's
- * caching allocator) after start-up, and processes whose device memory was carved up
- * once at launch by another component.  This entry point takes exactly the arguments of
- * fjofc_embed and works in the caller's buffers plus one fixed device array of
- * FJOFC_NOALLOC_SCRATCH_BYTES inside the library (the paper has no counterpart: this is
- * a deployment variant of the same computation).  It calls no cudaMalloc, cudaFree,
- * stream-ordered allocator, event creation or host heap allocation.
+ * Some callers cannot allocate device memory while they run: real-time or embedded
+ * loops that must not enter an allocator (CUDA's or a framework's caching allocator)
+ * once start-up is over, processes whose device memory was carved up once at launch by
+ * another component, and code that must not fail part-way for lack of memory.  This
+ * entry point takes exactly the arguments of fjofc_embed and works in the caller's
+ * buffers plus one fixed device array of FJOFC_NOALLOC_SCRATCH_BYTES inside the library
+ * (the paper has no counterpart: this is a deployment variant of the same
+ * computation).  It calls no cudaMalloc, cudaFree, stream-ordered allocator, event
+ * creation or host heap allocation.  Like fjofc_embed it launches kernels and then
+ * synchronises cuda_stream, so it is called from ordinary host code (not from a host
+ * callback such as cudaLaunchHostFunc, where CUDA calls are not allowed).
  *
  *  - The array is part of the library's device code: every GPU on which that code is
  *    loaded holds it until the process exits.
  *  - The first call on a device looks up the array's device address on that device
- *    (cudaGetSymbolAddress) and caches it; make that first call before any stream
- *    capture on the device.
+ *    (cudaGetSymbolAddress) and caches it; with CUDA's lazy module loading (the default
+ *    since CUDA 12.2) that first call, and the first launch of each kernel it uses, also
+ *    load the library's device code, which does allocate.  So make one call per device
+ *    at start-up, before the period in which nothing may allocate, and before any
+ *    stream capture on the device (or set CUDA_MODULE_LOADING=EAGER so that the device
+ *    code is loaded when the context is created).
  *  - Calls share the array: two calls that overlap on the GPU (different streams, or
  *    different host threads on the same device) race and corrupt each other's results.
  *    Serialise them.  Each call clears what must start at zero.
- *  - A problem whose scratch does not fit (roughly 12 m n^2 d / RB bytes of partials
- *    plus 8 m n d bytes of iterates; n up to about 11000 at m = 2, d = 3) is rejected
- *    with FJOFC_ERR_UNSUPPORTED and a message naming the bytes it would need.
+ *  - A problem whose scratch does not fit is rejected with FJOFC_ERR_UNSUPPORTED and a
+ *    message naming the bytes it would need.  The scratch is, per call: the column
+ *    partials, 4 d CW bytes per all-pairs sub-tile, about 2 m d n^2 / RB bytes (RB = CW =
+ *    128 for d <= 4, 64 x 128 for d = 5-6, smaller beyond); two iterate buffers of 4 m n d
+ *    bytes each; 8 (max_iter + 2) bytes of stress history; and tables of about
+ *    4 m n d + (m + 1) d n / 2 bytes.  At m = 2, d = 3, float32 Delta that allows n up to
+ *    12800 with max_iter = 200 (12416 with max_iter = 100000).
  *  - opts->profile must be 0; res->ms_total and the profiling fields are returned as 0;
  *    res->stress_history, when given, receives max_iter + 1 entries (those past iters
  *    are 0).
@@ -392,6 +420,16 @@ typedef struct {
  * non-NULL the call synchronises the stream. */
 int fjofc_mlp_train(float* params, int32_t n_in, int32_t hidden, int32_t n_out, const uint16_t* x, const float* y,
                     int64_t count, const fjofc_mlp_train_opts* opts, float* loss_history, void* cuda_stream);
+
+/* Test support for the bounded-wait error path (the paper has no counterpart).  The
+ * next in-sample loop started by fjofc_embed or fjofc_embed_noalloc in this process
+ * expects `extra` more arrivals at the first grid-wide wait of its first pass than its
+ * CTAs make, so that wait cannot complete: every CTA gives up after
+ * opts->wait_limit_us, waits for its own copies in flight and returns, and the call
+ * returns FJOFC_ERR_TIMEOUT with X as given.  The setting is consumed by that one call
+ * (later calls run normally); extra <= 0 clears it.  Loops with a single CTA have no
+ * grid-wide wait and ignore it. */
+void fjofc_test_barrier_skew(int32_t extra);
 
 /* Message for a status code (static string). */
 const char* fjofc_strerror(int status);

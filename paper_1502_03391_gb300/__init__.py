@@ -37,7 +37,8 @@ MAX_M, MAX_D = 8, 16
 EXPORTS = ("fjofc_embed", "fjofc_embed_noalloc", "fjofc_stress", "fjofc_oos", "fjofc_strerror", "fjofc_version",
            "fjofc_mlp_param_count", "fjofc_mlp_init", "fjofc_mlp_features", "fjofc_mlp_forward", "fjofc_mlp_gradient",
            "fjofc_mlp_train", "fjofc_mlp_broadcast", "fjofc_mlp_select", "fjofc_plan_create", "fjofc_plan_run",
-           "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy", "fjofc_plan_autotune", "fjofc_init_cmds")
+           "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy", "fjofc_plan_autotune", "fjofc_init_cmds",
+           "fjofc_test_barrier_skew")
 
 
 class FjofcError(RuntimeError):
@@ -49,7 +50,8 @@ class FjofcError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("tol_mode", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("relax", ctypes.c_float), ("oos_form", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("check_inputs", ctypes.c_int32), ("deterministic", ctypes.c_int32),
+                ("wait_limit_us", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class _Result(ctypes.Structure):
@@ -109,6 +111,8 @@ def _load():
     lib.fjofc_init_cmds.argtypes = [i32, i64, i32, ctypes.POINTER(vp), i64, i32, ctypes.POINTER(ctypes.c_float),
                                     vp, ctypes.POINTER(_InitOpts), ctypes.POINTER(i32), vp]
     lib.fjofc_init_cmds.restype = ctypes.c_int
+    lib.fjofc_test_barrier_skew.argtypes = [i32]
+    lib.fjofc_test_barrier_skew.restype = None
     lib.fjofc_strerror.argtypes = [ctypes.c_int]
     lib.fjofc_strerror.restype = ctypes.c_char_p
     lib.fjofc_version.argtypes = []
@@ -232,12 +236,15 @@ class EmbedResult:
 
 def embed(deltas: Sequence, weights, X, max_iter: int, tol: float = -1.0, tol_mode: str = "relative",
           delta_scale=None, stream=None, history: bool = True, check: bool = True,
-          profile: int = 0, relax: float = 1.0) -> EmbedResult:
+          profile: int = 0, relax: float = 1.0, check_inputs: bool = False,
+          wait_limit_us: int = 0) -> EmbedResult:
     """In-sample fJOFC from ``X`` (in place).  ``deltas``: m CUDA n x n views (float32,
     float16 or bfloat16; row stride a multiple of 16 bytes); ``weights``: m x m;
     ``X``: contiguous float32 CUDA tensor of shape (m*n, d).  ``profile``: 0 none, 1 one
     launch per pass with per-kernel timing, 2 the persistent loop kernel timed.
-    ``relax``: relaxed updates (1 = the plain Guttman transform, up to 2).  See
+    ``relax``: relaxed updates (1 = the plain Guttman transform, up to 2).
+    ``check_inputs``: validate every Delta (finite, non-negative, symmetric) first.
+    ``wait_limit_us``: bound of the loop's grid-wide waits (0 = 2 s).  See
     ``fjofc_embed``."""
     m = len(deltas)
     n = int(deltas[0].shape[0])
@@ -249,6 +256,9 @@ def embed(deltas: Sequence, weights, X, max_iter: int, tol: float = -1.0, tol_mo
     Wn = _weights(weights, m)
     opts = _Opts(int(max_iter), float(tol), TOL_RELATIVE if tol_mode == "relative" else TOL_ABS_NORMALIZED,
                  int(profile), float(relax))
+    opts.check_inputs = 1 if check_inputs else 0
+    opts.deterministic = 1
+    opts.wait_limit_us = int(wait_limit_us)
     hist = np.zeros(int(max_iter) + 1, dtype=np.float64) if history else None
     res = _Result()
     if hist is not None:
@@ -263,6 +273,12 @@ def embed(deltas: Sequence, weights, X, max_iter: int, tol: float = -1.0, tol_mo
         hist = hist[:upto]
     return EmbedResult(st, res.iters, res.stress, res.stress_normalized, hist, res.ms_total, res.passes,
                        res.ms_pass, res.ms_apply, res.launches)
+
+
+def test_barrier_skew(extra: int) -> None:
+    """Test support: the next in-sample loop's first grid-wide wait expects ``extra``
+    arrivals more than its CTAs make (``fjofc_test_barrier_skew``)."""
+    _lib.fjofc_test_barrier_skew(int(extra))
 
 
 def stress(deltas: Sequence, weights, X, delta_scale=None, stream=None) -> float:

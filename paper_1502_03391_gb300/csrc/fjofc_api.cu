@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -46,6 +47,7 @@ int arg_error(const char* msg) {
 // diagonally dominant when every w_ii > 0 (proof of Thm 1), hence invertible.
 int weights_inverse(int m, int64_t n, const double* w, double* winv) {
     if (!w) return arg_error("weights is NULL");
+    if (m < 1 || m > FJOFC_MAX_M) return arg_error("m outside 1..FJOFC_MAX_M");
     for (int i = 0; i < m; ++i) {
         if (!(w[i * m + i] > 0.0) || !std::isfinite(w[i * m + i]))
             return arg_error("fidelity weights w_ii must be finite and > 0");
@@ -56,7 +58,10 @@ int weights_inverse(int m, int64_t n, const double* w, double* winv) {
             if (a != b) return arg_error("weights must be symmetric (w_ij == w_ji)");
         }
     }
-    std::vector<double> A(size_t(m) * 2 * m, 0.0);
+    // [m][2m] augmented matrix on the stack: no heap allocation (fjofc_embed_noalloc
+    // relies on this)
+    double A[FJOFC_MAX_M * 2 * FJOFC_MAX_M];
+    for (int e = 0; e < 2 * m * m; ++e) A[e] = 0.0;
     for (int i = 0; i < m; ++i) {
         double diag = double(n) * w[i * m + i];
         for (int j = 0; j < m; ++j)
@@ -288,6 +293,41 @@ EmbedPlan make_plan(int m, int64_t n, int d, int dtype, bool persistent, int G_o
     return P;
 }
 
+// The option fields every entry point that takes fjofc_opts validates the same way.
+int check_common_opts(const fjofc_opts& o) {
+    if (o.check_inputs != 0 && o.check_inputs != 1) return arg_error("check_inputs must be 0 or 1");
+    if (o.deterministic != 0 && o.deterministic != 1) return arg_error("deterministic must be 0 or 1");
+    if (o.wait_limit_us < 0) return arg_error("wait_limit_us must be >= 0");
+    for (int r = 0; r < 3; ++r)
+        if (o.reserved[r] != 0) return arg_error("opts.reserved must be zero");
+    return FJOFC_OK;
+}
+
+// Bound of the grid-wide waits in nanoseconds (0 = the default).
+uint64_t wait_limit_ns(const fjofc_opts& o) {
+    return o.wait_limit_us > 0 ? uint64_t(o.wait_limit_us) * 1000ull : kWaitLimitNs;
+}
+
+// Extra arrivals added to the first grid-wide wait of the next in-sample loop (test
+// support, fjofc_test_barrier_skew).
+std::atomic<int> g_barrier_skew{0};
+
+// Message for an error the in-sample kernels raised (status block copied to the host).
+void device_status_message(const DevStatus& h, int64_t n) {
+    if (h.error == FJOFC_ERR_TIMEOUT)
+        snprintf(g_last_msg, sizeof(g_last_msg), "device wait timed out (site %d)", h.timeout_site);
+    if (h.error == FJOFC_ERR_NONFINITE) snprintf(g_last_msg, sizeof(g_last_msg), "stress became non-finite");
+    if (h.error == FJOFC_ERR_ARG && h.bad != kNoBadEntry) {
+        const unsigned long long pos = h.bad >> 2;
+        const int kind = int(h.bad & 3ull);
+        const long long col = (long long)(pos % (unsigned long long)n);
+        const long long row = (long long)((pos / (unsigned long long)n) % (unsigned long long)n);
+        const int l = int(pos / ((unsigned long long)n * (unsigned long long)n));
+        snprintf(g_last_msg, sizeof(g_last_msg), "check_inputs: Delta_%d[%lld][%lld] %s", l + 1, row, col,
+                 kind == 1 ? "is negative" : kind == 2 ? "is not finite" : "differs from its transposed entry");
+    }
+}
+
 // Common validation of the in-sample arguments.
 int validate_insample(int32_t m, int64_t n, int32_t d, const void* const* delta, int64_t ld, int32_t dtype,
                       const float* delta_scale, const void* X) {
@@ -439,6 +479,8 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
     pp.rb_shift = k2.rb_shift; pp.cw_shift = k2.cw_shift;
     pp.max_iter = o.max_iter; pp.tol_mode = o.tol_mode; pp.tol = o.tol; pp.npairs = k2.npairs; pp.inv_n = k2.inv_n;
     pp.relax = k2.relax; pp.centre = k2.centre;
+    pp.bar_skew = 0;
+    pp.wait_ns = wait_limit_ns(o);
     for (int j = 0; j < FJOFC_MAX_M; ++j)
         for (int l = 0; l < FJOFC_MAX_M; ++l) { pp.coef[j][l] = k2.coef[j][l]; pp.wcomm[j][l] = k2.wcomm[j][l]; }
     pp.tb = k2.tb;
@@ -465,8 +507,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         if (std::isnan(o.tol)) return arg_error("tol is NaN");
         if (o.profile < 0 || o.profile > 2) return arg_error("profile must be 0, 1 or 2");
         if (!(o.relax >= 0.f && o.relax <= 2.f)) return arg_error("relax must be in [0, 2]");
-        for (int r = 0; r < 2; ++r)
-            if (o.reserved[r] != 0) return arg_error("opts.reserved must be zero");
+        if ((rc = check_common_opts(o))) return rc;
     } else {
         o.max_iter = 0;
         o.tol = -1.0;
@@ -522,7 +563,16 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         FJ_CUDA(cudaEventRecord(ev0, stream));
     }
 
+    int launches = 2;   // init + finalize (or init + the persistent kernel)
     FJ_CUDA(launch_init(S.ip, stream));
+    if (o.check_inputs) {
+        CheckParams cp{};
+        for (int l = 0; l < m; ++l) cp.delta[l] = delta[l];
+        cp.n = n; cp.ld = ld; cp.m = m; cp.dtype = dtype; cp.st = st;
+        if ((n + 31) / 32 > 65535) return arg_error("check_inputs supports n <= 2097120");
+        FJ_CUDA(launch_check_delta(cp, stream));
+        ++launches;
+    }
 
     float* bufs[3] = {X, buf1, buf2};
     const bool prof = o.profile == 1;
@@ -531,9 +581,9 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         pev.resize(size_t(3) * (o.max_iter + 1));
         for (auto& e : pev) FJ_CUDA(cudaEventCreate(&e));
     }
-    int launches = 2;   // init + finalize (or init + the persistent kernel)
     cudaEvent_t pe0 = nullptr, pe1 = nullptr;
     if (persist) {
+        S.pp.bar_skew = unsigned(g_barrier_skew.exchange(0));
         const PersistParams& pp = S.pp;
         if (o.profile == 2) {
             FJ_CUDA(cudaEventCreate(&pe0));
@@ -579,8 +629,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
                                     cudaMemcpyDeviceToHost, stream));
         FJ_CUDA(cudaStreamSynchronize(stream));
         rc = hst.error;
-        if (rc == FJOFC_ERR_TIMEOUT) snprintf(g_last_msg, sizeof(g_last_msg), "device wait timed out (site %d)", hst.timeout_site);
-        if (rc == FJOFC_ERR_NONFINITE) snprintf(g_last_msg, sizeof(g_last_msg), "stress became non-finite");
+        device_status_message(hst, n);
         if (res) {
             res->status = rc;
             res->iters = hst.final_iter;
@@ -626,8 +675,7 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
     }
 
     rc = hst.error;
-    if (rc == FJOFC_ERR_TIMEOUT) snprintf(g_last_msg, sizeof(g_last_msg), "device wait timed out (site %d)", hst.timeout_site);
-    if (rc == FJOFC_ERR_NONFINITE) snprintf(g_last_msg, sizeof(g_last_msg), "stress became non-finite");
+    device_status_message(hst, n);
     if (stress_out) *stress_out = (hst.error == FJOFC_ERR_NONFINITE) ? hh[0] : hst.stress;
     if (res) {
         res->status = rc;
@@ -670,6 +718,10 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
             if (!(delta_scale[i] > 0.f) || !std::isfinite(delta_scale[i])) return arg_error("delta_scale must be finite and > 0");
     if (o.oos_form != FJOFC_OOS_AUTO && o.oos_form != FJOFC_OOS_STREAMING && o.oos_form != FJOFC_OOS_RESIDENT)
         return arg_error("unknown oos_form");
+    {
+        const int orc = check_common_opts(o);
+        if (orc) return orc;
+    }
     const int nx = int((n + 3) / 4 * 4);
     const bool resident_fits = k3r_fits(m, nx, d);
     if (o.oos_form == FJOFC_OOS_RESIDENT && !resident_fits) {
@@ -881,6 +933,8 @@ const char* fjofc_strerror(int status) {
     }
     return "unknown status";
 }
+
+void fjofc_test_barrier_skew(int32_t extra) { g_barrier_skew.store(extra > 0 ? extra : 0); }
 
 const char* fjofc_version(void) { return "fjofc-gb300 0.1 (sm_103a; d=1..16; m<=8; f32/f16/bf16 Delta)"; }
 

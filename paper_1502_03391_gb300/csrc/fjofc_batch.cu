@@ -139,8 +139,13 @@ int create_plan(const fjofc_problem* probs, int32_t nprob, const fjofc_opts* opt
     if (std::isnan(o.tol)) return fail(FJOFC_ERR_ARG, "tol is NaN");
     if (o.profile != 0) return fail(FJOFC_ERR_ARG, "profile must be 0 for a plan");
     if (!(o.relax >= 0.f && o.relax <= 2.f)) return fail(FJOFC_ERR_ARG, "relax must be in [0, 2]");
-    for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < 3; ++r)
         if (o.reserved[r] != 0) return fail(FJOFC_ERR_ARG, "opts.reserved must be zero");
+    if (o.deterministic != 0 && o.deterministic != 1) return fail(FJOFC_ERR_ARG, "deterministic must be 0 or 1");
+    if (o.wait_limit_us < 0) return fail(FJOFC_ERR_ARG, "wait_limit_us must be >= 0");
+    if (o.check_inputs != 0)
+        return fail(FJOFC_ERR_UNSUPPORTED, "check_inputs is not available for plans (check each problem with "
+                                           "fjofc_embed and max_iter = 0)");
     int rc;
     if ((rc = fjofc::tensor_map_encoder())) return rc;
     int dev = 0, sms = 0, coop = 0;

@@ -22,7 +22,11 @@ struct DevStatus {
     int final_iter;    // index T of the returned iterate X_T
     int timeout_site;  // where a bounded wait gave up (diagnostics)
     double stress;     // sigma(X_T)
+    unsigned long long bad;   // input check: smallest ((l n + row) n + col) * 4 + kind of an
+                              // invalid Delta entry (kind 1 negative, 2 not finite,
+                              // 3 asymmetric), ~0 when none was found
 };
+constexpr unsigned long long kNoBadEntry = ~0ull;
 
 __device__ __forceinline__ int ld_volatile(const int* p) {
     return *reinterpret_cast<const volatile int*>(p);
@@ -53,8 +57,10 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
-// Upper bound of any device-side wait.  A healthy wait completes in microseconds; on
-// expiry the kernel records FJOFC_ERR_TIMEOUT and returns instead of spinning.
+// Upper bound of the device-side waits on mbarriers (TMA and copy completions, which
+// take microseconds when healthy); the grid-wide waits of the in-sample loop take their
+// bound from the call (fjofc_opts.wait_limit_us, this value by default).  On expiry the
+// kernel records FJOFC_ERR_TIMEOUT and returns instead of spinning.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -115,6 +115,8 @@ struct PersistParams {
     float inv_n;
     float relax;                // relaxed update factor (1: the plain Guttman transform)
     int centre;                 // 1: centre X_{t-1} in place with its column means
+    unsigned bar_skew;          // extra arrivals the first grid-wide wait expects (0; test support)
+    unsigned long long wait_ns; // bound of every grid-wide wait
     float coef[FJOFC_MAX_M][FJOFC_MAX_M];
     float wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
     BxTables tb;
@@ -140,6 +142,14 @@ struct InitParams {
     int m, n, RB, CW, nRB, G;
     int64_t T, Tm;
 };
+// Dissimilarity check of fjofc_opts.check_inputs (one pass over every Delta_l).
+struct CheckParams {
+    const void* delta[FJOFC_MAX_M];
+    int64_t n, ld;
+    int m, dtype;
+    DevStatus* st;
+};
+cudaError_t launch_check_delta(const CheckParams& p, cudaStream_t s);
 cudaError_t launch_init(const InitParams& p, cudaStream_t s);
 cudaError_t launch_init_batched(const InitParams* ps, int count, cudaStream_t s);
 // float32 Delta -> float16 storage for the batched tuner: largest |Delta| (float bits,

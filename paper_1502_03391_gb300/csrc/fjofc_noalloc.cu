@@ -1,21 +1,24 @@
 // fjofc_embed_noalloc: the in-sample embedding with all of its device scratch in one
 // fixed, file-scope device array instead of memory obtained at call time.
 //
-// Some callers cannot allocate device memory while they run: code that executes inside
-// a host callback or a driver-managed context where cudaMalloc/cudaMallocAsync is not
-// allowed, real-time or embedded loops that must not touch the allocator (or any
-// framework's caching allocator) after start-up, and processes whose device memory is
-// carved up once at launch by another component.  For them this entry point takes the
-// same arguments as fjofc_embed and uses only the caller's buffers plus the array below.
+// Some callers cannot allocate device memory while they run: real-time or embedded loops
+// that must not touch the allocator (or any framework's caching allocator) after
+// start-up, processes whose device memory is carved up once at launch by another
+// component, and code that must not fail part-way for lack of memory.  For them this
+// entry point takes the same arguments as fjofc_embed and uses only the caller's buffers
+// plus the array below.  It launches kernels and synchronises the caller's stream like
+// fjofc_embed, so it is called from ordinary host code.
 //
 // The array (kNoallocScratchBytes) lives in this translation unit's device module, so
 // every GPU on which that module is loaded keeps it until the process exits.  Its
 // device address is looked up once per device with cudaGetSymbolAddress (host code
 // cannot use the array's name as a device address: on the host that name refers to a
-// host-side shadow).  Calls share the array, which keeps whatever the previous call
-// left there; the kernels clear everything that must start at zero (status block, work
-// ticket, centring means, walk offsets) at the start of every call, and every partial
-// is written before it is read.
+// host-side shadow).  Under lazy module loading that first lookup, and the first launch
+// of each kernel, load device code, which allocates: callers make one call per device at
+// start-up.  Calls share the array, which keeps whatever the previous call left there;
+// the kernels clear everything that must start at zero (status block, work ticket,
+// barrier counter, centring means, walk offsets) at the start of every call, and every
+// partial is written before it is read.
 #include <cuda_runtime.h>
 
 #include <cstdio>

@@ -133,6 +133,7 @@ __device__ __forceinline__ void init_problem(const InitParams& p) {
         p.st->final_iter = 0;
         p.st->timeout_site = 0;
         p.st->stress = 0.0;
+        p.st->bad = kNoBadEntry;
         *p.ticket = 0u;
         if (p.bar) *p.bar = 0u;
     }
@@ -237,6 +238,65 @@ __global__ void k_finalize(float* Xout, const float* buf1, const float* buf2, in
         Xout[e] = src[e];
 }
 
+// Input check (fjofc_opts.check_inputs): Delta_l must hold dissimilarities (Sec. 1.2):
+// finite, non-negative and symmetric.  CTA (I, J, l) with I <= J compares the 32 x 32
+// block (I, J) of Delta_l with block (J, I), both staged in shared memory by coalesced
+// rows; every off-diagonal entry is read once.  A thread that finds an invalid entry
+// lowers st->bad to that entry's key (atomicMin: the first entry in (l, row, column)
+// order wins whatever the schedule) and marks the loop as stopped with FJOFC_ERR_ARG, so
+// the kernels that follow on the stream return at once and leave X as given.
+template <typename TD>
+__device__ __forceinline__ float check_load(const void* base, int64_t ld, int64_t r, int64_t c) {
+    return DeltaLoad<TD>::to_f32(static_cast<const TD*>(base)[r * ld + c]);
+}
+
+template <typename TD>
+__global__ void __launch_bounds__(256) k_check_delta(const __grid_constant__ CheckParams p) {
+    const int I = blockIdx.x, J = blockIdx.y, l = blockIdx.z;
+    if (I > J) return;
+    __shared__ float a[32][33], b[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t n = p.n;
+    const void* base = p.delta[l];
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t ra = int64_t(I) * 32 + r, ca = int64_t(J) * 32 + tx;
+        const int64_t rb = int64_t(J) * 32 + r, cb = int64_t(I) * 32 + tx;
+        a[r][tx] = (ra < n && ca < n) ? check_load<TD>(base, p.ld, ra, ca) : 0.f;
+        b[r][tx] = (rb < n && cb < n) ? check_load<TD>(base, p.ld, rb, cb) : 0.f;
+    }
+    __syncthreads();
+    unsigned long long worst = kNoBadEntry;
+    auto flag = [&](int64_t row, int64_t col, unsigned kind) {
+        const unsigned long long key =
+            ((unsigned long long)((int64_t(l) * n + row) * n + col) << 2) | (unsigned long long)kind;
+        worst = key < worst ? key : worst;
+    };
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t row = int64_t(I) * 32 + r, col = int64_t(J) * 32 + tx;
+        if (!(row < col && col < n)) continue;          // strict upper triangle of the block pair
+        const float u = a[r][tx], v = b[tx][r];         // Delta[row][col], Delta[col][row]
+        if (!isfinite(u)) flag(row, col, 2u);
+        else if (u < 0.f) flag(row, col, 1u);
+        if (!isfinite(v)) flag(col, row, 2u);
+        else if (v < 0.f) flag(col, row, 1u);
+        if (isfinite(u) && isfinite(v) && u != v) flag(row, col, 3u);
+    }
+    if (worst != kNoBadEntry) {
+        atomicMin(&p.st->bad, worst);
+        p.st->error = FJOFC_ERR_ARG;
+        p.st->done = 1;
+    }
+}
+
+cudaError_t launch_check_delta(const CheckParams& p, cudaStream_t s) {
+    const int nt = int((p.n + 31) / 32);
+    const dim3 grid(nt, nt, p.m);
+    if (p.dtype == FJOFC_F32) k_check_delta<float><<<grid, 256, 0, s>>>(p);
+    else if (p.dtype == FJOFC_F16) k_check_delta<__half><<<grid, 256, 0, s>>>(p);
+    else k_check_delta<__nv_bfloat16><<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(float* Xout, const float* buf1, const float* buf2, int64_t count,
                             const DevStatus* st, cudaStream_t s) {
     const int threads = 256;
@@ -277,6 +337,7 @@ __global__ void k_oos_prep(const OOSPrepParams p) {
             p.st->final_iter = 0;
             p.st->timeout_site = 0;
             p.st->stress = 0.0;
+            p.st->bad = kNoBadEntry;
         }
     }
 }

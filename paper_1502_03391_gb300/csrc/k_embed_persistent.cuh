@@ -37,9 +37,9 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 
 // Barrier of the G CTAs of one problem over a monotone counter: arrival k of every CTA
 // waits for G*k arrivals (G == 1: a CTA barrier).  Bounded: returns false after
-// kWaitLimitNs (or when *abort_flag is set).
+// limit_ns (or when *abort_flag is set).
 __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int* s_flag,
-                                             const volatile int* abort_flag, int G) {
+                                             const volatile int* abort_flag, int G, uint64_t limit_ns) {
     if (G == 1) {
         __threadfence();
         __syncthreads();
@@ -54,7 +54,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
             const uint64_t t0 = globaltimer_ns();
             for (uint32_t it = 1;; ++it) {
                 if (ld_acquire_gpu(ctr) >= target) break;
-                if ((it & 63u) == 0u && (*abort_flag || globaltimer_ns() - t0 > kWaitLimitNs)) {
+                if ((it & 63u) == 0u && (*abort_flag || globaltimer_ns() - t0 > limit_ns)) {
                     ok = false;
                     break;
                 }
@@ -78,7 +78,7 @@ __device__ __forceinline__ void grid_arrive(unsigned* ctr, int G) {
     }
 }
 __device__ __forceinline__ bool grid_wait(unsigned* ctr, unsigned target, int* s_flag, const volatile int* abort_flag,
-                                          int G) {
+                                          int G, uint64_t limit_ns) {
     if (G == 1) {
         __threadfence();
         __syncthreads();
@@ -91,7 +91,7 @@ __device__ __forceinline__ bool grid_wait(unsigned* ctr, unsigned target, int* s
             const uint64_t t0 = globaltimer_ns();
             for (uint32_t it = 1;; ++it) {
                 if (ld_acquire_gpu(ctr) >= target) break;
-                if ((it & 63u) == 0u && (*abort_flag || globaltimer_ns() - t0 > kWaitLimitNs)) {
+                if ((it & 63u) == 0u && (*abort_flag || globaltimer_ns() - t0 > limit_ns)) {
                     ok = false;
                     break;
                 }
@@ -163,6 +163,9 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
     const int bcap = int(S::RED_FLOATS / size_t(phase_b_floats_per_unit(m)));
     static_assert(S::RED_FLOATS >= size_t(phase_b_floats_per_unit(FJOFC_MAX_M)), "phase-B overlay does not fit");
 
+    // a failed input check stopped the loop before it started: every CTA of the problem
+    // reads the same value (written by an earlier kernel) and leaves X as given
+    if (ld_volatile(&p.st->done)) return;
     if (tid == 0) {
         s_stop = 0;
         s_final = 0;
@@ -269,7 +272,8 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
         FJ_STAMP(t, 3);
         // every CTA has finished phase A (its partial tables are complete) and no CTA still
         // reads X_{t-1} for phase A
-        if (!grid_wait(P.bar, bar_target, &s_flag, abort_flag, G) || *abort_flag) {
+        if (!grid_wait(P.bar, bar_target + (t == 1 ? P.bar_skew : 0u), &s_flag, abort_flag, G, P.wait_ns) ||
+            *abort_flag) {
             if (ok) fail_site = 32;
             ok = false;
             break;
@@ -301,7 +305,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
         // X_t is complete, and every CTA is done with pass t's partial tables, before any
         // CTA starts pass t+1
         bar_target += unsigned(G);
-        if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag, G)) {
+        if (!grid_barrier(P.bar, bar_target, &s_flag, abort_flag, G, P.wait_ns)) {
             fail_site = 33;
             ok = false;
             break;

@@ -16,11 +16,9 @@ import pytest
 
 from oracle import fjofc_oracle as O
 import synthetic
+from parity_rule import X_TOL, assert_stress
 
 pytestmark = pytest.mark.gpu
-
-X_TOL = 1e-5
-S_TOL = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -44,34 +42,14 @@ SHAPES = [  # m, n, d, delta type
 ]
 
 
-RSQRT_EPS = 2.0 ** -22.9     # bound of the hardware reciprocal square root's relative error
-
-
-def _stress_tol(rounded, W, X):
-    """1e-6 relative, plus the float32 distance error the all-pairs pass cannot avoid:
-    each fidelity term (Delta - d)^2 moves by at most about 2 |Delta - d| d eps when d
-    carries the reciprocal square root's relative error eps, so small, well-fitted
-    problems (large sum |e| d / sum e^2) get that much more."""
-    X = np.asarray(X, np.float64)
-    m = len(rounded)
-    n = X.shape[0] // m
-    extra = 0.0
-    for l in range(m):
-        Xl = X[l * n:(l + 1) * n]
-        D = np.sqrt(((Xl[:, None, :] - Xl[None, :, :]) ** 2).sum(-1))
-        iu = np.triu_indices(n, 1)
-        extra += float(W[l][l]) * float(np.sum(np.abs(rounded[l][iu] - D[iu]) * D[iu]))
-    return 2.0 * RSQRT_EPS * extra
-
-
 def _check_stress(got, p, ref, where):
-    """The device's stress of its own X_T against the oracle's stress of that X_T (the
-    arithmetic: 1e-6 relative plus the float32 distance bound), and the oracle's stresses
-    of the device and oracle iterates against each other (1e-5 relative, as X)."""
+    """The device's stress of its own X_T against the oracle's stress of that X_T under
+    the parity rule (1e-6 relative plus the float32 distance term, which carries the
+    small, well-fitted problems of this batch), and the oracle's stresses of the device
+    and oracle iterates against each other (1e-5 relative, as X)."""
     Xg = p["X"].cpu().numpy().astype(np.float64)
     s_dev_x = O.stress_blocks(p["rounded"], p["prob"].W, Xg)
-    tol = S_TOL * s_dev_x + _stress_tol(p["rounded"], p["prob"].W, Xg)
-    assert abs(got - s_dev_x) <= tol, where
+    assert_stress(got, s_dev_x, p["rounded"], p["prob"].W, Xg, where)
     assert abs(s_dev_x - ref.stress[-1]) <= X_TOL * ref.stress[-1], where
 
 

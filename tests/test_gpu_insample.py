@@ -2,21 +2,22 @@
 oracle, through the C ABI.
 
 Tolerances (float32 arithmetic on the device vs float64 in the oracle, same float32
-inputs): X after T transforms within relative Frobenius error 1e-5, stress within 1e-6
-relative.  Sizes span several RB x CW tiles with ragged tails; edge cases cover the
-smallest n, duplicate points (d_ij = 0), a non-zero Delta diagonal, general weights,
-float16/bfloat16 Delta, the stopping rule, determinism and non-finite input.
+inputs; ``tests/parity_rule.py``): X after T transforms within relative Frobenius
+error 1e-5; every stress within 1e-6 relative plus the fidelity error that float32
+distances alone cause, 2 |Delta - d| eps_d d + (eps_d d)^2 per pair with eps_d =
+2^-22.9 + (d + 3) 2^-25 (negligible except near zero stress).  Sizes span several
+RB x CW tiles with ragged tails; edge cases cover the smallest n, duplicate points
+(d_ij = 0), a non-zero Delta diagonal, exact configurations (zero stress), general
+weights, float16/bfloat16 Delta, the stopping rule, determinism and non-finite input.
 """
 import numpy as np
 import pytest
 
 from oracle import fjofc_oracle as O
 import synthetic
+from parity_rule import X_TOL, S_TOL, assert_history, assert_stress
 
 pytestmark = pytest.mark.gpu
-
-X_TOL = 1e-5
-S_TOL = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +48,12 @@ def _run(fj, deltas, W, X0, iters, tol=-1.0, tol_mode="relative", dtype=None, sc
 
 
 def _oracle(deltas, W, X0, iters, **kw):
-    return O.jofc_embed([_f32(D) for D in deltas], W, _f32(X0), max_iter=iters, **kw)
+    return O.jofc_embed([_f32(D) for D in deltas], W, _f32(X0), max_iter=iters, keep_iterates=True, **kw)
+
+
+def _hist(res, ref, deltas, W, where=""):
+    """The device's stress history against the oracle's (the parity rule)."""
+    assert_history(res.history, ref.stress, [_f32(D) for D in deltas], W, ref.iterates, where)
 
 
 CASES = [  # m, n, d
@@ -64,9 +70,10 @@ def test_parity_fixed_iterations(fj, m, n, d):
     assert res.status == 0 and res.iters == T
     ref = _oracle(prob.deltas, prob.W, prob.X0, T)
     assert _rel(X, ref.X) <= X_TOL, _rel(X, ref.X)
-    np.testing.assert_allclose(res.history, ref.stress, rtol=S_TOL)
+    _hist(res, ref, prob.deltas, prob.W)
     # the returned stress is that of the returned X
-    assert abs(res.stress - O.stress_blocks([_f32(D) for D in prob.deltas], prob.W, X)) <= S_TOL * res.stress
+    d32 = [_f32(D) for D in prob.deltas]
+    assert_stress(res.stress, O.stress_blocks(d32, prob.W, X), d32, prob.W, X)
     # Guttman outputs are centred per modality
     for l in range(m):
         assert np.abs(X[l * n:(l + 1) * n].mean(0)).max() <= 1e-6 * np.abs(X).max()
@@ -77,9 +84,9 @@ def test_parity_against_float64_delta(fj):
     Delta: the float32 input rounding stays inside the same tolerances."""
     prob = synthetic.make_insample(0)
     X, res = _run(fj, prob.deltas, prob.W, prob.X0, 20)
-    ref = O.jofc_embed(prob.deltas, prob.W, prob.X0, max_iter=20)
+    ref = O.jofc_embed(prob.deltas, prob.W, prob.X0, max_iter=20, keep_iterates=True)
     assert _rel(X, ref.X) <= X_TOL
-    np.testing.assert_allclose(res.history, ref.stress, rtol=S_TOL)
+    assert_history(res.history, ref.stress, prob.deltas, prob.W, ref.iterates)
 
 
 def test_workload0_100_iterations(fj):
@@ -87,25 +94,79 @@ def test_workload0_100_iterations(fj):
     prob = synthetic.make_insample(0)
     X, res = _run(fj, prob.deltas, prob.W, prob.X0, 100)
     ref = _oracle(prob.deltas, prob.W, prob.X0, 100)
-    np.testing.assert_allclose(res.history, ref.stress, rtol=S_TOL)
+    _hist(res, ref, prob.deltas, prob.W)
+    # past the 20-transform gate the float32 and float64 trajectories may part slowly
+    # (near-flat directions of the stress); X is held to 1e-4 here, its stress to the rule
     assert _rel(X, ref.X) <= 1e-4
 
 
 def test_full_size_workload1_steps(fj):
     """Workload 1 at full size (m=2, n=5000, d=3) in the launch configuration the
-    benchmark uses: three transforms against the oracle's Cor. 1 form and blockwise
-    stress (both pinned to the dense definitions at small n)."""
+    benchmark uses: twenty transforms (the parity gate) against the oracle's Cor. 1 form,
+    X within 1e-5 after the twentieth, and the stress of iterates 0, 1, 2, 3, 5, 10, 15
+    and 20 against the oracle's blockwise stress (both oracle forms pinned to the dense
+    definitions at small n) under the parity rule."""
     prob = synthetic.make_insample(1)
-    T = 3
+    T = 20
     X, res = _run(fj, prob.deltas, prob.W, prob.X0, T)
+    assert res.status == 0 and res.iters == T
     d32 = [_f32(D) for D in prob.deltas]
     Xr = _f32(prob.X0)
-    hist = [O.stress_blocks(d32, prob.W, Xr)]
-    for _ in range(T):
-        Xr = O.guttman_step_closed_form(d32, prob.W, Xr)
-        hist.append(O.stress_blocks(d32, prob.W, Xr))
-    assert _rel(X, Xr) <= X_TOL
-    np.testing.assert_allclose(res.history, hist, rtol=S_TOL)
+    checked = (0, 1, 2, 3, 5, 10, 15, 20)
+    for t in range(T + 1):
+        if t > 0:
+            Xr = O.guttman_step_closed_form(d32, prob.W, Xr)
+        if t in checked:
+            assert_stress(res.history[t], O.stress_blocks(d32, prob.W, Xr), d32, prob.W, Xr, t)
+    assert _rel(X, Xr) <= X_TOL, _rel(X, Xr)
+
+
+def _exact_problem(n, m, d, seed):
+    """Every Delta_i holds the distances of one centred configuration Y (float32), so
+    X = [Y; ...; Y] has zero stress (Eq. stress) and is a fixed point of the transform."""
+    rng = np.random.default_rng(seed)
+    Y = rng.standard_normal((n, d))
+    Y -= Y.mean(0)
+    Y = _f32(Y)
+    Dy = np.sqrt(((Y[:, None, :] - Y[None, :, :]) ** 2).sum(-1))
+    W = synthetic.weights_matrix(m, 1.0, 0.5)
+    return Y, [Dy] * m, W, rng
+
+
+@pytest.mark.parametrize("n,m,d", [(300, 2, 2), (257, 3, 3)])
+def test_exact_configuration_fixed_point(fj, n, m, d):
+    """X_0 = [Y; ...; Y] with Delta_i = D(Y): sigma(X_0) = 0 up to float32 distances (the
+    rule's bound, with sigma = 0) and one transform returns X_0 within 1e-5."""
+    Y, deltas, W, _ = _exact_problem(n, m, d, seed=1100 + n)
+    X0 = np.vstack([Y] * m)
+    X, res = _run(fj, deltas, W, X0, 1)
+    d32 = [_f32(D) for D in deltas]
+    assert res.status == 0 and res.iters == 1
+    assert_stress(res.history[0], 0.0, d32, W, X0, "sigma(X_0)")
+    assert_stress(res.history[1], O.stress_blocks(d32, W, X), d32, W, X, "sigma(X_1)")
+    assert _rel(X, X0) <= X_TOL, _rel(X, X0)
+    ref = _oracle(deltas, W, X0, 1)
+    assert _rel(X, ref.X) <= X_TOL
+
+
+def test_exact_configuration_recovery(fj):
+    """From X_0 = [Y; Y] + 0.01 N(0, 1) the loop heads back to the zero-stress
+    configuration along the oracle's trajectory: X after 20 transforms within 1e-5 of the
+    oracle's, every stress of 200 transforms under the parity rule (whose float32
+    distance term is what remains of the tolerance as sigma falls), and sigma(X_200)
+    below 1e-6 sigma(X_0) (the float64 oracle reaches 2.8e-7 here; the slow part is the
+    rotation of one modality against the other, held only by the commensurability
+    weight)."""
+    n, m, d = 400, 2, 2
+    Y, deltas, W, rng = _exact_problem(n, m, d, seed=1200)
+    X0 = _f32(np.vstack([Y] * m) + 0.01 * rng.standard_normal((m * n, d)))
+    X, res = _run(fj, deltas, W, X0, 20)
+    ref = _oracle(deltas, W, X0, 20)
+    assert _rel(X, ref.X) <= X_TOL, _rel(X, ref.X)
+    X, res = _run(fj, deltas, W, X0, 200)
+    ref = _oracle(deltas, W, X0, 200)
+    _hist(res, ref, deltas, W)
+    assert res.history[-1] <= 1e-6 * res.history[0], (res.history[-1], res.history[0])
 
 
 def test_duplicate_points_and_nonzero_diagonal(fj):
@@ -121,7 +182,7 @@ def test_duplicate_points_and_nonzero_diagonal(fj):
     X, res = _run(fj, noisy, prob.W, X0, 15)
     ref = _oracle(prob.deltas, prob.W, X0, 15)
     assert _rel(X, ref.X) <= X_TOL
-    np.testing.assert_allclose(res.history, ref.stress, rtol=S_TOL)
+    _hist(res, ref, prob.deltas, prob.W)
 
 
 @pytest.mark.parametrize("kind", ["W2", "W3"])
@@ -141,7 +202,7 @@ def test_general_weights(fj, kind):
     X, res = _run(fj, prob.deltas, W, prob.X0, 20)
     ref = _oracle(prob.deltas, W, prob.X0, 20)
     assert _rel(X, ref.X) <= X_TOL
-    np.testing.assert_allclose(res.history, ref.stress, rtol=S_TOL)
+    _hist(res, ref, prob.deltas, W)
 
 
 @pytest.mark.parametrize("dt", ["float16", "bfloat16"])
@@ -155,9 +216,9 @@ def test_half_precision_delta(fj, dt):
     X, res = _run(fj, prob.deltas, prob.W, prob.X0, 20, dtype=dtype, scales=scales)
     rounded = [scales[i] * torch.as_tensor(prob.deltas[i] / scales[i]).to(dtype).double().numpy()
                for i in range(2)]
-    ref = O.jofc_embed(rounded, prob.W, _f32(prob.X0), max_iter=20)
+    ref = O.jofc_embed(rounded, prob.W, _f32(prob.X0), max_iter=20, keep_iterates=True)
     assert _rel(X, ref.X) <= X_TOL
-    np.testing.assert_allclose(res.history, ref.stress, rtol=S_TOL)
+    assert_history(res.history, ref.stress, rounded, prob.W, ref.iterates)
 
 
 @pytest.mark.parametrize("mode,tol", [("relative", 1e-4), ("abs_normalized", 1e-5)])
@@ -184,12 +245,13 @@ def test_max_iter_zero_and_stress_entry(fj):
     X, res = _run(fj, prob.deltas, prob.W, X0, 0)
     assert res.iters == 0
     np.testing.assert_array_equal(X, _f32(X0))
-    ref = O.stress_blocks([_f32(D) for D in prob.deltas], prob.W, _f32(X0))
-    assert abs(res.stress - ref) <= S_TOL * ref
+    d32 = [_f32(D) for D in prob.deltas]
+    ref = O.stress_blocks(d32, prob.W, _f32(X0))
+    assert_stress(res.stress, ref, d32, prob.W, _f32(X0))
     dev = [fj.to_device_delta(D) for D in prob.deltas]
     Xt = torch.as_tensor(np.asarray(X0, np.float32)).cuda()
     s = fj.stress(dev, prob.W, Xt)
-    assert abs(s - ref) <= S_TOL * ref
+    assert_stress(s, ref, d32, prob.W, _f32(X0))
     np.testing.assert_array_equal(Xt.cpu().numpy(), np.asarray(X0, np.float32))
 
 
@@ -273,7 +335,7 @@ def test_relaxed_updates_match_oracle(fj, m, n, d, relax):
     X, r = outs[0]
     assert r.status == 0 and r.iters == 20
     assert _rel(X, ref.X) <= X_TOL
-    np.testing.assert_allclose(r.history, ref.stress, rtol=S_TOL)
+    assert_history(r.history, ref.stress, [_f32(D) for D in prob.deltas], prob.W, ref.iterates)
     np.testing.assert_array_equal(outs[1][0], X)
     np.testing.assert_array_equal(outs[1][1].history, r.history)
 

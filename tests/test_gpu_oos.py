@@ -5,6 +5,8 @@ after T transforms must match the oracle's dense Eq. (joosupdate) iteration (sma
 its pinned O(nmd) form (large n) within relative error 1e-5 per object, stresses within
 1e-6.  Cases: k not a multiple of the object group, n not a multiple of the point tile,
 general weights, float16 delta, per-object stopping, exact-configuration fixed points.
+Stresses follow the parity rule of ``tests/parity_rule.py`` (1e-6 relative plus the
+fidelity error float32 distances alone cause, which decides only near zero stress).
 Each case runs both kernel forms: the streaming one (one warp slot per object, the
 dissimilarities streamed every iteration) and the resident one (one CTA per object with
 -X^T and the object's dissimilarities in shared memory; d <= 8).
@@ -14,6 +16,7 @@ import pytest
 
 from oracle import fjofc_oracle as O
 import synthetic
+from parity_rule import X_TOL, oos_stress_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -75,8 +78,8 @@ def test_oos_parity_fixed_iterations(fj, m, n, d, k, form):
     for o in range(k):
         ref = oracle(X, _f32(dnew[o]), _f32(Y0[o]), prob.W, max_iter=T)
         err = np.linalg.norm(Y[o] - ref.y) / np.linalg.norm(ref.y)
-        assert err <= 1e-5, (o, err)
-        assert abs(sig[o] - ref.stress[-1]) <= 1e-6 * ref.stress[-1]
+        assert err <= X_TOL, (o, err)
+        assert abs(sig[o] - ref.stress[-1]) <= oos_stress_tol(ref.stress[-1], X, _f32(dnew[o]), ref.y, prob.W)
     assert abs(res.stress_sum - sig.sum()) <= 1e-12 * sig.sum()
 
 
@@ -93,8 +96,8 @@ def test_oos_full_size_workload(fj):
     sig = st.cpu().numpy()
     for o in range(0, 40, 3):
         ref = O.oos_embed_closed_form(X, _f32(dnew[o]), _f32(Y0[o]), prob.W, max_iter=T)
-        assert np.linalg.norm(Y[o] - ref.y) / np.linalg.norm(ref.y) <= 1e-5
-        assert abs(sig[o] - ref.stress[-1]) <= 1e-6 * ref.stress[-1]
+        assert np.linalg.norm(Y[o] - ref.y) / np.linalg.norm(ref.y) <= X_TOL
+        assert abs(sig[o] - ref.stress[-1]) <= oos_stress_tol(ref.stress[-1], X, _f32(dnew[o]), ref.y, prob.W)
 
 
 @pytest.mark.parametrize("form", FORMS)
@@ -154,7 +157,10 @@ def test_oos_exact_configuration_fixed_point(fj, form):
     dn, Xd, Yd, it, st = _device_inputs(fj, X, dnew, Y0)
     fj.oos(Xd, dn, W, Yd, max_iter=5, stress_out=st, form=form)
     np.testing.assert_allclose(Yd.cpu().numpy(), Y0, atol=2e-5)
-    assert float(st.max()) < 1e-6
+    sig = st.cpu().numpy()
+    for o in range(len(idx)):
+        # the oracle's stress there is zero: the rule leaves the float32 distance term
+        assert sig[o] <= oos_stress_tol(0.0, X, dnew[o], Y0[o], W), (o, sig[o])
 
 
 def test_oos_forms_agree_and_auto_picks_resident_for_few_objects(fj):

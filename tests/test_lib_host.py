@@ -33,7 +33,7 @@ def test_header_declares_expected_api():
                                             "fjofc_mlp_gradient", "fjofc_mlp_train", "fjofc_mlp_broadcast",
                                             "fjofc_mlp_select", "fjofc_plan_create", "fjofc_plan_run",
                                             "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy",
-                                            "fjofc_plan_autotune", "fjofc_init_cmds"])
+                                            "fjofc_plan_autotune", "fjofc_init_cmds", "fjofc_test_barrier_skew"])
 
 
 def test_library_loads_and_exports_every_declared_symbol():
@@ -57,11 +57,16 @@ class _Call:
         self.lib.fjofc_embed.restype = ctypes.c_int
 
     def embed(self, m=2, n=8, d=2, ld=8, dtype=0, W=None, ptr=4096, X=8192, max_iter=5, tol_mode=1,
-              scales=None, relax=0.0):
+              scales=None, relax=0.0, **fields):
         fj = self.fj
         W = np.array([[1.0, 0.5], [0.5, 1.0]]) if W is None else np.asarray(W, dtype=np.float64)
         ptrs = (ctypes.c_void_p * max(m, 1))(*([ptr] * max(m, 1)))
         opts = fj._Opts(max_iter, -1.0, tol_mode, 0, relax)
+        for k, v in fields.items():
+            if k == "reserved":
+                opts.reserved[0] = v
+            else:
+                setattr(opts, k, v)
         sc = None if scales is None else (ctypes.c_float * m)(*scales)
         return self.lib.fjofc_embed(ctypes.c_int32(m), ctypes.c_int64(n), ctypes.c_int32(d), ptrs,
                                     ctypes.c_int64(ld), ctypes.c_int32(dtype), sc,
@@ -96,6 +101,10 @@ def call():
     (dict(relax=2.5), -1),                  # relaxed updates only up to 2
     (dict(relax=-0.5), -1),
     (dict(relax=float("nan")), -1),
+    (dict(check_inputs=2), -1),             # the new option fields take 0 or 1 ...
+    (dict(deterministic=-1), -1),
+    (dict(wait_limit_us=-5), -1),           # ... and a non-negative wait bound
+    (dict(reserved=1), -1),
 ])
 def test_invalid_arguments_rejected_before_cuda(call, kw, code):
     assert call.embed(**kw) == code

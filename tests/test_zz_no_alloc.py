@@ -1,15 +1,17 @@
 """fjofc_embed_noalloc against fjofc_embed, through the C ABI.
 
 fjofc_embed_noalloc serves callers that cannot allocate device memory while they run
-(host callbacks and driver-managed contexts where cudaMalloc is not allowed, real-time
-loops that must stay out of every allocator after start-up, processes whose device
-memory is partitioned at launch).  It runs the same kernels in one fixed device array
-inside the library.  This test calls it twice in a row, on two different problems, and
-checks each result against fjofc_embed on the same inputs with the parity tolerances
-(X within relative Frobenius 1e-5, stress within 1e-6 relative); the second call runs
-in the array the first call left behind.  It also checks that a problem too large for
-the array is refused.  This file is collected last (its name) so that a run that stops
-at the first failure has run every other test first; it also passes alone.
+(real-time loops that must stay out of every allocator after start-up, processes whose
+device memory is partitioned at launch, code that must not fail part-way for lack of
+memory).  It runs the same kernels in one fixed device array inside the library.  This
+test calls it twice in a row, on two different problems, and checks each result against
+fjofc_embed on the same inputs with the parity tolerances (X within relative Frobenius
+1e-5, stress within 1e-6 relative); the second call runs in the array the first call
+left behind.  It checks that a call after the first one on the device allocates nothing
+from the device's stream-ordered memory pool (the allocator fjofc_embed uses), and that
+a problem too large for the array is refused.  This file is collected last (its name) so
+that a run that stops at the first failure has run every other test first; it also
+passes alone.
 """
 import ctypes
 
@@ -87,3 +89,66 @@ def test_noalloc_refuses_problems_beyond_its_array(env):
     st, res, _ = _noalloc(torch, fj, lib, dev, synthetic.weights_matrix(2), X, 3, -1.0, "relative")
     assert st == fj.FJOFC_ERR_UNSUPPORTED
     assert "scratch" in fj.strerror(st)
+
+
+def _cudart():
+    import ctypes.util
+    for name in (ctypes.util.find_library("cudart"), "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+        if not name:
+            continue
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    return None
+
+
+class _Pool:
+    """Used-memory high-water mark of the current device's default memory pool (the pool
+    cudaMallocAsync draws from), read and reset through the CUDA runtime."""
+    USED_CURRENT, USED_HIGH, RESERVED_CURRENT = 7, 8, 5
+
+    def __init__(self, rt, dev):
+        self.rt = rt
+        self.pool = ctypes.c_void_p()
+        assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(self.pool), ctypes.c_int(dev)) == 0
+
+    def get(self, attr):
+        v = ctypes.c_uint64(0)
+        assert self.rt.cudaMemPoolGetAttribute(self.pool, ctypes.c_int(attr), ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):
+        zero = ctypes.c_uint64(0)
+        assert self.rt.cudaMemPoolSetAttribute(self.pool, ctypes.c_int(self.USED_HIGH), ctypes.byref(zero)) == 0
+
+
+def test_noalloc_call_allocates_nothing(env):
+    """After the first call on the device (which may load device code), a call leaves the
+    pool's used-memory high-water mark where it was; an ordinary fjofc_embed call on the
+    same problem raises it (the probe sees the library's allocations)."""
+    torch, fj, lib = env
+    rt = _cudart()
+    if rt is None:
+        pytest.skip("CUDA runtime library not found for the memory-pool probe")
+    prob = synthetic.make_insample(0, n=700, m=2, d=3, seed=903)
+    dev = [fj.to_device_delta(D) for D in prob.deltas]
+    X0 = torch.as_tensor(np.asarray(prob.X0, np.float32)).cuda()
+    X = X0.clone()
+    st, _, _ = _noalloc(torch, fj, lib, dev, prob.W, X, 10, -1.0, "relative")      # start-up call
+    assert st == 0, fj.strerror(st)
+    torch.cuda.synchronize()
+    pool = _Pool(rt, torch.cuda.current_device())
+    pool.reset_high()
+    used0 = pool.get(_Pool.USED_CURRENT)
+    X = X0.clone()
+    st, _, _ = _noalloc(torch, fj, lib, dev, prob.W, X, 10, -1.0, "relative")
+    torch.cuda.synchronize()
+    assert st == 0, fj.strerror(st)
+    assert pool.get(_Pool.USED_HIGH) == used0
+    assert pool.get(_Pool.USED_CURRENT) == used0
+    # control: the allocating entry point draws its scratch from this pool
+    X = X0.clone()
+    fj.embed(dev, prob.W, X, max_iter=10)
+    torch.cuda.synchronize()
+    assert pool.get(_Pool.USED_HIGH) > used0
