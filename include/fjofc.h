@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define FJOFC_MAX_M 8
+#define FJOFC_MAX_M 32
 #define FJOFC_MAX_D 16
 
 /* status codes */

@@ -31,7 +31,7 @@ FJOFC_ERR_UNSUPPORTED = -6
 
 F32, F16, BF16 = 0, 1, 2
 TOL_ABS_NORMALIZED, TOL_RELATIVE = 0, 1
-MAX_M, MAX_D = 8, 16
+MAX_M, MAX_D = 32, 16
 
 # Every symbol declared in include/fjofc.h.
 EXPORTS = ("fjofc_embed", "fjofc_embed_noalloc", "fjofc_stress", "fjofc_oos", "fjofc_strerror", "fjofc_version",

@@ -204,18 +204,18 @@ cudaError_t k3_launch_dt(int d, int grid, const CUtensorMap& tm, const K3Params&
     return cudaErrorInvalidValue;
 }
 template <typename TD>
-int k3_bps_dt(int d) {
+int k3_bps_dt(int d, int m) {
     switch (d) {
-#define C_(D) case D: return k3_bps_impl<D, TD>();
+#define C_(D) case D: return k3_bps_impl<D, TD>(m);
         C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13) C_(14) C_(15) C_(16)
 #undef C_
     }
     return 0;
 }
 template <typename TD>
-K3Geom k3_geom_dt(int d) {
+K3Geom k3_geom_dt(int d, int m) {
     switch (d) {
-#define C_(D) case D: return k3_geom_impl<D, TD>();
+#define C_(D) case D: return k3_geom_impl<D, TD>(m);
         C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(9) C_(10) C_(11) C_(12) C_(13) C_(14) C_(15) C_(16)
 #undef C_
     }
@@ -385,6 +385,7 @@ int InsampleSetup::plan(int m_, int64_t n_, int d_, int dtype_, const fjofc_opts
     o_cbase = cv.take<int64_t>(size_t(P.nRB));
     o_contr = cv.take<int2>(size_t(m) * P.nRB);
     o_bar = cv.take<unsigned>(1);
+    o_tab = cv.take<float>(2 * size_t(m) * m);
     bytes = (cv.off + 255) & ~size_t(255);
     return FJOFC_OK;
 }
@@ -447,11 +448,10 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
     k2.centre = (k2.relax == 1.f) ? 1 : 0;
     k2.npairs = double(m * n) * double(m * n - 1) / 2.0;
     k2.inv_n = float(1.0 / double(n));
-    for (int j = 0; j < m; ++j)
-        for (int l = 0; l < m; ++l) {
-            k2.coef[j][l] = float(winv[j * m + l] * weights[l * m + l] * dsc[l]);
-            k2.wcomm[j][l] = (j < l) ? float(weights[j * m + l]) : 0.f;
-        }
+    float* coef_g = reinterpret_cast<float*>(base + o_tab);
+    float* wcomm_g = coef_g + size_t(m) * m;
+    k2.coef_g = coef_g;
+    k2.wcomm_g = wcomm_g;
     unsigned* bar = reinterpret_cast<unsigned*>(base + o_bar);
     k2.tb.colpart = k1.colpart;
     k2.tb.rowhead = k1.rowhead;
@@ -461,9 +461,23 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
     k2.tb.Tm = P.Tm;
     k2.tb.d = d; k2.tb.RB = RB; k2.tb.CW = CW; k2.tb.rb_shift = k2.rb_shift; k2.tb.cw_shift = k2.cw_shift;
     k2.tb.nRB = P.nRB;
-    ip = InitParams{st, k2.ticket, k2.mu, const_cast<int64_t*>(k1.walk_off), const_cast<int64_t*>(k2.cta_start),
+    ip = InitParams{coef_g, wcomm_g, {}, {}, st, k2.ticket, k2.mu, const_cast<int64_t*>(k1.walk_off), const_cast<int64_t*>(k2.cta_start),
                     bar, const_cast<int64_t*>(k2.tb.cbase), const_cast<int2*>(k2.tb.cont), m, int(n), RB, CW,
                     P.nRB, P.G, P.T, P.Tm};
+    // the per-object mix: [Wmod^-1]_{jl} w_ll s_l and the commensurability weights, in
+    // the set-up kernel's parameters (written to global memory for any m) and, for
+    // m <= kMSmall, in the kernels' own parameters (their fast path)
+    for (int j = 0; j < m; ++j)
+        for (int l = 0; l < m; ++l) {
+            const float c = float(winv[j * m + l] * weights[l * m + l] * dsc[l]);
+            const float w = (j < l) ? float(weights[j * m + l]) : 0.f;
+            ip.coef[j * m + l] = c;
+            ip.wcomm[j * m + l] = w;
+            if (m <= kMSmall) {
+                k2.coef[j][l] = c;
+                k2.wcomm[j][l] = w;
+            }
+        }
 
     pp = PersistParams{};
     pp.k1 = k1;
@@ -481,8 +495,10 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
     pp.relax = k2.relax; pp.centre = k2.centre;
     pp.bar_skew = 0;
     pp.wait_ns = wait_limit_ns(o);
-    for (int j = 0; j < FJOFC_MAX_M; ++j)
-        for (int l = 0; l < FJOFC_MAX_M; ++l) { pp.coef[j][l] = k2.coef[j][l]; pp.wcomm[j][l] = k2.wcomm[j][l]; }
+    for (int j = 0; j < kMSmall; ++j)
+        for (int l = 0; l < kMSmall; ++l) { pp.coef[j][l] = k2.coef[j][l]; pp.wcomm[j][l] = k2.wcomm[j][l]; }
+    pp.coef_g = k2.coef_g;
+    pp.wcomm_g = k2.wcomm_g;
     pp.tb = k2.tb;
     return FJOFC_OK;
 }
@@ -755,8 +771,12 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
         return FJOFC_ERR_UNSUPPORTED;
     }
     if ((rc = get_encoder())) return rc;
-    const K3Geom g = (dtype == FJOFC_F32) ? k3_geom_dt<float>(d) : (dtype == FJOFC_F16) ? k3_geom_dt<__half>(d)
-                                                                                      : k3_geom_dt<__nv_bfloat16>(d);
+    const K3Geom g = (dtype == FJOFC_F32) ? k3_geom_dt<float>(d, m) : (dtype == FJOFC_F16) ? k3_geom_dt<__half>(d, m)
+                                                                                         : k3_geom_dt<__nv_bfloat16>(d, m);
+    if (!resident && g.WARPS < 1) {
+        snprintf(g_last_msg, sizeof(g_last_msg), "the streaming out-of-sample form does not fit m=%d at d=%d", m, d);
+        return FJOFC_ERR_UNSUPPORTED;
+    }
 
     Carver cv;
     const size_t o_xt = cv.take<float>(size_t(m) * d * nx);
@@ -766,6 +786,8 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
     const size_t o_it = cv.take<int32_t>(size_t(k));
     const size_t o_sig = cv.take<double>(size_t(k));
     const size_t o_sum = cv.take<double>(2);
+    const size_t o_winv = cv.take<float>(size_t(m) * m);
+    const size_t o_wcomm = cv.take<double>(size_t(m) * m);
     const size_t total = cv.off;
     ScopedDeviceMem mem;
     mem.s = stream;
@@ -805,17 +827,28 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
         p.wfid[j] = j < m ? float(weights[j * m + j]) : 0.f;
         p.dscale[j] = (j < m && delta_scale) ? delta_scale[j] : 1.f;
     }
-    for (int j = 0; j < m; ++j)
-        for (int l = 0; l < m; ++l) {
-            p.winv[j][l] = float(winv[j * m + l]);
-            p.wcomm[j][l] = (j != l) ? weights[j * m + l] : 0.0;
-        }
+    p.winv = reinterpret_cast<const float*>(base + o_winv);
+    p.wcomm = reinterpret_cast<const double*>(base + o_wcomm);
+    p.warp_bytes = g.smem_bytes;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     FJ_CUDA(cudaEventCreate(&ev0));
     FJ_CUDA(cudaEventCreate(&ev1));
     FJ_CUDA(cudaEventRecord(ev0, stream));
-    OOSPrepParams pp{X, const_cast<float*>(p.XT), const_cast<float*>(p.SX), m, int(n), nx, d, p.next_block, st};
+    OOSPrepParams pp{};
+    pp.X = X;
+    pp.XT = const_cast<float*>(p.XT);
+    pp.SX = const_cast<float*>(p.SX);
+    pp.winv_g = reinterpret_cast<float*>(base + o_winv);
+    pp.wcomm_g = reinterpret_cast<double*>(base + o_wcomm);
+    for (int j = 0; j < m; ++j)
+        for (int l = 0; l < m; ++l) {
+            pp.winv[j * m + l] = float(winv[j * m + l]);
+            pp.wcomm[j * m + l] = (j != l) ? weights[j * m + l] : 0.0;
+        }
+    pp.m = m; pp.n = int(n); pp.nx = nx; pp.d = d;
+    pp.next_block = p.next_block;
+    pp.st = st;
     FJ_CUDA(launch_oos_prep(pp, stream));
     cudaError_t e;
     if (resident) {
@@ -825,8 +858,8 @@ int run_oos(int32_t m, int64_t n, int32_t d, int64_t k, const float* X, const vo
           : (dtype == FJOFC_F16) ? k3r_launch_dt<__half>(d, int(grid), p, stream)
                                  : k3r_launch_dt<__nv_bfloat16>(d, int(grid), p, stream);
     } else {
-        const int bps = std::max(1, (dtype == FJOFC_F32) ? k3_bps_dt<float>(d) : (dtype == FJOFC_F16) ? k3_bps_dt<__half>(d)
-                                                                                                  : k3_bps_dt<__nv_bfloat16>(d));
+        const int bps = std::max(1, (dtype == FJOFC_F32) ? k3_bps_dt<float>(d, m)
+                                    : (dtype == FJOFC_F16) ? k3_bps_dt<__half>(d, m) : k3_bps_dt<__nv_bfloat16>(d, m));
         const int64_t groups = (k + g.R - 1) / g.R;
         int64_t grid = int64_t(bps) * sm_count();
         const int64_t need = (groups + g.WARPS - 1) / g.WARPS;
@@ -936,6 +969,6 @@ const char* fjofc_strerror(int status) {
 
 void fjofc_test_barrier_skew(int32_t extra) { g_barrier_skew.store(extra > 0 ? extra : 0); }
 
-const char* fjofc_version(void) { return "fjofc-gb300 0.1 (sm_103a; d=1..16; m<=8; f32/f16/bf16 Delta)"; }
+const char* fjofc_version(void) { return "fjofc-gb300 0.2 (sm_103a; d=1..16; m<=32; f32/f16/bf16 Delta)"; }
 
 }  // extern "C"

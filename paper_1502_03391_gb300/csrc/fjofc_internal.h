@@ -12,6 +12,11 @@ namespace fjofc {
 
 struct DevStatus;
 
+// Modalities whose per-object mix runs from register arrays and shared-memory tables of
+// this size (the fast path of phase B); larger m (up to FJOFC_MAX_M) uses rolled loops over
+// the m x m tables in global memory that the set-up kernel writes.
+constexpr int kMSmall = 8;
+
 // Tensor maps of the m dissimilarity matrices (one 2-D map per modality), passed to
 // the kernels as a __grid_constant__ parameter.
 struct TMaps {
@@ -91,8 +96,10 @@ struct K2Params {
     float inv_n;               // 1 / n (column means)
     float relax;               // relaxed update factor (1: the plain Guttman transform)
     int centre;                // 1: centre X_{t-1} in place with its column means (relax == 1)
-    float coef[FJOFC_MAX_M][FJOFC_MAX_M];    // [Wmod^-1]_{jl} * w_ll * s_l
-    float wcomm[FJOFC_MAX_M][FJOFC_MAX_M];   // w_jl for j < l, else 0
+    float coef[kMSmall][kMSmall];    // [Wmod^-1]_{jl} * w_ll * s_l (m <= kMSmall)
+    float wcomm[kMSmall][kMSmall];   // w_jl for j < l, else 0 (m <= kMSmall)
+    const float* coef_g;             // the same two tables, m x m row-major, global (any m)
+    const float* wcomm_g;
     BxTables tb;
 };
 
@@ -117,8 +124,10 @@ struct PersistParams {
     int centre;                 // 1: centre X_{t-1} in place with its column means
     unsigned bar_skew;          // extra arrivals the first grid-wide wait expects (0; test support)
     unsigned long long wait_ns; // bound of every grid-wide wait
-    float coef[FJOFC_MAX_M][FJOFC_MAX_M];
-    float wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
+    float coef[kMSmall][kMSmall];
+    float wcomm[kMSmall][kMSmall];
+    const float* coef_g;        // m x m tables in global memory (any m; see K2Params)
+    const float* wcomm_g;
     BxTables tb;
 };
 
@@ -131,6 +140,10 @@ struct BatchLaunch {
 };
 
 struct InitParams {
+    float* coef_g;             // destinations of the m x m tables below (global memory)
+    float* wcomm_g;
+    float coef[FJOFC_MAX_M * FJOFC_MAX_M];    // [Wmod^-1]_{jl} w_ll s_l, row-major m x m
+    float wcomm[FJOFC_MAX_M * FJOFC_MAX_M];   // w_jl for j < l, else 0
     DevStatus* st;
     unsigned* ticket;
     float* mu;
@@ -185,8 +198,9 @@ struct K3Params {
     double tol, npairs;
     float wfid[FJOFC_MAX_M];
     float dscale[FJOFC_MAX_M];
-    float winv[FJOFC_MAX_M][FJOFC_MAX_M];    // Wmod^-1
-    double wcomm[FJOFC_MAX_M][FJOFC_MAX_M];  // w_jl, j != l (per-object stress, once per pass)
+    const float* winv;         // Wmod^-1, m x m row-major (global memory, written by the set-up kernel)
+    const double* wcomm;       // w_jl, j != l, m x m (per-object stress, once per pass)
+    size_t warp_bytes;         // streaming form: shared memory of one warp (depends on m)
 };
 
 // ---------------------------------------------------------------------------
@@ -221,7 +235,8 @@ struct InsampleSetup {
     int64_t n = 0;
     fjofc_opts o{};
     size_t o_buf1 = 0, o_buf2 = 0, o_col = 0, o_head = 0, o_cont = 0, o_fid = 0, o_woff = 0, o_cta = 0, o_mu = 0,
-           o_bpart = 0, o_ticket = 0, o_st = 0, o_hist = 0, o_fid2 = 0, o_cbase = 0, o_contr = 0, o_bar = 0;
+           o_bpart = 0, o_ticket = 0, o_st = 0, o_hist = 0, o_fid2 = 0, o_cbase = 0, o_contr = 0, o_bar = 0,
+           o_tab = 0;
     size_t bytes = 0;
     TMaps tm;
     K1Params k1;
@@ -244,6 +259,10 @@ struct OOSPrepParams {
     const float* X;
     float* XT;
     float* SX;
+    float* winv_g;             // destinations of the m x m tables below
+    double* wcomm_g;
+    float winv[FJOFC_MAX_M * FJOFC_MAX_M];
+    double wcomm[FJOFC_MAX_M * FJOFC_MAX_M];
     int m, n, nx, d;
     unsigned long long* next_block;
     DevStatus* st;

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(K2_THREADS)
 k_apply(const K2Params p) {
     extern __shared__ float s_dyn[];             // d * phase_b_floats_per_unit(m)
     __shared__ float s_mu[FJOFC_MAX_M * FJOFC_MAX_D];
-    __shared__ float s_coef[FJOFC_MAX_M][FJOFC_MAX_M], s_wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
+    __shared__ float s_coef[kMSmall][kMSmall], s_wcomm[kMSmall][kMSmall];
     __shared__ bool s_last;
 
     if (ld_volatile(&p.st->done)) return;
@@ -37,9 +37,9 @@ k_apply(const K2Params p) {
     const float* mu_prev = p.mu + ((p.t - 1) & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
     float* mu_next = p.mu + (p.t & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
     for (int e = tid; e < FJOFC_MAX_M * FJOFC_MAX_D; e += K2_THREADS) s_mu[e] = mu_prev[e];
-    for (int e = tid; e < FJOFC_MAX_M * FJOFC_MAX_M; e += K2_THREADS) {
-        s_coef[e / FJOFC_MAX_M][e % FJOFC_MAX_M] = p.coef[e / FJOFC_MAX_M][e % FJOFC_MAX_M];
-        s_wcomm[e / FJOFC_MAX_M][e % FJOFC_MAX_M] = p.wcomm[e / FJOFC_MAX_M][e % FJOFC_MAX_M];
+    for (int e = tid; e < kMSmall * kMSmall; e += K2_THREADS) {
+        s_coef[e / kMSmall][e % kMSmall] = p.coef[e / kMSmall][e % kMSmall];
+        s_wcomm[e / kMSmall][e % kMSmall] = p.wcomm[e / kMSmall][e % kMSmall];
     }
     __syncthreads();
 
@@ -49,8 +49,11 @@ k_apply(const K2Params p) {
     a.Xnext = p.Xnext;
     a.bpart = p.bpart;
     a.mu_prev = s_mu;
+    a.mu_stride = FJOFC_MAX_D;
     a.coef = s_coef;
     a.wcomm = s_wcomm;
+    a.coef_g = p.coef_g;
+    a.wcomm_g = p.wcomm_g;
     a.m = m; a.n = n; a.d = d; a.t = p.t; a.ngroups = p.nbx;
     a.centre = p.centre != 0;
     a.relax = p.relax;
@@ -74,7 +77,8 @@ k_apply(const K2Params p) {
     __shared__ FF s_tot[FJOFC_MAX_M * FJOFC_MAX_D + FJOFC_MAX_D + 1];
     pass_totals(p.bpart, npart, int(gridDim.x), p.fid, p.G, s_tot);
     __syncthreads();
-    if (tid < m * d) mu_next[(tid / d) * FJOFC_MAX_D + (tid % d)] = (s_tot[tid].hi + s_tot[tid].lo) * p.inv_n;
+    for (int e = tid; e < m * d; e += K2_THREADS)
+        mu_next[(e / d) * FJOFC_MAX_D + (e % d)] = (s_tot[e].hi + s_tot[e].lo) * p.inv_n;
 
     if (tid == 0) {
         const double sigma = stress_from_totals(s_tot, s_tot[npart], m, d);
@@ -106,6 +110,10 @@ int k2_blocks(int n) { return (n + kGroupObjects - 1) / kGroupObjects; }
 
 cudaError_t launch_k2(const K2Params& p, cudaStream_t s) {
     const size_t smem = size_t(p.d) * phase_b_floats_per_unit(p.m) * sizeof(float);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+    }
     k_apply<<<p.nbx, K2_THREADS, smem, s>>>(p);
     return cudaGetLastError();
 }
@@ -127,6 +135,10 @@ __device__ __forceinline__ int64_t walk_len(int P, const InitParams& p) {
 __device__ __forceinline__ void init_problem(const InitParams& p) {
     __shared__ int64_t s_part[kInitThreads];
     const int tid = threadIdx.x;
+    for (int e = tid; e < p.m * p.m; e += kInitThreads) {
+        p.coef_g[e] = p.coef[e];
+        p.wcomm_g[e] = p.wcomm[e];
+    }
     if (tid == 0) {
         p.st->done = 0;
         p.st->error = 0;
@@ -191,7 +203,7 @@ __device__ __forceinline__ void init_problem(const InitParams& p) {
     }
 }
 
-__global__ void __launch_bounds__(kInitThreads) k_init(const InitParams p) { init_problem(p); }
+__global__ void __launch_bounds__(kInitThreads) k_init(const __grid_constant__ InitParams p) { init_problem(p); }
 
 // One CTA per problem of a batch.
 __global__ void __launch_bounds__(kInitThreads) k_init_batched(const InitParams* __restrict__ ps) {
@@ -314,8 +326,13 @@ namespace fjofc {
 // Out-of-sample set-up: X transposed to [m][d][nx] (row stride nx, a multiple of 4 so
 // that vector loads stay aligned), the column sums of every X^(j) in float64 (fixed
 // order per block), the group counter and the status block.
-__global__ void k_oos_prep(const OOSPrepParams p) {
+__global__ void k_oos_prep(const __grid_constant__ OOSPrepParams p) {
     const int j = blockIdx.x / p.d, kk = blockIdx.x - j * p.d;
+    if (blockIdx.x == 0)
+        for (int e = threadIdx.x; e < p.m * p.m; e += blockDim.x) {
+            p.winv_g[e] = p.winv[e];
+            p.wcomm_g[e] = p.wcomm[e];
+        }
     __shared__ double sh[32];
     double s = 0.0;
     for (int i = threadIdx.x; i < p.nx; i += blockDim.x) {

@@ -137,8 +137,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
     const K1Params& p = P.k1;
 
     __shared__ FF s_ff[CWARPS];
-    __shared__ float s_mu[FJOFC_MAX_M * FJOFC_MAX_D];
-    __shared__ float s_coef[FJOFC_MAX_M][FJOFC_MAX_M], s_wcomm[FJOFC_MAX_M][FJOFC_MAX_M];
+    __shared__ float s_coef[kMSmall][kMSmall], s_wcomm[kMSmall][kMSmall];
     __shared__ int s_abort, s_issued, s_flag, s_stop, s_final;
     __shared__ double s_prev;
 
@@ -155,11 +154,14 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
 
     K1Ring<D, TD> rg;
     rg.carve(smem_raw);
-    // phases C and B reuse the column-partial ring (free between passes)
+    // phases C and B reuse the column-partial ring (free between passes), and the means of
+    // X_{t-1} ([m][D], from phase C to phase B) sit in the walk rows of phase A
     float* s_phb = rg.red;
-    FF* s_tot = reinterpret_cast<FF*>(rg.red);     // [MAX_M*MAX_D + MAX_D + 1], phase C only
-    static_assert(S::RED_FLOATS * sizeof(float) >= (FJOFC_MAX_M * FJOFC_MAX_D + FJOFC_MAX_D + 1) * sizeof(FF),
+    FF* s_tot = reinterpret_cast<FF*>(rg.red);     // [m*D + D + 1], phase C only
+    float* s_mu = rg.xrow;
+    static_assert(S::RED_FLOATS * sizeof(float) >= (FJOFC_MAX_M * D + D + 1) * sizeof(FF),
                   "phase-C totals do not fit");
+    static_assert(S::XROW_FLOATS >= FJOFC_MAX_M * D, "the means do not fit in the walk rows");
     const int bcap = int(S::RED_FLOATS / size_t(phase_b_floats_per_unit(m)));
     static_assert(S::RED_FLOATS >= size_t(phase_b_floats_per_unit(FJOFC_MAX_M)), "phase-B overlay does not fit");
 
@@ -171,10 +173,9 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
         s_final = 0;
         s_prev = 0.0;
     }
-    for (int e = tid; e < FJOFC_MAX_M * FJOFC_MAX_D; e += NT) s_mu[e] = 0.f;
-    for (int e = tid; e < FJOFC_MAX_M * FJOFC_MAX_M; e += NT) {
-        s_coef[e / FJOFC_MAX_M][e % FJOFC_MAX_M] = P.coef[e / FJOFC_MAX_M][e % FJOFC_MAX_M];
-        s_wcomm[e / FJOFC_MAX_M][e % FJOFC_MAX_M] = P.wcomm[e / FJOFC_MAX_M][e % FJOFC_MAX_M];
+    for (int e = tid; e < kMSmall * kMSmall; e += NT) {
+        s_coef[e / kMSmall][e % kMSmall] = P.coef[e / kMSmall][e % kMSmall];
+        s_wcomm[e / kMSmall][e % kMSmall] = P.wcomm[e / kMSmall][e % kMSmall];
     }
     // ring over every pass's sub-tiles; Delta does not change, so it prefetches the next
     // pass's first sub-tiles while phase B runs
@@ -234,9 +235,8 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
                     P.fid2 + ((t - 1) & 1) * G, t >= 2 ? G : 0, s_tot);
         __syncthreads();
         FJ_STAMP(t, 5);
-        if (tid < m * D)
-            s_mu[(tid / D) * FJOFC_MAX_D + (tid % D)] =
-                (t >= 2 && t - 1 < passes) ? (s_tot[tid].hi + s_tot[tid].lo) * P.inv_n : 0.f;
+        for (int e = tid; e < m * D; e += NT)
+            s_mu[e] = (t >= 2 && t - 1 < passes) ? (s_tot[e].hi + s_tot[e].lo) * P.inv_n : 0.f;
         if (tid == 0) {
             int stop = 0;
             if (t >= 2) {
@@ -289,8 +289,11 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
             a.Xnext = Xnext;
             a.bpart = P.bpart + int64_t(t & 1) * P.ngroups * npart;
             a.mu_prev = s_mu;
+            a.mu_stride = D;
             a.coef = s_coef;
             a.wcomm = s_wcomm;
+            a.coef_g = P.coef_g;
+            a.wcomm_g = P.wcomm_g;
             a.m = m; a.n = n; a.d = D; a.t = t; a.ngroups = P.ngroups;
             a.centre = P.centre != 0;
             a.relax = P.relax;

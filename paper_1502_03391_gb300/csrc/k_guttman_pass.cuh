@@ -735,7 +735,7 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
 // not: per-kernel timing).  Same ring, tiles and partials as the persistent kernel.
 template <int D, typename TD>
 __global__ void __launch_bounds__(K1Shape<D, TD>::NT, FJOFC_K1_MINB)
-k_guttman_pass(const __grid_constant__ TMaps tm, const K1Params p) {
+k_guttman_pass(const __grid_constant__ TMaps tm, const __grid_constant__ K1Params p) {
     using S = K1Shape<D, TD>;
     constexpr int CWARPS = S::CWARPS;
     extern __shared__ unsigned char smem_raw[];

@@ -50,17 +50,25 @@ struct K3Shape {
     static constexpr int STAGE_ELEMS = R * CW;
     static constexpr uint32_t STAGE_BYTES = STAGE_ELEMS * sizeof(TD);
     static constexpr int STAGES = (16384 / int(STAGE_BYTES)) < 4 ? 4 : ((16384 / int(STAGE_BYTES)) > 8 ? 8 : (16384 / int(STAGE_BYTES)));
-    // per warp: ring, y state, reduced sums (sum b x: D, sum b: 1), fid (double)
+    // per warp: ring, y state, reduced sums (sum b x: D, sum b: 1), fid (double); the
+    // per-slot arrays hold m modalities, so a warp's share depends on m
     static constexpr size_t RING_BYTES = size_t(STAGES) * STAGE_BYTES;
-    static constexpr size_t Y_FLOATS = size_t(R) * FJOFC_MAX_M * D;
-    static constexpr size_t ACC_FLOATS = size_t(R) * FJOFC_MAX_M * (D + 1);
     // y_j of the slots as (y, y) pairs: YB float4 per slot
     static constexpr int YB = (D + 1) / 2;
     static constexpr size_t YB_FLOATS = size_t(R) * YB * 4;
-    static constexpr size_t WARP_BYTES =
-        ((RING_BYTES + YB_FLOATS * 4 + (2 * Y_FLOATS + ACC_FLOATS) * 4 + size_t(R) * FJOFC_MAX_M * 8 + 2 * R * 8 +
-          R * 8 + STAGES * 8 + R * 8 + R * 4) + 127) & ~size_t(127);
-    static constexpr size_t SMEM = WARPS * WARP_BYTES + 128;
+    static __host__ __device__ size_t warp_bytes(int m) {
+        const size_t y = size_t(R) * m * D, acc = size_t(R) * m * (D + 1);
+        return ((RING_BYTES + YB_FLOATS * 4 + (2 * y + acc) * 4 + size_t(R) * m * 8 + 2 * R * 8 + R * 8 +
+                 STAGES * 8 + R * 8 + R * 4) + 127) & ~size_t(127);
+    }
+    // shared memory of a CTA (at most 227 KB, less its static variables)
+    static constexpr size_t BUDGET = 232448 - 1024;
+    // warps per CTA for m modalities: all WARPS when they fit, else as many as fit
+    static __host__ int warps_for(int m) {
+        const size_t wb = warp_bytes(m);
+        const size_t fit = (BUDGET - 128) / wb;
+        return int(fit < size_t(WARPS) ? fit : size_t(WARPS));
+    }
 };
 
 template <int D, typename TD>
@@ -74,21 +82,21 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char* wb = smem + size_t(warp) * S::WARP_BYTES;
+    const int m = p.m, n = p.n;
+    unsigned char* wb = smem + size_t(warp) * p.warp_bytes;
     TD* ring = reinterpret_cast<TD*>(wb);
     float* yb = reinterpret_cast<float*>(wb + S::RING_BYTES);          // [R][YB] float4 (y, y) pairs
-    float* ys = yb + S::YB_FLOATS;                                       // [R][MAXM][D]  y_{t-1}
-    float* yn = ys + S::Y_FLOATS;                                        // [R][MAXM][D]  y_t
-    float* acc = yn + S::Y_FLOATS;                                       // [R][MAXM][D+1]
-    double* fidj = reinterpret_cast<double*>(acc + S::ACC_FLOATS);       // [R][MAXM]
-    double* sprev = fidj + R * FJOFC_MAX_M;                              // [R]
+    float* ys = yb + S::YB_FLOATS;                                       // [R][m][D]  y_{t-1}
+    float* yn = ys + size_t(R) * m * D;                                  // [R][m][D]  y_t
+    float* acc = yn + size_t(R) * m * D;                                 // [R][m][D+1]
+    double* fidj = reinterpret_cast<double*>(acc + size_t(R) * m * (D + 1));   // [R][m]
+    double* sprev = fidj + R * m;                                        // [R]
     double* scur = sprev + R;                                            // [R]
     int* flags = reinterpret_cast<int*>(scur + R);                       // [R] state, [R] iters
     uint64_t* full = reinterpret_cast<uint64_t*>(flags + 2 * R);         // [STAGES]
     long long* slot_obj = reinterpret_cast<long long*>(full + STAGES);  // [R] object (-1: empty)
     int* slot_pass = reinterpret_cast<int*>(slot_obj + R);               // [R] pass of the slot's object
 
-    const int m = p.m, n = p.n;
     const int nsub = (n + CW - 1) / CW;
     const int passes = p.max_iter + 1;
     const int64_t per_pass = int64_t(m) * nsub;
@@ -114,7 +122,7 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
         const long long o = slot_obj[r];
         for (int e = lane; e < m * D; e += 32) {
             const int j = e / D, kk = e - j * D;
-            ys[(r * FJOFC_MAX_M + j) * D + kk] = (o >= 0) ? p.Y[(int64_t(o) * m + j) * D + kk] : 0.f;
+            ys[(r * m + j) * D + kk] = (o >= 0) ? p.Y[(int64_t(o) * m + j) * D + kk] : 0.f;
         }
         if (lane == 0) {
             flags[r] = (o >= 0) ? 0 : 1;   // 0 iterating, 1 empty
@@ -163,7 +171,7 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                 // by every lane from the same address
                 for (int e = lane; e < R * D; e += 32) {
                     const int r = e / D, kk = e - r * D;
-                    const float y = ys[(r * FJOFC_MAX_M + j) * D + kk];
+                    const float y = ys[(r * m + j) * D + kk];
                     *reinterpret_cast<float2*>(yb + (r * YB + kk / 2) * 4 + 2 * (kk & 1)) = make_float2(y, y);
                 }
                 __syncwarp();
@@ -270,13 +278,13 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                     const FF fr = warp_sum_ff(ff_add(fff[r], f2[r].x + f2[r].y));
                     const float br = warp_sum_f32(bs[r].x + bs[r].y);
                     if (lane == 0) {
-                        fidj[r * FJOFC_MAX_M + j] = double(fr.hi) + double(fr.lo);
-                        acc[(r * FJOFC_MAX_M + j) * (D + 1) + D] = br;
+                        fidj[r * m + j] = double(fr.hi) + double(fr.lo);
+                        acc[(r * m + j) * (D + 1) + D] = br;
                     }
 #pragma unroll
                     for (int kk = 0; kk < D; ++kk) {
                         const float v = warp_sum_f32(bx[r][kk].x + bx[r][kk].y);
-                        if (lane == ((r * D + kk) & 31)) acc[(r * FJOFC_MAX_M + j) * (D + 1) + kk] = v;
+                        if (lane == ((r * D + kk) & 31)) acc[(r * m + j) * (D + 1) + kk] = v;
                     }
                 }
                 __syncwarp();
@@ -290,16 +298,16 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                 const int r = lane;
                 const int pass = slot_pass[r];
                 double sig = 0.0;
-                for (int j = 0; j < m; ++j) sig += double(p.wfid[j]) * fidj[r * FJOFC_MAX_M + j];
+                for (int j = 0; j < m; ++j) sig += double(p.wfid[j]) * fidj[r * m + j];
                 for (int a = 0; a < m; ++a)
                     for (int b2 = a + 1; b2 < m; ++b2) {
                         double s2 = 0.0;
                         for (int kk = 0; kk < D; ++kk) {
-                            const double df = double(ys[(r * FJOFC_MAX_M + a) * D + kk]) -
-                                              double(ys[(r * FJOFC_MAX_M + b2) * D + kk]);
+                            const double df = double(ys[(r * m + a) * D + kk]) -
+                                              double(ys[(r * m + b2) * D + kk]);
                             s2 += df * df;
                         }
-                        sig += p.wcomm[a][b2] * s2;
+                        sig += __ldg(p.wcomm + a * m + b2) * s2;
                     }
                 bool stop = (pass == passes) || !isfinite(sig);
                 if (!stop && pass >= 2 && p.tol >= 0.0) {
@@ -320,24 +328,24 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                 if (flags[r] != 0) continue;
                 float v = 0.f;
                 for (int i2 = 0; i2 < m; ++i2) {
-                    const float* a = acc + (r * FJOFC_MAX_M + i2) * (D + 1);
+                    const float* a = acc + (r * m + i2) * (D + 1);
                     const float wi = p.wfid[i2], si = p.dscale[i2];
                     const float xi = wi * fmaf(si, a[kk], p.SX[i2 * D + kk]);   // a[kk] = -sum_k b_k x_k
                     const float psi = wi * si * a[D];
-                    v = fmaf(p.winv[j][i2], fmaf(psi, ys[(r * FJOFC_MAX_M + i2) * D + kk], xi), v);
+                    v = fmaf(__ldg(p.winv + j * m + i2), fmaf(psi, ys[(r * m + i2) * D + kk], xi), v);
                 }
-                yn[(r * FJOFC_MAX_M + j) * D + kk] = v;
+                yn[(r * m + j) * D + kk] = v;
             }
             __syncwarp();
             for (int e = lane; e < R * m * D; e += 32) {
                 const int r = e / (m * D), rem = e - r * m * D, j = rem / D, kk = rem - j * D;
-                if (flags[r] == 0) ys[(r * FJOFC_MAX_M + j) * D + kk] = yn[(r * FJOFC_MAX_M + j) * D + kk];
+                if (flags[r] == 0) ys[(r * m + j) * D + kk] = yn[(r * m + j) * D + kk];
             }
             __syncwarp();
             // outputs of the objects that stopped at this pass
             for (int e = lane; e < R * m * D; e += 32) {
                 const int r = e / (m * D), rem = e - r * m * D, j = rem / D, kk = rem - j * D;
-                if (flags[r] == 2) p.Y[(slot_obj[r] * m + j) * D + kk] = ys[(r * FJOFC_MAX_M + j) * D + kk];
+                if (flags[r] == 2) p.Y[(slot_obj[r] * m + j) * D + kk] = ys[(r * m + j) * D + kk];
             }
             __syncwarp();
             if (lane < R) {
@@ -375,36 +383,45 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
 template <int D, typename TD>
 cudaError_t k3_launch_impl(int grid, const CUtensorMap& tmap, const K3Params& p, cudaStream_t s) {
     using S = K3Shape<D, TD>;
-    cudaError_t e = cudaFuncSetAttribute(k_oos_solve<D, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::SMEM));
+    const int warps = S::warps_for(p.m);
+    if (warps < 1) return cudaErrorInvalidConfiguration;
+    const size_t smem = size_t(warps) * p.warp_bytes + 128;
+    cudaError_t e = cudaFuncSetAttribute(k_oos_solve<D, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k_oos_solve<D, TD><<<grid, S::NT, S::SMEM, s>>>(tmap, p);
+    k_oos_solve<D, TD><<<grid, warps * 32, smem, s>>>(tmap, p);
     return cudaGetLastError();
 }
 
+// CTAs per SM for m modalities (0: not launchable)
 template <int D, typename TD>
-int k3_bps_impl() {
+int k3_bps_impl(int m) {
     using S = K3Shape<D, TD>;
-    cudaFuncSetAttribute(k_oos_solve<D, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::SMEM));
+    const int warps = S::warps_for(m);
+    if (warps < 1) return 0;
+    const size_t smem = size_t(warps) * S::warp_bytes(m) + 128;
+    cudaFuncSetAttribute(k_oos_solve<D, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_oos_solve<D, TD>, S::NT, S::SMEM) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_oos_solve<D, TD>, warps * 32, smem) != cudaSuccess) return 0;
     return nb;
 }
 
+// Geometry for m modalities: WARPS = warps per CTA, smem_bytes = one warp's share.
 template <int D, typename TD>
-K3Geom k3_geom_impl() {
+K3Geom k3_geom_impl(int m) {
     using S = K3Shape<D, TD>;
-    return K3Geom{S::R, S::C, S::WARPS, S::STAGES, S::R, S::CW, S::NT, S::SMEM};
+    const int warps = S::warps_for(m);
+    return K3Geom{S::R, S::C, warps, S::STAGES, S::R, S::CW, warps * 32, S::warp_bytes(m)};
 }
 
 #define FJOFC_INSTANTIATE_K3(D)                                                                        \
     template cudaError_t k3_launch_impl<D, float>(int, const CUtensorMap&, const K3Params&, cudaStream_t); \
     template cudaError_t k3_launch_impl<D, __half>(int, const CUtensorMap&, const K3Params&, cudaStream_t); \
     template cudaError_t k3_launch_impl<D, __nv_bfloat16>(int, const CUtensorMap&, const K3Params&, cudaStream_t); \
-    template int k3_bps_impl<D, float>();                                                              \
-    template int k3_bps_impl<D, __half>();                                                             \
-    template int k3_bps_impl<D, __nv_bfloat16>();                                                      \
-    template K3Geom k3_geom_impl<D, float>();                                                          \
-    template K3Geom k3_geom_impl<D, __half>();                                                         \
-    template K3Geom k3_geom_impl<D, __nv_bfloat16>();
+    template int k3_bps_impl<D, float>(int);                                                           \
+    template int k3_bps_impl<D, __half>(int);                                                          \
+    template int k3_bps_impl<D, __nv_bfloat16>(int);                                                   \
+    template K3Geom k3_geom_impl<D, float>(int);                                                       \
+    template K3Geom k3_geom_impl<D, __half>(int);                                                      \
+    template K3Geom k3_geom_impl<D, __nv_bfloat16>(int);
 
 }  // namespace fjofc

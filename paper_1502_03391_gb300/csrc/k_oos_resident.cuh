@@ -32,10 +32,10 @@ k_oos_resident(const K3Params p) {
     float* xs = reinterpret_cast<float*>(smem_f4);        // [m][D][nx]  -x
     const int m = p.m, n = p.n, nx = p.nx;
     float* dl = xs + size_t(m) * D * nx;                  // [m][nx]     delta of the object
-    __shared__ float s_y[FJOFC_MAX_M * D];                // y_{t-1}
-    __shared__ float s_part[kK3rWarps][FJOFC_MAX_M][D + 3];   // per warp: -sum b x, sum b, fid (hi, lo)
-    __shared__ float s_acc[FJOFC_MAX_M][D + 1];
-    __shared__ double s_fid[FJOFC_MAX_M];
+    float* s_y = dl + size_t(m) * nx;                     // [m][D]      y_{t-1}
+    float* s_part = s_y + m * D;                          // [warps][m][D + 3]: -sum b x, sum b, fid (hi, lo)
+    float* s_acc = s_part + kK3rWarps * m * (D + 3);      // [m][D + 1]
+    double* s_fid = reinterpret_cast<double*>(s_y + k3r_state_floats(m, D));   // [m]
     __shared__ double s_sig;
     __shared__ long long s_obj;
     __shared__ int s_stop;
@@ -101,25 +101,30 @@ k_oos_resident(const K3Params p) {
 #pragma unroll
                 for (int kk = 0; kk < D; ++kk) bx[kk] = warp_sum_f32(bx[kk]);
                 if (lane == 0) {
+                    float* sp = s_part + (warp * m + j) * (D + 3);
 #pragma unroll
-                    for (int kk = 0; kk < D; ++kk) s_part[warp][j][kk] = bx[kk];
-                    s_part[warp][j][D] = bs;
-                    s_part[warp][j][D + 1] = fr.hi;
-                    s_part[warp][j][D + 2] = fr.lo;
+                    for (int kk = 0; kk < D; ++kk) sp[kk] = bx[kk];
+                    sp[D] = bs;
+                    sp[D + 1] = fr.hi;
+                    sp[D + 2] = fr.lo;
                 }
             }
             __syncthreads();
-            // fixed-order totals over the warps
-            if (tid < m * (D + 1)) {
-                const int j = tid / (D + 1), c = tid - j * (D + 1);
-                float v = 0.f;
-                for (int w = 0; w < kK3rWarps; ++w) v += s_part[w][j][c];
-                s_acc[j][c] = v;
-            } else if (tid >= 32 * ((m * (D + 1) + 31) / 32) && tid < 32 * ((m * (D + 1) + 31) / 32) + m) {
-                const int j = tid - 32 * ((m * (D + 1) + 31) / 32);
-                FF f{0.f, 0.f};
-                for (int w = 0; w < kK3rWarps; ++w) f = ff_add(f, FF{s_part[w][j][D + 1], s_part[w][j][D + 2]});
-                s_fid[j] = double(f.hi) + double(f.lo);
+            // fixed-order totals over the warps: m (D + 1) float sums, then m float-float
+            // fidelities, one per thread
+            for (int e = tid; e < m * (D + 1) + m; e += kK3rThreads) {
+                if (e < m * (D + 1)) {
+                    const int j = e / (D + 1), c = e - j * (D + 1);
+                    float v = 0.f;
+                    for (int w = 0; w < kK3rWarps; ++w) v += s_part[(w * m + j) * (D + 3) + c];
+                    s_acc[j * (D + 1) + c] = v;
+                } else {
+                    const int j = e - m * (D + 1);
+                    FF f{0.f, 0.f};
+                    for (int w = 0; w < kK3rWarps; ++w)
+                        f = ff_add(f, FF{s_part[(w * m + j) * (D + 3) + D + 1], s_part[(w * m + j) * (D + 3) + D + 2]});
+                    s_fid[j] = double(f.hi) + double(f.lo);
+                }
             }
             __syncthreads();
             // stress of y_{t-1} and the stopping test (the streaming kernel's rule)
@@ -133,7 +138,7 @@ k_oos_resident(const K3Params p) {
                             const double df = double(s_y[a * D + kk]) - double(s_y[b2 * D + kk]);
                             s2 += df * df;
                         }
-                        sig += p.wcomm[a][b2] * s2;
+                        sig += __ldg(p.wcomm + a * m + b2) * s2;
                     }
                 bool stop = (pass == passes) || !isfinite(sig);
                 if (!stop && pass >= 2 && p.tol >= 0.0) {
@@ -156,16 +161,17 @@ k_oos_resident(const K3Params p) {
                 }
                 break;
             }
-            // y_t = Wmod^-1 (xi + psi o y_{t-1})
+            // y_t = Wmod^-1 (xi + psi o y_{t-1}); m D <= FJOFC_MAX_M kK3rMaxD = kK3rThreads
+            static_assert(FJOFC_MAX_M * kK3rMaxD <= kK3rThreads, "one thread per (j, k)");
             float v = 0.f;
             const bool mine = tid < m * D;
             if (mine) {
                 const int j = tid / D, kk = tid - j * D;
                 for (int i2 = 0; i2 < m; ++i2) {
                     const float wi = p.wfid[i2], si = p.dscale[i2];
-                    const float xi = wi * fmaf(si, s_acc[i2][kk], p.SX[i2 * D + kk]);   // s_acc = -sum b x
-                    const float psi = wi * si * s_acc[i2][D];
-                    v = fmaf(p.winv[j][i2], fmaf(psi, s_y[i2 * D + kk], xi), v);
+                    const float xi = wi * fmaf(si, s_acc[i2 * (D + 1) + kk], p.SX[i2 * D + kk]);   // s_acc = -sum b x
+                    const float psi = wi * si * s_acc[i2 * (D + 1) + D];
+                    v = fmaf(__ldg(p.winv + j * m + i2), fmaf(psi, s_y[i2 * D + kk], xi), v);
                 }
             }
             __syncthreads();

@@ -38,7 +38,7 @@ def _rel(a, b):
 SHAPES = [  # m, n, d, delta type
     (2, 37, 2, "float32"), (3, 150, 3, "float32"), (1, 90, 5, "float32"), (2, 300, 3, "float32"),
     (2, 257, 2, "float32"), (3, 64, 5, "float32"), (2, 700, 3, "float32"), (2, 129, 3, "float16"),
-    (2, 2, 2, "float32"), (3, 420, 2, "float32"),
+    (2, 2, 2, "float32"), (3, 420, 2, "float32"), (12, 60, 3, "float32"),
 ]
 
 

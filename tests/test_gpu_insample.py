@@ -59,6 +59,7 @@ def _hist(res, ref, deltas, W, where=""):
 CASES = [  # m, n, d
     (2, 200, 2), (1, 37, 2), (2, 2, 1), (2, 3, 2), (3, 65, 3), (2, 127, 3), (2, 128, 3), (2, 129, 3),
     (2, 130, 2), (3, 64, 5), (2, 100, 8), (2, 70, 10), (2, 50, 16), (4, 33, 2), (2, 300, 4),
+    (9, 40, 2), (12, 45, 3), (30, 20, 2), (32, 9, 5),      # beyond 8 modalities: the rolled mix
 ]
 
 
@@ -185,12 +186,12 @@ def test_duplicate_points_and_nonzero_diagonal(fj):
     _hist(res, ref, prob.deltas, prob.W)
 
 
-@pytest.mark.parametrize("kind", ["W2", "W3"])
-def test_general_weights(fj, kind):
+@pytest.mark.parametrize("kind,m", [("W2", 3), ("W3", 3), ("W2", 12), ("W3", 20)])
+def test_general_weights(fj, kind, m):
     """Per-modality fidelity and per-pair commensurability weights (Eq. W2), and the
-    product weights of Eq. (W3)."""
-    rng = np.random.default_rng(11)
-    m, n, d = 3, 150, 3
+    product weights of Eq. (W3), with few and with many modalities."""
+    rng = np.random.default_rng(11 + m)
+    n, d = (150, 3) if m <= 8 else (30, 3)
     prob = synthetic.make_insample(0, n=n, m=m, d=d, seed=12)
     if kind == "W2":
         A = rng.uniform(0.2, 2.0, (m, m))
@@ -296,7 +297,7 @@ def test_padded_row_stride_is_transparent(fj):
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("m,n,d", [(2, 300, 3), (3, 257, 2), (2, 90, 10), (2, 2200, 9)])
+@pytest.mark.parametrize("m,n,d", [(2, 300, 3), (3, 257, 2), (2, 90, 10), (2, 2200, 9), (14, 70, 3)])
 def test_persistent_and_per_pass_launches_agree(fj, m, n, d):
     """The default path (one persistent cooperative kernel for the whole loop) and the
     one-launch-per-pass path (profile=1) compute the same partials in the same order:

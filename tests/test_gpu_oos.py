@@ -61,7 +61,8 @@ FORMS = ["streaming", "resident"]
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("m,n,d,k", [(2, 10, 2, 1), (2, 63, 3, 7), (3, 64, 2, 33), (2, 65, 5, 9),
                                      (2, 200, 3, 17), (3, 130, 10, 5), (2, 40, 16, 3), (1, 50, 2, 4),
-                                     (8, 301, 3, 3), (4, 257, 8, 2)])
+                                     (8, 301, 3, 3), (4, 257, 8, 2), (12, 70, 3, 5), (30, 40, 2, 4),
+                                     (32, 33, 8, 3), (20, 50, 10, 2)])
 def test_oos_parity_fixed_iterations(fj, m, n, d, k, form):
     if form == "resident" and d > 8:
         pytest.skip("the resident form is built for d <= 8")

@@ -81,7 +81,7 @@ def call():
 
 @pytest.mark.parametrize("kw,code", [
     (dict(m=0), -1),
-    (dict(m=9, W=np.eye(9)), -6),
+    (dict(m=33, W=np.eye(33)), -6),      # beyond FJOFC_MAX_M = 32
     (dict(n=1, ld=4), -1),
     (dict(d=0), -1),
     (dict(d=17), -6),
