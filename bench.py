@@ -152,27 +152,56 @@ def oracle_rate(n, iters, seed_rep=0):
     return pairs_per_transform(WORKLOAD["m"], n) * res.iters / dt, dt
 
 
+# transforms of the float64 C Algorithm 2 timed per step (a bounded sample of the
+# workload's 200)
+CPU_TRANSFORMS = 20
+
+
+def cpu_fjofc_rate(deltas, W, X0, transforms):
+    """Pair-updates/s of the float64 C Algorithm 2 (oracle/fjofc_cpu.c, every host core)
+    on the full workload: ``transforms`` Guttman transforms from X0."""
+    from oracle import fjofc_cpu as C
+    m, n = len(deltas), deltas[0].shape[0]
+    t0 = time.perf_counter()
+    _, it, _ = C.cpu_embed(deltas, W, X0, transforms)
+    dt = time.perf_counter() - t0
+    return pairs_per_transform(m, n) * it / dt, dt, C.threads()
+
+
+def host_problem():
+    """Workload 1 on the host in float64 (Delta rounded to float32 first, as the device
+    path stores it)."""
+    import numpy as np
+    import synthetic
+    prob = synthetic.make_insample(WORKLOAD["k"])
+    deltas = [np.asarray(D, np.float32).astype(np.float64) for D in prob.deltas]
+    return prob, deltas, np.asarray(prob.X0, np.float32).astype(np.float64)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    n, iters = CPU_SAMPLE["n"], CPU_SAMPLE["iters"]
+    prob, deltas, X0 = host_problem()
+    from oracle import fjofc_cpu as C
+    C.build()
     for _ in range(args.warmup):
-        oracle_rate(200, 3)
-    vals, times = [], []
+        cpu_fjofc_rate(deltas, prob.W, X0, 1)
+    times = []
+    threads = 1
     for _ in range(args.steps):
-        v, dt = oracle_rate(n, iters)
-        vals.append(v)
+        _, dt, threads = cpu_fjofc_rate(deltas, prob.W, X0, CPU_TRANSFORMS)
         times.append(dt)
-    value = sum(iters * pairs_per_transform(WORKLOAD["m"], n) for _ in vals) / sum(times)
-    cores = os.cpu_count()
+    m, n = WORKLOAD["m"], WORKLOAD["n"]
+    value = args.steps * CPU_TRANSFORMS * pairs_per_transform(m, n) / sum(times)
+    sample = (f"float64 Algorithm 2 in C (oracle/fjofc_cpu.c, OpenMP on {threads} threads) on the full workload "
+              f"(m={m}, n={n}, d={WORKLOAD['d']}), {CPU_TRANSFORMS} of its 200 transforms per step")
     line = {
         "impl": "reference", "metric": "Guttman pair-updates/s", "value": value, "unit": "pair-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "insample-m2-n5000-d3", "sample": f"n={n} objects of the same generator, {iters} transforms",
-                   "m": WORKLOAD["m"], "d": WORKLOAD["d"], "parallelism": "cpu"},
-        "cpu_baseline": {"value": value, "unit": "pair-updates/s", "cores": cores, "kind": "oracle",
-                         "sample": f"dense float64 Algorithm 1 (pinv + dense B(X)) on n={n} (mn={2 * n}), {iters} transforms"},
+        "config": {"workload": "insample-m2-n5000-d3", "sample": sample, "m": m, "n": n, "d": WORKLOAD["d"],
+                   "parallelism": "cpu"},
+        "cpu_baseline": {"value": value, "unit": "pair-updates/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "pair-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -298,12 +327,18 @@ def run_gpu(args, rank, world, local_rank):
         e2e = {"value": ppt * it2 / (ems / 1e3), "unit": "pair-updates/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(hostX.numel() * 4 + 8 + 4)}
 
-    cpu = None
+    cpu = cpu_dense = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        hostD = [dd.double().cpu().numpy() for dd in deltas]         # the same float32 inputs
+        v, dt, thr = cpu_fjofc_rate(hostD, prob.W, X0.double().cpu().numpy(), CPU_TRANSFORMS)
+        cpu = {"value": v, "unit": "pair-updates/s", "cores": thr, "kind": "oracle",
+               "sample": f"float64 Algorithm 2 in C (oracle/fjofc_cpu.c, OpenMP) on the same inputs (m={m}, n={n}, "
+                         f"d={d}), {CPU_TRANSFORMS} of the 200 transforms, {dt:.1f} s", "same_config": True}
+        del hostD
         v, dt = oracle_rate(CPU_SAMPLE["n"], CPU_SAMPLE["iters"])
-        cpu = {"value": v, "unit": "pair-updates/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"dense float64 Algorithm 1 (pinv + dense B(X)) on n={CPU_SAMPLE['n']} objects of the same "
-                         f"generator (mn={2 * CPU_SAMPLE['n']}), {CPU_SAMPLE['iters']} transforms, {dt:.1f} s"}
+        cpu_dense = {"value": v, "unit": "pair-updates/s", "cores": os.cpu_count(), "kind": "oracle",
+                     "sample": f"dense float64 Algorithm 1 (pinv + dense B(X)) on n={CPU_SAMPLE['n']} objects of the "
+                               f"same generator (mn={2 * CPU_SAMPLE['n']}), {CPU_SAMPLE['iters']} transforms, {dt:.1f} s"}
 
     if rank == 0:
         line = {
@@ -317,7 +352,7 @@ def run_gpu(args, rank, world, local_rank):
                              "Delta 200 MB stored, 100 MB (upper triangles) read per pass",
                        "parallelism": f"{world} independent replica(s)"},
             "hbm_gbs_step": alg_bytes * total_iters / (elapsed_ms / 1e3) / 1e9,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "cpu_dense_oracle": cpu_dense, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
