@@ -284,6 +284,38 @@ int fjofc_embed_noalloc(int32_t m, int64_t n, int32_t d,
                         const float* delta_scale, const double* weights,
                         float* X, const fjofc_opts* opts, fjofc_result* res, void* cuda_stream);
 
+/*
+ * fjofc_transform_rows -- one Guttman transform (Eq. update) for the objects [r0, r1) of
+ * every modality: the building block of row-block sharding across GPUs.  The mix
+ * X_t^(j)_i = sum_l [Wmod^-1]_{jl} (B_l X^(l))_i of Eq. (update) / Cor. 1 is per object,
+ * and (B_l X^(l))_i needs only row i of Delta_l (Eq. B) and the whole X_{t-1}; so a GPU
+ * holding rows [r0, r1) of every Delta_l computes those rows of X_t, and the GPUs then
+ * all-gather X_t and add up the parts below before the next transform.
+ *
+ *  m, n, d      : as fjofc_embed; 0 <= r0 < r1 <= n.
+ *  delta_rows   : host array of m DEVICE pointers; delta_rows[l] holds rows r0..r1-1 of
+ *                 Delta_{l+1} (all n columns), row stride ld >= n, element type delta_dtype,
+ *                 used as delta_scale[l] * value (delta_scale may be NULL).  Delta must be
+ *                 symmetric: a row is used whole (both triangles), once from each side.
+ *  weights      : host m x m float64, as fjofc_embed.
+ *  X            : DEVICE float32 (m n) x d: the whole X_{t-1} (read only).
+ *  mu           : host m x d float64 or NULL: column means subtracted from X_{t-1}^(j) before
+ *                 use (the centring of the previous transform's output; NULL = 0).
+ *  Xout         : DEVICE float32 m x (r1 - r0) x d: rows [r0, r1) of X_t, modality-major.
+ *  parts        : host float64[2 + m d] out: [0] the range's share of the fidelity term of
+ *                 sigma(X_{t-1}) (sum over its objects i of w_ll sum_{j != i}
+ *                 (Delta_l,ij - d_ij)^2 / 2), [1] the commensurability of its objects
+ *                 (sum_{j<l} w_jl ||x_i^(j) - x_i^(l)||^2), [2 + j d + k] the column sums of its
+ *                 X_t^(j) rows.  Summed over ranges that cover [0, n): sigma(X_{t-1}) =
+ *                 parts[0] + parts[1], and n times the means of X_t.
+ * Float32 distances and sums, float-float group sums, float64 parts.  Allocates its small
+ * scratch with the stream-ordered allocator; synchronises the stream.  Errors as
+ * fjofc_embed.
+ */
+int fjofc_transform_rows(int32_t m, int64_t n, int32_t d, int64_t r0, int64_t r1, const void* const* delta_rows,
+                         int64_t ld, int32_t delta_dtype, const float* delta_scale, const double* weights,
+                         const float* X, const double* mu, float* Xout, double* parts, void* cuda_stream);
+
 /* ------------------------------------------------------------------------------------
  * Batched in-sample embedding (the paper has no counterpart: a deployment form that
  * runs many independent fJOFC problems, Algorithm 1 with Eq. update each, of uneven

@@ -38,7 +38,7 @@ EXPORTS = ("fjofc_embed", "fjofc_embed_noalloc", "fjofc_stress", "fjofc_oos", "f
            "fjofc_mlp_param_count", "fjofc_mlp_init", "fjofc_mlp_features", "fjofc_mlp_forward", "fjofc_mlp_gradient",
            "fjofc_mlp_train", "fjofc_mlp_broadcast", "fjofc_mlp_select", "fjofc_plan_create", "fjofc_plan_run",
            "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy", "fjofc_plan_autotune", "fjofc_init_cmds",
-           "fjofc_test_barrier_skew")
+           "fjofc_test_barrier_skew", "fjofc_transform_rows")
 
 
 class FjofcError(RuntimeError):
@@ -111,6 +111,9 @@ def _load():
     lib.fjofc_init_cmds.argtypes = [i32, i64, i32, ctypes.POINTER(vp), i64, i32, ctypes.POINTER(ctypes.c_float),
                                     vp, ctypes.POINTER(_InitOpts), ctypes.POINTER(i32), vp]
     lib.fjofc_init_cmds.restype = ctypes.c_int
+    lib.fjofc_transform_rows.argtypes = [i32, i64, i32, i64, i64, ctypes.POINTER(vp), i64, i32,
+                                         ctypes.POINTER(ctypes.c_float), dp, vp, dp, vp, dp, vp]
+    lib.fjofc_transform_rows.restype = ctypes.c_int
     lib.fjofc_test_barrier_skew.argtypes = [i32]
     lib.fjofc_test_barrier_skew.restype = None
     lib.fjofc_strerror.argtypes = [ctypes.c_int]
@@ -273,6 +276,39 @@ def embed(deltas: Sequence, weights, X, max_iter: int, tol: float = -1.0, tol_mo
         hist = hist[:upto]
     return EmbedResult(st, res.iters, res.stress, res.stress_normalized, hist, res.ms_total, res.passes,
                        res.ms_pass, res.ms_apply, res.launches)
+
+
+def transform_rows(delta_rows: Sequence, weights, X, r0: int, r1: int, mu=None, delta_scale=None, stream=None):
+    """One Guttman transform for objects [r0, r1) (``fjofc_transform_rows``).
+    ``delta_rows``: m CUDA views of shape (r1 - r0, n) (row stride a multiple of 16 bytes
+    not required); ``X``: contiguous float32 (m*n, d) CUDA tensor, the whole X_{t-1};
+    ``mu``: m x d means to subtract from X_{t-1} (or None).  Returns (Xout, parts):
+    Xout a float32 CUDA tensor (m, r1 - r0, d) with rows [r0, r1) of X_t, parts a float64
+    numpy vector [fidelity share, commensurability share, column sums of Xout (m*d)]."""
+    torch = _torch()
+    m = len(delta_rows)
+    n = int(delta_rows[0].shape[1])
+    d = int(X.shape[1])
+    if X.dtype != torch.float32 or not X.is_contiguous() or X.shape[0] != m * n:
+        raise ValueError("X must be a contiguous float32 (m*n, d) CUDA tensor")
+    for D in delta_rows:
+        if tuple(D.shape) != (r1 - r0, n) or D.stride(1) != 1:
+            raise ValueError("delta_rows[l] must be a (r1 - r0, n) view with unit column stride")
+    ld = int(delta_rows[0].stride(0)) if r1 - r0 > 1 else n
+    code = _dtype_code(delta_rows[0])
+    ptrs = (ctypes.c_void_p * m)(*[D.data_ptr() for D in delta_rows])
+    Wn = _weights(weights, m)
+    Xout = torch.empty((m, r1 - r0, d), dtype=torch.float32, device=X.device)
+    parts = np.zeros(2 + m * d, dtype=np.float64)
+    mu_arr = None if mu is None else np.ascontiguousarray(np.asarray(mu, dtype=np.float64).reshape(m * d))
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = _lib.fjofc_transform_rows(m, n, d, int(r0), int(r1), ptrs, ld, code, _scales(delta_scale, m),
+                                   Wn.ctypes.data_as(dp), ctypes.c_void_p(X.data_ptr()),
+                                   None if mu_arr is None else mu_arr.ctypes.data_as(dp),
+                                   ctypes.c_void_p(Xout.data_ptr()), parts.ctypes.data_as(dp),
+                                   _stream_handle(stream, X.device))
+    _check(st)
+    return Xout, parts
 
 
 def test_barrier_skew(extra: int) -> None:

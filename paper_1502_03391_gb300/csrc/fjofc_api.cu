@@ -133,10 +133,11 @@ CUtensorMapDataType tma_dtype(int dt) {
 
 // rank-r tiled map; dims/strides innermost first, strides in bytes (rank-1 entries)
 int encode_map(CUtensorMap* map, int dtype, int rank, const void* base, const cuuint64_t* dims,
-               const cuuint64_t* strides, const cuuint32_t* box) {
+               const cuuint64_t* strides, const cuuint32_t* box, bool swizzle128 = false) {
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUresult r = g_encode(map, tma_dtype(dtype), cuuint32_t(rank), const_cast<void*>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         snprintf(g_last_msg, sizeof(g_last_msg), "cuTensorMapEncodeTiled failed (CUresult %d)", int(r));
@@ -394,13 +395,15 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
                         const double* weights, const double* winv, float* X) {
     int rc;
     const int RB = P.g.RB, CW = P.g.CW;
-    // TMA descriptors: Delta_l as a 2-D tensor {n cols, n rows}, box {CW, RB}
+    // TMA descriptors: Delta_l as a 2-D tensor {n cols, n rows}, box {CW, RB} (row-band
+    // layout) or {128 bytes, RB} with the 128-byte swizzle (column-strip layout)
     std::memset(&tm, 0, sizeof(tm));
     for (int l = 0; l < m; ++l) {
         const cuuint64_t dims[2] = {cuuint64_t(n), cuuint64_t(n)};
         const cuuint64_t strides[1] = {cuuint64_t(ld) * dtype_size(dtype)};
-        const cuuint32_t box[2] = {cuuint32_t(CW), cuuint32_t(RB)};
-        if ((rc = encode_map(&tm.map[l], dtype, 2, delta[l], dims, strides, box))) return rc;
+        const bool strip = P.g.box_elems > 0;
+        const cuuint32_t box[2] = {cuuint32_t(strip ? P.g.box_elems : CW), cuuint32_t(RB)};
+        if ((rc = encode_map(&tm.map[l], dtype, 2, delta[l], dims, strides, box, strip))) return rc;
     }
     DevStatus* st = reinterpret_cast<DevStatus*>(base + o_st);
     double* hist = reinterpret_cast<double*>(base + o_hist);

@@ -36,6 +36,8 @@ struct K1Geom {
     int RB, CW;                 // row-block height (WARPS*R), sub-tile width (32*C)
     int threads;
     size_t smem_bytes;
+    int box_elems;              // > 0: Delta is staged as boxes of box_elems x RB with the 128-byte
+                                // swizzle (column-strip layout); 0: one CW x RB box, no swizzle
 };
 
 // Geometry of the K1 instantiation used for embedding dimension d.

@@ -98,19 +98,16 @@ __device__ __forceinline__ float bx_sum_wide(const BxTables& tb, int l, int k, i
     const int d = tb.d, RB = tb.RB, CW = tb.CW, rbs = tb.rb_shift, cws = tb.cw_shift, nRB = tb.nRB;
     const int i0 = g * kGroupObjects, i = i0 + lane;
     const int I = i0 >> rbs;
-    float head = 0.f;
-    if (on) {
-        head = __ldcg(tb.rowhead + ((int64_t(l) * nRB + I) * d + k) * RB + (i & (RB - 1)));
-        const int2 cr = __ldg(tb.cont + int64_t(l) * nRB + I);
-#pragma unroll 1
-        for (int b = cr.x; b < cr.y; ++b) head += __ldcg(tb.rowcont + (int64_t(b) * d + k) * RB + (i & (RB - 1)));
-    }
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     const float* cp = tb.colpart + int64_t(l) * tb.Tm * d * CW;
     const int nJ = on ? I + 1 : 0;
-#pragma unroll 1
-    for (int J0 = 0; J0 < nJ; J0 += kWideWalksPerRound) {
-        float4 v[kWideUnroll];
+    // every load of the first round goes out before any sum: the walk-head row partial, the
+    // continuation row partials (up to kContBatch of them) and the column partials of up to
+    // kWideWalksPerRound walks; the sums are then formed in the fixed order (head, the
+    // continuations in CTA order, the walks in order)
+    constexpr int kContBatch = 8;
+    const int2 cr = on ? __ldg(tb.cont + int64_t(l) * nRB + I) : make_int2(0, 0);
+    const float h0 = on ? __ldcg(tb.rowhead + ((int64_t(l) * nRB + I) * d + k) * RB + (i & (RB - 1))) : 0.f;
+    auto col_round = [&](int J0, float4 (&v)[kWideUnroll]) {
 #pragma unroll
         for (int u = 0; u < kWideUnroll; ++u) {
             const int J = J0 + 4 * u + q;
@@ -123,6 +120,23 @@ __device__ __forceinline__ float bx_sum_wide(const BxTables& tb, int l, int k, i
                 v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
+    };
+    float4 v[kWideUnroll];
+    col_round(0, v);
+    float cont[kContBatch];
+#pragma unroll
+    for (int u = 0; u < kContBatch; ++u)
+        cont[u] = (cr.x + u < cr.y) ? __ldcg(tb.rowcont + (int64_t(cr.x + u) * d + k) * RB + (i & (RB - 1))) : 0.f;
+    float head = h0;
+#pragma unroll
+    for (int u = 0; u < kContBatch; ++u)
+        if (cr.x + u < cr.y) head += cont[u];
+#pragma unroll 1
+    for (int b = cr.x + kContBatch; b < cr.y; ++b) head += __ldcg(tb.rowcont + (int64_t(b) * d + k) * RB + (i & (RB - 1)));
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int J0 = 0; J0 < nJ; J0 += kWideWalksPerRound) {
+        if (J0 > 0) col_round(J0, v);
 #pragma unroll
         for (int u = 0; u < kWideUnroll; ++u) {
             acc.x += v[u].x;

@@ -206,7 +206,10 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
         FJ_STAMP(t, 0);
         if (do_a) {
             FF fid_total{0.f, 0.f};
-            if (!phase_a<D, TD>(rg, tm, p, Xprev, int64_t(t - 1) * nq, b, fid_total)) {
+            bool ok_a;
+            if constexpr (S::STRIP) ok_a = phase_a_strip<D, TD>(rg, tm, p, Xprev, int64_t(t - 1) * nq, b, fid_total);
+            else ok_a = phase_a<D, TD>(rg, tm, p, Xprev, int64_t(t - 1) * nq, b, fid_total);
+            if (!ok_a) {
                 ok = false;
                 fail_site = 31;
             }

@@ -33,9 +33,19 @@
 namespace fjofc {
 
 template <int D> struct K1Cfg;
+// Largest embedding dimension that uses the column-strip layout of the sub-tile (every
+// warp owns a strip of columns, so column partials are reduced inside the warp); larger
+// d use the row-band layout (every warp owns a band of rows, column partials reduced
+// across the warps through shared memory).
+#ifndef FJOFC_K1_STRIP_MAX_D
+#define FJOFC_K1_STRIP_MAX_D 4
+#endif
 // rows/thread, cols/lane, compute warps, pipeline stages (float32)
 #define FJOFC_K1CFG(D_, R_, C_, W_, S_)                                                     \
-    template <> struct K1Cfg<D_> { static constexpr int R = R_, C = C_, CWARPS = W_, STAGES = S_; };
+    template <> struct K1Cfg<D_> {                                                          \
+        static constexpr int R = R_, C = C_, CWARPS = W_, STAGES = S_;                      \
+        static constexpr bool STRIP = (D_ <= FJOFC_K1_STRIP_MAX_D);                         \
+    };
 // The d <= 4 tile can be overridden at build time (tuning sweeps).
 #ifndef FJOFC_K1_SMALLD_R
 #define FJOFC_K1_SMALLD_R 16
@@ -95,14 +105,29 @@ constexpr size_t kK1SmemBudget = 232448 - 2048;
 template <int D, typename TD>
 struct K1Shape {
     static constexpr int R = K1Cfg<D>::R, C = K1Cfg<D>::C, CWARPS = K1Cfg<D>::CWARPS;
-    static constexpr int SLOTS = 2;                    // column-partial ring
+    static constexpr bool STRIP = K1Cfg<D>::STRIP;
+    static constexpr int SLOTS = 2;                    // column-partial ring (row-band layout)
     static constexpr int NT = CWARPS * 32;
     static constexpr int RB = CWARPS * R;
     static constexpr int CW = 32 * C;
     static constexpr int STAGE_ELEMS = RB * CW;
     static constexpr uint32_t STAGE_BYTES = STAGE_ELEMS * sizeof(TD);
-    static constexpr size_t RED_FLOATS = size_t(SLOTS) * CWARPS * D * CW;
-    static constexpr int XROW_FLOATS = CWARPS * R * XiBcast<D>::XB * 4;   // x_i of the walk, broadcast pairs
+    // column-strip layout: a stage is BOXES TMA boxes of RB rows x 128 bytes, each stored
+    // with the 128-byte swizzle (16-byte chunk j of row r at chunk j ^ (r & 7)), so that the
+    // eight rows a warp reads at once fall on different banks
+    static constexpr int BOX_ELEMS = 128 / int(sizeof(TD));
+    static constexpr int BOXES = STRIP ? (CW * int(sizeof(TD))) / 128 : 1;
+    static constexpr int SW = CW / CWARPS;             // columns of a warp's strip
+    static_assert(!STRIP || (CWARPS == 8 && SW == 4 * C && BOXES >= 1 && (CW * sizeof(TD)) % 128 == 0),
+                  "column-strip layout: 8 warps, 4 column groups of C per warp, whole 128-byte boxes");
+    static constexpr size_t PHB_FLOATS = size_t(2) * FJOFC_MAX_M * 32;   // phase B's staging of one unit
+    static constexpr size_t RED_FLOATS =
+        STRIP ? (size_t(CWARPS) * RB * D > PHB_FLOATS ? size_t(CWARPS) * RB * D : PHB_FLOATS)   // row hand-off
+              : size_t(SLOTS) * CWARPS * D * CW;
+    static constexpr size_t ALIGN = STRIP ? 1024 : 128;
+    // x_i of the walk as broadcast pairs (column-strip layout: one shared copy per walk
+    // segment, two buffers)
+    static constexpr int XROW_FLOATS = (STRIP ? 2 : 1) * CWARPS * R * XiBcast<D>::XB * 4;
     // every sub-tile's x_j (CW columns x d, a 16-byte aligned window) staged in shared
     // memory by the issuing warp (cp.async), STAGES uses ahead like Delta
     static constexpr bool XSTAGE = D >= FJOFC_K1_XSTAGE_MIN_D;
@@ -110,7 +135,7 @@ struct K1Shape {
     static constexpr size_t smem_for(int stages) {
         return size_t(stages) * STAGE_BYTES + RED_FLOATS * sizeof(float) + size_t(XROW_FLOATS) * sizeof(float) +
                size_t(stages) * XS_FLOATS * sizeof(float) + size_t(2 * stages + 2 * SLOTS) * 8 +
-               size_t(stages) * 4 + 128;
+               size_t(stages) * 4 + ALIGN;
     }
     // 16-bit Delta halves the stage: keep about the same bytes in flight, as many stages
     // as fit in the budget
@@ -329,9 +354,14 @@ struct K1Ring {
     int nq;
     int64_t total_q;
 
+    int nflush;            // row hand-offs done so far (column-strip layout; the same in every thread)
+
     __device__ __forceinline__ void carve(unsigned char* smem_raw) {
-        unsigned char* smem = reinterpret_cast<unsigned char*>(
-            (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+        // generic -> shared offsets: align the shared-window address (the 128-byte swizzle
+        // pattern repeats every 1024 bytes of shared address)
+        const uint32_t a0 = smem_u32(smem_raw);
+        const uint32_t a1 = (a0 + uint32_t(S::ALIGN) - 1) & ~uint32_t(S::ALIGN - 1);
+        unsigned char* smem = smem_raw + (a1 - a0);
         stages = reinterpret_cast<TD*>(smem);
         red = reinterpret_cast<float*>(smem + size_t(S::STAGES) * S::STAGE_BYTES);
         xrow = red + S::RED_FLOATS;
@@ -348,8 +378,16 @@ struct K1Ring {
         atomicMax(issued, int(qg + 1));
         const uint32_t bar = smem_u32(&full[stage]);
         mbar_arrive_expect_tx(bar, S::STAGE_BYTES);
-        tma_load_2d(smem_u32(stages + size_t(stage) * S::STAGE_ELEMS), &tm.map[pc.l],
-                    pc.I * S::RB + pc.s * S::CW, pc.I * S::RB, bar);
+        const uint32_t dst = smem_u32(stages + size_t(stage) * S::STAGE_ELEMS);
+        if constexpr (S::STRIP) {
+            // BOXES boxes of 128 bytes x RB rows; x is a multiple of 128 bytes
+#pragma unroll
+            for (int bx = 0; bx < S::BOXES; ++bx)
+                tma_load_2d(dst + uint32_t(bx) * S::RB * 128u, &tm.map[pc.l],
+                            pc.I * S::RB + pc.s * S::CW + bx * S::BOX_ELEMS, pc.I * S::RB, bar);
+        } else {
+            tma_load_2d(dst, &tm.map[pc.l], pc.I * S::RB + pc.s * S::CW, pc.I * S::RB, bar);
+        }
     }
 
     // x_j of use u (cursor c) into its stage, by all 32 lanes of one warp: the 16-byte
@@ -392,6 +430,7 @@ struct K1Ring {
         nq = nq_;
         total_q = total_q_;
         pc_local = 0;
+        nflush = 0;
         cursor_init(pc, t_begin, p);
         if (threadIdx.x == 0) {
             for (int s = 0; s < S::STAGES; ++s) {
@@ -731,6 +770,364 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
     return true;
 }
 
+// ---------------------------------------------------------------------------------------
+// Column-strip layout of a sub-tile (S::STRIP): warp w owns the SW = CW / 8 columns
+// [w SW, (w + 1) SW); lane (rg, cl) = (lane >> 2, lane & 3) owns the C columns
+// w SW + cl C + (0 .. C-1) and the R rows rg + 8 u (u = 0 .. R-1) of the row block.  Row
+// accumulators stay in registers for the whole walk segment (as in the row-band layout);
+// a sub-tile's column sums are complete inside the warp: a reduce-scatter over the eight
+// row groups (lane bits 2..4) leaves every (column, coordinate) total in one lane, which
+// writes it.  Warps meet only at the TMA ring (stage release) and, at the end of a walk
+// segment, to add their row partials (mbarrier hand-off through shared memory, bounded).
+// Sign convention here: q = +b (no negation of Delta), so the row accumulators hold
+// sum_j b (x_i - x_j) and the column accumulators its negation for the columns.
+// ---------------------------------------------------------------------------------------
+
+// Sum of v[0..V-1] over the lanes that differ in lane bits OFF, OFF/2, .., LOW (a
+// reduce-scatter, pairing as an xor butterfly): on return v[0..F-1] holds totals of
+// indices base .. base+F-1 and exactly one lane of each group has writer == true.
+template <int V, int OFF, int LOW>
+struct LaneScatter {
+    static constexpr int F = OFF < LOW ? V : (V % 2 == 0 ? LaneScatter<V / 2, OFF / 2, LOW>::F
+                                                        : LaneScatter<V, OFF / 2, LOW>::F);
+    static __device__ __forceinline__ void run(float* v, int lane, int& base, bool& writer) {
+        if constexpr (OFF >= LOW) {
+            if constexpr (V % 2 == 0) {
+                constexpr int H = V / 2;
+                const bool up = (lane & OFF) != 0;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const float send = up ? v[h] : v[h + H];
+                    const float keep = up ? v[h + H] : v[h];
+                    v[h] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+                }
+                if (up) base += H;
+                LaneScatter<H, OFF / 2, LOW>::run(v, lane, base, writer);
+            } else {
+#pragma unroll
+                for (int h = 0; h < V; ++h) v[h] += __shfl_xor_sync(0xffffffffu, v[h], OFF);
+                if (lane & OFF) writer = false;
+                LaneScatter<V, OFF / 2, LOW>::run(v, lane, base, writer);
+            }
+        }
+    }
+};
+
+// The pairs of one sub-tile owned by lane (rg, cl) of warp w in the column-strip layout.
+// tile: shared address of the stage (BOXES swizzled boxes); xib: the walk rows as
+// broadcast pairs, layout [XB][R][8] float4 (row rg + 8u at (x R + u) 8 + rg); nxj: -x_j
+// of the lane's columns as column pairs.  MASKED: only pairs with i < j < n count.
+template <int D, typename TD, int R, int C, int RB, int SW, bool MASKED>
+__device__ __forceinline__ void strip_pairs(uint32_t tile, int warp, int rg, int cl, int r0, int c0, int n,
+                                            uint32_t xib, const float2 (&nxj)[C / 2][D], float (&racc)[R][D],
+                                            float2 (&cacc)[C / 2][D], float2& sf) {
+    static_assert(C % 2 == 0, "columns are processed in pairs");
+    constexpr int CP = C / 2, XB = XiBcast<D>::XB;
+    constexpr int RI = (R % 2 == 0) ? 2 : 1;
+    // byte offset of the lane's columns inside a 128-column row, split into box, 16-byte
+    // chunk and offset inside the chunk
+    const int cbyte = (warp * SW + cl * C) * int(sizeof(TD));
+    const uint32_t box_off = uint32_t(cbyte >> 7) * RB * 128u;
+    const int chunk = (cbyte & 127) >> 4, sub = cbyte & 15;
+#pragma unroll
+    for (int cp = 0; cp < CP; ++cp)
+#pragma unroll
+        for (int k = 0; k < D; ++k) cacc[cp][k] = make_float2(0.f, 0.f);
+    sf = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int ub = 0; ub < R; ub += RI) {
+        float2 xb[RI][2 * XB];
+        float dl[RI][C];
+#pragma unroll
+        for (int h = 0; h < RI; ++h) {
+            const int u = ub + h, lr = rg + 8 * u;            // row of the block
+#pragma unroll
+            for (int x = 0; x < XB; ++x) {
+                const float4 v = lds_f4(xib + 16 * ((x * R + u) * 8 + rg));
+                xb[h][2 * x] = make_float2(v.x, v.y);
+                xb[h][2 * x + 1] = make_float2(v.z, v.w);
+            }
+            lds_delta_row<TD, C>(tile + box_off + uint32_t(lr) * 128u + uint32_t(((chunk ^ (lr & 7)) << 4) + sub),
+                                 dl[h]);
+        }
+#pragma unroll
+        for (int cp = 0; cp < CP; ++cp) {
+            float2 diff[RI][D], d2[RI], rinv[RI], q[RI], e[RI];
+#pragma unroll
+            for (int h = 0; h < RI; ++h) d2[h] = make_float2(FLT_MIN, FLT_MIN);
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+#pragma unroll
+                for (int h = 0; h < RI; ++h) {
+                    diff[h][k] = __fadd2_rn(xb[h][k], nxj[cp][k]);
+                    d2[h] = __ffma2_rn(diff[h][k], diff[h][k], d2[h]);
+                }
+#pragma unroll
+            for (int h = 0; h < RI; ++h) rinv[h] = make_float2(rsqrt_approx(d2[h].x), rsqrt_approx(d2[h].y));
+#pragma unroll
+            for (int h = 0; h < RI; ++h) {
+                q[h] = __fmul2_rn(make_float2(dl[h][2 * cp], dl[h][2 * cp + 1]), rinv[h]);   // b
+                e[h].x = fmaf(d2[h].x, rinv[h].x, -dl[h][2 * cp]);                           // d - Delta
+                e[h].y = fmaf(d2[h].y, rinv[h].y, -dl[h][2 * cp + 1]);
+                if (MASKED) {
+                    const int i = r0 + rg + 8 * (ub + h);
+                    const int j = c0 + warp * SW + cl * C + 2 * cp;
+                    const bool v0 = (j > i) && (j < n), v1 = (j + 1 > i) && (j + 1 < n);
+                    q[h].x = v0 ? q[h].x : 0.f;
+                    e[h].x = v0 ? e[h].x : 0.f;
+                    q[h].y = v1 ? q[h].y : 0.f;
+                    e[h].y = v1 ? e[h].y : 0.f;
+                }
+                sf = __ffma2_rn(e[h], e[h], sf);
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+#pragma unroll
+                for (int h = 0; h < RI; ++h) {
+                    const int u = ub + h;
+                    racc[u][k] = fmaf(q[h].x, diff[h][k].x, racc[u][k]);
+                    racc[u][k] = fmaf(q[h].y, diff[h][k].y, racc[u][k]);
+                    cacc[cp][k] = __ffma2_rn(q[h], diff[h][k], cacc[cp][k]);
+                }
+        }
+    }
+}
+
+// One all-pairs pass over the CTA's range in the column-strip layout (same inputs,
+// outputs and ring as phase_a).  Walk rows: one shared copy per walk segment, double
+// buffered (segment g uses buffer g & 1); every warp loads 1/8 of the next segment's rows
+// one sub-tile ahead and writes them during the row hand-off that ends the segment, which
+// every warp passes before it reads them.  The hand-off (rfull: partials and rows written,
+// rempty: partials read, count 8 each) is bounded like every other wait.
+template <int D, typename TD>
+__device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm, const K1Params& p, const float* X,
+                                              int64_t qbase, int b, FF& fid_total) {
+    using S = K1Shape<D, TD>;
+    constexpr int R = S::R, C = S::C, CWARPS = S::CWARPS, STAGES = S::STAGES, SW = S::SW;
+    constexpr int RB = S::RB, CW = S::CW, XB = XiBcast<D>::XB;
+    constexpr int XBUF = RB * XB * 4;                 // floats of one walk-rows buffer
+    constexpr int RSH = (RB * D + CWARPS * 32 - 1) / (CWARPS * 32);   // next rows per lane
+    static_assert(S::XSTAGE, "the column-strip layout stages x_j in shared memory");
+    static_assert(S::XROW_FLOATS == 2 * XBUF, "two walk-row buffers");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const int rgp = lane >> 2, cl = lane & 3;
+    const int n = p.n, nq = rg.nq;
+    const volatile int* abort_flag = rg.abort_flag;
+    fid_total = FF{0.f, 0.f};
+
+    Cursor cc, cn;
+    cursor_init(cc, rg.t_begin, p);
+    cn = cc;
+    bool seg_head = (cc.s == 0);
+    int seg = 0;                                       // walk segment of this pass
+    float racc[R][D];
+#pragma unroll
+    for (int u = 0; u < R; ++u)
+#pragma unroll
+        for (int k = 0; k < D; ++k) racc[u][k] = 0.f;
+
+    // element e = lr*D + k of a walk's RB x D rows, loaded by thread e % NT (round e / NT)
+    auto load_rows = [&](const Cursor& c, float (&v)[RSH]) {
+        const float* src = X + (int64_t(c.l) * n + int64_t(c.I) * RB) * D;
+        const int lim = (n - c.I * RB) * D;            // elements inside the modality
+#pragma unroll
+        for (int t = 0; t < RSH; ++t) {
+            const int e = t * CWARPS * 32 + tid;
+            v[t] = (e < RB * D && e < lim) ? __ldcg(src + e) : 0.f;
+        }
+    };
+    auto put_rows = [&](const float (&v)[RSH], float* buf, float xs) {
+#pragma unroll
+        for (int t = 0; t < RSH; ++t) {
+            const int e = t * CWARPS * 32 + tid;
+            if (e < RB * D) {
+                const int lr = e / D, k = e - lr * D;
+                const int u = lr >> 3, g = lr & 7;
+                const float x = v[t] * xs;
+                *reinterpret_cast<float2*>(buf + ((k / 2 * R + u) * 8 + g) * 4 + 2 * (k & 1)) = make_float2(x, x);
+            }
+        }
+    };
+    // the first segment's rows: every thread its share, then one CTA barrier (no wait of
+    // this pass has run yet, so every thread reaches it)
+    {
+        float v[RSH];
+        load_rows(cc, v);
+        put_rows(v, rg.xrow, p.xscale[cc.l]);
+        __syncthreads();
+    }
+    if (warp == 0) {
+        // x_j of this pass's first uses (their Delta may have been issued during the
+        // previous pass, before this iterate existed)
+        Cursor c = cc;
+        const int k0 = nq < STAGES ? nq : STAGES;
+        for (int j = 0; j < k0; ++j) {
+            rg.issue_x(p, X, qbase + j, c);
+            if (j + 1 < k0) cursor_next(c, p);
+        }
+    }
+    FF fid{0.f, 0.f};
+    int cur_l = cc.l;
+#ifdef FJOFC_STAMPS
+    unsigned long long fj_wait[4] = {0, 0, 0, 0};
+#endif
+
+    int stage = int(qbase % STAGES);
+    uint32_t kuse = uint32_t(qbase / STAGES);
+    for (int q = 0; q < nq; ++q) {
+        const int64_t qg = qbase + q;
+        const int r0 = cc.I * RB;
+        const int c0 = r0 + cc.s * CW;
+        const bool walk_ends = (cc.s + 1 == cc.L);
+        const bool last = (q + 1 == nq);
+        if (!last) cursor_next(cn, p);
+        float rs[RSH];                                 // the next segment's rows, in flight
+        if (walk_ends && !last) load_rows(cn, rs);
+        if (cc.l != cur_l) {                           // modality changed inside this CTA's range
+            fid_total = ff_add(fid_total, ff_mul(fid, p.wfid[cur_l]));
+            fid = FF{0.f, 0.f};
+            cur_l = cc.l;
+        }
+        {
+            FJ_WAIT_T0();
+            if (!mbar_wait_or_abort(smem_u32(&rg.full[stage]), kuse & 1u, abort_flag)) return false;
+            FJ_WAIT_ADD(1);
+        }
+        float2 nxj[C / 2][D];
+        {
+            FJ_WAIT_T0();
+            if (!mbar_wait_or_abort(smem_u32(&rg.xfull[stage]), kuse & 1u, abort_flag)) return false;
+            FJ_WAIT_ADD(2);
+            const int64_t start = (int64_t(cc.l) * n + c0) * D;
+            const int cbase = warp * SW + cl * C;      // first column of the lane
+            const uint32_t xsrc = smem_u32(rg.xs + size_t(stage) * S::XS_FLOATS + int(start & 3) + cbase * D);
+            const float nxsc = -p.xscale[cc.l];
+#pragma unroll
+            for (int c = 0; c < C; c += 2)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const bool in0 = c0 + cbase + c < n, in1 = c0 + cbase + c + 1 < n;
+                    nxj[c / 2][k] = make_float2(in0 ? lds_f1(xsrc + 4 * (c * D + k)) * nxsc : 0.f,
+                                                in1 ? lds_f1(xsrc + 4 * ((c + 1) * D + k)) * nxsc : 0.f);
+                }
+        }
+        const uint32_t tile = smem_u32(rg.stages + size_t(stage) * S::STAGE_ELEMS);
+        const bool masked = (cc.s * CW < RB) || (c0 + CW > n);
+        float2 cacc[C / 2][D];
+        float2 sf;
+        const uint32_t xib = smem_u32(rg.xrow + (seg & 1) * XBUF);
+        if (!masked)
+            strip_pairs<D, TD, R, C, RB, SW, false>(tile, warp, rgp, cl, r0, c0, n, xib, nxj, racc, cacc, sf);
+        else
+            strip_pairs<D, TD, R, C, RB, SW, true>(tile, warp, rgp, cl, r0, c0, n, xib, nxj, racc, cacc, sf);
+        // release the stage; the last warp to do so refills it with use qg + STAGES
+        const bool refill = qg + STAGES < rg.total_q;
+        __syncwarp();
+        int is_last = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            if (atomicAdd(&rg.released[stage], 1) == int(kuse + 1) * CWARPS - 1) {
+                __threadfence_block();
+                is_last = 1;
+                if (refill) rg.issue(tm, qg + STAGES);
+            }
+        }
+        is_last = __shfl_sync(0xffffffffu, is_last, 0);
+        if (is_last && refill && q + STAGES < nq) rg.issue_x(p, X, qg + STAGES, rg.pc);
+        if (refill) rg.advance(p);
+        fid = ff_add(fid, sf.x + sf.y);
+
+        // this sub-tile's column sums: reduce-scatter over the eight row groups (lane bits
+        // 2..4); the writer lane of each (column, coordinate) stores its total, negated
+        // (the accumulators hold the rows' sign)
+        {
+            float v[C * D];
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int k = 0; k < D; ++k) v[c * D + k] = (c & 1) ? cacc[c / 2][k].y : cacc[c / 2][k].x;
+            int base = 0;
+            bool writer = true;
+            LaneScatter<C * D, 16, 4>::run(v, lane, base, writer);
+            constexpr int F = LaneScatter<C * D, 16, 4>::F;
+            float* cpart = p.colpart + cc.t * int64_t(D * CW);
+            if (writer)
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    const int e = base + f, c = e / D, k = e - c * D;
+                    cpart[k * CW + warp * SW + cl * C + c] = -v[f];
+                }
+        }
+
+        if (walk_ends || last) {
+            // row partials of this walk segment: the sum over the four column groups in the
+            // warp (lane bits 0, 1), then over the eight warps through shared memory
+            FJ_WAIT_T0();
+            if (rg.nflush >= 1 &&
+                !mbar_wait_or_abort(smem_u32(&rg.rempty[0]), uint32_t((rg.nflush - 1) & 1), abort_flag))
+                return false;
+            FJ_WAIT_ADD(3);
+            {
+                float v[R * D];
+#pragma unroll
+                for (int u = 0; u < R; ++u)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) v[u * D + k] = racc[u][k];
+                int base = 0;
+                bool writer = true;
+                LaneScatter<R * D, 2, 1>::run(v, lane, base, writer);
+                constexpr int F = LaneScatter<R * D, 2, 1>::F;
+                if (writer)
+#pragma unroll
+                    for (int f = 0; f < F; ++f) {
+                        const int e = base + f, u = e / D, k = e - u * D;
+                        rg.red[(warp * D + k) * RB + rgp + 8 * u] = v[f];
+                    }
+            }
+            if (walk_ends && !last) put_rows(rs, rg.xrow + ((seg + 1) & 1) * XBUF, p.xscale[cn.l]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&rg.rfull[0]));
+            {
+                FJ_WAIT_T0();
+                if (!mbar_wait_or_abort(smem_u32(&rg.rfull[0]), uint32_t(rg.nflush & 1), abort_flag)) return false;
+                FJ_WAIT_ADD(0);
+            }
+            float* dst = seg_head ? p.rowhead + (int64_t(cc.l) * p.nRB + cc.I) * (D * RB)
+                                  : p.rowcont + int64_t(b) * (D * RB);
+            constexpr int SHARE = (RB * D + CWARPS - 1) / CWARPS;
+            for (int e = warp * SHARE + lane; e < (warp + 1) * SHARE && e < RB * D; e += 32) {
+                const int k = e / RB, row = e - k * RB;
+                float v = 0.f;
+#pragma unroll
+                for (int w = 0; w < CWARPS; ++w) v += rg.red[(w * D + k) * RB + row];
+                dst[e] = v;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&rg.rempty[0]));
+            ++rg.nflush;
+            ++seg;
+            seg_head = true;
+#pragma unroll
+            for (int u = 0; u < R; ++u)
+#pragma unroll
+                for (int k = 0; k < D; ++k) racc[u][k] = 0.f;
+        }
+        cursor_next(cc, p);
+        if (++stage == STAGES) {
+            stage = 0;
+            ++kuse;
+        }
+    }
+    fid_total = ff_add(fid_total, ff_mul(fid, p.wfid[cur_l]));
+#ifdef FJOFC_STAMPS
+    if (threadIdx.x == 0 && blockIdx.x < 1024) {
+        for (int x = 0; x < 4; ++x) atomicAdd(&g_waitcyc[blockIdx.x][x], fj_wait[x]);
+        atomicAdd(&g_waitcyc[blockIdx.x][4], 1ull);
+    }
+#endif
+    return true;
+}
+
 // Standalone pass (one launch per Guttman transform, used when the persistent kernel is
 // not: per-kernel timing).  Same ring, tiles and partials as the persistent kernel.
 template <int D, typename TD>
@@ -753,7 +1150,10 @@ k_guttman_pass(const __grid_constant__ TMaps tm, const __grid_constant__ K1Param
     rg.start(tm, p, t_begin, nq, nq, &s_issued, &s_abort);
 
     FF fid_total{0.f, 0.f};
-    if (!phase_a<D, TD>(rg, tm, p, p.X, 0, b, fid_total)) {
+    bool ok_a;
+    if constexpr (S::STRIP) ok_a = phase_a_strip<D, TD>(rg, tm, p, p.X, 0, b, fid_total);
+    else ok_a = phase_a<D, TD>(rg, tm, p, p.X, 0, b, fid_total);
+    if (!ok_a) {
         atomicExch(&s_abort, 1);
         if (lane == 0) raise_error(p.st, FJOFC_ERR_TIMEOUT, 2);
     }
@@ -802,7 +1202,7 @@ int k1_bps_impl() {
 template <int D, typename TD>
 K1Geom k1_geom_impl() {
     using S = K1Shape<D, TD>;
-    return K1Geom{S::R, S::C, S::CWARPS, S::STAGES, S::RB, S::CW, S::NT, S::SMEM};
+    return K1Geom{S::R, S::C, S::CWARPS, S::STAGES, S::RB, S::CW, S::NT, S::SMEM, S::STRIP ? S::BOX_ELEMS : 0};
 }
 
 #define FJOFC_INSTANTIATE_K1(D)                                                                   \

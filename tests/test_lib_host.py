@@ -33,7 +33,8 @@ def test_header_declares_expected_api():
                                             "fjofc_mlp_gradient", "fjofc_mlp_train", "fjofc_mlp_broadcast",
                                             "fjofc_mlp_select", "fjofc_plan_create", "fjofc_plan_run",
                                             "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy",
-                                            "fjofc_plan_autotune", "fjofc_init_cmds", "fjofc_test_barrier_skew"])
+                                            "fjofc_plan_autotune", "fjofc_init_cmds", "fjofc_test_barrier_skew",
+                                            "fjofc_transform_rows"])
 
 
 def test_library_loads_and_exports_every_declared_symbol():
