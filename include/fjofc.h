@@ -112,8 +112,17 @@ typedef struct fjofc_opts {
                              spinning; X then holds X_0 or an earlier iterate of the call
                              (the loop keeps every third iterate in the caller's buffer),
                              X_0 as given when the first pass timed out. */
-    int32_t reserved[3];  /* must be zero */
+    int32_t delta_layout; /* in-sample entry points: FJOFC_LAYOUT_FULL (each Delta_i a whole n x n
+                             matrix, row stride ld) or FJOFC_LAYOUT_PACKED (each Delta_i in
+                             the packed band layout of fjofc_pack_delta, ld = the packed row
+                             stride fjofc_packed_size returns): about half the memory, the same
+                             results bit for bit.  check_inputs is not available with it. */
+    int32_t reserved[2];  /* must be zero */
 } fjofc_opts;
+
+/* Delta storage layouts (fjofc_opts.delta_layout) */
+#define FJOFC_LAYOUT_FULL   0
+#define FJOFC_LAYOUT_PACKED 1
 
 typedef struct fjofc_result {
     int32_t status;             /* copy of the return value */
@@ -452,6 +461,23 @@ typedef struct {
  * non-NULL the call synchronises the stream. */
 int fjofc_mlp_train(float* params, int32_t n_in, int32_t hidden, int32_t n_out, const uint16_t* x, const float* y,
                     int64_t count, const fjofc_mlp_train_opts* opts, float* loss_history, void* cuda_stream);
+
+/*
+ * Packed storage of a symmetric Delta (the paper's Delta_i are symmetric, Sec. 1.2, and the
+ * all-pairs pass reads each unordered pair once, Remark faststress).  The rows are cut
+ * into bands of 128 rows; band b keeps its columns from the diagonal on, [128 b, n), and
+ * bands b and nB - 1 - b (nB = ceil(n / 128)) share packed rows side by side, so the
+ * packed matrix has ceil(nB / 2) * 128 rows of *ld_out elements (about n (n + 128) / 2
+ * elements in all; each band's width rounded up to 16 bytes).
+ *
+ * fjofc_packed_size: elements of one packed matrix for n objects and element type
+ * delta_dtype; *ld_out (may be NULL) receives its row stride.  -1 for invalid arguments.
+ * fjofc_pack_delta: writes the packed form of the DEVICE n x n matrix delta (row stride
+ * ld, element type delta_dtype) into the DEVICE buffer packed (fjofc_packed_size elements,
+ * 16-byte aligned); stream-ordered, no synchronisation.  Padding elements are zero.
+ */
+int64_t fjofc_packed_size(int64_t n, int32_t delta_dtype, int64_t* ld_out);
+int fjofc_pack_delta(int64_t n, const void* delta, int64_t ld, int32_t delta_dtype, void* packed, void* cuda_stream);
 
 /* Test support for the bounded-wait error path (the paper has no counterpart).  The
  * next in-sample loop started by fjofc_embed or fjofc_embed_noalloc in this process

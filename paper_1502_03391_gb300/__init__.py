@@ -38,7 +38,7 @@ EXPORTS = ("fjofc_embed", "fjofc_embed_noalloc", "fjofc_stress", "fjofc_oos", "f
            "fjofc_mlp_param_count", "fjofc_mlp_init", "fjofc_mlp_features", "fjofc_mlp_forward", "fjofc_mlp_gradient",
            "fjofc_mlp_train", "fjofc_mlp_broadcast", "fjofc_mlp_select", "fjofc_plan_create", "fjofc_plan_run",
            "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy", "fjofc_plan_autotune", "fjofc_init_cmds",
-           "fjofc_test_barrier_skew", "fjofc_transform_rows")
+           "fjofc_test_barrier_skew", "fjofc_transform_rows", "fjofc_packed_size", "fjofc_pack_delta")
 
 
 class FjofcError(RuntimeError):
@@ -51,7 +51,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("tol_mode", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("relax", ctypes.c_float), ("oos_form", ctypes.c_int32),
                 ("check_inputs", ctypes.c_int32), ("deterministic", ctypes.c_int32),
-                ("wait_limit_us", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("wait_limit_us", ctypes.c_int32), ("delta_layout", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class _Result(ctypes.Structure):
@@ -114,6 +114,10 @@ def _load():
     lib.fjofc_transform_rows.argtypes = [i32, i64, i32, i64, i64, ctypes.POINTER(vp), i64, i32,
                                          ctypes.POINTER(ctypes.c_float), dp, vp, dp, vp, dp, vp]
     lib.fjofc_transform_rows.restype = ctypes.c_int
+    lib.fjofc_packed_size.argtypes = [i64, i32, ctypes.POINTER(i64)]
+    lib.fjofc_packed_size.restype = ctypes.c_int64
+    lib.fjofc_pack_delta.argtypes = [i64, vp, i64, i32, vp, vp]
+    lib.fjofc_pack_delta.restype = ctypes.c_int
     lib.fjofc_test_barrier_skew.argtypes = [i32]
     lib.fjofc_test_barrier_skew.restype = None
     lib.fjofc_strerror.argtypes = [ctypes.c_int]
@@ -240,25 +244,33 @@ class EmbedResult:
 def embed(deltas: Sequence, weights, X, max_iter: int, tol: float = -1.0, tol_mode: str = "relative",
           delta_scale=None, stream=None, history: bool = True, check: bool = True,
           profile: int = 0, relax: float = 1.0, check_inputs: bool = False,
-          wait_limit_us: int = 0) -> EmbedResult:
+          wait_limit_us: int = 0, layout: str = "full", n: Optional[int] = None) -> EmbedResult:
     """In-sample fJOFC from ``X`` (in place).  ``deltas``: m CUDA n x n views (float32,
     float16 or bfloat16; row stride a multiple of 16 bytes); ``weights``: m x m;
     ``X``: contiguous float32 CUDA tensor of shape (m*n, d).  ``profile``: 0 none, 1 one
     launch per pass with per-kernel timing, 2 the persistent loop kernel timed.
     ``relax``: relaxed updates (1 = the plain Guttman transform, up to 2).
     ``check_inputs``: validate every Delta (finite, non-negative, symmetric) first.
-    ``wait_limit_us``: bound of the loop's grid-wide waits (0 = 2 s).  See
-    ``fjofc_embed``."""
+    ``wait_limit_us``: bound of the loop's grid-wide waits (0 = 2 s).
+    ``layout="packed"``: ``deltas`` are ``pack_delta`` outputs and ``n`` must be given.
+    See ``fjofc_embed``."""
     m = len(deltas)
-    n = int(deltas[0].shape[0])
+    packed = layout == "packed"
+    if packed and n is None:
+        raise ValueError("the packed layout needs n")
+    n = int(n) if packed else int(deltas[0].shape[0])
     if X.dtype != _torch().float32 or not X.is_contiguous() or X.dim() != 2 or X.shape[0] != m * n:
         raise ValueError("X must be a contiguous float32 (m*n, d) CUDA tensor")
     d = int(X.shape[1])
-    ld, code = _delta_layout(deltas, n)
+    if packed:
+        ld, code = int(deltas[0].shape[1]), _dtype_code(deltas[0])
+    else:
+        ld, code = _delta_layout(deltas, n)
     ptrs = (ctypes.c_void_p * m)(*[D.data_ptr() for D in deltas])
     Wn = _weights(weights, m)
     opts = _Opts(int(max_iter), float(tol), TOL_RELATIVE if tol_mode == "relative" else TOL_ABS_NORMALIZED,
                  int(profile), float(relax))
+    opts.delta_layout = 1 if packed else 0
     opts.check_inputs = 1 if check_inputs else 0
     opts.deterministic = 1
     opts.wait_limit_us = int(wait_limit_us)
@@ -309,6 +321,22 @@ def transform_rows(delta_rows: Sequence, weights, X, r0: int, r1: int, mu=None, 
                                    _stream_handle(stream, X.device))
     _check(st)
     return Xout, parts
+
+
+def pack_delta(D, stream=None):
+    """The packed band layout of a symmetric CUDA n x n matrix view (``fjofc_pack_delta``):
+    returns a 2-D CUDA tensor (packed rows, ld) to pass to ``embed(..., layout="packed")``."""
+    torch = _torch()
+    n = int(D.shape[0])
+    code = _dtype_code(D)
+    ld = ctypes.c_int64(0)
+    size = _lib.fjofc_packed_size(n, code, ctypes.byref(ld))
+    if size < 0:
+        raise ValueError("invalid size or type")
+    out = torch.empty(int(size), dtype=D.dtype, device=D.device).reshape(-1, ld.value)
+    _check(_lib.fjofc_pack_delta(n, ctypes.c_void_p(D.data_ptr()), int(D.stride(0)), code,
+                                 ctypes.c_void_p(out.data_ptr()), _stream_handle(stream, D.device)))
+    return out
 
 
 def test_barrier_skew(extra: int) -> None:
@@ -425,26 +453,34 @@ class Plan:
     same conventions as ``embed``; every problem gets the same loop options."""
 
     def __init__(self, problems, max_iter: int, tol: float = -1.0, tol_mode: str = "relative",
-                 autotune: bool = False, probe_iters: int = 8, allow_f16: bool = False, stream=None):
+                 autotune: bool = False, probe_iters: int = 8, allow_f16: bool = False, stream=None,
+                 layout: str = "full", n=None):
         """``autotune``: let ``fjofc_plan_autotune`` time candidate schedules (and float16
         storage of float32 Delta when ``allow_f16``) on ``probe_iters`` transforms and keep
-        the fastest; the choice is in ``self.tuning``."""
+        the fastest; the choice is in ``self.tuning``.  ``layout="packed"``: every Delta is
+        a ``pack_delta`` output and ``n`` lists the problems' object counts."""
         keep = []
+        packed = layout == "packed"
         arr = (_Problem * len(problems))()
         for i, pr in enumerate(problems):
             deltas, W, X = pr[0], pr[1], pr[2]
             scale = pr[3] if len(pr) > 3 else None
             m = len(deltas)
-            n = int(deltas[0].shape[0])
-            ld, code = _delta_layout(deltas, n)
+            if packed:
+                n_i = int(n[i])
+                ld, code = int(deltas[0].shape[1]), _dtype_code(deltas[0])
+            else:
+                n_i = int(deltas[0].shape[0])
+                ld, code = _delta_layout(deltas, n_i)
             ptrs = (ctypes.c_void_p * m)(*[D.data_ptr() for D in deltas])
             Wn = _weights(W, m)
             sc = _scales(scale, m)
             keep += [ptrs, Wn, sc]
-            arr[i] = _Problem(m, n, int(X.shape[1]), ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p)), ld, code,
+            arr[i] = _Problem(m, n_i, int(X.shape[1]), ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p)), ld, code,
                               ctypes.cast(sc, ctypes.POINTER(ctypes.c_float)) if sc is not None else None,
                               Wn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(X.data_ptr()))
         opts = _Opts(int(max_iter), float(tol), TOL_RELATIVE if tol_mode == "relative" else TOL_ABS_NORMALIZED)
+        opts.delta_layout = 1 if packed else 0
         h = ctypes.c_void_p()
         self.tuning = None
         if autotune:

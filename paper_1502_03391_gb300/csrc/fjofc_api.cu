@@ -299,7 +299,9 @@ int check_common_opts(const fjofc_opts& o) {
     if (o.check_inputs != 0 && o.check_inputs != 1) return arg_error("check_inputs must be 0 or 1");
     if (o.deterministic != 0 && o.deterministic != 1) return arg_error("deterministic must be 0 or 1");
     if (o.wait_limit_us < 0) return arg_error("wait_limit_us must be >= 0");
-    for (int r = 0; r < 3; ++r)
+    if (o.delta_layout != FJOFC_LAYOUT_FULL && o.delta_layout != FJOFC_LAYOUT_PACKED)
+        return arg_error("unknown delta_layout");
+    for (int r = 0; r < 2; ++r)
         if (o.reserved[r] != 0) return arg_error("opts.reserved must be zero");
     return FJOFC_OK;
 }
@@ -395,11 +397,20 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
                         const double* weights, const double* winv, float* X) {
     int rc;
     const int RB = P.g.RB, CW = P.g.CW;
-    // TMA descriptors: Delta_l as a 2-D tensor {n cols, n rows}, box {CW, RB} (row-band
-    // layout) or {128 bytes, RB} with the 128-byte swizzle (column-strip layout)
+    // TMA descriptors: Delta_l as a 2-D tensor {n cols, n rows} (packed layout: {L cols,
+    // packed rows}), box {CW, RB} (row-band layout) or {128 bytes, RB} with the 128-byte
+    // swizzle (column-strip layout)
     std::memset(&tm, 0, sizeof(tm));
+    const bool packed = o.delta_layout == FJOFC_LAYOUT_PACKED;
+    if (packed && ld != pack_width(n, int(dtype_size(dtype)))) {
+        snprintf(g_last_msg, sizeof(g_last_msg), "packed Delta needs ld = %lld (fjofc_packed_size)",
+                 (long long)pack_width(n, int(dtype_size(dtype))));
+        return FJOFC_ERR_ARG;
+    }
+    const int64_t nbands = (n + kPackBand - 1) / kPackBand;
     for (int l = 0; l < m; ++l) {
-        const cuuint64_t dims[2] = {cuuint64_t(n), cuuint64_t(n)};
+        const cuuint64_t dims[2] = {cuuint64_t(packed ? ld : n),
+                                    cuuint64_t(packed ? (nbands + 1) / 2 * kPackBand : n)};
         const cuuint64_t strides[1] = {cuuint64_t(ld) * dtype_size(dtype)};
         const bool strip = P.g.box_elems > 0;
         const cuuint32_t box[2] = {cuuint32_t(strip ? P.g.box_elems : CW), cuuint32_t(RB)};
@@ -417,6 +428,7 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
     k1.st = st;
     k1.m = m; k1.n = int(n); k1.d = d; k1.nRB = P.nRB; k1.G = P.G;
     k1.Tm = P.Tm; k1.T = P.T;
+    k1.packed = packed ? 1 : 0;
     // the all-pairs pass works in Delta's stored units (x / s_l), so its fidelity sum
     // carries s_l^2
     double dsc[FJOFC_MAX_M];
@@ -533,6 +545,15 @@ int run_insample_impl(int32_t m, int64_t n, int32_t d, const void* const* delta,
         o.tol_mode = FJOFC_TOL_RELATIVE;
     }
     if (ext && o.profile) return arg_error("profile timing is not available without allocation");
+    if (o.delta_layout == FJOFC_LAYOUT_PACKED && o.check_inputs) {
+        snprintf(g_last_msg, sizeof(g_last_msg), "check_inputs is not available with the packed Delta layout");
+        return FJOFC_ERR_UNSUPPORTED;
+    }
+    if (o.delta_layout == FJOFC_LAYOUT_PACKED && ld != pack_width(n, int(dtype_size(dtype)))) {
+        snprintf(g_last_msg, sizeof(g_last_msg), "packed Delta needs ld = %lld (fjofc_packed_size)",
+                 (long long)pack_width(n, int(dtype_size(dtype))));
+        return FJOFC_ERR_ARG;
+    }
     double winv[FJOFC_MAX_M * FJOFC_MAX_M];
     rc = weights_inverse(m, n, weights, winv);
     if (rc) return rc;
@@ -968,6 +989,26 @@ const char* fjofc_strerror(int status) {
         case FJOFC_ERR_UNSUPPORTED: return g_last_msg[0] ? g_last_msg : "unsupported configuration";
     }
     return "unknown status";
+}
+
+int64_t fjofc_packed_size(int64_t n, int32_t delta_dtype, int64_t* ld_out) {
+    if (n < 1 || n > (int64_t(1) << 30) ||
+        (delta_dtype != FJOFC_F32 && delta_dtype != FJOFC_F16 && delta_dtype != FJOFC_BF16))
+        return -1;
+    const int es = int(dtype_size(delta_dtype));
+    const int64_t L = pack_width(n, es);
+    const int64_t nb = (n + kPackBand - 1) / kPackBand;
+    if (ld_out) *ld_out = L;
+    return (nb + 1) / 2 * kPackBand * L;
+}
+
+int fjofc_pack_delta(int64_t n, const void* delta, int64_t ld, int32_t delta_dtype, void* packed, void* cuda_stream) {
+    if (fjofc_packed_size(n, delta_dtype, nullptr) < 0) return arg_error("invalid n or delta_dtype");
+    if (!delta || !packed) return arg_error("NULL pointer");
+    if (ld < n) return arg_error("ld must be >= n");
+    if (reinterpret_cast<uintptr_t>(packed) % 16 != 0) return arg_error("packed must be 16-byte aligned");
+    FJ_CUDA(launch_pack_delta(delta, n, ld, delta_dtype, packed, static_cast<cudaStream_t>(cuda_stream)));
+    return FJOFC_OK;
 }
 
 void fjofc_test_barrier_skew(int32_t extra) { g_barrier_skew.store(extra > 0 ? extra : 0); }

@@ -139,8 +139,10 @@ int create_plan(const fjofc_problem* probs, int32_t nprob, const fjofc_opts* opt
     if (std::isnan(o.tol)) return fail(FJOFC_ERR_ARG, "tol is NaN");
     if (o.profile != 0) return fail(FJOFC_ERR_ARG, "profile must be 0 for a plan");
     if (!(o.relax >= 0.f && o.relax <= 2.f)) return fail(FJOFC_ERR_ARG, "relax must be in [0, 2]");
-    for (int r = 0; r < 3; ++r)
+    for (int r = 0; r < 2; ++r)
         if (o.reserved[r] != 0) return fail(FJOFC_ERR_ARG, "opts.reserved must be zero");
+    if (o.delta_layout != FJOFC_LAYOUT_FULL && o.delta_layout != FJOFC_LAYOUT_PACKED)
+        return fail(FJOFC_ERR_ARG, "unknown delta_layout");
     if (o.deterministic != 0 && o.deterministic != 1) return fail(FJOFC_ERR_ARG, "deterministic must be 0 or 1");
     if (o.wait_limit_us < 0) return fail(FJOFC_ERR_ARG, "wait_limit_us must be >= 0");
     if (o.check_inputs != 0)
@@ -411,7 +413,8 @@ extern "C" int fjofc_plan_autotune(const fjofc_problem* probs, int32_t nprob, co
     *out = nullptr;
     if (!probs || nprob < 1 || !opts) return fail(FJOFC_ERR_ARG, "need problems and opts");
     const int probe = (topts && topts->probe_iters > 0) ? topts->probe_iters : 8;
-    const bool allow16 = topts && topts->allow_f16;
+    // float16 copies are made of whole n x n matrices: not for the packed layout
+    const bool allow16 = topts && topts->allow_f16 && !(opts && opts->delta_layout == FJOFC_LAYOUT_PACKED);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e;
 

@@ -43,6 +43,38 @@ struct K1Geom {
 // Geometry of the K1 instantiation used for embedding dimension d.
 K1Geom k1_geometry(int d, int dtype);
 
+// Packed storage of a symmetric Delta (fjofc_opts.delta_layout = FJOFC_LAYOUT_PACKED): the
+// rows are cut into bands of kPackBand rows; band b keeps only its columns from the
+// diagonal on, [kPackBand b, n), row stride aligned to 16 bytes (width W_b = align(n -
+// kPackBand b)), and bands b and nB - 1 - b share packed rows side by side (b first), so
+// the packed matrix is ceil(nB / 2) kPackBand rows of width L = max over pairs of the two
+// widths: about half of n^2.  kPackBand is a multiple of every all-pairs row block.
+constexpr int kPackBand = 128;
+__host__ __device__ inline int64_t pack_align(int64_t w, int esize) {
+    const int64_t a = 16 / esize;
+    return (w + a - 1) / a * a;
+}
+// Width of the packed rows (elements).
+__host__ __device__ inline int64_t pack_width(int64_t n, int esize) {
+    const int64_t nb = (n + kPackBand - 1) / kPackBand;
+    int64_t L = 0;
+    for (int64_t b = 0; b <= (nb - 1) / 2; ++b) {
+        const int64_t c = nb - 1 - b;
+        const int64_t w = pack_align(n - kPackBand * b, esize) + (c != b ? pack_align(n - kPackBand * c, esize) : 0);
+        L = w > L ? w : L;
+    }
+    return L;
+}
+// Packed position (x = column, y = row) of Delta[row r][column c >= the band's start].
+__host__ __device__ inline void pack_pos(int64_t n, int esize, int64_t r, int64_t c, int64_t& x, int64_t& y) {
+    const int64_t nb = (n + kPackBand - 1) / kPackBand;
+    const int64_t b = r / kPackBand, pb = nb - 1 - b;
+    const bool right = b > pb;                       // the second band of its pair
+    const int64_t pair = right ? pb : b;
+    x = (right ? pack_align(n - kPackBand * pb, esize) : 0) + (c - kPackBand * b);
+    y = kPackBand * pair + (r - kPackBand * b);
+}
+
 struct K1Params {
     const float* X;            // X_{t-1}: (m*n) x d row-major
     float* colpart;            // [T][d][CW]   column partials of B'X per sub-tile
@@ -56,6 +88,7 @@ struct K1Params {
     int64_t Tm, T;             // sub-tiles per modality, total
     float wfid[FJOFC_MAX_M];   // w_ll s_l^2: weight of the fidelity sum in scaled units
     float xscale[FJOFC_MAX_M]; // 1 / s_l: coordinates of modality l in Delta's stored units
+    int packed;                // 1: Delta in the packed band layout (pack_pos)
 };
 
 // CTAs of the K1 instantiation that fit on one SM.
@@ -165,6 +198,7 @@ struct CheckParams {
     DevStatus* st;
 };
 cudaError_t launch_check_delta(const CheckParams& p, cudaStream_t s);
+cudaError_t launch_pack_delta(const void* D, int64_t n, int64_t ld, int dtype, void* P, cudaStream_t s);
 cudaError_t launch_init(const InitParams& p, cudaStream_t s);
 cudaError_t launch_init_batched(const InitParams* ps, int count, cudaStream_t s);
 // float32 Delta -> float16 storage for the batched tuner: largest |Delta| (float bits,

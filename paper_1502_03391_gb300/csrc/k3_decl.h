@@ -18,14 +18,15 @@ constexpr int kK3rMaxD = 8;                       // instantiated for d = 1..8
 // alignment stay inside the 227 KB per CTA)
 constexpr size_t kK3rSmemBudget = size_t(200) * 1024;
 // [m][d][nx] -x and [m][nx] delta, then the per-object state: y [m][d], per-warp sums
-// [warps][m][d + 3], totals [m][d + 1] (floats) and the fidelities [m] (doubles)
+// [warps][m][d + 3], totals [m][d + 1] (floats), the fidelities [m] and the
+// commensurability parts [m] (doubles)
 __host__ __device__ inline size_t k3r_state_floats(int m, int d) {
     const size_t f = size_t(m) * d + size_t(kK3rWarps) * m * (d + 3) + size_t(m) * (d + 1);
     return (f + 1) & ~size_t(1);                  // the doubles after it stay 8-byte aligned
 }
 inline size_t k3r_smem_bytes(int m, int64_t nx, int d) {
     return size_t(m) * size_t(nx) * size_t(d + 1) * sizeof(float) + k3r_state_floats(m, d) * sizeof(float) +
-           size_t(m) * sizeof(double);
+           2 * size_t(m) * sizeof(double);
 }
 inline bool k3r_fits(int m, int64_t nx, int d) {
     return d >= 1 && d <= kK3rMaxD && k3r_smem_bytes(m, nx, d) <= kK3rSmemBudget;

@@ -309,6 +309,46 @@ cudaError_t launch_check_delta(const CheckParams& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Packed band layout of a symmetric Delta (pack_pos): CTA y writes packed row y; element x
+// comes from band b = the pair's left band while x < its width, else the right band;
+// padding and positions past n are zero.
+template <typename TD>
+__global__ void __launch_bounds__(256) k_pack_delta(const TD* __restrict__ D, int64_t n, int64_t ld, TD* __restrict__ P,
+                                                    int64_t L) {
+    const int64_t y = blockIdx.x;
+    const int64_t nb = (n + kPackBand - 1) / kPackBand;
+    const int64_t pair = y / kPackBand, ro = y - pair * kPackBand, other = nb - 1 - pair;
+    const int es = int(sizeof(TD));
+    const int64_t wl = pack_align(n - kPackBand * pair, es);
+    const int64_t wr = other != pair ? pack_align(n - kPackBand * other, es) : 0;
+    for (int64_t x = threadIdx.x; x < L; x += blockDim.x) {
+        int64_t b = -1, rel = 0;
+        if (x < wl) { b = pair; rel = x; }
+        else if (x - wl < wr) { b = other; rel = x - wl; }
+        TD v = TD(0.f);
+        if (b >= 0) {
+            const int64_t r = kPackBand * b + ro, c = kPackBand * b + rel;
+            if (r < n && c < n) v = D[r * ld + c];
+        }
+        P[y * L + x] = v;
+    }
+}
+
+cudaError_t launch_pack_delta(const void* D, int64_t n, int64_t ld, int dtype, void* P, cudaStream_t s) {
+    const int es = dtype == FJOFC_F32 ? 4 : 2;
+    const int64_t L = pack_width(n, es);
+    const int64_t nb = (n + kPackBand - 1) / kPackBand;
+    const int64_t rows = (nb + 1) / 2 * kPackBand;
+    if (dtype == FJOFC_F32)
+        k_pack_delta<float><<<unsigned(rows), 256, 0, s>>>(static_cast<const float*>(D), n, ld, static_cast<float*>(P), L);
+    else if (dtype == FJOFC_F16)
+        k_pack_delta<__half><<<unsigned(rows), 256, 0, s>>>(static_cast<const __half*>(D), n, ld, static_cast<__half*>(P), L);
+    else
+        k_pack_delta<__nv_bfloat16><<<unsigned(rows), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(D), n, ld,
+                                                                   static_cast<__nv_bfloat16*>(P), L);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(float* Xout, const float* buf1, const float* buf2, int64_t count,
                             const DevStatus* st, cudaStream_t s) {
     const int threads = 256;

@@ -350,6 +350,8 @@ struct K1Ring {
     int* abort_flag;       // set by a warp whose bounded wait gave up
     Cursor pc;             // cursor of the next use to issue (every thread keeps a copy)
     int pc_local;
+    int packed;            // Delta in the packed band layout
+    int64_t n;
     int64_t t_begin;
     int nq;
     int64_t total_q;
@@ -379,14 +381,16 @@ struct K1Ring {
         const uint32_t bar = smem_u32(&full[stage]);
         mbar_arrive_expect_tx(bar, S::STAGE_BYTES);
         const uint32_t dst = smem_u32(stages + size_t(stage) * S::STAGE_ELEMS);
+        // the sub-tile's first element: Delta[I RB][I RB + s CW], or its packed position
+        int64_t x0 = int64_t(pc.I) * S::RB + int64_t(pc.s) * S::CW, y0 = int64_t(pc.I) * S::RB;
+        if (packed) pack_pos(n, int(sizeof(TD)), y0, x0, x0, y0);
         if constexpr (S::STRIP) {
-            // BOXES boxes of 128 bytes x RB rows; x is a multiple of 128 bytes
+            // BOXES boxes of 128 bytes x RB rows; x is a multiple of 16 bytes
 #pragma unroll
             for (int bx = 0; bx < S::BOXES; ++bx)
-                tma_load_2d(dst + uint32_t(bx) * S::RB * 128u, &tm.map[pc.l],
-                            pc.I * S::RB + pc.s * S::CW + bx * S::BOX_ELEMS, pc.I * S::RB, bar);
+                tma_load_2d(dst + uint32_t(bx) * S::RB * 128u, &tm.map[pc.l], int(x0) + bx * S::BOX_ELEMS, int(y0), bar);
         } else {
-            tma_load_2d(dst, &tm.map[pc.l], pc.I * S::RB + pc.s * S::CW, pc.I * S::RB, bar);
+            tma_load_2d(dst, &tm.map[pc.l], int(x0), int(y0), bar);
         }
     }
 
@@ -431,6 +435,8 @@ struct K1Ring {
         total_q = total_q_;
         pc_local = 0;
         nflush = 0;
+        packed = p.packed;
+        n = p.n;
         cursor_init(pc, t_begin, p);
         if (threadIdx.x == 0) {
             for (int s = 0; s < S::STAGES; ++s) {

@@ -4,12 +4,14 @@
 //
 // Everything runs in the kernels of this file: landmark gather (float16 features),
 // forward, backward, loss, Adam, parameter initialisation, batch gather.  The matrix
-// products are small (at most 512 x 512 x batch; about 0.1 % of the out-of-sample solve's
-// time) and are computed by one SIMT float32 kernel, k_gemm, over strided operand views:
+// products are small (at most 512 x 512 x batch) and are computed by one SIMT float32
+// kernel, k_gemm, over strided operand views:
 //   C[i][j] = sum_k A(i, k) B(k, j),  A(i,k) = a[i*sar + k*sac],  B(k,j) = b[k*sbr + j*sbc],
-// 64 x 64 output tiles, 16-deep k slices staged in shared memory, 4 x 4 outputs per
-// thread accumulated in a fixed k order (deterministic results).  Epilogues: + bias
-// (per column), GELU (storing the pre-activation too), or x GELU'(z) (backward).
+// 64 x 64 output tiles, 16-deep k slices staged in shared memory in the order of each
+// view's unit stride (coalesced), the next slice prefetched into registers, 4 x 4 outputs
+// per thread accumulated in a fixed k order; products with few tiles split k into up to 4
+// ranges whose partial sums are added in range order (deterministic results).  Epilogues:
+// + bias (per column), GELU (storing the pre-activation too), or x GELU'(z) (backward).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -38,45 +40,88 @@ __device__ __forceinline__ float ld_as_float(const TA* p) { return float(*p); }
 template <>
 __device__ __forceinline__ float ld_as_float<__half>(const __half* p) { return __half2float(*p); }
 
-// C (M x N, row stride ldc) = A B with the epilogue E.
+// Epilogue of one output element (the pre-activation z goes to zout for BiasGelu).
+template <Epi E>
+__device__ __forceinline__ float epilogue(float v, int64_t o, int j, const float* __restrict__ bias,
+                                          float* __restrict__ zout, const float* __restrict__ zin) {
+    if constexpr (E == Epi::BiasGelu) {
+        v += bias[j];
+        zout[o] = v;
+        v = gelu_f(v);
+    } else if constexpr (E == Epi::Bias) {
+        v += bias[j];
+    } else if constexpr (E == Epi::GeluGrad) {
+        v *= gelu_grad_f(zin[o]);
+    }
+    return v;
+}
+
+// C (M x N, row stride ldc) = A B with the epilogue E, over the k range [kb, ke) of
+// split blockIdx.z (ke - kb a multiple of TK except at K).  With splits > 1 the kernel
+// writes raw partial products to part[z][M][N] and k_gemm_reduce applies the epilogue.
 //   BiasGelu: Z = AB + bias[j] -> zout, C = gelu(Z)
 //   Bias:     C = AB + bias[j]
 //   GeluGrad: C = AB * gelu'(zin[i*ldc + j])
+// Operand slabs are staged in shared memory in the order of their unit stride (k or i for
+// A, j or k for B) so that a warp's loads are coalesced for every view, and the next slab
+// is loaded into registers while the current one is used (two shared buffers).
 template <typename TA, typename TB, Epi E>
 __global__ void __launch_bounds__(GEMM_THREADS)
-k_gemm(int M, int N, int K, const TA* __restrict__ a, int64_t sar, int64_t sac, const TB* __restrict__ b,
+k_gemm(int M, int N, int K, int kspan, const TA* __restrict__ a, int64_t sar, int64_t sac, const TB* __restrict__ b,
        int64_t sbr, int64_t sbc, float* __restrict__ c, int64_t ldc, const float* __restrict__ bias,
-       float* __restrict__ zout, const float* __restrict__ zin) {
-    __shared__ float As[TK][TM + 4];
-    __shared__ float Bs[TK][TN + 4];
+       float* __restrict__ zout, const float* __restrict__ zin, float* __restrict__ part) {
+    __shared__ float As[2][TK][TM + 4];
+    __shared__ float Bs[2][TK][TN + 4];
     const int tid = threadIdx.x;
     const int ty = tid / 16, tx = tid % 16;          // 16 x 16 threads, 4 x 4 outputs each
     const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += TK) {
-        // stage A[i0..i0+63][k0..k0+15] and B[k0..k0+15][j0..j0+63] (zero outside)
-        for (int e = tid; e < TM * TK; e += GEMM_THREADS) {
-            const int ii = e / TK, kk = e % TK;
+    const int kb = blockIdx.z * kspan, ke = min(K, kb + kspan);
+    const bool a_kfast = (sac == 1), b_jfast = (sbc == 1);
+    constexpr int PER = TM * TK / GEMM_THREADS;      // 4 elements of each operand per thread
+    float ra[PER], rb[PER];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int e = t * GEMM_THREADS + tid;
+            const int ii = a_kfast ? e / TK : e % TM, kk = a_kfast ? e % TK : e / TM;
             const int i = i0 + ii, k = k0 + kk;
-            As[kk][ii] = (i < M && k < K) ? ld_as_float(a + int64_t(i) * sar + int64_t(k) * sac) : 0.f;
+            ra[t] = (i < M && k < ke) ? ld_as_float(a + int64_t(i) * sar + int64_t(k) * sac) : 0.f;
+            const int jj = b_jfast ? e % TN : e / TK, kb2 = b_jfast ? e / TN : e % TK;
+            const int j = j0 + jj, k2 = k0 + kb2;
+            rb[t] = (k2 < ke && j < N) ? ld_as_float(b + int64_t(k2) * sbr + int64_t(j) * sbc) : 0.f;
         }
-        for (int e = tid; e < TK * TN; e += GEMM_THREADS) {
-            const int kk = e / TN, jj = e % TN;
-            const int k = k0 + kk, j = j0 + jj;
-            Bs[kk][jj] = (k < K && j < N) ? ld_as_float(b + int64_t(k) * sbr + int64_t(j) * sbc) : 0.f;
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int e = t * GEMM_THREADS + tid;
+            const int ii = a_kfast ? e / TK : e % TM, kk = a_kfast ? e % TK : e / TM;
+            As[buf][kk][ii] = ra[t];
+            const int jj = b_jfast ? e % TN : e / TK, kb2 = b_jfast ? e / TN : e % TK;
+            Bs[buf][kb2][jj] = rb[t];
         }
-        __syncthreads();
+    };
+    float acc[4][4] = {};
+    int buf = 0;
+    load(kb);
+    store(0);
+    __syncthreads();
+    for (int k0 = kb; k0 < ke; k0 += TK) {
+        const bool more = k0 + TK < ke;
+        if (more) load(k0 + TK);
 #pragma unroll
         for (int kk = 0; kk < TK; ++kk) {
-            float av[4], bv[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) av[r] = As[kk][ty * 4 + r];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) bv[q] = Bs[kk][tx * 4 + q];
+            const float4 av = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+            const float4 bv = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+            const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(av[r], bv[q], acc[r][q]);
+                for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(a4[r], b4[q], acc[r][q]);
+        }
+        if (more) {
+            store(buf ^ 1);
+            buf ^= 1;
         }
         __syncthreads();
     }
@@ -88,27 +133,58 @@ k_gemm(int M, int N, int K, const TA* __restrict__ a, int64_t sar, int64_t sac, 
         for (int q = 0; q < 4; ++q) {
             const int j = j0 + tx * 4 + q;
             if (j >= N) continue;
-            const int64_t o = int64_t(i) * ldc + j;
-            float v = acc[r][q];
-            if constexpr (E == Epi::BiasGelu) {
-                v += bias[j];
-                zout[o] = v;
-                v = gelu_f(v);
-            } else if constexpr (E == Epi::Bias) {
-                v += bias[j];
-            } else if constexpr (E == Epi::GeluGrad) {
-                v *= gelu_grad_f(zin[o]);
+            if (part) {
+                part[(int64_t(blockIdx.z) * M + i) * N + j] = acc[r][q];
+            } else {
+                const int64_t o = int64_t(i) * ldc + j;
+                c[o] = epilogue<E>(acc[r][q], o, j, bias, zout, zin);
             }
-            c[o] = v;
         }
     }
 }
 
+// Sum of the split partial products in split order, then the epilogue.
+template <Epi E>
+__global__ void __launch_bounds__(256) k_gemm_reduce(int M, int N, int splits, const float* __restrict__ part,
+                                                     float* __restrict__ c, int64_t ldc, const float* __restrict__ bias,
+                                                     float* __restrict__ zout, const float* __restrict__ zin) {
+    const int64_t total = int64_t(M) * N;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+        float v = 0.f;
+        for (int z = 0; z < splits; ++z) v += part[int64_t(z) * total + e];
+        const int i = int(e / N), j = int(e - int64_t(i) * N);
+        const int64_t o = int64_t(i) * ldc + j;
+        c[o] = epilogue<E>(v, o, j, bias, zout, zin);
+    }
+}
+
+// Split-K workspace (floats) a training step uses: at most 4 splits of a 256 x 512 or 2
+// of a 512 x 512 product, reused call after call (stream order).
+constexpr int64_t kSplitFloats = int64_t(4) * 256 * 512;
+
+// Splits of the k range so that the tiles and splits fill about 128 CTAs, each split at
+// least 4 slabs long; 1 when no workspace is available.
+int choose_splits(int M, int N, int K, const float* ws, int64_t ws_floats) {
+    const int tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+    int s = 1;
+    while (s < 4 && tiles * s * 2 <= 160 && K / (2 * s) >= 4 * TK && int64_t(2 * s) * M * N <= ws_floats) s *= 2;
+    return ws ? s : 1;
+}
+
 template <typename TA, typename TB, Epi E>
 cudaError_t gemm(int M, int N, int K, const TA* a, int64_t sar, int64_t sac, const TB* b, int64_t sbr, int64_t sbc,
-                 float* c, int64_t ldc, const float* bias, float* zout, const float* zin, cudaStream_t s) {
-    const dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-    k_gemm<TA, TB, E><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, a, sar, sac, b, sbr, sbc, c, ldc, bias, zout, zin);
+                 float* c, int64_t ldc, const float* bias, float* zout, const float* zin, cudaStream_t s,
+                 float* ws = nullptr, int64_t ws_floats = 0) {
+    const int splits = choose_splits(M, N, K, ws, ws_floats);
+    const int kspan = splits == 1 ? K : ((K + splits - 1) / splits + TK - 1) / TK * TK;
+    const dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, splits);
+    k_gemm<TA, TB, E><<<grid, GEMM_THREADS, 0, s>>>(M, N, K, kspan, a, sar, sac, b, sbr, sbc, c, ldc, bias, zout, zin,
+                                                    splits > 1 ? ws : nullptr);
+    if (splits > 1) {
+        const int64_t total = int64_t(M) * N;
+        const int blocks = int((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);
+        k_gemm_reduce<E><<<blocks, 256, 0, s>>>(M, N, splits, ws, c, ldc, bias, zout, zin);
+    }
     return cudaGetLastError();
 }
 
@@ -122,8 +198,9 @@ __global__ void k_colsum(int rows, int cols, const float* __restrict__ x, int64_
 }
 
 // dY = (yhat - y) / B and the batch loss sum ||yhat - y||^2 / (2B) (one CTA, fixed order).
+// With idx (training graphs) the loss goes to loss_out[*idx].
 __global__ void k_mse(int B, int O, const float* __restrict__ yhat, const float* __restrict__ y,
-                      float* __restrict__ dy, float* __restrict__ loss_out) {
+                      float* __restrict__ dy, float* __restrict__ loss_out, const long long* __restrict__ idx = nullptr) {
     __shared__ float s[256];
     float acc = 0.f;
     for (int e = threadIdx.x; e < B * O; e += blockDim.x) {
@@ -137,12 +214,19 @@ __global__ void k_mse(int B, int O, const float* __restrict__ yhat, const float*
         if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0 && loss_out) *loss_out = s[0] / (2.f * float(B));
+    if (threadIdx.x == 0 && loss_out) loss_out[idx ? *idx : 0] = s[0] / (2.f * float(B));
 }
 
-// Adam with bias correction; c1 = 1/(1-beta1^t), c2 = 1/(1-beta2^t) from the host.
+// Adam with bias correction; c1 = 1/(1-beta1^t), c2 = 1/(1-beta2^t) from the host (with
+// idx: from the host-made tables c1t[*idx], c2t[*idx], step t = *idx + 1).
 __global__ void k_adam(int64_t P, float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, float lr, float beta1, float beta2, float eps, float c1, float c2) {
+                       float* __restrict__ v, float lr, float beta1, float beta2, float eps, float c1, float c2,
+                       const float* __restrict__ c1t = nullptr, const float* __restrict__ c2t = nullptr,
+                       const long long* __restrict__ idx = nullptr) {
+    if (idx) {
+        c1 = c1t[*idx];
+        c2 = c2t[*idx];
+    }
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < P; e += int64_t(gridDim.x) * blockDim.x) {
         const float ge = g[e];
         const float me = beta1 * m[e] + (1.f - beta1) * ge;
@@ -171,16 +255,23 @@ __global__ void k_init_uniform(float* __restrict__ theta, int64_t off, int64_t c
     }
 }
 
-// Rows perm(i) = (a*i + c) mod N, i in [start, start+B), of x (N x ni) and y (N x no).
-__global__ void k_gather_batch(int B, int ni, int no, int64_t N, int64_t start, uint64_t a, uint64_t c,
-                               const __half* __restrict__ x, const float* __restrict__ y, __half* __restrict__ xb,
-                               float* __restrict__ yb) {
+// The batch of training step *step (steps counted over all epochs, nb batches per epoch):
+// epoch ep = step / nb uses the order i -> (pa[ep] i + pc[ep]) mod N; the same rows as
+// rows (pa[ep] i + pc[ep]) mod N for i in [(step % nb) B, (step % nb + 1) B).
+__global__ void k_gather_step(int B, int ni, int no, int64_t N, int64_t nb, const long long* __restrict__ step,
+                              const uint64_t* __restrict__ pa, const uint64_t* __restrict__ pc,
+                              const __half* __restrict__ x, const float* __restrict__ y, __half* __restrict__ xb,
+                              float* __restrict__ yb) {
     const int row = blockIdx.x;
     if (row >= B) return;
-    const int64_t src = int64_t((a * uint64_t(start + row) + c) % uint64_t(N));
+    const long long st = *step;
+    const long long ep = st / nb, bi = st - ep * nb;
+    const int64_t src = int64_t((pa[ep] * uint64_t(bi * B + row) + pc[ep]) % uint64_t(N));
     for (int e = threadIdx.x; e < ni; e += blockDim.x) xb[int64_t(row) * ni + e] = x[src * ni + e];
     for (int e = threadIdx.x; e < no; e += blockDim.x) yb[int64_t(row) * no + e] = y[src * no + e];
 }
+
+__global__ void k_step_advance(long long* step) { *step += 1; }
 
 // Features of new objects: out[o][j*L + t] = half(delta_new[o][j][landmark[t]] * inv_mean[j]).
 struct FeatParams {
@@ -248,42 +339,44 @@ struct Acts {
     }
 };
 
-cudaError_t forward(const Net& n, const __half* x, int B, Acts& a, cudaStream_t s) {
+cudaError_t forward(const Net& n, const __half* x, int B, Acts& a, cudaStream_t s, float* ws = nullptr,
+                    int64_t wsf = 0) {
     cudaError_t e;
     // z1 = x W1^T + b1: A = x (B x ni), B(k, j) = W1[j][k]
     if ((e = gemm<__half, float, Epi::BiasGelu>(B, n.nh, n.ni, x, n.ni, 1, n.W1, 1, n.ni, a.h1, n.nh, n.b1, a.z1,
-                                                nullptr, s)))
+                                                nullptr, s, ws, wsf)))
         return e;
     if ((e = gemm<float, float, Epi::BiasGelu>(B, n.nh, n.nh, a.h1, n.nh, 1, n.W2, 1, n.nh, a.h2, n.nh, n.b2, a.z2,
-                                               nullptr, s)))
+                                               nullptr, s, ws, wsf)))
         return e;
     return gemm<float, float, Epi::Bias>(B, n.no, n.nh, a.h2, n.nh, 1, n.W3, 1, n.nh, a.y, n.no, n.b3, nullptr,
-                                         nullptr, s);
+                                         nullptr, s, ws, wsf);
 }
 
 // Gradient of the batch loss into g (P floats), given dL/dyhat in a.dy.
-cudaError_t backward(const Net& n, const __half* x, int B, Acts& a, float* g, cudaStream_t s) {
+cudaError_t backward(const Net& n, const __half* x, int B, Acts& a, float* g, cudaStream_t s, float* ws = nullptr,
+                     int64_t wsf = 0) {
     cudaError_t e;
     // gW3 = dy^T h2 (no x nh): A(i, k=b) = dy[b][i], B(b, j) = h2[b][j]
     if ((e = gemm<float, float, Epi::Plain>(n.no, n.nh, B, a.dy, 1, n.no, a.h2, n.nh, 1, g + n.oW3, n.nh, nullptr,
-                                            nullptr, nullptr, s)))
+                                            nullptr, nullptr, s, ws, wsf)))
         return e;
     k_colsum<<<(n.no + 255) / 256, 256, 0, s>>>(B, n.no, a.dy, n.no, g + n.ob3);
     // dz2 = (dy W3) * gelu'(z2): A = dy (B x no), B = W3 (no x nh)
     if ((e = gemm<float, float, Epi::GeluGrad>(B, n.nh, n.no, a.dy, n.no, 1, n.W3, n.nh, 1, a.dz2, n.nh, nullptr,
-                                               nullptr, a.z2, s)))
+                                               nullptr, a.z2, s, ws, wsf)))
         return e;
     if ((e = gemm<float, float, Epi::Plain>(n.nh, n.nh, B, a.dz2, 1, n.nh, a.h1, n.nh, 1, g + n.oW2, n.nh, nullptr,
-                                            nullptr, nullptr, s)))
+                                            nullptr, nullptr, s, ws, wsf)))
         return e;
     k_colsum<<<(n.nh + 255) / 256, 256, 0, s>>>(B, n.nh, a.dz2, n.nh, g + n.ob2);
     // dz1 = (dz2 W2) * gelu'(z1)
     if ((e = gemm<float, float, Epi::GeluGrad>(B, n.nh, n.nh, a.dz2, n.nh, 1, n.W2, n.nh, 1, a.dz1, n.nh, nullptr,
-                                               nullptr, a.z1, s)))
+                                               nullptr, a.z1, s, ws, wsf)))
         return e;
     // gW1 = dz1^T x (nh x ni): A(i, k=b) = dz1[b][i], B(b, j) = x[b][j] (float16)
     if ((e = gemm<float, __half, Epi::Plain>(n.nh, n.ni, B, a.dz1, 1, n.nh, x, n.ni, 1, g + n.oW1, n.ni, nullptr,
-                                             nullptr, nullptr, s)))
+                                             nullptr, nullptr, s, ws, wsf)))
         return e;
     k_colsum<<<(n.nh + 255) / 256, 256, 0, s>>>(B, n.nh, a.dz1, n.nh, g + n.ob1);
     return cudaGetLastError();
@@ -408,13 +501,15 @@ extern "C" int fjofc_mlp_gradient(const float* params, int32_t n_in, int32_t hid
     const Net n(params, n_in, hidden, n_out);
     const int B = int(count);
     Scratch w(s);
-    if ((rc = cuda_status(w.alloc(Acts::floats(B, hidden, n_out) + 1), "scratch"))) return rc;
+    const int64_t act = Acts::floats(B, hidden, n_out);
+    if ((rc = cuda_status(w.alloc(act + 4 + kSplitFloats), "scratch"))) return rc;
     Acts a(w.p, B, hidden, n_out);
     float* dloss = a.dy + int64_t(B) * n_out;
+    float* ws = w.p + act + 4;
     const __half* xh = reinterpret_cast<const __half*>(x);
-    if ((rc = cuda_status(forward(n, xh, B, a, s), "forward"))) return rc;
+    if ((rc = cuda_status(forward(n, xh, B, a, s, ws, kSplitFloats), "forward"))) return rc;
     k_mse<<<1, 256, 0, s>>>(B, n_out, a.y, y, a.dy, dloss);
-    if ((rc = cuda_status(backward(n, xh, B, a, grad, s), "backward"))) return rc;
+    if ((rc = cuda_status(backward(n, xh, B, a, grad, s, ws, kSplitFloats), "backward"))) return rc;
     float hl = 0.f;
     if ((rc = cuda_status(cudaMemcpyAsync(&hl, dloss, 4, cudaMemcpyDeviceToHost, s), "copy"))) return rc;
     if ((rc = cuda_status(cudaStreamSynchronize(s), "sync"))) return rc;
@@ -439,7 +534,11 @@ extern "C" int fjofc_mlp_train(float* params, int32_t n_in, int32_t hidden, int3
     const int64_t P = n.P;
     const int64_t act = Acts::floats(B, hidden, n_out);
     const int64_t xb_floats = (int64_t(B) * n_in + 1) / 2;    // float16 batch rows
-    const int64_t total = act + 3 * P + xb_floats + int64_t(B) * n_out + nb * opts->epochs + 1;
+    const int64_t steps = nb * opts->epochs;
+    // scratch: activations, gradient, Adam moments, batch, losses, split-K workspace, and the
+    // step tables of the training graph (counter, epoch orders, bias corrections)
+    const int64_t tab_floats = 2 + 4 * int64_t(opts->epochs) + 2 * steps;
+    const int64_t total = act + 3 * P + xb_floats + int64_t(B) * n_out + steps + 4 + kSplitFloats + tab_floats + 4;
     Scratch w(s);
     if ((rc = cuda_status(w.alloc(total), "scratch"))) return rc;
     Acts a(w.p, B, hidden, n_out);
@@ -449,15 +548,27 @@ extern "C" int fjofc_mlp_train(float* params, int32_t n_in, int32_t hidden, int3
     __half* xb = reinterpret_cast<__half*>(vel + P);
     float* yb = vel + P + xb_floats;
     float* losses = yb + int64_t(B) * n_out;
+    float* ws = losses + steps + 4;
+    float* tabs = ws + kSplitFloats;
+    // 8-byte aligned tables
+    tabs = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tabs) + 7) & ~uintptr_t(7));
+    long long* ctl = reinterpret_cast<long long*>(tabs);
+    uint64_t* tpa = reinterpret_cast<uint64_t*>(ctl + 1);
+    uint64_t* tpc = tpa + opts->epochs;
+    float* tc1 = reinterpret_cast<float*>(tpc + opts->epochs);
+    float* tc2 = tc1 + steps;
     if ((rc = cuda_status(cudaMemsetAsync(mom, 0, size_t(2 * P) * 4, s), "memset"))) return rc;
     const __half* xh = reinterpret_cast<const __half*>(x);
     const float beta1 = opts->beta1 > 0.f ? opts->beta1 : 0.9f, beta2 = opts->beta2 > 0.f ? opts->beta2 : 0.999f;
     const float eps = opts->eps > 0.f ? opts->eps : 1e-8f;
+    if (steps == 0) return FJOFC_OK;
+    // the epoch orders (i -> (a i + c) mod count, gcd(a, count) = 1) and the bias
+    // corrections of every step, made on the host
+    std::vector<uint64_t> hpa(size_t(opts->epochs)), hpc(size_t(opts->epochs));
+    std::vector<float> hc1(static_cast<size_t>(steps)), hc2(static_cast<size_t>(steps));
     uint64_t rng = opts->seed;
-    int64_t step = 0;
     for (int ep = 0; ep < opts->epochs; ++ep) {
-        // epoch order: i -> (a i + c) mod count with gcd(a, count) = 1
-        uint64_t pa = 1, pc = 0;
+        uint64_t pa = 1;
         for (;;) {
             rng = splitmix64(rng);
             pa = (rng % uint64_t(count)) | 1u;
@@ -466,18 +577,47 @@ extern "C" int fjofc_mlp_train(float* params, int32_t n_in, int32_t hidden, int3
             if (x0 == 1) break;
         }
         rng = splitmix64(rng);
-        pc = rng % uint64_t(count);
-        for (int64_t bi = 0; bi < nb; ++bi) {
-            ++step;
-            k_gather_batch<<<B, 128, 0, s>>>(B, n_in, n_out, count, bi * B, pa, pc, xh, y, xb, yb);
-            if ((rc = cuda_status(forward(n, xb, B, a, s), "forward"))) return rc;
-            k_mse<<<1, 256, 0, s>>>(B, n_out, a.y, yb, a.dy, losses + ep * nb + bi);
-            if ((rc = cuda_status(backward(n, xb, B, a, g, s), "backward"))) return rc;
-            const float c1 = float(1.0 / (1.0 - std::pow(double(beta1), double(step))));
-            const float c2 = float(1.0 / (1.0 - std::pow(double(beta2), double(step))));
-            k_adam<<<512, 256, 0, s>>>(P, params, g, mom, vel, opts->lr, beta1, beta2, eps, c1, c2);
-        }
+        hpa[size_t(ep)] = pa;
+        hpc[size_t(ep)] = rng % uint64_t(count);
     }
+    for (int64_t st = 0; st < steps; ++st) {
+        hc1[size_t(st)] = float(1.0 / (1.0 - std::pow(double(beta1), double(st + 1))));
+        hc2[size_t(st)] = float(1.0 / (1.0 - std::pow(double(beta2), double(st + 1))));
+    }
+    if ((rc = cuda_status(cudaMemsetAsync(ctl, 0, sizeof(long long), s), "memset"))) return rc;
+    if ((rc = cuda_status(cudaMemcpyAsync(tpa, hpa.data(), hpa.size() * 8, cudaMemcpyHostToDevice, s), "copy")) ||
+        (rc = cuda_status(cudaMemcpyAsync(tpc, hpc.data(), hpc.size() * 8, cudaMemcpyHostToDevice, s), "copy")) ||
+        (rc = cuda_status(cudaMemcpyAsync(tc1, hc1.data(), hc1.size() * 4, cudaMemcpyHostToDevice, s), "copy")) ||
+        (rc = cuda_status(cudaMemcpyAsync(tc2, hc2.data(), hc2.size() * 4, cudaMemcpyHostToDevice, s), "copy")))
+        return rc;
+    // one training step, captured once into a CUDA graph on a private stream: every kernel
+    // takes its step from the device counter, which the last node advances; the graph is
+    // then launched once per step on the caller's stream
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+    };
+    if ((rc = cuda_status(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream"))) return rc;
+    if ((rc = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "capture"))) {
+        cleanup();
+        return rc;
+    }
+    k_gather_step<<<B, 128, 0, cs>>>(B, n_in, n_out, count, nb, ctl, tpa, tpc, xh, y, xb, yb);
+    cudaError_t ce = forward(n, xb, B, a, cs, ws, kSplitFloats);
+    k_mse<<<1, 256, 0, cs>>>(B, n_out, a.y, yb, a.dy, losses, ctl);
+    if (ce == cudaSuccess) ce = backward(n, xb, B, a, g, cs, ws, kSplitFloats);
+    k_adam<<<512, 256, 0, cs>>>(P, params, g, mom, vel, opts->lr, beta1, beta2, eps, 1.f, 1.f, tc1, tc2, ctl);
+    k_step_advance<<<1, 1, 0, cs>>>(ctl);
+    const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+    if (ce == cudaSuccess) ce = ee;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+    for (int64_t st = 0; ce == cudaSuccess && st < steps; ++st) ce = cudaGraphLaunch(exec, s);
+    cleanup();
+    if ((rc = cuda_status(ce, "training graph"))) return rc;
     if ((rc = cuda_status(cudaGetLastError(), "train launches"))) return rc;
     if (loss_history && opts->epochs > 0) {
         std::vector<float> hl(size_t(nb) * opts->epochs);

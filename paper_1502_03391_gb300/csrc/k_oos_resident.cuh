@@ -36,6 +36,7 @@ k_oos_resident(const K3Params p) {
     float* s_part = s_y + m * D;                          // [warps][m][D + 3]: -sum b x, sum b, fid (hi, lo)
     float* s_acc = s_part + kK3rWarps * m * (D + 3);      // [m][D + 1]
     double* s_fid = reinterpret_cast<double*>(s_y + k3r_state_floats(m, D));   // [m]
+    double* s_comm = s_fid + m;                                                 // [m]
     __shared__ double s_sig;
     __shared__ long long s_obj;
     __shared__ int s_stop;
@@ -126,20 +127,27 @@ k_oos_resident(const K3Params p) {
                     s_fid[j] = double(f.hi) + double(f.lo);
                 }
             }
+            // commensurability of y_{t-1}: thread a < m sums its pairs (a, b > a) in b order
+            // (float64), thread 0 adds the m parts in a order after the fidelities
+            if (tid < m) {
+                const int a = tid;
+                double ca = 0.0;
+                for (int b2 = a + 1; b2 < m; ++b2) {
+                    double s2 = 0.0;
+                    for (int kk = 0; kk < D; ++kk) {
+                        const double df = double(s_y[a * D + kk]) - double(s_y[b2 * D + kk]);
+                        s2 += df * df;
+                    }
+                    ca += __ldg(p.wcomm + a * m + b2) * s2;
+                }
+                s_comm[a] = ca;
+            }
             __syncthreads();
             // stress of y_{t-1} and the stopping test (the streaming kernel's rule)
             if (tid == 0) {
                 double sig = 0.0;
                 for (int j = 0; j < m; ++j) sig += double(p.wfid[j]) * s_fid[j];
-                for (int a = 0; a < m; ++a)
-                    for (int b2 = a + 1; b2 < m; ++b2) {
-                        double s2 = 0.0;
-                        for (int kk = 0; kk < D; ++kk) {
-                            const double df = double(s_y[a * D + kk]) - double(s_y[b2 * D + kk]);
-                            s2 += df * df;
-                        }
-                        sig += __ldg(p.wcomm + a * m + b2) * s2;
-                    }
+                for (int a = 0; a < m; ++a) sig += s_comm[a];
                 bool stop = (pass == passes) || !isfinite(sig);
                 if (!stop && pass >= 2 && p.tol >= 0.0) {
                     const double dec = sprev - sig;

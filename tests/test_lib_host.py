@@ -34,7 +34,7 @@ def test_header_declares_expected_api():
                                             "fjofc_mlp_select", "fjofc_plan_create", "fjofc_plan_run",
                                             "fjofc_plan_results", "fjofc_plan_info", "fjofc_plan_destroy",
                                             "fjofc_plan_autotune", "fjofc_init_cmds", "fjofc_test_barrier_skew",
-                                            "fjofc_transform_rows"])
+                                            "fjofc_transform_rows", "fjofc_packed_size", "fjofc_pack_delta"])
 
 
 def test_library_loads_and_exports_every_declared_symbol():
@@ -106,6 +106,8 @@ def call():
     (dict(deterministic=-1), -1),
     (dict(wait_limit_us=-5), -1),           # ... and a non-negative wait bound
     (dict(reserved=1), -1),
+    (dict(delta_layout=2), -1),             # unknown Delta layout
+    (dict(delta_layout=1, ld=16), -1),      # packed storage needs its own row stride (8 here)
 ])
 def test_invalid_arguments_rejected_before_cuda(call, kw, code):
     assert call.embed(**kw) == code
@@ -172,3 +174,23 @@ def test_oos_argument_validation(call):
     assert oos_form(2, d=9) == -6                 # resident form: d <= 8
     assert oos_form(2, n=100000) == -6            # resident form: does not fit in shared memory
     assert "shared memory" in fj.strerror(-6)
+
+
+def test_packed_size_matches_the_band_layout(call):
+    """fjofc_packed_size against the layout written out: bands of 128 rows from the
+    diagonal, band b paired with band nB - 1 - b, widths rounded to 16 bytes."""
+    lib = call.lib
+    lib.fjofc_packed_size.restype = ctypes.c_int64
+    lib.fjofc_packed_size.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+    for n, dt, es in [(5000, 0, 4), (5000, 1, 2), (129, 0, 4), (1, 0, 4), (300, 2, 2), (20000, 1, 2)]:
+        ld = ctypes.c_int64(0)
+        size = lib.fjofc_packed_size(n, dt, ctypes.byref(ld))
+        nb = -(-n // 128)
+        al = lambda w: -(-w // (16 // es)) * (16 // es)          # noqa: E731
+        widths = [al(n - 128 * b) + (al(n - 128 * (nb - 1 - b)) if nb - 1 - b != b else 0)
+                  for b in range(0, (nb - 1) // 2 + 1)]
+        assert ld.value == max(widths)
+        assert size == -(-nb // 2) * 128 * ld.value
+        assert size <= n * (n + 256) // 2 + 128 * ld.value       # about half of n^2, one band of slack
+    assert lib.fjofc_packed_size(0, 0, None) == -1
+    assert lib.fjofc_packed_size(10, 7, None) == -1
