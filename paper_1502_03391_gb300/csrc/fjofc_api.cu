@@ -389,6 +389,7 @@ int InsampleSetup::plan(int m_, int64_t n_, int d_, int dtype_, const fjofc_opts
     o_contr = cv.take<int2>(size_t(m) * P.nRB);
     o_bar = cv.take<unsigned>(1);
     o_tab = cv.take<float>(2 * size_t(m) * m);
+    o_pub = cv.take<float2>(size_t(m) * d + d + 1);
     bytes = (cv.off + 255) & ~size_t(255);
     return FJOFC_OK;
 }
@@ -510,6 +511,20 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
     pp.relax = k2.relax; pp.centre = k2.centre;
     pp.bar_skew = 0;
     pp.wait_ns = wait_limit_ns(o);
+    pp.pub = reinterpret_cast<float2*>(base + o_pub);
+    // CTA b owns sub-tiles [b T / G, (b + 1) T / G): the first with the fewest is the
+    // totals CTA
+    pp.tc = 0;
+    {
+        int64_t best = -1;
+        for (int cb = 0; cb < P.G; ++cb) {
+            const int64_t cnt = (int64_t(cb) + 1) * P.T / P.G - int64_t(cb) * P.T / P.G;
+            if (best < 0 || cnt < best) {
+                best = cnt;
+                pp.tc = cb;
+            }
+        }
+    }
     for (int j = 0; j < kMSmall; ++j)
         for (int l = 0; l < kMSmall; ++l) { pp.coef[j][l] = k2.coef[j][l]; pp.wcomm[j][l] = k2.wcomm[j][l]; }
     pp.coef_g = k2.coef_g;

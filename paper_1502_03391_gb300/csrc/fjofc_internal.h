@@ -157,6 +157,8 @@ struct PersistParams {
     float inv_n;
     float relax;                // relaxed update factor (1: the plain Guttman transform)
     int centre;                 // 1: centre X_{t-1} in place with its column means
+    float2* pub;                // [m*d + d + 1] the pass totals published by the totals CTA
+    int tc;                     // the totals CTA: the first with the fewest sub-tiles
     unsigned bar_skew;          // extra arrivals the first grid-wide wait expects (0; test support)
     unsigned long long wait_ns; // bound of every grid-wide wait
     float coef[kMSmall][kMSmall];
@@ -272,7 +274,7 @@ struct InsampleSetup {
     fjofc_opts o{};
     size_t o_buf1 = 0, o_buf2 = 0, o_col = 0, o_head = 0, o_cont = 0, o_fid = 0, o_woff = 0, o_cta = 0, o_mu = 0,
            o_bpart = 0, o_ticket = 0, o_st = 0, o_hist = 0, o_fid2 = 0, o_cbase = 0, o_contr = 0, o_bar = 0,
-           o_tab = 0;
+           o_tab = 0, o_pub = 0;
     size_t bytes = 0;
     TMaps tm;
     K1Params k1;

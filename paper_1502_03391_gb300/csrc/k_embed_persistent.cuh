@@ -4,12 +4,12 @@
 // Pass t (reads X_{t-1}, writes X_t):
 //   A. the fused all-pairs sub-tiles of this CTA's fixed range (phase_a, the same code as
 //      the standalone pass k_guttman_pass), fidelity partial -> fid2[t&1][b];
-//   -- grid barrier (arrival) --
-//   C. while waiting for the slowest CTA, every CTA reduces the fidelity partials of pass
-//      t-1 and phase B's per-group parts of pass t-1 in the same fixed order, so all CTAs
-//      obtain the same means of X_{t-1}, sigma(X_{t-2}) and stopping decision about
-//      X_{t-2} (Algorithm 1 with the decrease reading); CTA 0 records the history;
-//   -- grid barrier (completion) --
+//   C. one CTA with the fewest sub-tiles reduces the fidelity partials of pass t-1 and
+//      phase B's per-group parts of pass t-1 in a fixed order and publishes the totals;
+//   -- grid barrier --
+//      every CTA reads the totals and takes the same means of X_{t-1}, sigma(X_{t-2}) and
+//      stopping decision about X_{t-2} (Algorithm 1 with the decrease reading); the totals
+//      CTA records the history;
 //   B. for the (group, coordinate) units of this CTA (phase_b, the same code as K2): sum
 //      the partials, centre X_{t-1} in place with its means, its commensurability, the
 //      Wmod^-1 mix into X_t (Eq. update / Cor. 1) and per-group float-float sums;
@@ -227,17 +227,39 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
         }
         FJ_STAMP(t, 1);
         bar_target += unsigned(G);
-        grid_arrive(P.bar, G);
-
         // ================================================================ phase C
-        // While the other CTAs finish phase A: the totals of pass t-1 (phase B's parts and
-        // the fidelity partials of A(t-1), complete since the previous barriers), the same
-        // in every CTA and in the same order -> means of X_{t-1}, sigma(X_{t-2}) and the
-        // stopping decision about X_{t-2}
-        pass_totals(P.bpart + int64_t((t - 1) & 1) * P.ngroups * npart, npart, t >= 2 ? P.ngroups : 0,
-                    P.fid2 + ((t - 1) & 1) * G, t >= 2 ? G : 0, s_tot);
-        __syncthreads();
+        // The totals of pass t-1 (phase B's parts and the fidelity partials of A(t-1),
+        // complete since the previous barriers) -> means of X_{t-1}, sigma(X_{t-2}) and the
+        // stopping decision about X_{t-2}.  One CTA with the fewest sub-tiles (P.tc) forms
+        // them before it arrives at the barrier and publishes them; every other CTA reads
+        // them after the barrier, so the slowest CTA does not compute them on the critical
+        // path.  Every CTA then takes the same decision from the same values.
+        const bool tc = (b == P.tc);
+        if (tc) {
+            pass_totals(P.bpart + int64_t((t - 1) & 1) * P.ngroups * npart, npart, t >= 2 ? P.ngroups : 0,
+                        P.fid2 + ((t - 1) & 1) * G, t >= 2 ? G : 0, s_tot);
+            __syncthreads();
+            if (G > 1)
+                for (int e = tid; e <= npart; e += NT) P.pub[e] = make_float2(s_tot[e].hi, s_tot[e].lo);
+        }
         FJ_STAMP(t, 5);
+        grid_arrive(P.bar, G);
+        // every CTA has finished phase A (its partial tables are complete) and no CTA still
+        // reads X_{t-1} for phase A
+        if (!grid_wait(P.bar, bar_target + (t == 1 ? P.bar_skew : 0u), &s_flag, abort_flag, G, P.wait_ns) ||
+            *abort_flag) {
+            if (ok) fail_site = 32;
+            ok = false;
+            break;
+        }
+        FJ_STAMP(t, 2);
+        if (!tc) {
+            for (int e = tid; e <= npart; e += NT) {
+                const float2 v = __ldcg(P.pub + e);
+                s_tot[e] = FF{v.x, v.y};
+            }
+            __syncthreads();
+        }
         for (int e = tid; e < m * D; e += NT)
             s_mu[e] = (t >= 2 && t - 1 < passes) ? (s_tot[e].hi + s_tot[e].lo) * P.inv_n : 0.f;
         if (tid == 0) {
@@ -246,7 +268,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
                 const int tp = t - 2;                        // the iterate decided about
                 const double sigma = stress_from_totals(s_tot, s_tot[npart], m, D);
                 stop = (tp == P.max_iter) ? 1 : 0;
-                if (b == 0) P.hist[tp] = sigma;
+                if (tc) P.hist[tp] = sigma;
                 if (!isfinite(sigma)) {
                     stop = 2;                                // non-finite: keep the last finite iterate
                 } else {
@@ -259,7 +281,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
                     }
                     s_prev = sigma;
                 }
-                if (b == 0) {
+                if (tc) {
                     DevStatus* st = p.st;
                     if (stop == 2) st->error = FJOFC_ERR_NONFINITE;
                     else {
@@ -272,16 +294,8 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
             s_stop = stop;
             s_final = last_finite;
         }
+        __syncthreads();
         FJ_STAMP(t, 3);
-        // every CTA has finished phase A (its partial tables are complete) and no CTA still
-        // reads X_{t-1} for phase A
-        if (!grid_wait(P.bar, bar_target + (t == 1 ? P.bar_skew : 0u), &s_flag, abort_flag, G, P.wait_ns) ||
-            *abort_flag) {
-            if (ok) fail_site = 32;
-            ok = false;
-            break;
-        }
-        FJ_STAMP(t, 2);
         if (s_stop || !do_a) break;
 
         // ================================================================ phase B
