@@ -597,8 +597,10 @@ def run_paper(args, rank, world, local_rank):
 
 
 def _loglog_slope(xs, ys):
-    """Least-squares slope of log(y) against log(x)."""
+    """Least-squares slope of log(y) against log(x) (None for fewer than two sizes)."""
     import numpy as np
+    if len(set(xs)) < 2:
+        return None
     return float(np.polyfit(np.log(np.asarray(xs, float)), np.log(np.asarray(ys, float)), 1)[0])
 
 
@@ -646,6 +648,8 @@ def run_paper_oos(args, rank, world, local_rank):
     d, tol, mode = 3, 1e-6, "abs_normalized"
     cap = args.max_iter or 2000
     cases = [(m, 200) for m in (2, 4, 6, 8, 10, 15, 20, 25, 30)] + [(10, n) for n in (300, 400, 500, 600)]
+    if args.paper_case:
+        cases = [tuple(int(v) for v in args.paper_case.split(","))]
     rows = []
     with ClockSampler(local_rank) as clk:
         for m, n in cases:
@@ -708,8 +712,8 @@ def run_paper_oos(args, rank, world, local_rank):
                 row["oos_rel_diff_to_oracle"] = float(np.linalg.norm(Y_h - ref.y) / np.linalg.norm(ref.y))
             rows.append(row)
     if rank == 0:
-        by_m = [r for r in rows if r["n"] == 200]
-        by_n = [r for r in rows if r["m"] == 10]
+        by_m = [r for r in rows if r["n"] == 200] or rows
+        by_n = [r for r in rows if r["m"] == 10] or rows
         slopes = {}
         for key in ("insample_ms", "insample_us_per_transform", "oos_ms", "oos_us_per_iteration"):
             slopes[key] = {"over_m_at_n200": _loglog_slope([r["m"] for r in by_m], [r[key] for r in by_m]),
@@ -1036,6 +1040,7 @@ def main():
     ap.add_argument("--max-iter", type=int, default=0, help="precision / relaxed / paper-oos workloads: "
                     "iteration cap (default 300 / 3000 / 2000)")
     ap.add_argument("--k", type=int, default=0, help="oos / learned workloads: test objects (default 100000)")
+    ap.add_argument("--paper-case", default="", help="paper-oos workload: run only the case 'm,n' (e.g. 30,200)")
     ap.add_argument("--problems", type=int, default=0, help="batched workload: problems (default 256)")
     ap.add_argument("--workload", default="insample",
                     choices=["insample", "precision", "oos", "learned", "batched", "relaxed", "paper",
