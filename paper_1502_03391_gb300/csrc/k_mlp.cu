@@ -188,13 +188,29 @@ cudaError_t gemm(int M, int N, int K, const TA* a, int64_t sar, int64_t sac, con
     return cudaGetLastError();
 }
 
-// out[j] = sum_i x[i*ld + j] for i < rows, in row order (bias gradients); one thread per j.
-__global__ void k_colsum(int rows, int cols, const float* __restrict__ x, int64_t ld, float* __restrict__ out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= cols) return;
+// out[j] = sum_i x[i*ld + j] for i < rows (bias gradients).  CTA c takes columns
+// 32c .. 32c+31 (lane = column); warp w sums rows w, w + 8, ... in row order, then lane j
+// adds the eight warp sums in warp order (a fixed order: deterministic).
+constexpr int kColsumWarps = 8;
+__global__ void __launch_bounds__(kColsumWarps * 32) k_colsum(int rows, int cols, const float* __restrict__ x,
+                                                              int64_t ld, float* __restrict__ out) {
+    __shared__ float part[kColsumWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (int i = 0; i < rows; ++i) s += x[int64_t(i) * ld + j];
-    out[j] = s;
+    if (j < cols)
+        for (int i = warp; i < rows; i += kColsumWarps) s += x[int64_t(i) * ld + j];
+    part[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && j < cols) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < kColsumWarps; ++w) t += part[w][lane];
+        out[j] = t;
+    }
+}
+void colsum(int rows, int cols, const float* x, int64_t ld, float* out, cudaStream_t s) {
+    k_colsum<<<(cols + 31) / 32, kColsumWarps * 32, 0, s>>>(rows, cols, x, ld, out);
 }
 
 // dY = (yhat - y) / B and the batch loss sum ||yhat - y||^2 / (2B) (one CTA, fixed order).
@@ -361,7 +377,7 @@ cudaError_t backward(const Net& n, const __half* x, int B, Acts& a, float* g, cu
     if ((e = gemm<float, float, Epi::Plain>(n.no, n.nh, B, a.dy, 1, n.no, a.h2, n.nh, 1, g + n.oW3, n.nh, nullptr,
                                             nullptr, nullptr, s, ws, wsf)))
         return e;
-    k_colsum<<<(n.no + 255) / 256, 256, 0, s>>>(B, n.no, a.dy, n.no, g + n.ob3);
+    colsum(B, n.no, a.dy, n.no, g + n.ob3, s);
     // dz2 = (dy W3) * gelu'(z2): A = dy (B x no), B = W3 (no x nh)
     if ((e = gemm<float, float, Epi::GeluGrad>(B, n.nh, n.no, a.dy, n.no, 1, n.W3, n.nh, 1, a.dz2, n.nh, nullptr,
                                                nullptr, a.z2, s, ws, wsf)))
@@ -369,7 +385,7 @@ cudaError_t backward(const Net& n, const __half* x, int B, Acts& a, float* g, cu
     if ((e = gemm<float, float, Epi::Plain>(n.nh, n.nh, B, a.dz2, 1, n.nh, a.h1, n.nh, 1, g + n.oW2, n.nh, nullptr,
                                             nullptr, nullptr, s, ws, wsf)))
         return e;
-    k_colsum<<<(n.nh + 255) / 256, 256, 0, s>>>(B, n.nh, a.dz2, n.nh, g + n.ob2);
+    colsum(B, n.nh, a.dz2, n.nh, g + n.ob2, s);
     // dz1 = (dz2 W2) * gelu'(z1)
     if ((e = gemm<float, float, Epi::GeluGrad>(B, n.nh, n.nh, a.dz2, n.nh, 1, n.W2, n.nh, 1, a.dz1, n.nh, nullptr,
                                                nullptr, a.z1, s, ws, wsf)))
@@ -378,7 +394,7 @@ cudaError_t backward(const Net& n, const __half* x, int B, Acts& a, float* g, cu
     if ((e = gemm<float, __half, Epi::Plain>(n.nh, n.ni, B, a.dz1, 1, n.nh, x, n.ni, 1, g + n.oW1, n.ni, nullptr,
                                              nullptr, nullptr, s, ws, wsf)))
         return e;
-    k_colsum<<<(n.nh + 255) / 256, 256, 0, s>>>(B, n.nh, a.dz1, n.nh, g + n.ob1);
+    colsum(B, n.nh, a.dz1, n.nh, g + n.ob1, s);
     return cudaGetLastError();
 }
 
