@@ -84,6 +84,19 @@ __device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Untiled bulk copy (cp.async.bulk) of `bytes` from global to shared memory, completing on
+// the mbarrier `bar` (complete_tx).  Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar) : "memory");
+}
+
+// Orders this thread's view of global memory written through ordinary stores (by any
+// thread, once acquired) before its later asynchronous-proxy reads (bulk copies, TMA).
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // Invalidate an mbarrier before its memory is initialised again (a CTA that runs several
 // problems re-initialises its ring barriers for each one).
 __device__ __forceinline__ void mbar_inval(uint32_t bar) {

@@ -135,7 +135,7 @@ struct K1Shape {
     static constexpr size_t smem_for(int stages) {
         return size_t(stages) * STAGE_BYTES + RED_FLOATS * sizeof(float) + size_t(XROW_FLOATS) * sizeof(float) +
                size_t(stages) * XS_FLOATS * sizeof(float) + size_t(2 * stages + 2 * SLOTS) * 8 +
-               size_t(stages) * 4 + ALIGN;
+               size_t((stages + 1) & ~1) * 4 + 64 + ALIGN;
     }
     // 16-bit Delta halves the stage: keep about the same bytes in flight, as many stages
     // as fit in the budget
@@ -346,6 +346,12 @@ struct K1Ring {
     uint64_t* rfull;       // [SLOTS]
     uint64_t* rempty;      // [SLOTS]
     int* released;         // [STAGES] releases so far (monotone)
+    Cursor* pc_start;      // cursor of the range's first sub-tile (read when the ring wraps)
+    int* xissued;          // uses whose x_j have been issued (monotone)
+    int* red_cnt;          // arrivals at segment ends summed inside a pass (column-strip layout)
+    uint64_t* red_full;    // those arrivals (count CWARPS)
+    uint64_t* red_empty;   // the row buffer summed (count 1)
+    int nred;              // segments summed inside a pass so far (the same in every thread)
     int* issued;           // ring uses issued so far
     int* abort_flag;       // set by a warp whose bounded wait gave up
     Cursor pc;             // cursor of the next use to issue (every thread keeps a copy)
@@ -373,30 +379,41 @@ struct K1Ring {
         rfull = xfull + S::STAGES;
         rempty = rfull + S::SLOTS;
         released = reinterpret_cast<int*>(rempty + S::SLOTS);
+        pc_start = reinterpret_cast<Cursor*>(released + ((S::STAGES + 1) & ~1));
+        xissued = reinterpret_cast<int*>(pc_start + 1);
+        red_cnt = xissued + 1;
+        red_full = reinterpret_cast<uint64_t*>(xissued + 2);
+        red_empty = red_full + 1;
     }
 
-    __device__ __forceinline__ void issue(const TMaps& tm, int64_t qg) {
+    __device__ __forceinline__ void issue(const TMaps& tm, int64_t qg) { issue_at(tm, qg, pc); }
+
+    // Delta of use qg, the sub-tile at cursor c, into its stage (one thread).
+    __device__ __forceinline__ void issue_at(const TMaps& tm, int64_t qg, const Cursor& c) {
         const int stage = int(qg % S::STAGES);
         atomicMax(issued, int(qg + 1));
         const uint32_t bar = smem_u32(&full[stage]);
         mbar_arrive_expect_tx(bar, S::STAGE_BYTES);
         const uint32_t dst = smem_u32(stages + size_t(stage) * S::STAGE_ELEMS);
         // the sub-tile's first element: Delta[I RB][I RB + s CW], or its packed position
-        int64_t x0 = int64_t(pc.I) * S::RB + int64_t(pc.s) * S::CW, y0 = int64_t(pc.I) * S::RB;
+        int64_t x0 = int64_t(c.I) * S::RB + int64_t(c.s) * S::CW, y0 = int64_t(c.I) * S::RB;
         if (packed) pack_pos(n, int(sizeof(TD)), y0, x0, x0, y0);
         if constexpr (S::STRIP) {
             // BOXES boxes of 128 bytes x RB rows; x is a multiple of 16 bytes
 #pragma unroll
             for (int bx = 0; bx < S::BOXES; ++bx)
-                tma_load_2d(dst + uint32_t(bx) * S::RB * 128u, &tm.map[pc.l], int(x0) + bx * S::BOX_ELEMS, int(y0), bar);
+                tma_load_2d(dst + uint32_t(bx) * S::RB * 128u, &tm.map[c.l], int(x0) + bx * S::BOX_ELEMS, int(y0), bar);
         } else {
-            tma_load_2d(dst, &tm.map[pc.l], int(x0), int(y0), bar);
+            tma_load_2d(dst, &tm.map[c.l], int(x0), int(y0), bar);
         }
     }
 
     // x_j of use u (cursor c) into its stage, by all 32 lanes of one warp: the 16-byte
-    // aligned window of X (16-byte aligned) that holds the CW columns' coordinates, cut
-    // at the end of X; each lane arrives on xfull once its copies have landed.
+    // aligned window of X (16-byte aligned) that holds the CW columns' coordinates.  Inside
+    // X: one bulk copy completing on xfull (lane 0 arrives with its byte count, the other
+    // lanes plainly); at the end of X: 16-byte cp.async copies cut there (zero-filled
+    // beyond), each lane arriving on xfull once its copies have landed.  32 arrivals
+    // either way.
     __device__ __forceinline__ void issue_x(const K1Params& p, const float* X, int64_t u, const Cursor& c) {
         const int lane = threadIdx.x & 31;
         const int stage = int(u % S::STAGES);
@@ -405,6 +422,17 @@ struct K1Ring {
         const int64_t base = start & ~int64_t(3);
         const int nch = (int(start - base) + S::CW * D + 3) / 4;
         float* dst = xs + size_t(stage) * S::XS_FLOATS;
+        if (lane == 0) atomicMax(xissued, int(u + 1));
+        if (base + 4 * int64_t(nch) <= total) {
+            const uint32_t bar = smem_u32(&xfull[stage]);
+            if (lane == 0) {
+                mbar_arrive_expect_tx(bar, uint32_t(nch) * 16u);
+                bulk_load(smem_u32(dst), X + base, uint32_t(nch) * 16u, bar);
+            } else {
+                mbar_arrive(bar);
+            }
+            return;
+        }
         for (int k = lane; k < nch; k += 32) {
             const int64_t f = base + 4 * int64_t(k);
             const int64_t left = total - f;
@@ -418,7 +446,7 @@ struct K1Ring {
     __device__ __forceinline__ void advance(const K1Params& p) {
         if (++pc_local == nq) {
             pc_local = 0;
-            cursor_init(pc, t_begin, p);
+            pc = *pc_start;
         } else {
             cursor_next(pc, p);
         }
@@ -435,6 +463,7 @@ struct K1Ring {
         total_q = total_q_;
         pc_local = 0;
         nflush = 0;
+        nred = 0;
         packed = p.packed;
         n = p.n;
         cursor_init(pc, t_begin, p);
@@ -448,8 +477,13 @@ struct K1Ring {
                 mbar_init(smem_u32(&rfull[s]), S::CWARPS);
                 mbar_init(smem_u32(&rempty[s]), S::CWARPS);
             }
+            mbar_init(smem_u32(red_full), S::CWARPS);
+            mbar_init(smem_u32(red_empty), 1);
+            *red_cnt = 0;
             *abort_flag = 0;
             *issued = 0;
+            *xissued = 0;
+            *pc_start = pc;
             fence_barrier_init();
             for (int l = 0; l < p.m; ++l) tma_prefetch_desc(&tm.map[l]);
         }
@@ -476,6 +510,8 @@ struct K1Ring {
             mbar_inval(smem_u32(&rfull[s]));
             mbar_inval(smem_u32(&rempty[s]));
         }
+        mbar_inval(smem_u32(red_full));
+        mbar_inval(smem_u32(red_empty));
     }
 
     // After an abort: wait (bounded) for the copies that may still be in flight, the most
@@ -484,6 +520,12 @@ struct K1Ring {
         const int hi = *issued;
         for (int qq = (hi > S::STAGES ? hi - S::STAGES : 0); qq < hi; ++qq)
             (void)mbar_wait_bounded(smem_u32(&full[qq % S::STAGES]), uint32_t((qq / S::STAGES) & 1));
+        // the x_j windows in flight (bulk copies are not covered by cp.async.wait_all)
+        if (S::XSTAGE) {
+            const int xh = *xissued;
+            for (int qq = (xh > S::STAGES ? xh - S::STAGES : 0); qq < xh; ++qq)
+                (void)mbar_wait_bounded(smem_u32(&xfull[qq % S::STAGES]), uint32_t((qq / S::STAGES) & 1));
+        }
     }
 };
 
@@ -498,6 +540,19 @@ static __device__ unsigned long long g_waitcyc[1024][5];
 #else
 #define FJ_WAIT_T0() do { } while (0)
 #define FJ_WAIT_ADD(which_) do { } while (0)
+#endif
+// Instrumented builds (-DFJOFC_SECTIONS): clock cycles thread 0 of every CTA spends in each
+// section of the column-strip loop, summed over every launch of the process.
+#ifdef FJOFC_SECTIONS
+static __device__ unsigned long long g_seccyc[1024][8];
+#define FJ_SEC(i_)                                                                  \
+    do {                                                                            \
+        const long long now_ = clock64();                                           \
+        if (threadIdx.x == 0) s_sec[i_] += (unsigned long long)(now_ - fj_last);    \
+        fj_last = now_;                                                             \
+    } while (0)
+#else
+#define FJ_SEC(i_) do { } while (0)
 #endif
 
 // One all-pairs pass over the CTA's range (ring uses qbase .. qbase + nq - 1) against the
@@ -566,6 +621,8 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
     };
     load_cols(cn);
     if constexpr (S::XSTAGE) {
+        // the iterate was written with ordinary stores; x_j windows are bulk copies
+        fence_proxy_async_global();
         // x_j of this pass's first uses (their Delta may have been issued during the
         // previous pass, before this iterate existed)
         if (warp == 0) {
@@ -920,12 +977,25 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
     const int n = p.n, nq = rg.nq;
     const volatile int* abort_flag = rg.abort_flag;
     fid_total = FF{0.f, 0.f};
+    // A wait that gives up ends this warp's loop and raises the CTA's abort flag, so that
+    // every other warp's next wait gives up too; every warp then reaches the barriers after
+    // the loop.
+    bool failed = false;
+    auto fail = [&]() {
+        failed = true;
+        *reinterpret_cast<volatile int*>(rg.abort_flag) = 1;
+    };
+#ifdef FJOFC_SECTIONS
+    __shared__ unsigned long long s_sec[8];
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 8; ++i) s_sec[i] = 0ull;
+    long long fj_last = clock64();
+#endif
 
     Cursor cc, cn;
     cursor_init(cc, rg.t_begin, p);
     cn = cc;
     bool seg_head = (cc.s == 0);
-    int seg = 0;                                       // walk segment of this pass
     float racc[R][D];
 #pragma unroll
     for (int u = 0; u < R; ++u)
@@ -954,17 +1024,12 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
             }
         }
     };
-    // the first segment's rows: every thread its share, then one CTA barrier (no wait of
-    // this pass has run yet, so every thread reaches it)
-    {
-        float v[RSH];
-        load_rows(cc, v);
-        put_rows(v, rg.xrow, p.xscale[cc.l]);
-        __syncthreads();
-    }
+    // the iterate was written with ordinary stores (by the previous per-object phase);
+    // any thread of the CTA may copy parts of it with bulk copies during this pass
+    fence_proxy_async_global();
     if (warp == 0) {
         // x_j of this pass's first uses (their Delta may have been issued during the
-        // previous pass, before this iterate existed)
+        // previous pass, before this iterate existed), in flight while the rows load
         Cursor c = cc;
         const int k0 = nq < STAGES ? nq : STAGES;
         for (int j = 0; j < k0; ++j) {
@@ -972,15 +1037,61 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
             if (j + 1 < k0) cursor_next(c, p);
         }
     }
-    FF fid{0.f, 0.f};
-    int cur_l = cc.l;
 #ifdef FJOFC_STAMPS
     unsigned long long fj_wait[4] = {0, 0, 0, 0};
 #endif
-
+    // Walk rows of segment s (counted over the ring's life, rg.nflush) sit in buffer s & 1:
+    // every warp writes its share once segment s - 2 is done by every warp (rempty[s & 1])
+    // and arrives on rfull[s & 1]; a warp reads them once all eight have (rfull).
+    auto rows_write = [&](int sg, const float (&v)[RSH], int l) -> bool {
+        if (sg >= 2) {
+            FJ_WAIT_T0();
+            if (!mbar_wait_or_abort(smem_u32(&rg.rempty[sg & 1]), uint32_t(((sg >> 1) - 1) & 1), abort_flag))
+                return false;
+            FJ_WAIT_ADD(3);
+        }
+        put_rows(v, rg.xrow + (sg & 1) * XBUF, p.xscale[l]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&rg.rfull[sg & 1]));
+        return true;
+    };
+    // the first segment's rows
+    {
+        float v[RSH];
+        load_rows(cc, v);
+        if (!rows_write(rg.nflush, v, cc.l)) fail();
+    }
+    bool rows_pending = true;                          // the segment's rows are not yet waited for
+    int mid_done = 0;                                  // segments of this pass summed inside the loop
+    float* end_dst = nullptr;                          // destination of the pass's last segment
+    FF fid{0.f, 0.f};
+    int cur_l = cc.l;
     int stage = int(qbase % STAGES);
     uint32_t kuse = uint32_t(qbase / STAGES);
-    for (int q = 0; q < nq; ++q) {
+    // -x_j of the lane's columns of the sub-tile at cursor c (ring stage stg, use count
+    // ku of that stage) as column pairs, once its staged x_j have landed; columns at or
+    // beyond n read as 0
+    const int cbase = warp * SW + cl * C;              // first column of the lane in a sub-tile
+    auto load_nxj = [&](const Cursor& c, int stg, uint32_t ku, float2 (&o)[C / 2][D]) -> bool {
+        FJ_WAIT_T0();
+        if (!mbar_wait_or_abort(smem_u32(&rg.xfull[stg]), ku & 1u, abort_flag)) return false;
+        FJ_WAIT_ADD(2);
+        const int cc0 = c.I * RB + c.s * CW;
+        const int64_t start = (int64_t(c.l) * n + cc0) * D;
+        const uint32_t xsrc = smem_u32(rg.xs + size_t(stg) * S::XS_FLOATS + int(start & 3) + cbase * D);
+        const float nxsc = -p.xscale[c.l];
+#pragma unroll
+        for (int cx = 0; cx < C; cx += 2)
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const bool in0 = cc0 + cbase + cx < n, in1 = cc0 + cbase + cx + 1 < n;
+                o[cx / 2][k] = make_float2(in0 ? lds_f1(xsrc + 4 * (cx * D + k)) * nxsc : 0.f,
+                                           in1 ? lds_f1(xsrc + 4 * ((cx + 1) * D + k)) * nxsc : 0.f);
+            }
+        return true;
+    };
+    FJ_SEC(7);
+    for (int q = 0; q < nq && !failed; ++q) {
         const int64_t qg = qbase + q;
         const int r0 = cc.I * RB;
         const int c0 = r0 + cc.s * CW;
@@ -994,46 +1105,43 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
             fid = FF{0.f, 0.f};
             cur_l = cc.l;
         }
+        FJ_SEC(0);
         {
             FJ_WAIT_T0();
-            if (!mbar_wait_or_abort(smem_u32(&rg.full[stage]), kuse & 1u, abort_flag)) return false;
+            if (!mbar_wait_or_abort(smem_u32(&rg.full[stage]), kuse & 1u, abort_flag)) { fail(); break; }
             FJ_WAIT_ADD(1);
         }
+        FJ_SEC(1);
         float2 nxj[C / 2][D];
-        {
-            FJ_WAIT_T0();
-            if (!mbar_wait_or_abort(smem_u32(&rg.xfull[stage]), kuse & 1u, abort_flag)) return false;
-            FJ_WAIT_ADD(2);
-            const int64_t start = (int64_t(cc.l) * n + c0) * D;
-            const int cbase = warp * SW + cl * C;      // first column of the lane
-            const uint32_t xsrc = smem_u32(rg.xs + size_t(stage) * S::XS_FLOATS + int(start & 3) + cbase * D);
-            const float nxsc = -p.xscale[cc.l];
-#pragma unroll
-            for (int c = 0; c < C; c += 2)
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    const bool in0 = c0 + cbase + c < n, in1 = c0 + cbase + c + 1 < n;
-                    nxj[c / 2][k] = make_float2(in0 ? lds_f1(xsrc + 4 * (c * D + k)) * nxsc : 0.f,
-                                                in1 ? lds_f1(xsrc + 4 * ((c + 1) * D + k)) * nxsc : 0.f);
-                }
-        }
+        if (!load_nxj(cc, stage, kuse, nxj)) { fail(); break; }
         const uint32_t tile = smem_u32(rg.stages + size_t(stage) * S::STAGE_ELEMS);
         const bool masked = (cc.s * CW < RB) || (c0 + CW > n);
         float2 cacc[C / 2][D];
         float2 sf;
-        const uint32_t xib = smem_u32(rg.xrow + (seg & 1) * XBUF);
+        if (rows_pending) {
+            FJ_WAIT_T0();
+            if (!mbar_wait_or_abort(smem_u32(&rg.rfull[rg.nflush & 1]), uint32_t((rg.nflush >> 1) & 1), abort_flag)) {
+                fail();
+                break;
+            }
+            FJ_WAIT_ADD(0);
+            rows_pending = false;
+        }
+        const uint32_t xib = smem_u32(rg.xrow + (rg.nflush & 1) * XBUF);
+        FJ_SEC(2);
         if (!masked)
             strip_pairs<D, TD, R, C, RB, SW, false>(tile, warp, rgp, cl, r0, c0, n, xib, nxj, racc, cacc, sf);
         else
             strip_pairs<D, TD, R, C, RB, SW, true>(tile, warp, rgp, cl, r0, c0, n, xib, nxj, racc, cacc, sf);
+        FJ_SEC(3);
         // release the stage; the last warp to do so refills it with use qg + STAGES
         const bool refill = qg + STAGES < rg.total_q;
+        // (every lane's reads of the stage have returned: their values were consumed
+        // above, so no fence is needed before the count)
         __syncwarp();
         int is_last = 0;
         if (lane == 0) {
-            __threadfence_block();
             if (atomicAdd(&rg.released[stage], 1) == int(kuse + 1) * CWARPS - 1) {
-                __threadfence_block();
                 is_last = 1;
                 if (refill) rg.issue(tm, qg + STAGES);
             }
@@ -1042,6 +1150,7 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
         if (is_last && refill && q + STAGES < nq) rg.issue_x(p, X, qg + STAGES, rg.pc);
         if (refill) rg.advance(p);
         fid = ff_add(fid, sf.x + sf.y);
+        FJ_SEC(4);
 
         // this sub-tile's column sums: reduce-scatter over the eight row groups (lane bits
         // 2..4); the writer lane of each (column, coordinate) stores its total, negated
@@ -1064,15 +1173,24 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
                     cpart[k * CW + warp * SW + cl * C + c] = -v[f];
                 }
         }
+        FJ_SEC(5);
 
         if (walk_ends || last) {
             // row partials of this walk segment: the sum over the four column groups in the
-            // warp (lane bits 0, 1), then over the eight warps through shared memory
-            FJ_WAIT_T0();
-            if (rg.nflush >= 1 &&
-                !mbar_wait_or_abort(smem_u32(&rg.rempty[0]), uint32_t((rg.nflush - 1) & 1), abort_flag))
-                return false;
-            FJ_WAIT_ADD(3);
+            // warp (lane bits 0, 1) into the warp's part of the shared buffer, then the sum
+            // over the eight warps in warp order: for a segment that ends inside the pass by
+            // the last warp to get there (the others go on), for the pass's last segment by
+            // every warp after the loop
+            float* dst = seg_head ? p.rowhead + (int64_t(cc.l) * p.nRB + cc.I) * (D * RB)
+                                  : p.rowcont + int64_t(b) * (D * RB);
+            if (mid_done > 0) {                        // the buffer's previous segment is summed
+                FJ_WAIT_T0();
+                if (!mbar_wait_or_abort(smem_u32(rg.red_empty), uint32_t((rg.nred - 1) & 1), abort_flag)) {
+                    fail();
+                    break;
+                }
+                FJ_WAIT_ADD(3);
+            }
             {
                 float v[R * D];
 #pragma unroll
@@ -1090,48 +1208,78 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
                         rg.red[(warp * D + k) * RB + rgp + 8 * u] = v[f];
                     }
             }
-            if (walk_ends && !last) put_rows(rs, rg.xrow + ((seg + 1) & 1) * XBUF, p.xscale[cn.l]);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&rg.rfull[0]));
-            {
-                FJ_WAIT_T0();
-                if (!mbar_wait_or_abort(smem_u32(&rg.rfull[0]), uint32_t(rg.nflush & 1), abort_flag)) return false;
-                FJ_WAIT_ADD(0);
-            }
-            float* dst = seg_head ? p.rowhead + (int64_t(cc.l) * p.nRB + cc.I) * (D * RB)
-                                  : p.rowcont + int64_t(b) * (D * RB);
-            constexpr int SHARE = (RB * D + CWARPS - 1) / CWARPS;
-            for (int e = warp * SHARE + lane; e < (warp + 1) * SHARE && e < RB * D; e += 32) {
-                const int k = e / RB, row = e - k * RB;
-                float v = 0.f;
+            if (!last) {
+                __syncwarp();
+                int lastw = 0;
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(rg.red_full));
+                    lastw = (atomicAdd(rg.red_cnt, 1) & (CWARPS - 1)) == CWARPS - 1;
+                }
+                lastw = __shfl_sync(0xffffffffu, lastw, 0);
+                if (lastw) {
+                    FJ_WAIT_T0();
+                    if (!mbar_wait_or_abort(smem_u32(rg.red_full), uint32_t(rg.nred & 1), abort_flag)) { fail(); break; }
+                    FJ_WAIT_ADD(0);
+                    for (int e = lane; e < RB * D; e += 32) {
+                        const int k = e / RB, row = e - k * RB;
+                        float sv = 0.f;
 #pragma unroll
-                for (int w = 0; w < CWARPS; ++w) v += rg.red[(w * D + k) * RB + row];
-                dst[e] = v;
+                        for (int w = 0; w < CWARPS; ++w) sv += rg.red[(w * D + k) * RB + row];
+                        dst[e] = sv;
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(rg.red_empty));
+                }
+                ++rg.nred;
+                ++mid_done;
+            } else {
+                end_dst = dst;
             }
+            if (walk_ends && !last && !rows_write(rg.nflush + 1, rs, cn.l)) { fail(); break; }
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&rg.rempty[0]));
+            if (lane == 0) mbar_arrive(smem_u32(&rg.rempty[rg.nflush & 1]));   // done with this segment's rows
             ++rg.nflush;
-            ++seg;
+            rows_pending = true;
             seg_head = true;
 #pragma unroll
             for (int u = 0; u < R; ++u)
 #pragma unroll
                 for (int k = 0; k < D; ++k) racc[u][k] = 0.f;
         }
-        cursor_next(cc, p);
+        cc = cn;                                       // cn is one sub-tile ahead (unused after the last)
         if (++stage == STAGES) {
             stage = 0;
             ++kuse;
         }
+        FJ_SEC(6);
     }
     fid_total = ff_add(fid_total, ff_mul(fid, p.wfid[cur_l]));
+    // the pass's last segment: every warp has written its part (a warp whose wait gave up
+    // gets here too, and the abort flag ends every other warp's loop at its next wait); each
+    // warp sums a share over the eight warps, and the buffer is free after the second barrier
+    __syncthreads();
+    if (!failed) {
+        constexpr int SHARE = (RB * D + CWARPS - 1) / CWARPS;
+        for (int e = warp * SHARE + lane; e < (warp + 1) * SHARE && e < RB * D; e += 32) {
+            const int k = e / RB, row = e - k * RB;
+            float sv = 0.f;
+#pragma unroll
+            for (int w = 0; w < CWARPS; ++w) sv += rg.red[(w * D + k) * RB + row];
+            end_dst[e] = sv;
+        }
+    }
+    __syncthreads();
 #ifdef FJOFC_STAMPS
     if (threadIdx.x == 0 && blockIdx.x < 1024) {
         for (int x = 0; x < 4; ++x) atomicAdd(&g_waitcyc[blockIdx.x][x], fj_wait[x]);
         atomicAdd(&g_waitcyc[blockIdx.x][4], 1ull);
     }
 #endif
-    return true;
+#ifdef FJOFC_SECTIONS
+    if (threadIdx.x == 0 && blockIdx.x < 1024)
+        for (int x = 0; x < 8; ++x) atomicAdd(&g_seccyc[blockIdx.x][x], s_sec[x]);
+#endif
+    return !failed;
 }
 
 // Standalone pass (one launch per Guttman transform, used when the persistent kernel is

@@ -20,3 +20,10 @@ extern "C" int fjofc_debug_waits(unsigned long long* host) {
     return cudaMemcpyFromSymbol(host, fjofc::g_waitcyc, sizeof(fjofc::g_waitcyc)) == cudaSuccess ? 0 : -1;
 }
 #endif
+#ifdef FJOFC_SECTIONS
+// Cycles thread 0 of every CTA spent per section of the column-strip loop (d <= 4
+// persistent kernels), summed over the process: [1024][8].
+extern "C" int fjofc_debug_sections(unsigned long long* host) {
+    return cudaMemcpyFromSymbol(host, fjofc::g_seccyc, sizeof(fjofc::g_seccyc)) == cudaSuccess ? 0 : -1;
+}
+#endif
