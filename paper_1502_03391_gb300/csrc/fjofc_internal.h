@@ -158,7 +158,7 @@ struct PersistParams {
     float relax;                // relaxed update factor (1: the plain Guttman transform)
     int centre;                 // 1: centre X_{t-1} in place with its column means
     float2* pub;                // [m*d + d + 1] the pass totals published by the totals CTA
-    int tc;                     // the totals CTA: the first with the fewest sub-tiles
+    const int* tc;              // the totals CTA (chosen by the set-up kernel: the least work)
     unsigned bar_skew;          // extra arrivals the first grid-wide wait expects (0; test support)
     unsigned long long wait_ns; // bound of every grid-wide wait
     float coef[kMSmall][kMSmall];
@@ -191,7 +191,16 @@ struct InitParams {
     int2* cont;                // [m][nRB]
     int m, n, RB, CW, nRB, G;
     int64_t T, Tm;
+    int64_t* cost_off;         // [nRB+1] modelled cost before walk position P (split_cost units)
+    int* tc;                   // out: the totals CTA
 };
+
+// Modelled cost of the all-pairs sub-tiles, used to split them over the CTAs (units of
+// 1/100 of an unmasked sub-tile; fitted to per-CTA clock stamps of the column-strip pass
+// at m = 2, n = 5000, d = 3): a masked sub-tile (a diagonal or ragged one) costs 0.15
+// more, a walk that ends inside a CTA's range 0.76 more (its row sums and the hand-over
+// of the next walk's rows).  Ranges stay contiguous; only their lengths change.
+constexpr int64_t kSplitCostSub = 100, kSplitCostMask = 15, kSplitCostWalkEnd = 76;
 // Dissimilarity check of fjofc_opts.check_inputs (one pass over every Delta_l).
 struct CheckParams {
     const void* delta[FJOFC_MAX_M];
@@ -274,6 +283,7 @@ struct InsampleSetup {
     fjofc_opts o{};
     size_t o_buf1 = 0, o_buf2 = 0, o_col = 0, o_head = 0, o_cont = 0, o_fid = 0, o_woff = 0, o_cta = 0, o_mu = 0,
            o_bpart = 0, o_ticket = 0, o_st = 0, o_hist = 0, o_fid2 = 0, o_cbase = 0, o_contr = 0, o_bar = 0,
+           o_coff = 0, o_tcs = 0,
            o_tab = 0, o_pub = 0;
     size_t bytes = 0;
     TMaps tm;

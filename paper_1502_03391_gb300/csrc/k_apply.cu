@@ -120,7 +120,10 @@ cudaError_t launch_k2(const K2Params& p, cudaStream_t s) {
 
 // Per-call initialisation (one CTA of kInitThreads): status block, ticket, mu_0 = 0, then
 //   walk_off[P]  = sub-tiles before walk position P (prefix sums of the walk lengths),
-//   cta_start[b] = first sub-tile of CTA b (b*T/G),
+//   cost_off[P]  = the modelled cost of those sub-tiles (kSplitCost*),
+//   cta_start[b] = first sub-tile of CTA b: the ranges cut the modelled cost into G equal
+//                  parts when every CTA gets at least 4 sub-tiles on average, else b*T/G,
+//   tc           = the CTA with the least modelled cost (the first such),
 //   cbase[I]     = first sub-tile (within a modality) of row block I's walk,
 //   cont[l][I]   = the CTAs whose range starts strictly inside that walk.
 // Each step reads only what earlier steps of this CTA wrote (global memory, ordered by
@@ -132,8 +135,32 @@ __device__ __forceinline__ int64_t walk_len(int P, const InitParams& p) {
     return (cols + p.CW - 1) / p.CW;
 }
 
+// Modelled cost of walk position P's sub-tiles: each kSplitCostSub, the diagonal one and a
+// ragged last one kSplitCostMask more, the walk's end kSplitCostWalkEnd.
+__device__ __forceinline__ int64_t walk_cost(int P, const InitParams& p) {
+    const int64_t cols = int64_t(p.n) - int64_t(walk_row(P, p.nRB)) * p.RB;
+    const int64_t L = (cols + p.CW - 1) / p.CW;
+    const int64_t masked = 1 + ((L >= 2 && cols % p.CW != 0) ? 1 : 0);
+    return L * kSplitCostSub + masked * kSplitCostMask + kSplitCostWalkEnd;
+}
+
+// Modelled cost of sub-tiles [0, t) (walk_off and cost_off complete).
+__device__ __forceinline__ int64_t cum_cost(int64_t t, const InitParams& p) {
+    const int64_t Cm = p.cost_off[p.nRB];
+    const int64_t l = t / p.Tm, r = t - l * p.Tm;
+    if (r == 0) return l * Cm;
+    int lo = 0, hi = p.nRB - 1;                        // last position with walk_off <= r
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.walk_off[mid] <= r) lo = mid; else hi = mid - 1;
+    }
+    const int64_t s = r - p.walk_off[lo];
+    return l * Cm + p.cost_off[lo] + s * kSplitCostSub + (s >= 1 ? kSplitCostMask : 0);
+}
+
 __device__ __forceinline__ void init_problem(const InitParams& p) {
     __shared__ int64_t s_part[kInitThreads];
+    __shared__ int64_t s_cost[kInitThreads];
     const int tid = threadIdx.x;
     for (int e = tid; e < p.m * p.m; e += kInitThreads) {
         p.coef_g[e] = p.coef[e];
@@ -154,30 +181,74 @@ __device__ __forceinline__ void init_problem(const InitParams& p) {
     // walk_off: block scan over contiguous chunks of positions
     const int per = (p.nRB + kInitThreads - 1) / kInitThreads;
     const int P0 = tid * per, P1 = min(P0 + per, p.nRB);
-    int64_t local = 0;
-    for (int P = P0; P < P1; ++P) local += walk_len(P, p);
+    int64_t local = 0, lcost = 0;
+    for (int P = P0; P < P1; ++P) {
+        local += walk_len(P, p);
+        lcost += walk_cost(P, p);
+    }
     s_part[tid] = local;
+    s_cost[tid] = lcost;
     __syncthreads();
     if (tid == 0) {
-        int64_t run = 0;
+        int64_t run = 0, crun = 0;
         for (int e = 0; e < kInitThreads; ++e) {
-            const int64_t v = s_part[e];
+            const int64_t v = s_part[e], c = s_cost[e];
             s_part[e] = run;
+            s_cost[e] = crun;
             run += v;
+            crun += c;
         }
     }
     __syncthreads();
     {
-        int64_t run = s_part[tid];
+        int64_t run = s_part[tid], crun = s_cost[tid];
         for (int P = P0; P < P1; ++P) {
             p.walk_off[P] = run;
+            p.cost_off[P] = crun;
             run += walk_len(P, p);
+            crun += walk_cost(P, p);
         }
-        if (P1 == p.nRB && P0 < P1) p.walk_off[p.nRB] = run;
+        if (P1 == p.nRB && P0 < P1) {
+            p.walk_off[p.nRB] = run;
+            p.cost_off[p.nRB] = crun;
+        }
     }
     __syncthreads();
 
-    for (int b = tid; b <= p.G; b += kInitThreads) p.cta_start[b] = int64_t(b) * p.T / p.G;
+    // CTA ranges: equal parts of the modelled cost (a part holds more than the costliest
+    // sub-tile when T >= 4 G, so no range is empty), else of the sub-tile count
+    const bool weighted = p.T >= 4 * int64_t(p.G);
+    const int64_t Ctot = int64_t(p.m) * p.cost_off[p.nRB];
+    for (int b = tid; b <= p.G; b += kInitThreads) {
+        int64_t start = int64_t(b) * p.T / p.G;
+        if (weighted && b > 0 && b < p.G) {
+            const int64_t target = int64_t(b) * Ctot / p.G;
+            int64_t lo = 0, hi = p.T;                  // first t with cum_cost(t) >= target
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (cum_cost(mid, p) >= target) hi = mid; else lo = mid + 1;
+            }
+            start = lo;
+        }
+        p.cta_start[b] = start;
+    }
+    __syncthreads();
+    // the totals CTA: least modelled cost, then lowest index (key = cost * 2^20 + b)
+    {
+        int64_t key = INT64_MAX;
+        for (int b = tid; b < p.G; b += kInitThreads) {
+            const int64_t c = cum_cost(p.cta_start[b + 1], p) - cum_cost(p.cta_start[b], p);
+            const int64_t k = (c << 20) + b;
+            key = k < key ? k : key;
+        }
+        s_part[tid] = key;
+        __syncthreads();
+        for (int h = kInitThreads / 2; h > 0; h >>= 1) {
+            if (tid < h && s_part[tid + h] < s_part[tid]) s_part[tid] = s_part[tid + h];
+            __syncthreads();
+        }
+        if (tid == 0) *p.tc = int(s_part[0] & ((int64_t(1) << 20) - 1));
+    }
     __syncthreads();
 
     // row-block tables

@@ -35,6 +35,14 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     return v;
 }
 
+// Arrival on a grid barrier counter: a reduction with release semantics at GPU scope (the
+// CTA's earlier writes, ordered before this thread by the preceding CTA barrier, are
+// visible to any thread that acquires the counter's new value; no separate fence, no
+// returned value).  The waiting side's ld.acquire.gpu orders the CTA's later reads.
+__device__ __forceinline__ void grid_count_arrive(unsigned* ctr) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(ctr) : "memory");
+}
+
 // Barrier of the G CTAs of one problem over a monotone counter: arrival k of every CTA
 // waits for G*k arrivals (G == 1: a CTA barrier).  Bounded: returns false after
 // limit_ns (or when *abort_flag is set).
@@ -47,8 +55,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
+        grid_count_arrive(ctr);
         bool ok = true;
         if (ld_acquire_gpu(ctr) < target) {
             const uint64_t t0 = globaltimer_ns();
@@ -60,7 +67,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
                 }
             }
         }
-        __threadfence();
         *s_flag = ok ? 1 : 0;
     }
     __syncthreads();
@@ -72,10 +78,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
 // the arrival) and grid_wait (every thread; bounded like grid_barrier).
 __device__ __forceinline__ void grid_arrive(unsigned* ctr, int G) {
     __syncthreads();
-    if (G > 1 && threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
-    }
+    if (G > 1 && threadIdx.x == 0) grid_count_arrive(ctr);
 }
 __device__ __forceinline__ bool grid_wait(unsigned* ctr, unsigned target, int* s_flag, const volatile int* abort_flag,
                                           int G, uint64_t limit_ns) {
@@ -97,7 +100,6 @@ __device__ __forceinline__ bool grid_wait(unsigned* ctr, unsigned target, int* s
                 }
             }
         }
-        __threadfence();
         *s_flag = ok ? 1 : 0;
     }
     __syncthreads();
@@ -148,6 +150,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
     const int64_t t_begin = P.cta_start[b];
     const int nq = static_cast<int>(P.cta_start[b + 1] - t_begin);
     const int npart = phase_b_parts(m, D);
+    const int tcb = *P.tc;                         // the totals CTA (written by the set-up kernel)
     // phase-B units (group, coordinate) of this CTA
     const int64_t nunits = int64_t(P.ngroups) * D;
     const int u0 = int(int64_t(b) * nunits / G), u1 = int(int64_t(b + 1) * nunits / G);
@@ -230,11 +233,11 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
         // ================================================================ phase C
         // The totals of pass t-1 (phase B's parts and the fidelity partials of A(t-1),
         // complete since the previous barriers) -> means of X_{t-1}, sigma(X_{t-2}) and the
-        // stopping decision about X_{t-2}.  One CTA with the fewest sub-tiles (P.tc) forms
+        // stopping decision about X_{t-2}.  One CTA with the least work (*P.tc) forms
         // them before it arrives at the barrier and publishes them; every other CTA reads
         // them after the barrier, so the slowest CTA does not compute them on the critical
         // path.  Every CTA then takes the same decision from the same values.
-        const bool tc = (b == P.tc);
+        const bool tc = (b == tcb);
         if (tc) {
             pass_totals(P.bpart + int64_t((t - 1) & 1) * P.ngroups * npart, npart, t >= 2 ? P.ngroups : 0,
                         P.fid2 + ((t - 1) & 1) * G, t >= 2 ? G : 0, s_tot);

@@ -1064,6 +1064,7 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
     bool rows_pending = true;                          // the segment's rows are not yet waited for
     int mid_done = 0;                                  // segments of this pass summed inside the loop
     float* end_dst = nullptr;                          // destination of the pass's last segment
+
     FF fid{0.f, 0.f};
     int cur_l = cc.l;
     int stage = int(qbase % STAGES);
@@ -1209,6 +1210,12 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
                     }
             }
             if (!last) {
+                // the next segment's rows first: the other warps wait for every share of
+                // them, not for this warp's sum below
+                if (!rows_write(rg.nflush + 1, rs, cn.l)) {
+                    fail();
+                    break;
+                }
                 __syncwarp();
                 int lastw = 0;
                 if (lane == 0) {
@@ -1235,7 +1242,6 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
             } else {
                 end_dst = dst;
             }
-            if (walk_ends && !last && !rows_write(rg.nflush + 1, rs, cn.l)) { fail(); break; }
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&rg.rempty[rg.nflush & 1]));   // done with this segment's rows
             ++rg.nflush;
