@@ -392,6 +392,7 @@ int InsampleSetup::plan(int m_, int64_t n_, int d_, int dtype_, const fjofc_opts
     o_pub = cv.take<float2>(size_t(m) * d + d + 1);
     o_coff = cv.take<int64_t>(size_t(P.nRB) + 1);
     o_tcs = cv.take<int>(1);
+    o_pseq = cv.take<unsigned>(1);
     bytes = (cv.off + 255) & ~size_t(255);
     return FJOFC_OK;
 }
@@ -482,7 +483,7 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
     ip = InitParams{coef_g, wcomm_g, {}, {}, st, k2.ticket, k2.mu, const_cast<int64_t*>(k1.walk_off), const_cast<int64_t*>(k2.cta_start),
                     bar, const_cast<int64_t*>(k2.tb.cbase), const_cast<int2*>(k2.tb.cont), m, int(n), RB, CW,
                     P.nRB, P.G, P.T, P.Tm, reinterpret_cast<int64_t*>(base + o_coff),
-                    reinterpret_cast<int*>(base + o_tcs)};
+                    reinterpret_cast<int*>(base + o_tcs), reinterpret_cast<unsigned*>(base + o_pseq)};
     // the per-object mix: [Wmod^-1]_{jl} w_ll s_l and the commensurability weights, in
     // the set-up kernel's parameters (written to global memory for any m) and, for
     // m <= kMSmall, in the kernels' own parameters (their fast path)
@@ -515,6 +516,7 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
     pp.bar_skew = 0;
     pp.wait_ns = wait_limit_ns(o);
     pp.pub = reinterpret_cast<float2*>(base + o_pub);
+    pp.pub_seq = ip.pub_seq;
     pp.tc = ip.tc;   // written by the set-up kernel with the CTA ranges
     for (int j = 0; j < kMSmall; ++j)
         for (int l = 0; l < kMSmall; ++l) { pp.coef[j][l] = k2.coef[j][l]; pp.wcomm[j][l] = k2.wcomm[j][l]; }

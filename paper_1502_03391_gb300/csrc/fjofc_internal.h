@@ -158,6 +158,7 @@ struct PersistParams {
     float relax;                // relaxed update factor (1: the plain Guttman transform)
     int centre;                 // 1: centre X_{t-1} in place with its column means
     float2* pub;                // [m*d + d + 1] the pass totals published by the totals CTA
+    unsigned* pub_seq;          // the pass whose totals pub holds (written after them, release)
     const int* tc;              // the totals CTA (chosen by the set-up kernel: the least work)
     unsigned bar_skew;          // extra arrivals the first grid-wide wait expects (0; test support)
     unsigned long long wait_ns; // bound of every grid-wide wait
@@ -193,6 +194,7 @@ struct InitParams {
     int64_t T, Tm;
     int64_t* cost_off;         // [nRB+1] modelled cost before walk position P (split_cost units)
     int* tc;                   // out: the totals CTA
+    unsigned* pub_seq;         // cleared: the pass whose totals were last published
 };
 
 // Modelled cost of the all-pairs sub-tiles, used to split them over the CTAs (units of
@@ -283,7 +285,7 @@ struct InsampleSetup {
     fjofc_opts o{};
     size_t o_buf1 = 0, o_buf2 = 0, o_col = 0, o_head = 0, o_cont = 0, o_fid = 0, o_woff = 0, o_cta = 0, o_mu = 0,
            o_bpart = 0, o_ticket = 0, o_st = 0, o_hist = 0, o_fid2 = 0, o_cbase = 0, o_contr = 0, o_bar = 0,
-           o_coff = 0, o_tcs = 0,
+           o_coff = 0, o_tcs = 0, o_pseq = 0,
            o_tab = 0, o_pub = 0;
     size_t bytes = 0;
     TMaps tm;

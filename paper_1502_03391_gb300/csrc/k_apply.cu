@@ -175,6 +175,7 @@ __device__ __forceinline__ void init_problem(const InitParams& p) {
         p.st->bad = kNoBadEntry;
         *p.ticket = 0u;
         if (p.bar) *p.bar = 0u;
+        if (p.pub_seq) *p.pub_seq = 0u;
     }
     for (int e = tid; e < 2 * FJOFC_MAX_M * FJOFC_MAX_D; e += kInitThreads) p.mu[e] = 0.f;
 
@@ -222,13 +223,25 @@ __device__ __forceinline__ void init_problem(const InitParams& p) {
     for (int b = tid; b <= p.G; b += kInitThreads) {
         int64_t start = int64_t(b) * p.T / p.G;
         if (weighted && b > 0 && b < p.G) {
+            // the first t with cum_cost(t) >= target: the modality and the walk position
+            // holding the target, then the sub-tile inside that walk in closed form
             const int64_t target = int64_t(b) * Ctot / p.G;
-            int64_t lo = 0, hi = p.T;                  // first t with cum_cost(t) >= target
+            const int64_t Cm = p.cost_off[p.nRB];
+            const int64_t l = target / Cm, rem = target - l * Cm;
+            int lo = 0, hi = p.nRB - 1;                // last position with cost_off <= rem
             while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (cum_cost(mid, p) >= target) hi = mid; else lo = mid + 1;
+                const int mid = (lo + hi + 1) >> 1;
+                if (p.cost_off[mid] <= rem) lo = mid; else hi = mid - 1;
             }
-            start = lo;
+            const int64_t need = rem - p.cost_off[lo];
+            const int64_t L = p.walk_off[lo + 1] - p.walk_off[lo];
+            int64_t sub = 0;
+            if (need > 0) {
+                sub = (need - kSplitCostMask + kSplitCostSub - 1) / kSplitCostSub;
+                if (sub < 1) sub = 1;
+                if (sub > L) sub = L;                  // the next walk's first sub-tile
+            }
+            start = l * p.Tm + p.walk_off[lo] + sub;
         }
         p.cta_start[b] = start;
     }

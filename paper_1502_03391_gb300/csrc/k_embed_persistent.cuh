@@ -34,6 +34,9 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
 
 // Arrival on a grid barrier counter: a reduction with release semantics at GPU scope (the
 // CTA's earlier writes, ordered before this thread by the preceding CTA barrier, are
@@ -80,6 +83,37 @@ __device__ __forceinline__ void grid_arrive(unsigned* ctr, int G) {
     __syncthreads();
     if (G > 1 && threadIdx.x == 0) grid_count_arrive(ctr);
 }
+// grid_wait that, while it spins, also copies the pass totals the totals CTA published
+// (npub float2 at pub, valid once *seq == t) into out; *s_have tells whether it did.
+__device__ __forceinline__ bool grid_wait_pub(unsigned* ctr, unsigned target, int* s_flag,
+                                              const volatile int* abort_flag, int G, uint64_t limit_ns,
+                                              const unsigned* seq, unsigned t, const float2* pub, int npub, FF* out,
+                                              int* s_have) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = true, have = false;
+        const uint64_t t0 = globaltimer_ns();
+        for (uint32_t it = 1;; ++it) {
+            if (!have && ld_acquire_gpu(seq) == t) {
+                for (int e = 0; e < npub; ++e) {
+                    const float2 v = __ldcg(pub + e);
+                    out[e] = FF{v.x, v.y};
+                }
+                have = true;
+            }
+            if (ld_acquire_gpu(ctr) >= target) break;
+            if ((it & 63u) == 0u && (*abort_flag || globaltimer_ns() - t0 > limit_ns)) {
+                ok = false;
+                break;
+            }
+        }
+        *s_flag = ok ? 1 : 0;
+        *s_have = have ? 1 : 0;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
 __device__ __forceinline__ bool grid_wait(unsigned* ctr, unsigned target, int* s_flag, const volatile int* abort_flag,
                                           int G, uint64_t limit_ns) {
     if (G == 1) {
@@ -140,7 +174,7 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
 
     __shared__ FF s_ff[CWARPS];
     __shared__ float s_coef[kMSmall][kMSmall], s_wcomm[kMSmall][kMSmall];
-    __shared__ int s_abort, s_issued, s_flag, s_stop, s_final;
+    __shared__ int s_abort, s_issued, s_flag, s_stop, s_final, s_have;
     __shared__ double s_prev;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -242,21 +276,30 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
             pass_totals(P.bpart + int64_t((t - 1) & 1) * P.ngroups * npart, npart, t >= 2 ? P.ngroups : 0,
                         P.fid2 + ((t - 1) & 1) * G, t >= 2 ? G : 0, s_tot);
             __syncthreads();
-            if (G > 1)
+            if (G > 1) {
                 for (int e = tid; e <= npart; e += NT) P.pub[e] = make_float2(s_tot[e].hi, s_tot[e].lo);
+                __syncthreads();
+                if (tid == 0) st_release_gpu(P.pub_seq, unsigned(t));   // after the totals
+            }
         }
         FJ_STAMP(t, 5);
         grid_arrive(P.bar, G);
         // every CTA has finished phase A (its partial tables are complete) and no CTA still
-        // reads X_{t-1} for phase A
-        if (!grid_wait(P.bar, bar_target + (t == 1 ? P.bar_skew : 0u), &s_flag, abort_flag, G, P.wait_ns) ||
+        // reads X_{t-1} for phase A; the waiting thread of a CTA other than the totals CTA
+        // copies the published totals as soon as they are out (few of them only)
+        const bool prefetch = !tc && G > 1 && npart + 1 <= 64;
+        const unsigned wtarget = bar_target + (t == 1 ? P.bar_skew : 0u);
+        s_have = 0;
+        if (!(prefetch ? grid_wait_pub(P.bar, wtarget, &s_flag, abort_flag, G, P.wait_ns, P.pub_seq, unsigned(t),
+                                       P.pub, npart + 1, s_tot, &s_have)
+                       : grid_wait(P.bar, wtarget, &s_flag, abort_flag, G, P.wait_ns)) ||
             *abort_flag) {
             if (ok) fail_site = 32;
             ok = false;
             break;
         }
         FJ_STAMP(t, 2);
-        if (!tc) {
+        if (!tc && !s_have) {
             for (int e = tid; e <= npart; e += NT) {
                 const float2 v = __ldcg(P.pub + e);
                 s_tot[e] = FF{v.x, v.y};
