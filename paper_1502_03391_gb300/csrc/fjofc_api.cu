@@ -485,18 +485,11 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
                     P.nRB, P.G, P.T, P.Tm, reinterpret_cast<int64_t*>(base + o_coff),
                     reinterpret_cast<int*>(base + o_tcs), reinterpret_cast<unsigned*>(base + o_pseq)};
     // the per-object mix: [Wmod^-1]_{jl} w_ll s_l and the commensurability weights, in
-    // the set-up kernel's parameters (written to global memory for any m) and, for
-    // m <= kMSmall, in the kernels' own parameters (their fast path)
+    // the set-up kernel's parameters (it writes them to global memory for the kernels)
     for (int j = 0; j < m; ++j)
         for (int l = 0; l < m; ++l) {
-            const float c = float(winv[j * m + l] * weights[l * m + l] * dsc[l]);
-            const float w = (j < l) ? float(weights[j * m + l]) : 0.f;
-            ip.coef[j * m + l] = c;
-            ip.wcomm[j * m + l] = w;
-            if (m <= kMSmall) {
-                k2.coef[j][l] = c;
-                k2.wcomm[j][l] = w;
-            }
+            ip.coef[j * m + l] = float(winv[j * m + l] * weights[l * m + l] * dsc[l]);
+            ip.wcomm[j * m + l] = (j < l) ? float(weights[j * m + l]) : 0.f;
         }
 
     pp = PersistParams{};
@@ -518,8 +511,6 @@ int InsampleSetup::bind(char* base, const void* const* delta, int64_t ld, const 
     pp.pub = reinterpret_cast<float2*>(base + o_pub);
     pp.pub_seq = ip.pub_seq;
     pp.tc = ip.tc;   // written by the set-up kernel with the CTA ranges
-    for (int j = 0; j < kMSmall; ++j)
-        for (int l = 0; l < kMSmall; ++l) { pp.coef[j][l] = k2.coef[j][l]; pp.wcomm[j][l] = k2.wcomm[j][l]; }
     pp.coef_g = k2.coef_g;
     pp.wcomm_g = k2.wcomm_g;
     pp.tb = k2.tb;

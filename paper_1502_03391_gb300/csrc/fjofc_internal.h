@@ -12,10 +12,6 @@ namespace fjofc {
 
 struct DevStatus;
 
-// Modalities whose per-object mix runs from register arrays and shared-memory tables of
-// this size (the fast path of phase B); larger m (up to FJOFC_MAX_M) uses rolled loops over
-// the m x m tables in global memory that the set-up kernel writes.
-constexpr int kMSmall = 8;
 
 // Tensor maps of the m dissimilarity matrices (one 2-D map per modality), passed to
 // the kernels as a __grid_constant__ parameter.
@@ -131,10 +127,8 @@ struct K2Params {
     float inv_n;               // 1 / n (column means)
     float relax;               // relaxed update factor (1: the plain Guttman transform)
     int centre;                // 1: centre X_{t-1} in place with its column means (relax == 1)
-    float coef[kMSmall][kMSmall];    // [Wmod^-1]_{jl} * w_ll * s_l (m <= kMSmall)
-    float wcomm[kMSmall][kMSmall];   // w_jl for j < l, else 0 (m <= kMSmall)
-    const float* coef_g;             // the same two tables, m x m row-major, global (any m)
-    const float* wcomm_g;
+    const float* coef_g;             // [Wmod^-1]_{jl} * w_ll * s_l, m x m row-major (global)
+    const float* wcomm_g;            // w_jl for j < l, else 0
     BxTables tb;
 };
 
@@ -162,9 +156,7 @@ struct PersistParams {
     const int* tc;              // the totals CTA (chosen by the set-up kernel: the least work)
     unsigned bar_skew;          // extra arrivals the first grid-wide wait expects (0; test support)
     unsigned long long wait_ns; // bound of every grid-wide wait
-    float coef[kMSmall][kMSmall];
-    float wcomm[kMSmall][kMSmall];
-    const float* coef_g;        // m x m tables in global memory (any m; see K2Params)
+    const float* coef_g;        // m x m tables in global memory (see K2Params)
     const float* wcomm_g;
     BxTables tb;
 };

@@ -27,7 +27,6 @@ __global__ void __launch_bounds__(K2_THREADS)
 k_apply(const K2Params p) {
     extern __shared__ float s_dyn[];             // d * phase_b_floats_per_unit(m)
     __shared__ float s_mu[FJOFC_MAX_M * FJOFC_MAX_D];
-    __shared__ float s_coef[kMSmall][kMSmall], s_wcomm[kMSmall][kMSmall];
     __shared__ bool s_last;
 
     if (ld_volatile(&p.st->done)) return;
@@ -37,10 +36,6 @@ k_apply(const K2Params p) {
     const float* mu_prev = p.mu + ((p.t - 1) & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
     float* mu_next = p.mu + (p.t & 1) * (FJOFC_MAX_M * FJOFC_MAX_D);
     for (int e = tid; e < FJOFC_MAX_M * FJOFC_MAX_D; e += K2_THREADS) s_mu[e] = mu_prev[e];
-    for (int e = tid; e < kMSmall * kMSmall; e += K2_THREADS) {
-        s_coef[e / kMSmall][e % kMSmall] = p.coef[e / kMSmall][e % kMSmall];
-        s_wcomm[e / kMSmall][e % kMSmall] = p.wcomm[e / kMSmall][e % kMSmall];
-    }
     __syncthreads();
 
     PhaseBArgs a;
@@ -50,8 +45,6 @@ k_apply(const K2Params p) {
     a.bpart = p.bpart;
     a.mu_prev = s_mu;
     a.mu_stride = FJOFC_MAX_D;
-    a.coef = s_coef;
-    a.wcomm = s_wcomm;
     a.coef_g = p.coef_g;
     a.wcomm_g = p.wcomm_g;
     a.m = m; a.n = n; a.d = d; a.t = p.t; a.ngroups = p.nbx;

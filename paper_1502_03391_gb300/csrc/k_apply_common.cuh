@@ -169,10 +169,8 @@ struct PhaseBArgs {
     float2* bpart;                              // [npart][ngroups] (part-major), npart = m*d + d
     const float* mu_prev;                       // means of X_{t-1}: mean of (j, k) at j*mu_stride + k (shared memory)
     int mu_stride;
-    const float (*coef)[kMSmall];               // Wmod^-1 w_ll s_l (shared memory; m <= kMSmall)
-    const float (*wcomm)[kMSmall];              // w_jl for j < l, else 0 (shared memory; m <= kMSmall)
-    const float* coef_g;                        // the same tables, m x m row-major, global (m > kMSmall)
-    const float* wcomm_g;
+    const float* coef_g;                        // [Wmod^-1]_{jl} w_ll s_l, m x m row-major (global)
+    const float* wcomm_g;                       // w_jl for j < l, else 0
     int m, n, d, t, ngroups;
     bool final_pass;                            // only centre and score X_{t-1}
     bool centre;                                // centre X_{t-1} in place (plain transform)
@@ -256,57 +254,9 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int u0, int u1, int
         // 2. per unit: centre, commensurability, mix, column sums.  The group's column
         //    sums of X_t (used only for the next centring) are float32 butterflies; the
         //    commensurability (part of sigma) is float-float; all m+1 in one butterfly.
-        if (m <= kMSmall) {
-#pragma unroll 1
-        for (int ui = warp; ui < nc; ui += nwarps) {
-            const int u = c0 + ui, g = u / d, k = u - g * d;
-            const int i = g * kGroupObjects + lane;
-            const bool in = i < n;
-            float xc[kMSmall], cs[kMSmall];
-            float c = 0.f;
-#pragma unroll
-            for (int j = 0; j < kMSmall; ++j) {
-                xc[j] = (j < m && in) ? s_xp[(ui * m + j) * kGroupObjects + lane] -
-                                            (a.centre ? a.mu_prev[j * a.mu_stride + k] : 0.f)
-                                      : 0.f;
-                if (j < m && in && a.centre && a.t > 1) a.Xprev[(int64_t(j) * n + i) * d + k] = xc[j];
-            }
-#pragma unroll
-            for (int j = 0; j < kMSmall; ++j)
-#pragma unroll
-                for (int l = j + 1; l < kMSmall; ++l)
-                    if (l < m) {
-                        const float df = xc[j] - xc[l];
-                        c = fmaf(a.wcomm[j][l] * df, df, c);
-                    }
-#pragma unroll
-            for (int j = 0; j < kMSmall; ++j) {
-                float v = 0.f;
-                if (j < m && !a.final_pass && in) {
-                    for (int l = 0; l < m; ++l) v = fmaf(a.coef[j][l], s_bx[(ui * m + l) * kGroupObjects + lane], v);
-                    if (a.relax != 1.f) v = fmaf(1.f - a.relax, xc[j], a.relax * v);   // relaxed update
-                    a.Xnext[(int64_t(j) * n + i) * d + k] = v;
-                }
-                cs[j] = v;
-            }
-            FF cw{c, 0.f};
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const FF w{__shfl_xor_sync(0xffffffffu, cw.hi, o), __shfl_xor_sync(0xffffffffu, cw.lo, o)};
-                cw = ((lane & o) == 0) ? ff_add(cw, w) : ff_add(w, cw);
-#pragma unroll
-                for (int j = 0; j < kMSmall; ++j)
-                    if (j < m) cs[j] += __shfl_xor_sync(0xffffffffu, cs[j], o);     // m is warp-uniform
-            }
-            if (lane == 0) {
-                a.bpart[int64_t(md + k) * a.ngroups + g] = make_float2(cw.hi, cw.lo);
-                for (int j = 0; j < m; ++j)
-                    a.bpart[int64_t(j * d + k) * a.ngroups + g] = make_float2(a.final_pass ? 0.f : cs[j], 0.f);
-            }
-        }
-        } else {
-        // m > kMSmall: the same steps in the same order with rolled loops; the centred
-        // x_{t-1} stay in s_xp, the tables come from global memory
+        // rolled loops (this code runs once per pass: a compact body is fetched faster than
+        // one unrolled for every m); the centred x_{t-1} stay in s_xp, the tables come from
+        // global memory
 #pragma unroll 1
         for (int ui = warp; ui < nc; ui += nwarps) {
             const int u = c0 + ui, g = u / d, k = u - g * d;
@@ -350,7 +300,6 @@ __device__ __forceinline__ void phase_b(const PhaseBArgs& a, int u0, int u1, int
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (lane == 0) a.bpart[int64_t(j * d + k) * a.ngroups + g] = make_float2(a.final_pass ? 0.f : v, 0.f);
             }
-        }
         }
         __syncthreads();
     }

@@ -173,7 +173,6 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
     const K1Params& p = P.k1;
 
     __shared__ FF s_ff[CWARPS];
-    __shared__ float s_coef[kMSmall][kMSmall], s_wcomm[kMSmall][kMSmall];
     __shared__ int s_abort, s_issued, s_flag, s_stop, s_final, s_have;
     __shared__ double s_prev;
 
@@ -209,10 +208,6 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
         s_stop = 0;
         s_final = 0;
         s_prev = 0.0;
-    }
-    for (int e = tid; e < kMSmall * kMSmall; e += NT) {
-        s_coef[e / kMSmall][e % kMSmall] = P.coef[e / kMSmall][e % kMSmall];
-        s_wcomm[e / kMSmall][e % kMSmall] = P.wcomm[e / kMSmall][e % kMSmall];
     }
     // ring over every pass's sub-tiles; Delta does not change, so it prefetches the next
     // pass's first sub-tiles while phase B runs
@@ -353,8 +348,6 @@ __device__ __forceinline__ void persist_problem(const TMaps& tm, const PersistPa
             a.bpart = P.bpart + int64_t(t & 1) * P.ngroups * npart;
             a.mu_prev = s_mu;
             a.mu_stride = D;
-            a.coef = s_coef;
-            a.wcomm = s_wcomm;
             a.coef_g = P.coef_g;
             a.wcomm_g = P.wcomm_g;
             a.m = m; a.n = n; a.d = D; a.t = t; a.ngroups = P.ngroups;
