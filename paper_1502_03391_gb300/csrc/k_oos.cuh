@@ -114,7 +114,7 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
 
     // Slots: every slot holds one object (or none) and its own pass count; a slot whose
     // object stops is refilled from the global object counter at the end of the round.
-    auto fetch = [&](int r) {              // lane 0: next object into slot r
+    auto fetch = [&](int r) {              // one lane: next object into slot r
         const unsigned long long o = atomicAdd(p.next_block, 1ull);
         slot_obj[r] = (int64_t(o) < p.k) ? (long long)o : -1ll;
     };
@@ -139,18 +139,19 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
 
     bool failed = false;
     // sub-tile qq of a round: modality qq / nsub, points (qq % nsub) * CW; one box per
-    // occupied slot, all completing on the stage's mbarrier
+    // occupied slot, all completing on the stage's mbarrier.  Every lane of the warp calls
+    // it: lane r issues slot r's box, lane 0 first announces the bytes of all of them.
     auto issue_sub = [&](int64_t qq) {
         const int j = int(qq / nsub), s = int(qq % nsub);
         const int stage = int(q_iss % STAGES);
         const uint32_t bar = smem_u32(&full[stage]);
-        int nact = 0;
-        for (int r = 0; r < R; ++r) nact += (slot_obj[r] >= 0);
-        mbar_arrive_expect_tx(bar, uint32_t(nact) * box_bytes);
-        for (int r = 0; r < R; ++r)
-            if (slot_obj[r] >= 0)
-                tma_load_3d(smem_u32(ring + size_t(stage) * S::STAGE_ELEMS + size_t(r) * CW), &tmap, s * CW, j,
-                            int(slot_obj[r]), bar);
+        const bool act = lane < R && slot_obj[lane] >= 0;
+        const unsigned occ = __ballot_sync(0xffffffffu, act);
+        if (lane == 0) mbar_arrive_expect_tx(bar, uint32_t(__popc(occ)) * box_bytes);
+        __syncwarp();
+        if (act)
+            tma_load_3d(smem_u32(ring + size_t(stage) * S::STAGE_ELEMS + size_t(lane) * CW), &tmap, s * CW, j,
+                        int(slot_obj[lane]), bar);
     };
 
     for (;;) {
@@ -161,7 +162,7 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
         if (ld_volatile(&p.st->error)) break;
         int64_t issued_in_round = 0;
         for (int e = 0; e < STAGES && issued_in_round < per_pass; ++e) {
-            if (lane == 0) issue_sub(issued_in_round);
+            issue_sub(issued_in_round);
             ++issued_in_round;
             ++q_iss;
         }
@@ -267,7 +268,7 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                     __syncwarp();
                     ++q_cons;
                     if (issued_in_round < per_pass) {
-                        if (lane == 0) issue_sub(issued_in_round);
+                        issue_sub(issued_in_round);
                         ++issued_in_round;
                         ++q_iss;
                     }
@@ -359,13 +360,14 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                 }
             }
             __syncwarp();
-            // refill the slots whose object stopped
+            // refill the slots whose object stopped: their claims on the object counter go
+            // out together (lane r for slot r), then each new object's state
+            if (lane < R && flags[lane] == 2) fetch(lane);
+            __syncwarp();
             for (int r = 0; r < R; ++r) {
                 if (flags[r] != 2) continue;       // uniform across the warp (shared memory)
-                if (lane == 0) fetch(r);
-                __syncwarp();
                 init_slot(r);
-                __syncwarp();
+                __syncwarp();                      // (init_slot rewrites flags[r])
             }
         }
     }
