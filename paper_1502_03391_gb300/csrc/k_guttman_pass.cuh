@@ -571,7 +571,7 @@ __device__ __forceinline__ bool phase_a(K1Ring<D, TD>& rg, const TMaps& tm, cons
     fid_total = FF{0.f, 0.f};
 
     Cursor cc, cn;
-    cursor_init(cc, rg.t_begin, p);
+    cc = *rg.pc_start;                                 // the range's first cursor (set by start())
     cn = cc;
     bool seg_head = (cc.s == 0);
     constexpr int XB = XiBcast<D>::XB;
@@ -993,7 +993,7 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
 #endif
 
     Cursor cc, cn;
-    cursor_init(cc, rg.t_begin, p);
+    cc = *rg.pc_start;                                 // the range's first cursor (set by start())
     cn = cc;
     bool seg_head = (cc.s == 0);
     float racc[R][D];
@@ -1024,6 +1024,10 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
             }
         }
     };
+    // the first segment's rows: their loads go out first, so that their latency overlaps
+    // the fence and the x_j copies below
+    float v0[RSH];
+    load_rows(cc, v0);
     // the iterate was written with ordinary stores (by the previous per-object phase);
     // any thread of the CTA may copy parts of it with bulk copies during this pass
     fence_proxy_async_global();
@@ -1055,11 +1059,9 @@ __device__ __forceinline__ bool phase_a_strip(K1Ring<D, TD>& rg, const TMaps& tm
         if (lane == 0) mbar_arrive(smem_u32(&rg.rfull[sg & 1]));
         return true;
     };
-    // the first segment's rows
+    // the first segment's rows into their buffer
     {
-        float v[RSH];
-        load_rows(cc, v);
-        if (!rows_write(rg.nflush, v, cc.l)) fail();
+        if (!rows_write(rg.nflush, v0, cc.l)) fail();
     }
     bool rows_pending = true;                          // the segment's rows are not yet waited for
     int mid_done = 0;                                  // segments of this pass summed inside the loop
