@@ -159,7 +159,9 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
         int any = 0;
         if (lane < R) any = slot_obj[lane] >= 0;
         if (!__any_sync(0xffffffffu, any)) break;
-        if (ld_volatile(&p.st->error)) break;
+        // an error raised elsewhere ends the loop after this round: the flag is read now and
+        // tested at the round's end, so that its load latency overlaps the round
+        const int err_seen = ld_volatile(&p.st->error);
         int64_t issued_in_round = 0;
         for (int e = 0; e < STAGES && issued_in_round < per_pass; ++e) {
             issue_sub(issued_in_round);
@@ -370,6 +372,7 @@ k_oos_solve(const __grid_constant__ CUtensorMap tmap, const K3Params p) {
                 __syncwarp();                      // (init_slot rewrites flags[r])
             }
         }
+        if (__any_sync(0xffffffffu, err_seen != 0)) break;
     }
 
     // drain the sub-tiles issued but not consumed (only after a failure)
