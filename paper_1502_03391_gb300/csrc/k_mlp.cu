@@ -370,14 +370,35 @@ cudaError_t forward(const Net& n, const __half* x, int B, Acts& a, cudaStream_t 
 }
 
 // Gradient of the batch loss into g (P floats), given dL/dyhat in a.dy.
+// A second stream for the bias-gradient sums, which depend only on the layer's output
+// gradient: forked from the main stream after that gradient and joined before the
+// caller's next kernel, so they run beside the following products (used while a training
+// step is captured into a graph, where the fork becomes parallel branches).
+struct SideSums {
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
 cudaError_t backward(const Net& n, const __half* x, int B, Acts& a, float* g, cudaStream_t s, float* ws = nullptr,
-                     int64_t wsf = 0) {
+                     int64_t wsf = 0, const SideSums* ss = nullptr) {
     cudaError_t e;
+    int fork = 0;
+    auto bias_sum = [&](int rows, int cols, const float* v, int64_t ld, float* out) -> cudaError_t {
+        if (!ss) {
+            colsum(rows, cols, v, ld, out, s);
+            return cudaSuccess;
+        }
+        cudaError_t r = cudaEventRecord(ss->ev[fork], s);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(ss->side, ss->ev[fork], 0);
+        ++fork;
+        if (r == cudaSuccess) colsum(rows, cols, v, ld, out, ss->side);
+        return r;
+    };
     // gW3 = dy^T h2 (no x nh): A(i, k=b) = dy[b][i], B(b, j) = h2[b][j]
     if ((e = gemm<float, float, Epi::Plain>(n.no, n.nh, B, a.dy, 1, n.no, a.h2, n.nh, 1, g + n.oW3, n.nh, nullptr,
                                             nullptr, nullptr, s, ws, wsf)))
         return e;
-    colsum(B, n.no, a.dy, n.no, g + n.ob3, s);
+    if ((e = bias_sum(B, n.no, a.dy, n.no, g + n.ob3))) return e;
     // dz2 = (dy W3) * gelu'(z2): A = dy (B x no), B = W3 (no x nh)
     if ((e = gemm<float, float, Epi::GeluGrad>(B, n.nh, n.no, a.dy, n.no, 1, n.W3, n.nh, 1, a.dz2, n.nh, nullptr,
                                                nullptr, a.z2, s, ws, wsf)))
@@ -385,7 +406,7 @@ cudaError_t backward(const Net& n, const __half* x, int B, Acts& a, float* g, cu
     if ((e = gemm<float, float, Epi::Plain>(n.nh, n.nh, B, a.dz2, 1, n.nh, a.h1, n.nh, 1, g + n.oW2, n.nh, nullptr,
                                             nullptr, nullptr, s, ws, wsf)))
         return e;
-    colsum(B, n.nh, a.dz2, n.nh, g + n.ob2, s);
+    if ((e = bias_sum(B, n.nh, a.dz2, n.nh, g + n.ob2))) return e;
     // dz1 = (dz2 W2) * gelu'(z1)
     if ((e = gemm<float, float, Epi::GeluGrad>(B, n.nh, n.nh, a.dz2, n.nh, 1, n.W2, n.nh, 1, a.dz1, n.nh, nullptr,
                                                nullptr, a.z1, s, ws, wsf)))
@@ -394,7 +415,10 @@ cudaError_t backward(const Net& n, const __half* x, int B, Acts& a, float* g, cu
     if ((e = gemm<float, __half, Epi::Plain>(n.nh, n.ni, B, a.dz1, 1, n.nh, x, n.ni, 1, g + n.oW1, n.ni, nullptr,
                                              nullptr, nullptr, s, ws, wsf)))
         return e;
-    colsum(B, n.nh, a.dz1, n.nh, g + n.ob1, s);
+    if ((e = bias_sum(B, n.nh, a.dz1, n.nh, g + n.ob1))) return e;
+    if (ss) {                                      // join the side stream
+        if ((e = cudaEventRecord(ss->ev[3], ss->side)) || (e = cudaStreamWaitEvent(s, ss->ev[3], 0))) return e;
+    }
     return cudaGetLastError();
 }
 
@@ -612,12 +636,24 @@ extern "C" int fjofc_mlp_train(float* params, int32_t n_in, int32_t hidden, int3
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    SideSums ss;
     auto cleanup = [&]() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (cs) cudaStreamDestroy(cs);
+        if (ss.side) cudaStreamDestroy(ss.side);
+        for (cudaEvent_t ev : ss.ev)
+            if (ev) cudaEventDestroy(ev);
     };
     if ((rc = cuda_status(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream"))) return rc;
+    {
+        cudaError_t se = cudaStreamCreateWithFlags(&ss.side, cudaStreamNonBlocking);
+        for (int i = 0; i < 4 && se == cudaSuccess; ++i) se = cudaEventCreateWithFlags(&ss.ev[i], cudaEventDisableTiming);
+        if ((rc = cuda_status(se, "side stream"))) {
+            cleanup();
+            return rc;
+        }
+    }
     if ((rc = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "capture"))) {
         cleanup();
         return rc;
@@ -625,7 +661,7 @@ extern "C" int fjofc_mlp_train(float* params, int32_t n_in, int32_t hidden, int3
     k_gather_step<<<B, 128, 0, cs>>>(B, n_in, n_out, count, nb, ctl, tpa, tpc, xh, y, xb, yb);
     cudaError_t ce = forward(n, xb, B, a, cs, ws, kSplitFloats);
     k_mse<<<1, 256, 0, cs>>>(B, n_out, a.y, yb, a.dy, losses, ctl);
-    if (ce == cudaSuccess) ce = backward(n, xb, B, a, g, cs, ws, kSplitFloats);
+    if (ce == cudaSuccess) ce = backward(n, xb, B, a, g, cs, ws, kSplitFloats, &ss);
     k_adam<<<512, 256, 0, cs>>>(P, params, g, mom, vel, opts->lr, beta1, beta2, eps, 1.f, 1.f, tc1, tc2, ctl);
     k_step_advance<<<1, 1, 0, cs>>>(ctl);
     const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
